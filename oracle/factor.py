@@ -1,0 +1,79 @@
+"""Approximate LDM^t factorization over the box tree (paper Algorithm 2).
+
+Reading R1 (the one this oracle implements): every Schur complement is
+replaced by its HSS approximant H (Algorithm 2, steps 1 and 2), the parent
+front is assembled from the children's H and the original coupling blocks
+(eq. (32)), its interior block is factored densely, and the top block
+A^(0) = [[H^1, A^(1,2)], [A^(2,1), H^2]] (eq. (36)) is factored densely.
+
+Per box sigma, with front index set [I ; B] (I = I^sigma at leaves, I^ above):
+  F      = A(front, front) at a leaf; above, F(i,j) = H^mu(i,j) when i,j lie in
+           B^mu, H^nu(i,j) when i,j lie in B^nu, and A(i,j) otherwise (eq. (32));
+  W      = F_ii^-1 F_ib                (M^(sigma)(B,I)^t, Sec. 4.1)
+  S      = F_bb - F_bi W               (eq. (32))
+  H      = HSS approximant of S        (Theorem 1), or S when compression is off.
+Stored for the apply: the LU factors of F_ii, F_bi and W.
+"""
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .hss import hss_tree_for_front, hss_compress
+
+
+def csr_from_bsr(nb, bs, row_ptr, col_idx, val):
+    M = sp.bsr_matrix((np.asarray(val, dtype=np.float64).reshape(-1, bs, bs),
+                       np.asarray(col_idx), np.asarray(row_ptr)), shape=(nb * bs, nb * bs))
+    return M.tocsr()
+
+
+def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=10):
+    """Returns a dict with the per-box factors, the top block LU and logs."""
+    A = A_csr.tocsr()
+    boxes = {}
+    H = {}
+    log = []
+    for b in nd["order"]:
+        b = int(b)
+        I = nd["iset"][b]
+        B = nd["bset"][b]
+        ni = I.size
+        if nd["is_leaf"][b]:
+            idx = np.concatenate([I, B])
+            F = A[idx][:, idx].toarray()
+        else:
+            mu, nu = (int(c) for c in nd["child"][b])
+            idx = np.concatenate([I, B])
+            F = A[idx][:, idx].toarray()
+            for c in (mu, nu):
+                fm = nd["fmap"][c]
+                F[np.ix_(fm, fm)] = H.pop(c)
+        Fii, Fib = F[:ni, :ni], F[:ni, ni:]
+        Fbi, Fbb = F[ni:, :ni], F[ni:, ni:]
+        if ni > 0:
+            lu = sla.lu_factor(Fii)
+            W = sla.lu_solve(lu, Fib)
+        else:
+            lu = None
+            W = np.zeros((0, B.size))
+        S = Fbb - Fbi @ W
+        rec = dict(box=b, level=int(nd["level"][b]), ni=ni, nb=B.size)
+        if compress and B.size > 0:
+            nodes = hss_tree_for_front(nd, b)
+            Hs, rep = hss_compress(S, nodes, tol, seed, b, r0=r0, dr=dr, oversample=oversample)
+            rec.update(r=rep["r"], rounds=rep["rounds"],
+                       kmax=max(list(rep["krow"].values()) + list(rep["kcol"].values()) + [0]),
+                       nnodes=len(nodes), rep=rep)
+        else:
+            Hs = S.copy()
+        H[b] = Hs
+        boxes[b] = dict(lu=lu, Fbi=Fbi.copy(), W=W, S=S, F=F)
+        log.append(rec)
+    # top block, eq. (36)
+    B0, B1 = nd["bset"][0], nd["bset"][1]
+    top = np.concatenate([B0, B1])
+    A0 = A[top][:, top].toarray()
+    A0[np.ix_(nd["fmap"][0], nd["fmap"][0])] = H.pop(0)
+    A0[np.ix_(nd["fmap"][1], nd["fmap"][1])] = H.pop(1)
+    top_lu = sla.lu_factor(A0) if top.size else None
+    return dict(boxes=boxes, top=top, top_lu=top_lu, A0=A0, log=log, nd=nd)

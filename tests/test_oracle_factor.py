@@ -1,0 +1,113 @@
+"""Oracle pins for Algorithm 2, the apply and FGMRES."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+import oracle
+from paper_1508_07798_gb300 import dg_inputs as dg
+
+
+def _setup(dim, n, p, leaf=64, kind="poisson", seed=0):
+    if kind == "poisson":
+        mesh = dg.Mesh(dim, tuple(n) + (1,) * (3 - dim), p)
+        A = dg.assemble_sipg(mesh)
+    else:
+        mesh = dg.Mesh(dim, tuple(n) + (1,) * (3 - dim), p)
+        c = dg.cosine_field(mesh, seed)
+        A = dg.assemble_sipg(mesh, c_elem=c, kappa=dg.helmholtz_kappa(n[0], p))
+    nd = oracle.nd_order(dim, mesh.n, p, A.row_ptr, A.col_idx, leaf_max=leaf)
+    return mesh, A, nd, dg.bsr_to_csr(A)
+
+
+EXACT = [(2, (16, 16), 1, 64, "poisson"), (2, (2, 2), 1, 4, "poisson"), (2, (3, 2), 2, 9, "poisson"),
+         (2, (4, 4), 3, 16, "poisson"), (2, (6, 6), 2, 18, "helm"), (3, (2, 2, 2), 1, 8, "poisson"),
+         (3, (3, 3, 2), 1, 16, "poisson")]
+
+
+@pytest.mark.parametrize("dim,n,p,leaf,kind", EXACT)
+def test_exact_mode_equals_dense_solve(dim, n, p, leaf, kind):
+    """With compression off the LDM^t factorization is exact (Sec. 3/4.1), so
+    M^-1 = A^-1: the apply equals a dense LU solve."""
+    mesh, A, nd, Acsr = _setup(dim, n, p, leaf, kind)
+    fac = oracle.factor(Acsr, nd, compress=False)
+    B = dg.random_rhs(A.n, 3, 1)
+    X = oracle.apply(fac, B)
+    Xe = np.linalg.solve(Acsr.toarray(), B)
+    assert np.linalg.norm(X - Xe) <= 1e-12 * np.linalg.norm(Xe) * max(1.0, np.linalg.cond(Acsr.toarray()) / 1e4)
+
+
+def test_exact_mode_gmres_one_iteration():
+    mesh, A, nd, Acsr = _setup(2, (16, 16), 1)
+    fac = oracle.factor(Acsr, nd, compress=False)
+    b = dg.random_rhs(A.n, 1, 0)[:, 0]
+    x, info = oracle.fgmres(lambda v: Acsr @ v, lambda v: oracle.apply(fac, v), b, rtol=1e-10)
+    assert info["iters"] == 1 and info["relres"] <= 1e-10
+
+
+def test_schur_is_inverse_of_trailing_block_of_front_inverse():
+    """Sec. 3: the bottom-right block of F^-1 is S^-1."""
+    mesh, A, nd, Acsr = _setup(2, (8, 8), 2, 36, "helm")
+    fac = oracle.factor(Acsr, nd, tol=1e-6)
+    checked = 0
+    for b, f in fac["boxes"].items():
+        ni = nd["ni"][b]
+        if ni == 0 or nd["nb"][b] == 0:
+            continue
+        Finv = np.linalg.inv(f["F"])
+        Sref = np.linalg.inv(Finv[ni:, ni:])
+        assert np.linalg.norm(f["S"] - Sref) <= 1e-8 * np.linalg.norm(Sref)
+        checked += 1
+    assert checked > 5
+
+
+def test_front_assembly_from_children_and_A():
+    """eq. (32): a parent front holds H of each child on its diagonal blocks and
+    the original couplings A(B^mu, B^nu) across."""
+    mesh, A, nd, Acsr = _setup(2, (8, 8), 1, 16)
+    fac = oracle.factor(Acsr, nd, compress=False)
+    Ad = Acsr.toarray()
+    for b in range(nd["nbox"]):
+        if nd["is_leaf"][b]:
+            continue
+        mu, nu = nd["child"][b]
+        F = fac["boxes"][b]["F"]
+        fm, fn = nd["fmap"][mu], nd["fmap"][nu]
+        assert np.array_equal(F[np.ix_(fm, fn)], Ad[np.ix_(nd["bset"][mu], nd["bset"][nu])])
+        assert np.allclose(F[np.ix_(fm, fm)], fac["boxes"][mu]["S"], rtol=0, atol=0)
+
+
+def test_approximate_preconditioner_poisson():
+    mesh, A, nd, Acsr = _setup(2, (16, 16), 1)
+    fac = oracle.factor(Acsr, nd, tol=1e-6, seed=0)
+    b = dg.random_rhs(A.n, 1, 0)[:, 0]
+    x, info = oracle.fgmres(lambda v: Acsr @ v, lambda v: oracle.apply(fac, v), b, rtol=1e-10)
+    assert info["converged"] and info["iters"] <= 4
+    assert np.linalg.norm(b - Acsr @ x) <= 1e-10 * np.linalg.norm(b)
+    # compression error of every compressed front stays near the tolerance
+    for rec in fac["log"]:
+        if rec.get("nnodes", 1) > 1:
+            assert rec["kmax"] <= rec["r"] - 10 or rec["r"] >= rec["nb"]
+
+
+def test_gmres_matches_scipy_unpreconditioned():
+    mesh, A, nd, Acsr = _setup(2, (6, 6), 1)
+    b = dg.random_rhs(A.n, 1, 2)[:, 0]
+    x, info = oracle.fgmres(lambda v: Acsr @ v, None, b, restart=20, rtol=1e-9, maxit=20)
+    ref = []
+    spla.gmres(Acsr, b, restart=20, maxiter=1, rtol=1e-30, callback=lambda r: ref.append(r),
+               callback_type="pr_norm")
+    ref = np.array(ref)
+    ours = np.array(info["hist"][: ref.size])
+    assert ref.size >= 10
+    assert np.allclose(ours, ref, rtol=1e-7, atol=1e-14)
+
+
+def test_gmres_restart_and_nonconvergence():
+    mesh, A, nd, Acsr = _setup(2, (8, 8), 1)
+    b = dg.random_rhs(A.n, 1, 3)[:, 0]
+    x, info = oracle.fgmres(lambda v: Acsr @ v, None, b, restart=5, rtol=1e-8, maxit=2000)
+    assert info["converged"]
+    assert np.linalg.norm(b - Acsr @ x) <= 1e-8 * np.linalg.norm(b)
+    x2, info2 = oracle.fgmres(lambda v: Acsr @ v, None, b, restart=5, rtol=1e-12, maxit=3)
+    assert not info2["converged"] and info2["iters"] == 3
