@@ -27,8 +27,10 @@ def csr_from_bsr(nb, bs, row_ptr, col_idx, val):
     return M.tocsr()
 
 
-def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=10):
-    """Returns a dict with the per-box factors, the top block LU and logs."""
+def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=10, rmax=None,
+           keep_h=False):
+    """Returns a dict with the per-box factors, the top block LU and logs.
+    rmax caps the HSS sample width; keep_h stores each approximant H."""
     A = A_csr.tocsr()
     boxes = {}
     H = {}
@@ -60,7 +62,7 @@ def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=
         rec = dict(box=b, level=int(nd["level"][b]), ni=ni, nb=B.size)
         if compress and B.size > 0:
             nodes = hss_tree_for_front(nd, b)
-            Hs, rep = hss_compress(S, nodes, tol, seed, b, r0=r0, dr=dr, oversample=oversample)
+            Hs, rep = hss_compress(S, nodes, tol, seed, b, r0=r0, dr=dr, oversample=oversample, rmax=rmax)
             rec.update(r=rep["r"], rounds=rep["rounds"],
                        kmax=max(list(rep["krow"].values()) + list(rep["kcol"].values()) + [0]),
                        nnodes=len(nodes), rep=rep)
@@ -68,6 +70,8 @@ def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=
             Hs = S.copy()
         H[b] = Hs
         boxes[b] = dict(lu=lu, Fbi=Fbi.copy(), W=W, S=S, F=F)
+        if keep_h:
+            boxes[b]["H"] = Hs.copy()
         log.append(rec)
     # top block, eq. (36)
     B0, B1 = nd["bset"][0], nd["bset"][1]

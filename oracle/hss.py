@@ -24,7 +24,8 @@ Readings where the paper is silent:
     to B^sigma, with empty boxes removed and single-child chains collapsed;
   * oversampling p = 10 (Theorem 1's typical value); the sample width r starts
     at 32 and grows by 32 (whole front redone, earlier columns kept) while some
-    node's rank exceeds r - 10 and r < n;
+    node's rank exceeds r - 10 and r < n (and, when a cap rmax is given, while
+    r + 32 <= rmax);
   * the ID tolerance is relative per ID (see idecomp.py).
 The approximant is returned expanded to a dense matrix H (the parent front is
 built from H, eq. (32)), together with the representation and its ranks.
@@ -75,8 +76,10 @@ def hss_tree_for_front(nd, box):
     return nodes
 
 
-def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10):
-    """Randomized HSS approximant of S.  Returns (H, rep) with H dense."""
+def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rmax=None):
+    """Randomized HSS approximant of S.  Returns (H, rep) with H dense.
+
+    rmax (optional) caps the sample width: growth stops once r + dr > rmax."""
     S = np.asarray(S, dtype=np.float64)
     n = S.shape[0]
     root = len(nodes) - 1
@@ -84,7 +87,7 @@ def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10):
         return S.copy(), dict(r=0, rounds=0, krow={}, kcol={}, nodes=nodes, swaps=0)
     # process order: deeper nodes first (children before parents)
     order = sorted(range(root), key=lambda i: (-nodes[i]["depth"], i))
-    r = r0
+    r = r0 if rmax is None else min(r0, rmax)
     rounds = 0
     while True:
         rounds += 1
@@ -117,7 +120,7 @@ def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10):
             st[t] = dict(U=U, V=V, J=rows[Jl], K=cols[Kl], Yskel=Yl[Jl], Zskel=Zl[Kl],
                          Omt=V.T @ Oml, Pst=U.T @ Psl, swaps=iu["swaps"] + iv["swaps"])
         kmax = max(max(st[t]["U"].shape[1], st[t]["V"].shape[1]) for t in order)
-        if kmax > r - oversample and r < n:
+        if kmax > r - oversample and r < n and (rmax is None or r + dr <= rmax):
             r += dr
             continue
         break
