@@ -1,0 +1,211 @@
+/*
+ * hssnd.h -- C ABI of libhssnd.so, a GB300 (sm_103a) implementation of the
+ * preconditioner of Gatto & Hesthaven, "A Preconditioner Based on Low-Rank
+ * Approximation of Schur Complements" (arXiv 1508.07798):
+ *
+ *   nd_order      nested-dissection box tree and interior/boundary dof sets
+ *                 (paper Sec. 4.0, graph (1), eq. (30)/(31) ordering)
+ *   hss_factor    approximate LDM^t factorization, Algorithm 2: fronts are
+ *                 eliminated level by level (eq. (32)), each Schur complement is
+ *                 replaced by a randomized HSS/ID approximant (Theorem 1), the top
+ *                 block A^(0) of eq. (36) is inverted
+ *   hss_apply     y = M^-t D^-1 L^-1 x (end of Sec. 4.2)
+ *   fgmres_solve  right-preconditioned restarted flexible GMRES (Sec. 5 measures
+ *                 the preconditioner in GMRES iterations)
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* or documented as "device" are CUDA device pointers;
+ *     everything else is host memory.  The caller owns all buffers it passes;
+ *     the library owns the opaque handles (hss_tree, hss_factor_t) and the
+ *     device memory behind them until the matching *_destroy call.
+ *   - No call modifies the matrix A.
+ *   - Dense vectors/matrices are column-major with a leading dimension (ld >= N).
+ *     Vectors use the ORIGINAL dof numbering (global dof = element*bs + local).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is stream-ordered; calls that must size allocations or report
+ *     statistics synchronize the stream (stated per call).
+ *   - Every int-returning call returns HSS_OK (0) or an error code; no
+ *     exception crosses the ABI.  hss_last_error() describes the last error of
+ *     the calling thread.  Handles are not thread-safe.
+ *   - The library never falls back to a CPU implementation: without a usable
+ *     CUDA device every compute call fails with HSS_ECUDA.
+ */
+#ifndef HSSND_H
+#define HSSND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HSS_OK = 0,
+    HSS_EINVAL = 1,      /* invalid argument (sizes, null pointers, NaN/Inf in A) */
+    HSS_ENOMEM = 2,      /* device allocation failed or over the memory budget   */
+    HSS_ESINGULAR = 3,   /* zero pivot in a front; the box id is in hss_last_error */
+    HSS_ENOCONV = 4,     /* FGMRES hit maxit; x holds the last iterate            */
+    HSS_ETIMEOUT = 5,    /* a bounded device-side wait expired                    */
+    HSS_ECUDA = 6        /* CUDA runtime error (including: no device)            */
+};
+
+enum { HSS_SCHEME_BOX = 0, HSS_SCHEME_HSLAB = 1, HSS_SCHEME_VSLAB = 2 };
+enum { HSS_FP64 = 0, HSS_FP32 = 1 };
+
+/* Square block-sparse matrix, DEVICE pointers.  nb block rows (one per
+ * element), bs x bs dense blocks stored row-major (row = test function),
+ * block columns sorted ascending in each block row. */
+typedef struct hss_bsr {
+    int nb;
+    int bs;
+    const int *row_ptr;     /* [nb+1] */
+    const int *col_idx;     /* [nnzb] */
+    const double *val;      /* [nnzb*bs*bs] */
+} hss_bsr;
+
+/* Structured element grid on the unit square/cube: element
+ * e = ix + n[0]*(iy + n[1]*iz), bs = (p+1)^dim dofs per element. */
+typedef struct hss_mesh {
+    int dim;
+    int n[3];
+    int p;
+} hss_mesh;
+
+typedef struct hss_nd_opts {
+    int leaf_max;           /* a box with <= leaf_max dofs (or one element) is a leaf; default 64 */
+    int scheme;             /* HSS_SCHEME_*; default BOX */
+} hss_nd_opts;
+
+typedef struct hss_factor_opts {
+    double tol;             /* relative ID tolerance per interpolative decomposition; default 1e-6 */
+    int compress;           /* 1: replace each Schur complement by its HSS approximant (default);
+                               0: exact LDM^t (no approximation) */
+    int r0;                 /* initial sample width; default 32 */
+    int dr;                 /* sample width growth step; default 32 */
+    int rmax;               /* largest sample width; default 96 */
+    int oversample;         /* p of Theorem 1; a node rank above r - p triggers growth; default 10 */
+    int precision;          /* HSS_FP64 (default) or HSS_FP32 (mixed form) */
+    uint64_t seed;          /* seed of the +-1 test matrices; default 0 */
+    int keep_schur;         /* 1: keep a copy of every front's S and H for hss_factor_export_front */
+} hss_factor_opts;
+
+typedef struct fgmres_opts {
+    int restart;            /* default 30 */
+    double rtol;            /* relative residual target ||b - A x|| / ||b||; default 1e-8 */
+    int maxit;              /* total Arnoldi steps per right-hand side; default 1000 */
+} fgmres_opts;
+
+typedef struct fgmres_stats {
+    int iters;              /* Arnoldi steps, summed over right-hand sides */
+    int max_iters;          /* largest per right-hand side */
+    double relres;          /* largest final true relative residual over right-hand sides */
+    int converged;          /* 1 when every right-hand side reached rtol */
+} fgmres_stats;
+
+typedef struct hss_tree hss_tree;
+typedef struct hss_factor_t hss_factor_t;
+
+/* Default option values (host structs). */
+void hss_nd_opts_default(hss_nd_opts *o);
+void hss_factor_opts_default(hss_factor_opts *o);
+void fgmres_opts_default(fgmres_opts *o);
+
+/* Sec. 4.0: build the box tree of `mesh` (recursive bisection of the element
+ * grid; at a tie the last axis is cut; the lower child gets floor(n/2)
+ * elements), classify each box's dofs as boundary (coupled by a stored block of
+ * A to a dof outside the box) or interior, and form the eq. (31) elimination
+ * order.  `A` (device) supplies the coupling structure only.  The element
+ * flags and set compaction run on the device; the call synchronizes `stream`
+ * once to size the sets.  *out receives a new handle.  Errors: HSS_EINVAL
+ * (mesh/BSR mismatch, fewer than two elements), HSS_ENOMEM, HSS_ECUDA. */
+int nd_order(const hss_mesh *mesh, const hss_bsr *A, const hss_nd_opts *opts,
+             void *stream, hss_tree **out);
+
+/* Sizes of a tree: N, number of boxes, deepest level, total lengths of the
+ * concatenated interior / boundary set arrays. */
+typedef struct hss_tree_desc {
+    int ndof, nbox, maxlev, iset_len, bset_len, bs;
+} hss_tree_desc;
+int hss_tree_info(const hss_tree *t, hss_tree_desc *d);
+
+/* Copy the tree to HOST arrays (any pointer may be NULL to skip it).
+ * Per box (length nbox): level, parent (-1 for level 1), child0/child1 (-1 at
+ * leaves), ni, nb (sizes of the I and B sets), ioff, boff (offsets of the sets
+ * inside iset/bset), lohi (6 ints per box: lo[3], hi[3] element ranges).
+ * iset[iset_len], bset[bset_len]: global dof ids, boxes concatenated in id order;
+ * fmap[bset_len]: position of each B dof inside its parent front [I^;B^] (level 1:
+ * inside the top block [B^1;B^2]); perm[ndof]: eq. (31) elimination order. */
+int hss_tree_export(const hss_tree *t, int *level, int *parent, int *child0, int *child1,
+                    int *ni, int *nb, int *ioff, int *boff, int *lohi,
+                    int *iset, int *bset, int *fmap, int *perm);
+
+/* Algorithm 2: eliminate every front level by level (leaves first), compress
+ * each Schur complement S = F_bb - F_bi F_ii^-1 F_ib (eq. (32)) to its
+ * randomized HSS approximant H (Theorem 1; ID with relative tolerance
+ * opts->tol, +-1 test matrices from a counter hash), assemble the parent front
+ * from H^mu, H^nu and A(B^mu, B^nu), and invert the top block
+ * A^(0) = [[H^1, A12], [A21, H^2]] (eq. (36)).  The factor keeps, per front,
+ * F_ii^-1, -F_bi F_ii^-1 and F_ii^-1 F_ib in FP64 (or FP32 with
+ * precision = HSS_FP32).  Synchronizes `stream` once per tree level (rank
+ * decisions).  Errors: HSS_EINVAL, HSS_ENOMEM, HSS_ESINGULAR (box id in
+ * hss_last_error), HSS_ECUDA. */
+int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_factor_opts *opts,
+               void *stream, hss_factor_t **out);
+
+/* Statistics of a factorization (host): stored factor bytes, algorithmic
+ * flops of the front eliminations (2/3 ni^3 + 2 ni^2 nb + 2 nb^2 ni summed),
+ * sample rounds, largest HSS rank and sample width. */
+typedef struct hss_factor_info {
+    double factor_bytes;
+    double front_flops;
+    double executed_flops;
+    int max_rank;
+    int max_r;
+    int rounds;
+    int nfronts;
+} hss_factor_info;
+int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info);
+
+/* Test/inspection hook (needs opts.keep_schur = 1): copy box `box`'s Schur
+ * complement S (nb x nb, column-major, before compression) and its
+ * approximant H to HOST buffers (either may be NULL), plus the largest rank
+ * and final sample width of that front.  Synchronizes the stream. */
+int hss_factor_export_front(const hss_factor_t *f, int box, double *S, double *H,
+                            int *kmax, int *r);
+
+/* y = M^-t D^-1 L^-1 x for nrhs columns (x, y DEVICE, column-major, leading
+ * dimensions ldx, ldy >= N, original dof order; x and y may alias).  Forward
+ * sweep over the levels, top block, backward sweep.  Asynchronous on `stream`.
+ * Errors: HSS_EINVAL, HSS_ENOMEM (workspace for a larger nrhs), HSS_ECUDA. */
+int hss_apply(const hss_factor_t *f, int nrhs, const double *x, int ldx, double *y, int ldy,
+              void *stream);
+
+/* y = A x for nrhs columns (DEVICE, column-major).  Asynchronous. */
+int hss_spmv(const hss_bsr *A, int nrhs, const double *x, int ldx, double *y, int ldy,
+             void *stream);
+
+/* Right-preconditioned flexible GMRES(restart) for A x = b, one Krylov space
+ * per right-hand side.  f == NULL means no preconditioner.  b, x DEVICE
+ * (column-major; x holds x0 on entry and the iterate on exit).  FP64 Arnoldi
+ * with classical Gram-Schmidt applied twice, Givens rotations on the device;
+ * stops when the true FP64 residual, recomputed at every restart, is
+ * <= rtol ||b||.  Synchronizes once per Arnoldi step and fills *stats (HOST,
+ * may be NULL).  Returns HSS_ENOCONV when some right-hand side did not reach
+ * rtol within maxit steps. */
+int fgmres_solve(const hss_bsr *A, const hss_factor_t *f, int nrhs, const double *b, int ldb,
+                 double *x, int ldx, const fgmres_opts *opts, fgmres_stats *stats, void *stream);
+
+/* Convergence history of the last fgmres_solve on this thread: Arnoldi residual
+ * estimates |g_{j+1}|/||b|| of right-hand side `rhs` (HOST, up to cap values);
+ * returns the count. */
+int fgmres_history(int rhs, double *hist, int cap);
+
+void hss_tree_destroy(hss_tree *t);
+void hss_factor_destroy(hss_factor_t *f);
+const char *hss_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSSND_H */

@@ -1,0 +1,198 @@
+// hss_apply: y = M^-t D^-1 L^-1 x (end of Sec. 4.2), level by level.
+//
+// After the Gauss-Jordan sweep every front holds [F_ii^-1 P^t ; -F_bi F_ii^-1 P^t]
+// in its I columns and W = F_ii^-1 F_ib in the top-right block, so
+//   forward  (deepest level first, then the top block):
+//       z = x(Iperm);  t = F_ii^-1 x_I = rows [0,ni) of [..] z;  x_B += rows [ni,n) of [..] z
+//   backward (top block first, then down to the leaves):
+//       x_I = t - W x_B
+// t is parked in a second vector so that all row tiles of a front read the
+// same x_I.  Fronts of one level touch disjoint dofs, so one launch per level
+// covers all of them; each CTA handles APPLY_ROWS rows of one front.
+#include "internal.h"
+#include "front.h"
+#include "factor.h"
+
+namespace hssnd {
+
+constexpr int AP_NT = 256;
+constexpr int AP_RG = AP_NT / APPLY_ROWS;   // column groups per CTA
+constexpr int AP_ZC = 1024;                  // z entries staged per chunk (per right-hand side block)
+
+template <class T, int RB>
+__global__ void __launch_bounds__(AP_NT) k_apply_fwd(const ApplyTile *__restrict__ tiles, const FrontDev *__restrict__ fr,
+                                                   const T *__restrict__ arena, const int *__restrict__ iperm,
+                                                   const int *__restrict__ ilist, const int *__restrict__ blist,
+                                                   double *__restrict__ w, long ldw, double *__restrict__ tv, long ldt,
+                                                   int nrhs) {
+    __shared__ double zs[AP_ZC * RB];
+    __shared__ double red[AP_RG][APPLY_ROWS][RB];
+    const ApplyTile tl = tiles[blockIdx.x];
+    const FrontDev F = fr[tl.front];
+    const T *M = arena + F.foff;
+    const int tx = threadIdx.x % APPLY_ROWS, ty = threadIdx.x / APPLY_ROWS;
+    const int i = tl.row0 + tx;
+    for (int rb0 = 0; rb0 < nrhs; rb0 += RB) {
+        double acc[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) acc[q] = 0.0;
+        for (int c0 = 0; c0 < F.ni; c0 += AP_ZC) {
+            int cn = min(AP_ZC, F.ni - c0);
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < cn * RB; idx += AP_NT) {
+                int c = idx % cn, q = idx / cn;
+                int rr = rb0 + q;
+                zs[c + AP_ZC * q] = rr < nrhs ? w[iperm[F.iperm_off + c0 + c] + ldw * rr] : 0.0;
+            }
+            __syncthreads();
+            if (i < F.n) {
+                const T *col = M + i + (long)F.n * c0;
+                for (int c = ty; c < cn; c += AP_RG) {
+                    double m = (double)col[(long)F.n * c];
+#pragma unroll
+                    for (int q = 0; q < RB; ++q) acc[q] = fma(m, zs[c + AP_ZC * q], acc[q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) red[ty][tx][q] = acc[q];
+        __syncthreads();
+        if (ty == 0 && i < F.n) {
+#pragma unroll
+            for (int q = 0; q < RB; ++q) {
+                int rr = rb0 + q;
+                if (rr >= nrhs) break;
+                double y = 0.0;
+                for (int g = 0; g < AP_RG; ++g) y += red[g][tx][q];
+                if (i < F.ni)
+                    tv[ilist[F.iset_off + i] + ldt * rr] = y;
+                else
+                    w[blist[F.bset_off + i - F.ni] + ldw * rr] += y;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class T, int RB>
+__global__ void __launch_bounds__(AP_NT) k_apply_bwd(const ApplyTile *__restrict__ tiles, const FrontDev *__restrict__ fr,
+                                                   const T *__restrict__ arena, const int *__restrict__ ilist,
+                                                   const int *__restrict__ blist, double *__restrict__ w, long ldw,
+                                                   const double *__restrict__ tv, long ldt, int nrhs) {
+    __shared__ double zs[AP_ZC * RB];
+    __shared__ double red[AP_RG][APPLY_ROWS][RB];
+    const ApplyTile tl = tiles[blockIdx.x];
+    const FrontDev F = fr[tl.front];
+    const T *M = arena + F.foff;
+    const int tx = threadIdx.x % APPLY_ROWS, ty = threadIdx.x / APPLY_ROWS;
+    const int i = tl.row0 + tx;
+    for (int rb0 = 0; rb0 < nrhs; rb0 += RB) {
+        double acc[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) acc[q] = 0.0;
+        for (int c0 = 0; c0 < F.nb; c0 += AP_ZC) {
+            int cn = min(AP_ZC, F.nb - c0);
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < cn * RB; idx += AP_NT) {
+                int c = idx % cn, q = idx / cn;
+                int rr = rb0 + q;
+                zs[c + AP_ZC * q] = rr < nrhs ? w[blist[F.bset_off + c0 + c] + ldw * rr] : 0.0;
+            }
+            __syncthreads();
+            if (i < F.ni) {
+                const T *col = M + i + (long)F.n * (F.ni + c0);
+                for (int c = ty; c < cn; c += AP_RG) {
+                    double m = (double)col[(long)F.n * c];
+#pragma unroll
+                    for (int q = 0; q < RB; ++q) acc[q] = fma(m, zs[c + AP_ZC * q], acc[q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) red[ty][tx][q] = acc[q];
+        __syncthreads();
+        if (ty == 0 && i < F.ni) {
+#pragma unroll
+            for (int q = 0; q < RB; ++q) {
+                int rr = rb0 + q;
+                if (rr >= nrhs) break;
+                double y = 0.0;
+                for (int g = 0; g < AP_RG; ++g) y += red[g][tx][q];
+                int dof = ilist[F.iset_off + i];
+                w[dof + ldw * rr] = tv[dof + ldt * rr] - y;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+int apply_stage(const ApplyStage &st, bool forward, const FrontDev *fr, const T *arena, const int *iperm,
+                const int *ilist, const int *blist, double *w, long ldw, double *tv, long ldt, int nrhs,
+                cudaStream_t s) {
+    const ApplyTile *tiles = forward ? st.d_fwd : st.d_bwd;
+    int nt = forward ? st.nfwd : st.nbwd;
+    if (nt == 0) return HSS_OK;
+    if (forward) {
+        if (nrhs == 1)
+            k_apply_fwd<T, 1><<<nt, AP_NT, 0, s>>>(tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs);
+        else
+            k_apply_fwd<T, 4><<<nt, AP_NT, 0, s>>>(tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs);
+    } else {
+        if (nrhs == 1)
+            k_apply_bwd<T, 1><<<nt, AP_NT, 0, s>>>(tiles, fr, arena, ilist, blist, w, ldw, tv, ldt, nrhs);
+        else
+            k_apply_bwd<T, 4><<<nt, AP_NT, 0, s>>>(tiles, fr, arena, ilist, blist, w, ldw, tv, ldt, nrhs);
+    }
+    HSS_CHECK_LAUNCH("k_apply");
+    return HSS_OK;
+}
+
+template <class T> static int apply_impl(const hss_factor_t *f, int nrhs, double *y, long ldy, cudaStream_t s) {
+    const T *arena = f->arena_ptr<T>();
+    double *tv = f->tvec.as<double>();
+    long ldt = f->ndof;
+    int rc;
+    // forward: stages deepest first, then the top block
+    for (size_t k = 0; k < f->apply.size(); ++k) {
+        const ApplyStage &st = f->apply[k];
+        const int *ilist = st.top ? f->d_topset.as<int>() : f->tree->d_iset.as<int>();
+        if ((rc = apply_stage<T>(st, true, st.d_fronts, arena, f->d_iperm.as<int>(), ilist, f->tree->d_bset.as<int>(),
+                                 y, ldy, tv, ldt, nrhs, s)))
+            return rc;
+    }
+    for (size_t k = f->apply.size(); k-- > 0;) {
+        const ApplyStage &st = f->apply[k];
+        const int *ilist = st.top ? f->d_topset.as<int>() : f->tree->d_iset.as<int>();
+        if ((rc = apply_stage<T>(st, false, st.d_fronts, arena, f->d_iperm.as<int>(), ilist, f->tree->d_bset.as<int>(),
+                                 y, ldy, tv, ldt, nrhs, s)))
+            return rc;
+    }
+    return HSS_OK;
+}
+
+int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s) {
+    hss_factor_t *mf = const_cast<hss_factor_t *>(f);
+    int rc;
+    if ((rc = mf->tvec.alloc(sizeof(double) * (size_t)f->ndof * nrhs))) return rc;
+    if (x != y) {
+        HSS_CUDA(cudaMemcpy2DAsync(y, sizeof(double) * ldy, x, sizeof(double) * ldx, sizeof(double) * f->ndof, nrhs,
+                                   cudaMemcpyDeviceToDevice, s));
+    }
+    if (f->precision == HSS_FP32) return apply_impl<float>(f, nrhs, y, ldy, s);
+    return apply_impl<double>(f, nrhs, y, ldy, s);
+}
+
+}  // namespace hssnd
+
+using namespace hssnd;
+
+extern "C" int hss_apply(const hss_factor_t *f, int nrhs, const double *x, int ldx, double *y, int ldy,
+                         void *stream) {
+    if (!f || !x || !y || nrhs < 0 || ldx < f->ndof || ldy < f->ndof) {
+        set_error("hss_apply: invalid argument");
+        return HSS_EINVAL;
+    }
+    if (nrhs == 0) return HSS_OK;
+    return apply_factor(f, nrhs, x, ldx, y, ldy, (cudaStream_t)stream);
+}

@@ -1,0 +1,691 @@
+// hss_factor: Algorithm 2 of the paper, level by level on the device.
+//
+//   for each level, deepest first:
+//     assemble the fronts [I ; B]            (leaf: A; parent: A(B^mu,B^nu), H^mu/H^nu already in)
+//     Gauss-Jordan sweep over the I pivots   -> F_ii^-1, -F_bi F_ii^-1, W, S   (eq. (32))
+//     randomized HSS of every S              (Theorem 1; rank-adaptive sample width)
+//     expand H into the parent front         (eq. (32)) / the top block (eq. (36))
+//   invert the top block A^(0)
+//
+// The host only schedules: it builds per-level work lists from the tree and
+// reads back one small array per sampling round (node ranks and pivot
+// status) to decide sample growth and to size the expansion.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "factor.h"
+#include "hss.h"
+
+namespace hssnd {
+
+namespace {
+
+template <class T> struct StageCtx {
+    std::vector<FrontDev> fronts;       // stage-local fronts
+    std::vector<int> boxes;             // box of each front (-1: top)
+    std::vector<long> parent_off;       // arena offset of the parent front
+    std::vector<int> parent_n;
+    DevBuf d_status;
+};
+
+template <class T>
+int assemble_stage(const hss_bsr *A, const hss_tree *t, const std::vector<FrontDev> &fr, const FrontDev *d_fr,
+                   const std::vector<std::vector<int>> &dofs, const std::vector<std::vector<int>> &sides,
+                   int *elem_slot, T *arena, cudaStream_t s) {
+    std::vector<StageElem> se;
+    int bs = t->bs;
+    for (size_t f = 0; f < fr.size(); ++f) {
+        const auto &d = dofs[f];
+        for (size_t pos = 0; pos < d.size(); pos += bs) se.push_back({d[pos] / bs, (int)f, (int)pos, sides[f][pos / bs]});
+    }
+    if (se.empty()) return HSS_OK;
+    DevBuf d_se;
+    int rc;
+    if ((rc = upload(d_se, se, s))) return rc;
+    rc = launch_scatter_A<T>(A, d_se.as<StageElem>(), (int)se.size(), elem_slot, d_fr, arena, s);
+    if (rc) return rc;
+    // d_se must stay alive until the kernels ran
+    HSS_CUDA(cudaStreamSynchronize(s));
+    return HSS_OK;
+}
+
+template <class T> int choose_kb(int ni) {
+    for (int kb = PANEL_KB_MAX; kb >= 8; kb /= 2)
+        if ((long)ni * kb * (long)sizeof(T) <= PANEL_SMEM_MAX) return kb;
+    return PANEL_KB_MAX;  // global-memory panel
+}
+
+// Blocked Gauss-Jordan sweep over the I pivots of every front of a stage.
+template <class T>
+int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *arena, int *piv, int *status,
+                    double &exec_flops, cudaStream_t s) {
+    int nf = (int)fr.size();
+    std::vector<int> kb(nf), nsteps(nf);
+    std::vector<long> aoff(nf);
+    long aold_total = 0;
+    int maxsteps = 0;
+    for (int f = 0; f < nf; ++f) {
+        kb[f] = choose_kb<T>(fr[f].ni);
+        nsteps[f] = fr[f].ni > 0 ? cdiv(fr[f].ni, kb[f]) : 0;
+        aoff[f] = aold_total;
+        aold_total += (long)kb[f] * fr[f].n;
+        maxsteps = std::max(maxsteps, nsteps[f]);
+        exec_flops += 2.0 * fr[f].n * (double)fr[f].n * fr[f].ni;
+    }
+    if (maxsteps == 0) return HSS_OK;
+    std::vector<PanelJob> jobs;
+    std::vector<GemmDesc<T>> descs;
+    std::vector<GemmTile> tiles;
+    std::vector<int> job_off(maxsteps + 1), tile_off(maxsteps + 1);
+    std::vector<size_t> smem(maxsteps, 0);
+    for (int st = 0; st < maxsteps; ++st) {
+        job_off[st] = (int)jobs.size();
+        tile_off[st] = (int)tiles.size();
+        for (int f = 0; f < nf; ++f) {
+            if (st >= nsteps[f]) continue;
+            int k0 = st * kb[f];
+            int kbs = std::min(kb[f], fr[f].ni - k0);
+            size_t need = (size_t)(fr[f].ni - k0) * kbs * sizeof(T);
+            int use_smem = need <= (size_t)PANEL_SMEM_MAX;
+            if (use_smem) smem[st] = std::max(smem[st], need);
+            jobs.push_back({f, k0, kbs, use_smem, aoff[f]});
+            GemmDesc<T> d{};
+            d.A = nullptr;  // patched on the device side below (pointer arithmetic on arena)
+            d.A = arena + fr[f].foff + (long)fr[f].n * k0;
+            d.lda = fr[f].n;
+            d.B = nullptr;  // set after the workspace exists
+            d.C = arena + fr[f].foff;
+            d.ldc = fr[f].n;
+            d.ldb = kbs;
+            d.m = fr[f].n;
+            d.n = fr[f].n;
+            d.k = kbs;
+            d.transA = 0;
+            d.transB = 0;
+            d.alpha = T(1);
+            d.beta = T(1);
+            d.zr_lo = k0;
+            d.zr_hi = k0 + kbs;
+            d.skip_lo = k0;
+            d.skip_hi = k0 + kbs;
+            d.front = (int)(aoff[f] & 0x7fffffff);  // temporary: holds the Aold offset
+            descs.push_back(d);
+            gemm_tiles_for(descs.back(), (int)descs.size() - 1, tiles);
+        }
+    }
+    job_off[maxsteps] = (int)jobs.size();
+    tile_off[maxsteps] = (int)tiles.size();
+    DevBuf d_aold, d_jobs, d_descs, d_tiles;
+    int rc;
+    if ((rc = d_aold.alloc(sizeof(T) * std::max(aold_total, 1L)))) return rc;
+    for (size_t i = 0; i < descs.size(); ++i) {
+        descs[i].B = d_aold.as<T>() + jobs[i].aoff;
+        descs[i].front = 0;
+    }
+    if ((rc = upload(d_jobs, jobs, s)) || (rc = upload(d_descs, descs, s)) || (rc = upload(d_tiles, tiles, s)))
+        return rc;
+    for (int st = 0; st < maxsteps; ++st) {
+        int nj = job_off[st + 1] - job_off[st];
+        if ((rc = launch_gj_panel<T>(d_jobs.as<PanelJob>() + job_off[st], nj, smem[st], d_fr, arena, d_aold.as<T>(),
+                                     piv, status, s)))
+            return rc;
+        if ((rc = gemm_batched<T>(d_descs.as<GemmDesc<T>>(), d_tiles.as<GemmTile>() + tile_off[st],
+                                  tile_off[st + 1] - tile_off[st], s)))
+            return rc;
+    }
+    HSS_CUDA(cudaStreamSynchronize(s));
+    return HSS_OK;
+}
+
+struct RoundFront {     // a front of the current sampling round
+    int f;              // stage-local front
+    int r;
+};
+
+// Randomized HSS compression of the stage's Schur complements, written into
+// the parent fronts.  Fronts whose HSS tree is a single node (or with
+// compression off) copy S unchanged.
+template <class T>
+int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vector<FrontDev> &fr,
+                   const std::vector<int> &boxes, const std::vector<long> &poff, const std::vector<int> &pn,
+                   const std::vector<long> &keep_h, T *arena, T *keep, int *status_dev, int nstatus,
+                   std::vector<FrontLog> &logv, hss_factor_t *F, cudaStream_t s) {
+    int nf = (int)fr.size();
+    int rc;
+    std::vector<ExpandFront> ef(nf);
+    for (int f = 0; f < nf; ++f) {
+        const FrontDev &d = fr[f];
+        ef[f].S = arena + d.foff + d.ni + (long)d.n * d.ni;
+        ef[f].lds = d.n;
+        ef[f].nb = d.nb;
+        ef[f].fmap = t->d_fmap.as<int>() + t->boff[boxes[f]];
+        ef[f].poff = poff[f];
+        ef[f].pn = pn[f];
+        ef[f].keep_h = keep_h[f];
+    }
+    DevBuf d_ef;
+    if ((rc = upload(d_ef, ef, s))) return rc;
+
+    std::vector<RoundFront> active;
+    std::vector<ExpandItem> plain_items;
+    std::vector<int> rounds(nf, 0), kmax(nf, 0), rfin(nf, 0);
+    for (int f = 0; f < nf; ++f) {
+        int b = boxes[f];
+        if (fr[f].nb == 0) continue;
+        bool comp = o.compress && t->hss[b].size() > 1;
+        if (comp) {
+            active.push_back({f, std::min(o.r0, o.rmax)});
+        } else {
+            for (int r0 = 0; r0 < fr[f].nb; r0 += EXP_TILE)
+                for (int c0 = 0; c0 < fr[f].nb; c0 += EXP_TILE)
+                    plain_items.push_back({0, f, -1, -1, r0, c0, 0, fr[f].nb, 0, fr[f].nb});
+        }
+    }
+    if (!plain_items.empty()) {
+        DevBuf d_items;
+        if ((rc = upload(d_items, plain_items, s))) return rc;
+        if ((rc = launch_hss_expand<T>(d_items.as<ExpandItem>(), (int)plain_items.size(), nullptr, nullptr,
+                                       d_ef.as<ExpandFront>(), nullptr, nullptr, arena, keep, s)))
+            return rc;
+        HSS_CUDA(cudaStreamSynchronize(s));
+    }
+
+    while (!active.empty()) {
+        int nc = (int)active.size();
+        // ---- node table, workspace layout
+        std::vector<CompFront<T>> cfs(nc);
+        std::vector<NodeDev> nodes;
+        std::vector<int> node_base(nc + 1);
+        long wsz = 0, isz = 0;
+        for (int c = 0; c < nc; ++c) {
+            const FrontDev &d = fr[active[c].f];
+            int r = active[c].r;
+            cfs[c].S = arena + d.foff + d.ni + (long)d.n * d.ni;
+            cfs[c].lds = d.n;
+            cfs[c].nb = d.nb;
+            cfs[c].r = r;
+            cfs[c].box = boxes[active[c].f];
+            cfs[c].yoff = wsz;
+            wsz += (long)d.nb * r;
+            cfs[c].zoff = wsz;
+            wsz += (long)d.nb * r;
+            const auto &hn = t->hss[boxes[active[c].f]];
+            node_base[c] = (int)nodes.size();
+            int root = (int)hn.size() - 1;
+            for (int i = 0; i < (int)hn.size(); ++i) {
+                NodeDev nd{};
+                nd.cf = c;
+                nd.lo = hn[i].lo;
+                nd.hi = hn[i].hi;
+                nd.a = hn[i].a >= 0 ? node_base[c] + hn[i].a : -1;
+                nd.b = hn[i].b >= 0 ? node_base[c] + hn[i].b : -1;
+                int mcap = nd.a < 0 ? hn[i].hi - hn[i].lo
+                                    : nodes[nd.a].s[0].kcap + nodes[nd.b].s[0].kcap;
+                int kcap = std::min(mcap, r);
+                for (int sd = 0; sd < 2; ++sd) {
+                    NodeSide &ns = nd.s[sd];
+                    ns.mcap = mcap;
+                    ns.kcap = kcap;
+                    if (i == root) continue;
+                    ns.loff = wsz; wsz += (long)mcap * r;
+                    ns.toff = wsz; wsz += (long)kcap * mcap;
+                    ns.skoff = wsz; wsz += (long)kcap * r;
+                    ns.tloff = wsz; wsz += (long)kcap * r;
+                    ns.talloff = wsz; wsz += (long)(hn[i].hi - hn[i].lo) * kcap;
+                    ns.ordoff = isz; isz += mcap;
+                    ns.skioff = isz; isz += kcap;
+                }
+                nodes.push_back(nd);
+            }
+        }
+        node_base[nc] = (int)nodes.size();
+        int nn = (int)nodes.size();
+        DevBuf d_ws, d_iws, d_nodes, d_cfs, d_kout, d_fk;
+        if ((rc = d_ws.alloc(sizeof(T) * std::max(wsz, 1L))) || (rc = d_iws.alloc(sizeof(int) * std::max(isz, 1L))) ||
+            (rc = upload(d_nodes, nodes, s)) || (rc = upload(d_cfs, cfs, s)) ||
+            (rc = d_kout.alloc(sizeof(int) * 2 * nn)) || (rc = d_fk.alloc(sizeof(int) * nc)))
+            return rc;
+        HSS_CUDA(cudaMemsetAsync(d_kout.p, 0, sizeof(int) * 2 * nn, s));
+        HSS_CUDA(cudaMemsetAsync(d_fk.p, 0, sizeof(int) * nc, s));
+        T *ws = d_ws.as<T>();
+        // ---- sampling Y = S Omega, Z = S^t Psi, then the leaf corrections
+        std::vector<GemmDesc<T>> g1, g2;
+        std::vector<GemmTile> t1, t2;
+        for (int c = 0; c < nc; ++c) {
+            GemmDesc<T> d{};
+            d.A = cfs[c].S;
+            d.lda = (int)cfs[c].lds;
+            d.B = nullptr;
+            d.m = cfs[c].nb;
+            d.n = cfs[c].r;
+            d.k = cfs[c].nb;
+            d.alpha = T(1);
+            d.beta = T(0);
+            d.zr_lo = d.zr_hi = 0;
+            d.skip_lo = d.skip_hi = 0;
+            d.seed = o.seed;
+            d.front = cfs[c].box;
+            d.brow0 = 0;
+            d.ldc = cfs[c].nb;
+            d.C = ws + cfs[c].yoff;
+            d.transA = 0;
+            d.stream = 0;
+            g1.push_back(d);
+            gemm_tiles_for(g1.back(), (int)g1.size() - 1, t1);
+            d.C = ws + cfs[c].zoff;
+            d.transA = 1;
+            d.stream = 1;
+            g1.push_back(d);
+            gemm_tiles_for(g1.back(), (int)g1.size() - 1, t1);
+            for (int i = node_base[c]; i < node_base[c + 1]; ++i) {
+                if (nodes[i].a >= 0) continue;
+                int lo = nodes[i].lo, m = nodes[i].hi - nodes[i].lo;
+                GemmDesc<T> e = d;
+                e.A = cfs[c].S + lo + cfs[c].lds * lo;
+                e.m = m;
+                e.k = m;
+                e.alpha = T(-1);
+                e.beta = T(1);
+                e.brow0 = lo;
+                e.C = ws + cfs[c].yoff + lo;
+                e.transA = 0;
+                e.stream = 0;
+                g2.push_back(e);
+                gemm_tiles_for(g2.back(), (int)g2.size() - 1, t2);
+                e.C = ws + cfs[c].zoff + lo;
+                e.transA = 1;
+                e.stream = 1;
+                g2.push_back(e);
+                gemm_tiles_for(g2.back(), (int)g2.size() - 1, t2);
+            }
+        }
+        {
+            DevBuf a, b, c2, d2;
+            if ((rc = upload(a, g1, s)) || (rc = upload(b, t1, s)) || (rc = upload(c2, g2, s)) || (rc = upload(d2, t2, s)))
+                return rc;
+            if ((rc = gemm_batched<T>(a.as<GemmDesc<T>>(), b.as<GemmTile>(), (int)t1.size(), s))) return rc;
+            if ((rc = gemm_batched<T>(c2.as<GemmDesc<T>>(), d2.as<GemmTile>(), (int)t2.size(), s))) return rc;
+            HSS_CUDA(cudaStreamSynchronize(s));
+        }
+        // ---- interpolative decompositions, deepest HSS level first
+        int maxd = 0;
+        std::vector<int> ndepth(nn, 0);
+        for (int c = 0; c < nc; ++c) {
+            const auto &hn = t->hss[boxes[active[c].f]];
+            for (int i = 0; i < (int)hn.size(); ++i) {
+                ndepth[node_base[c] + i] = hn[i].depth;
+                maxd = std::max(maxd, hn[i].depth);
+            }
+        }
+        std::vector<std::vector<int>> work(maxd + 1);
+        std::vector<size_t> idsmem(maxd + 1, 0), tallsmem(maxd + 1, 0);
+        for (int i = 0; i < nn; ++i) {
+            int dpt = ndepth[i];
+            if (dpt == 0) continue;  // roots carry no basis
+            int r = cfs[nodes[i].cf].r;
+            int mcap = nodes[i].s[0].mcap, kcap = nodes[i].s[0].kcap;
+            work[dpt].push_back(2 * i);
+            work[dpt].push_back(2 * i + 1);
+            idsmem[dpt] = std::max(idsmem[dpt], sizeof(T) * ((size_t)r * mcap + r + mcap) + sizeof(int) * mcap + 16);
+            tallsmem[dpt] = std::max(tallsmem[dpt], sizeof(int) * (mcap + 2) + sizeof(T) * (size_t)mcap * kcap + 16);
+        }
+        std::vector<DevBuf> wbufs(maxd + 1);
+        for (int dpt = maxd; dpt >= 1; --dpt) {
+            if (work[dpt].empty()) continue;
+            if ((rc = upload(wbufs[dpt], work[dpt], s))) return rc;
+            if ((rc = launch_hss_id<T>(d_nodes.as<NodeDev>(), wbufs[dpt].as<int>(), (int)work[dpt].size(),
+                                       d_cfs.as<CompFront<T>>(), ws, d_iws.as<int>(), d_kout.as<int>(),
+                                       d_fk.as<int>(), (T)o.tol, o.seed, idsmem[dpt], s)))
+                return rc;
+        }
+        std::vector<int> hk(2 * nn), hfk(nc);
+        HSS_CUDA(cudaMemcpyAsync(hk.data(), d_kout.p, sizeof(int) * 2 * nn, cudaMemcpyDeviceToHost, s));
+        HSS_CUDA(cudaMemcpyAsync(hfk.data(), d_fk.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+        HSS_CUDA(cudaStreamSynchronize(s));
+        // ---- decide: fronts whose rank reached r - oversample sample again, wider
+        std::vector<RoundFront> next;
+        std::vector<char> done(nc, 0);
+        for (int c = 0; c < nc; ++c) {
+            int f = active[c].f, r = active[c].r;
+            rounds[f]++;
+            kmax[f] = hfk[c];
+            rfin[f] = r;
+            if (hfk[c] > r - o.oversample && r < fr[f].nb && r + o.dr <= o.rmax)
+                next.push_back({f, r + o.dr});
+            else
+                done[c] = 1;
+        }
+        // ---- expansion of the finished fronts: tall bases, then H tiles
+        for (int dpt = maxd; dpt >= 1; --dpt) {
+            std::vector<int> wk;
+            for (int x : work[dpt])
+                if (done[nodes[x >> 1].cf]) wk.push_back(x);
+            if (wk.empty()) continue;
+            DevBuf d_wk;
+            if ((rc = upload(d_wk, wk, s))) return rc;
+            if ((rc = launch_hss_tall<T>(d_nodes.as<NodeDev>(), d_wk.as<int>(), (int)wk.size(), d_kout.as<int>(), ws,
+                                         d_iws.as<int>(), tallsmem[dpt], s)))
+                return rc;
+            HSS_CUDA(cudaStreamSynchronize(s));
+        }
+        std::vector<ExpandItem> items;
+        for (int c = 0; c < nc; ++c) {
+            if (!done[c]) continue;
+            int f = active[c].f;
+            for (int i = node_base[c]; i < node_base[c + 1]; ++i) {
+                const NodeDev &N = nodes[i];
+                if (N.a < 0) {
+                    for (int r0 = N.lo; r0 < N.hi; r0 += EXP_TILE)
+                        for (int c0 = N.lo; c0 < N.hi; c0 += EXP_TILE)
+                            items.push_back({0, f, -1, -1, r0, c0, N.lo, N.hi, N.lo, N.hi});
+                    continue;
+                }
+                const NodeDev &Na = nodes[N.a], &Nb = nodes[N.b];
+                for (int pass = 0; pass < 2; ++pass) {
+                    int x = pass ? N.b : N.a, y = pass ? N.a : N.b;
+                    const NodeDev &X = pass ? Nb : Na, &Y = pass ? Na : Nb;
+                    for (int r0 = X.lo; r0 < X.hi; r0 += EXP_TILE)
+                        for (int c0 = Y.lo; c0 < Y.hi; c0 += EXP_TILE)
+                            items.push_back({1, f, x, y, r0, c0, X.lo, X.hi, Y.lo, Y.hi});
+                }
+            }
+        }
+        if (!items.empty()) {
+            DevBuf d_items;
+            if ((rc = upload(d_items, items, s))) return rc;
+            if ((rc = launch_hss_expand<T>(d_items.as<ExpandItem>(), (int)items.size(), d_nodes.as<NodeDev>(),
+                                           d_kout.as<int>(), d_ef.as<ExpandFront>(), ws, d_iws.as<int>(), arena,
+                                           keep, s)))
+                return rc;
+            HSS_CUDA(cudaStreamSynchronize(s));
+        }
+        active.swap(next);
+    }
+    for (int f = 0; f < nf; ++f) {
+        int b = boxes[f];
+        FrontLog lg{b, t->level[b], fr[f].ni, fr[f].nb, rfin[f], rounds[f], kmax[f], (int)t->hss[b].size()};
+        logv.push_back(lg);
+        F->max_rank = std::max(F->max_rank, kmax[f]);
+        F->max_r = std::max(F->max_r, rfin[f]);
+        F->rounds = std::max(F->rounds, rounds[f]);
+    }
+    (void)status_dev;
+    (void)nstatus;
+    return HSS_OK;
+}
+
+template <class T>
+int build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, DevBuf &&d_fronts, bool top, cudaStream_t s) {
+    as.top = top;
+    as.nfronts = (int)fr.size();
+    as.fronts_buf = std::move(d_fronts);
+    as.d_fronts = as.fronts_buf.as<FrontDev>();
+    std::vector<ApplyTile> fw, bw;
+    for (int f = 0; f < (int)fr.size(); ++f) {
+        if (fr[f].ni == 0) continue;
+        for (int r0 = 0; r0 < fr[f].n; r0 += APPLY_ROWS) fw.push_back({f, r0});
+        for (int r0 = 0; r0 < fr[f].ni; r0 += APPLY_ROWS) bw.push_back({f, r0});
+    }
+    int rc;
+    if ((rc = upload(as.fwd_buf, fw, s)) || (rc = upload(as.bwd_buf, bw, s))) return rc;
+    as.d_fwd = as.fwd_buf.as<ApplyTile>();
+    as.d_bwd = as.bwd_buf.as<ApplyTile>();
+    as.nfwd = (int)fw.size();
+    as.nbwd = (int)bw.size();
+    return HSS_OK;
+}
+
+template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hss_factor_opts &o, cudaStream_t s,
+                                   hss_factor_t *F) {
+    const int nbox = t->nbox;
+    int rc;
+    std::vector<long> foff(nbox);
+    long total = 0;
+    for (int b = 0; b < nbox; ++b) {
+        long n = t->ni[b] + t->nb[b];
+        foff[b] = total;
+        total += (n * n + 31) / 32 * 32;
+    }
+    const int ntop = t->nb[0] + t->nb[1];
+    const long foff_top = total;
+    total += (long)ntop * ntop;
+    F->ntop = ntop;
+    if ((rc = F->arena.alloc(sizeof(T) * std::max(total, 1L)))) return rc;
+    HSS_CUDA(cudaMemsetAsync(F->arena.p, 0, sizeof(T) * total, s));
+    T *arena = F->arena_ptr<T>();
+    const int ilen = t->ioff[nbox];
+    std::vector<int> topset(t->bset.begin() + t->boff[0], t->bset.begin() + t->boff[2]);
+    DevBuf d_piv, d_scratch, d_slot;
+    if ((rc = upload(F->d_topset, topset, s)) || (rc = F->d_iperm.alloc(sizeof(int) * (ilen + ntop + 1))) ||
+        (rc = d_piv.alloc(sizeof(int) * (ilen + ntop + 1))) || (rc = d_scratch.alloc(sizeof(int) * (ilen + ntop + 1))) ||
+        (rc = d_slot.alloc(sizeof(int) * t->nelem)))
+        return rc;
+    HSS_CUDA(cudaMemsetAsync(d_slot.p, 0xff, sizeof(int) * t->nelem, s));
+    // optional copies of S and H
+    F->keep_s.assign(nbox, -1);
+    F->keep_h.assign(nbox, -1);
+    if (o.keep_schur) {
+        long ks = 0;
+        for (int b = 0; b < nbox; ++b) {
+            F->keep_s[b] = ks;
+            ks += (long)t->nb[b] * t->nb[b];
+            F->keep_h[b] = ks;
+            ks += (long)t->nb[b] * t->nb[b];
+        }
+        if ((rc = F->keep.alloc(sizeof(T) * std::max(ks, 1L)))) return rc;
+    }
+    T *keep = F->keep.as<T>();
+    F->factor_bytes = 0;
+    F->front_flops = 0;
+    F->exec_flops = 0;
+
+    auto front_of = [&](int b) {
+        FrontDev d{};
+        d.foff = foff[b];
+        d.ni = t->ni[b];
+        d.nb = t->nb[b];
+        d.n = d.ni + d.nb;
+        d.ioff = t->ioff[b];
+        d.iset_off = t->ioff[b];
+        d.iperm_off = t->ioff[b];
+        d.bset_off = t->boff[b];
+        d.leaf = t->child0[b] < 0;
+        d.box = b;
+        return d;
+    };
+    // side of each element of a parent front: 0 = in B^child0, 1 = in B^child1
+    auto front_dofs = [&](int b, std::vector<int> &dofs, std::vector<int> &sides) {
+        dofs.assign(t->iset.begin() + t->ioff[b], t->iset.begin() + t->ioff[b + 1]);
+        dofs.insert(dofs.end(), t->bset.begin() + t->boff[b], t->bset.begin() + t->boff[b + 1]);
+        sides.assign(dofs.size() / t->bs, 0);
+        if (t->child0[b] >= 0) {
+            int c0 = t->child0[b];
+            std::vector<int> e0;
+            for (int i = t->boff[c0]; i < t->boff[c0 + 1]; i += t->bs) e0.push_back(t->bset[i] / t->bs);
+            std::sort(e0.begin(), e0.end());
+            for (size_t q = 0; q < sides.size(); ++q)
+                sides[q] = std::binary_search(e0.begin(), e0.end(), dofs[q * t->bs] / t->bs) ? 0 : 1;
+        }
+    };
+
+    for (size_t si = 0; si < t->stages.size(); ++si) {
+        const auto &boxes = t->stages[si];
+        std::vector<FrontDev> fr;
+        std::vector<std::vector<int>> dofs(boxes.size()), sides(boxes.size());
+        std::vector<long> poff(boxes.size()), keeph(boxes.size());
+        std::vector<int> pn(boxes.size());
+        for (size_t f = 0; f < boxes.size(); ++f) {
+            int b = boxes[f];
+            fr.push_back(front_of(b));
+            front_dofs(b, dofs[f], sides[f]);
+            int par = t->parent[b];
+            poff[f] = par >= 0 ? foff[par] : foff_top;
+            pn[f] = par >= 0 ? t->ni[par] + t->nb[par] : ntop;
+            keeph[f] = F->keep_h[b];
+            const double ni = fr.back().ni, nb = fr.back().nb;
+            F->front_flops += 2.0 / 3.0 * ni * ni * ni + 2.0 * ni * ni * nb + 2.0 * nb * nb * ni;
+            F->factor_bytes += sizeof(T) * (ni * (ni + nb) + ni * nb);
+        }
+        DevBuf d_fr, d_status;
+        if ((rc = upload(d_fr, fr, s)) || (rc = d_status.alloc(sizeof(int) * fr.size()))) return rc;
+        HSS_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int) * fr.size(), s));
+        if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, s))) return rc;
+        if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_status.as<int>(),
+                                     F->exec_flops, s)))
+            return rc;
+        std::vector<int> hst(fr.size());
+        HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status.p, sizeof(int) * fr.size(), cudaMemcpyDeviceToHost, s));
+        HSS_CUDA(cudaStreamSynchronize(s));
+        for (size_t f = 0; f < fr.size(); ++f)
+            if (hst[f]) {
+                set_error("hss_factor: zero pivot in the front of box " + std::to_string(boxes[f]));
+                return HSS_ESINGULAR;
+            }
+        if ((rc = launch_iperm(d_fr.as<FrontDev>(), (int)fr.size(), t->d_iset.as<int>(), d_piv.as<int>(),
+                               F->d_iperm.as<int>(), d_scratch.as<int>(), s)))
+            return rc;
+        if (o.keep_schur)
+            for (size_t f = 0; f < fr.size(); ++f) {
+                const FrontDev &d = fr[f];
+                if (d.nb == 0) continue;
+                HSS_CUDA(cudaMemcpy2DAsync(keep + F->keep_s[d.box], sizeof(T) * d.nb,
+                                           arena + d.foff + d.ni + (long)d.n * d.ni, sizeof(T) * d.n,
+                                           sizeof(T) * d.nb, d.nb, cudaMemcpyDeviceToDevice, s));
+            }
+        if ((rc = compress_stage<T>(t, o, fr, boxes, poff, pn, keeph, arena, keep, d_status.as<int>(),
+                                    (int)fr.size(), F->log, F, s)))
+            return rc;
+        F->apply.emplace_back();
+        if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), false, s))) return rc;
+    }
+    // ---- top block A^(0): cross couplings from A, then full Gauss-Jordan inversion
+    {
+        FrontDev top{};
+        top.foff = foff_top;
+        top.n = ntop;
+        top.ni = ntop;
+        top.nb = 0;
+        top.ioff = ilen;
+        top.iset_off = 0;
+        top.iperm_off = ilen;
+        top.bset_off = 0;
+        top.leaf = 0;
+        top.box = -1;
+        std::vector<FrontDev> fr = {top};
+        std::vector<std::vector<int>> dofs(1), sides(1);
+        dofs[0] = topset;
+        sides[0].assign(ntop / t->bs, 1);
+        for (int q = 0; q < t->nb[0] / t->bs; ++q) sides[0][q] = 0;
+        DevBuf d_fr, d_status;
+        if ((rc = upload(d_fr, fr, s)) || (rc = d_status.alloc(sizeof(int)))) return rc;
+        HSS_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s));
+        if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, s))) return rc;
+        if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_status.as<int>(),
+                                     F->exec_flops, s)))
+            return rc;
+        int hst = 0;
+        HSS_CUDA(cudaMemcpyAsync(&hst, d_status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        HSS_CUDA(cudaStreamSynchronize(s));
+        if (hst) {
+            set_error("hss_factor: zero pivot in the top block");
+            return HSS_ESINGULAR;
+        }
+        if ((rc = launch_iperm(d_fr.as<FrontDev>(), 1, F->d_topset.as<int>(), d_piv.as<int>(), F->d_iperm.as<int>(),
+                               d_scratch.as<int>(), s)))
+            return rc;
+        F->front_flops += 2.0 / 3.0 * (double)ntop * ntop * ntop;
+        F->factor_bytes += sizeof(T) * (double)ntop * ntop;
+        F->apply.emplace_back();
+        if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), true, s))) return rc;
+    }
+    HSS_CUDA(cudaStreamSynchronize(s));
+    return HSS_OK;
+}
+
+}  // namespace
+}  // namespace hssnd
+
+using namespace hssnd;
+
+extern "C" int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_factor_opts *opts, void *stream,
+                          hss_factor_t **out) {
+    if (!A || !tree || !out) {
+        set_error("hss_factor: null argument");
+        return HSS_EINVAL;
+    }
+    *out = nullptr;
+    hss_factor_opts o;
+    hss_factor_opts_default(&o);
+    if (opts) o = *opts;
+    if (A->nb != tree->nelem || A->bs != tree->bs || !A->val || !(o.tol >= 0) || o.r0 < 1 || o.dr < 1 ||
+        o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 || (o.precision != HSS_FP64 && o.precision != HSS_FP32)) {
+        set_error("hss_factor: invalid argument (matrix/tree mismatch or options out of range; rmax <= 128)");
+        return HSS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    hss_factor_t *F = new hss_factor_t();
+    F->tree = tree;
+    F->ndof = tree->ndof;
+    F->precision = o.precision;
+    F->opts = o;
+    int rc = o.precision == HSS_FP32 ? factor_impl<float>(A, tree, o, s, F) : factor_impl<double>(A, tree, o, s, F);
+    if (rc) {
+        cudaStreamSynchronize(s);
+        delete F;
+        return rc;
+    }
+    *out = F;
+    return HSS_OK;
+}
+
+extern "C" int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info) {
+    if (!f || !info) {
+        set_error("hss_factor_get_info: null argument");
+        return HSS_EINVAL;
+    }
+    info->factor_bytes = f->factor_bytes;
+    info->front_flops = f->front_flops;
+    info->executed_flops = f->exec_flops;
+    info->max_rank = f->max_rank;
+    info->max_r = f->max_r;
+    info->rounds = f->rounds;
+    info->nfronts = (int)f->log.size();
+    return HSS_OK;
+}
+
+extern "C" int hss_factor_export_front(const hss_factor_t *f, int box, double *S, double *H, int *kmax, int *r) {
+    if (!f || box < 0 || box >= f->tree->nbox) {
+        set_error("hss_factor_export_front: invalid argument");
+        return HSS_EINVAL;
+    }
+    for (const auto &lg : f->log)
+        if (lg.box == box) {
+            if (kmax) *kmax = lg.kmax;
+            if (r) *r = lg.r;
+        }
+    if (!S && !H) return HSS_OK;
+    if (f->keep_s.empty() || f->keep_s[box] < 0) {
+        set_error("hss_factor_export_front: factor built without keep_schur");
+        return HSS_EINVAL;
+    }
+    long nb = f->tree->nb[box];
+    size_t cnt = (size_t)nb * nb;
+    if (cnt == 0) return HSS_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError(), "export sync");
+    for (int which = 0; which < 2; ++which) {
+        double *dst = which ? H : S;
+        if (!dst) continue;
+        long off = which ? f->keep_h[box] : f->keep_s[box];
+        if (f->precision == HSS_FP32) {
+            std::vector<float> tmp(cnt);
+            HSS_CUDA(cudaMemcpy(tmp.data(), f->keep.as<float>() + off, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < cnt; ++i) dst[i] = tmp[i];
+        } else {
+            HSS_CUDA(cudaMemcpy(dst, f->keep.as<double>() + off, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+        }
+    }
+    return HSS_OK;
+}
+
+extern "C" void hss_factor_destroy(hss_factor_t *f) { delete f; }

@@ -1,0 +1,52 @@
+// The factorization handle.
+#pragma once
+#include <memory>
+
+#include "front.h"
+#include "internal.h"
+
+namespace hssnd {
+
+constexpr int APPLY_ROWS = 64;
+
+struct ApplyTile {
+    int front;   // stage-local front index
+    int row0;
+};
+
+// Per level (and the top block): fronts and the row tiles of the apply.
+struct ApplyStage {
+    bool top = false;
+    int nfronts = 0;
+    DevBuf fronts_buf, fwd_buf, bwd_buf;
+    FrontDev *d_fronts = nullptr;
+    ApplyTile *d_fwd = nullptr, *d_bwd = nullptr;
+    int nfwd = 0, nbwd = 0;
+};
+
+struct FrontLog {   // per-front record (rank logging, Sec. 5 empirical cost)
+    int box, level, ni, nb, r, rounds, kmax, nnodes;
+};
+
+int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);
+
+}  // namespace hssnd
+
+struct hss_factor_t {
+    const hss_tree *tree = nullptr;
+    int ndof = 0;
+    int precision = HSS_FP64;
+    hss_factor_opts opts{};
+    hssnd::DevBuf arena;         // all fronts and the top block (T = double or float)
+    hssnd::DevBuf d_iperm;       // gather lists of the apply (iset_len + ntop)
+    hssnd::DevBuf d_topset;      // [B^1 ; B^2]
+    hssnd::DevBuf tvec;          // apply scratch (N x nrhs)
+    hssnd::DevBuf keep;          // optional copies of S and H per front
+    std::vector<long> keep_s, keep_h;  // per box offsets (-1: none)
+    std::vector<hssnd::ApplyStage> apply;
+    std::vector<hssnd::FrontLog> log;
+    int ntop = 0;
+    double factor_bytes = 0, front_flops = 0, exec_flops = 0;
+    int max_rank = 0, max_r = 0, rounds = 0;
+    template <class T> T *arena_ptr() const { return arena.as<T>(); }
+};

@@ -1,0 +1,47 @@
+// Device-side descriptors of fronts and per-stage work lists.
+#pragma once
+#include "internal.h"
+
+namespace hssnd {
+
+constexpr int PANEL_NT = 512;
+constexpr int PANEL_KB_MAX = 32;
+constexpr int PANEL_SMEM_MAX = 200 * 1024;
+
+// One front (box) of the factorization, or the top block.
+struct FrontDev {
+    long foff;        // offset of the n x n column-major front matrix in the arena (elements)
+    int n, ni, nb;    // n = ni + nb
+    int ioff;         // offset of the front's I entries in per-I arrays (pivots, gather list)
+    int iset_off;     // offset of the I dof list in the tree's iset (top block: in topset)
+    int iperm_off;    // offset of the permuted I list (gather list of the apply)
+    int bset_off;     // offset of the B dof list in the tree's bset
+    int leaf;         // leaf front (all of A(front, front) comes from A)
+    int box;          // box id (-1 for the top block)
+};
+
+// A front element of the current stage: where its dofs start inside the front.
+struct StageElem {
+    int elem;
+    int front;        // stage-local front index
+    int fpos;         // position of the element's first dof inside [I ; B]
+    int side;         // which child's B it belongs to (parent fronts)
+};
+
+struct PanelJob {
+    int front;        // stage-local front index
+    int k0, kb;
+    int smem;         // 1: panel in shared memory
+    long aoff;        // offset of this job's Aold (kb x n) in the workspace
+};
+
+template <class T>
+int launch_scatter_A(const hss_bsr *A, const StageElem *se, int nse, int *elem_slot, const FrontDev *fr, T *arena,
+                     cudaStream_t s);
+template <class T>
+int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *aold, int *piv,
+                    int *status, cudaStream_t s);
+int launch_iperm(const FrontDev *fr, int nf, const int *iset, const int *piv, int *iperm, int *scratch,
+                 cudaStream_t s);
+
+}  // namespace hssnd

@@ -1,0 +1,131 @@
+// Batched tiled GEMM on a list of column-major problems (SIMT FMA, FP64 or
+// FP32).  Serves the Gauss-Jordan trailing updates of the fronts (the Schur
+// update S = F_bb - F_bi F_ii^-1 F_ib accumulates here), the randomized
+// sampling products Y = S Omega, Z = S^t Psi with the +-1 test matrix
+// generated in registers (never stored), and the leaf-local sample
+// corrections of the HSS construction.
+#include "internal.h"
+
+namespace hssnd {
+
+constexpr int GK = 16;      // k-chunk
+constexpr int GT = 256;     // threads per CTA (16 x 16, 4 x 4 outputs each)
+
+template <class T>
+__global__ void __launch_bounds__(GT) k_gemm(const GemmDesc<T> *__restrict__ descs, const GemmTile *__restrict__ tiles) {
+    __shared__ T As[2][GK][GEMM_TM + 1];
+    __shared__ T Bs[2][GK][GEMM_TN + 1];
+    const GemmTile tl = tiles[blockIdx.x];
+    const GemmDesc<T> d = descs[tl.desc];
+    const int row0 = tl.tm * GEMM_TM, col0 = tl.tn * GEMM_TN;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+
+    T ra[4], rb[4];
+    auto load_regs = [&](int k0) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            int idx = tid + GT * t;
+            int i, kk;
+            if (!d.transA) { i = idx & 63; kk = idx >> 6; }
+            else { kk = idx & 15; i = idx >> 4; }
+            int gi = row0 + i, gk = k0 + kk;
+            T v = T(0);
+            if (gi < d.m && gk < d.k) v = d.transA ? d.A[gk + (long)gi * d.lda] : d.A[gi + (long)gk * d.lda];
+            ra[t] = v;
+            int j;
+            if (d.B && d.transB) { j = idx & 63; kk = idx >> 6; }
+            else { kk = idx & 15; j = idx >> 4; }
+            int gj = col0 + j;
+            gk = k0 + kk;
+            T w = T(0);
+            if (gj < d.n && gk < d.k) {
+                if (!d.B) w = (T)rademacher(d.seed, d.stream, d.front, d.brow0 + gk, gj);
+                else w = d.transB ? d.B[gj + (long)gk * d.ldb] : d.B[gk + (long)gj * d.ldb];
+            }
+            rb[t] = w;
+        }
+    };
+    auto store_regs = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            int idx = tid + GT * t;
+            int i, kk, j;
+            if (!d.transA) { i = idx & 63; kk = idx >> 6; }
+            else { kk = idx & 15; i = idx >> 4; }
+            As[buf][kk][i] = ra[t];
+            if (d.B && d.transB) { j = idx & 63; kk = idx >> 6; }
+            else { kk = idx & 15; j = idx >> 4; }
+            Bs[buf][kk][j] = rb[t];
+        }
+    };
+    int nk = (d.k + GK - 1) / GK;
+    if (nk > 0) {
+        load_regs(0);
+        store_regs(0);
+    }
+    __syncthreads();
+    for (int kc = 0; kc < nk; ++kc) {
+        int buf = kc & 1;
+        if (kc + 1 < nk) load_regs((kc + 1) * GK);
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[buf][kk][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[buf][kk][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        if (kc + 1 < nk) store_regs(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        int gj = col0 + ty + 16 * b;
+        if (gj >= d.n || (gj >= d.skip_lo && gj < d.skip_hi)) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            int gi = row0 + tx + 16 * a;
+            if (gi >= d.m) continue;
+            T *c = d.C + gi + (long)gj * d.ldc;
+            T beta = (gi >= d.zr_lo && gi < d.zr_hi) ? T(0) : d.beta;
+            T v = d.alpha * acc[a][b];
+            if (beta != T(0)) v = fma(beta, *c, v);
+            *c = v;
+        }
+    }
+}
+
+template <class T>
+int gemm_batched(const GemmDesc<T> *d_desc, const GemmTile *d_tiles, int ntiles, cudaStream_t s) {
+    if (ntiles <= 0) return HSS_OK;
+    k_gemm<T><<<ntiles, GT, 0, s>>>(d_desc, d_tiles);
+    HSS_CHECK_LAUNCH("k_gemm");
+    return HSS_OK;
+}
+
+template <class T>
+void gemm_tiles_for(const GemmDesc<T> &d, int desc_index, std::vector<GemmTile> &tiles) {
+    int tm = cdiv(d.m, GEMM_TM), tn = cdiv(d.n, GEMM_TN);
+    for (int j = 0; j < tn; ++j) {
+        // whole tile column inside the skipped column range: nothing to write
+        int c0 = j * GEMM_TN, c1 = std::min(d.n, c0 + GEMM_TN);
+        if (c0 >= d.skip_lo && c1 <= d.skip_hi) continue;
+        for (int i = 0; i < tm; ++i) tiles.push_back({desc_index, i, j});
+    }
+}
+
+template int gemm_batched<double>(const GemmDesc<double> *, const GemmTile *, int, cudaStream_t);
+template int gemm_batched<float>(const GemmDesc<float> *, const GemmTile *, int, cudaStream_t);
+template void gemm_tiles_for<double>(const GemmDesc<double> &, int, std::vector<GemmTile> &);
+template void gemm_tiles_for<float>(const GemmDesc<float> &, int, std::vector<GemmTile> &);
+
+}  // namespace hssnd

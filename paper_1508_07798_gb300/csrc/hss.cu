@@ -1,0 +1,421 @@
+// Randomized HSS construction of a Schur complement (paper Sec. 2, Theorem 1)
+// with interpolative decompositions (Sec. 2, eq. (43) and its footnote).
+//
+// Per HSS node and side (rows: U, J; columns: V, K), one CTA:
+//   local samples  leaf:   Y(R,:) - S(R,R) Omega(R,:)           (precomputed by GEMM)
+//                  parent: [Y_a(J_a,:) - S(J_a,K_b) Om_b ; Y_b(J_b,:) - S(J_b,K_a) Om_a]
+//                  (columns: Z with S^t and Psi)
+//   row ID         column-pivoted Householder QR of the transposed samples,
+//                  rank k = first j with |R_jj| <= tol |R_11|, T = R11^-1 R12,
+//                  exchanges while some |T_ij| > 2 (largest entry first)
+//   outputs        k, skeleton indices, T, skeleton samples, and the
+//                  compressed test matrix U^t Psi_loc (rows) / V^t Omega_loc (cols)
+// Then, bottom-up, the tall bases U^tall = diag(U^tall_a, U^tall_b) U, and the
+// dense approximant H = D on leaf blocks, U^tall_a S(J_a,K_b) V^tall_b^t across
+// siblings, written straight into the parent front (eq. (32)).
+#include <climits>
+
+#include "hss.h"
+
+namespace hssnd {
+
+template <class T> struct AM {
+    T v;
+    int i;
+};
+
+template <class T> __device__ AM<T> blk_argmax(AM<T> x, AM<T> *sh) {
+    for (int o = 16; o > 0; o >>= 1) {
+        T v2 = __shfl_down_sync(0xffffffffu, x.v, o);
+        int i2 = __shfl_down_sync(0xffffffffu, x.i, o);
+        if (v2 > x.v || (v2 == x.v && i2 < x.i)) {
+            x.v = v2;
+            x.i = i2;
+        }
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        AM<T> b = sh[0];
+        for (int k = 1; k < ID_NT / 32; ++k)
+            if (sh[k].v > b.v || (sh[k].v == b.v && sh[k].i < b.i)) b = sh[k];
+        sh[0] = b;
+    }
+    __syncthreads();
+    AM<T> r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+template <class T> __device__ T blk_sum(T x, T *sh) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T s = 0;
+        for (int k = 0; k < ID_NT / 32; ++k) s += sh[k];
+        sh[0] = s;
+    }
+    __syncthreads();
+    T r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Householder step j on A (r x m, ld r), columns >= j; returns R_jj.
+template <class T> __device__ void householder_step(T *A, int r, int m, int j, T nrm, T *v, T *shs) {
+    T x0 = A[j + (long)r * j];
+    T alpha = (x0 != T(0)) ? -copysign(nrm, x0) : -nrm;
+    for (int i = j + threadIdx.x; i < r; i += ID_NT) v[i] = (i == j) ? x0 - alpha : A[i + (long)r * j];
+    __syncthreads();
+    T part = 0;
+    for (int i = j + threadIdx.x; i < r; i += ID_NT) part += v[i] * v[i];
+    T vn = blk_sum(part, shs);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (vn > T(0)) {
+        for (int c = j + 1 + w; c < m; c += ID_NT / 32) {
+            T d = 0;
+            for (int i = j + lane; i < r; i += 32) d += v[i] * A[i + (long)r * c];
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            T coef = T(2) * d / vn;
+            for (int i = j + lane; i < r; i += 32) A[i + (long)r * c] -= coef * v[i];
+        }
+    }
+    __syncthreads();
+    for (int i = j + threadIdx.x; i < r; i += ID_NT) A[i + (long)r * j] = (i == j) ? alpha : T(0);
+    __syncthreads();
+}
+
+// T = R11^-1 R12 by back substitution, one thread per column of R12.
+template <class T> __device__ void solve_T(const T *A, int r, int m, int k, T *Tm, int kcap) {
+    for (int c = k + threadIdx.x; c < m; c += ID_NT) {
+        T *tc = Tm + (long)kcap * (c - k);
+        for (int i = k - 1; i >= 0; --i) {
+            T t = A[i + (long)r * c];
+            for (int l = i + 1; l < k; ++l) t -= A[i + (long)r * l] * tc[l];
+            tc[i] = t / A[i + (long)r * i];
+        }
+    }
+    __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ nodes, const int *__restrict__ work,
+                                                const CompFront<T> *__restrict__ cfs, T *__restrict__ ws,
+                                                int *__restrict__ iws, int *__restrict__ kout,
+                                                int *__restrict__ front_kmax, T tol, uint64_t seed) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ AM<T> sham[ID_NT / 32];
+    __shared__ T shs[ID_NT / 32];
+    const int node = work[blockIdx.x] >> 1, side = work[blockIdx.x] & 1;
+    const NodeDev N = nodes[node];
+    const CompFront<T> C = cfs[N.cf];
+    const NodeSide me = N.s[side];
+    const int r = C.r, mcap = me.mcap, kcap = me.kcap;
+    const bool leaf = N.a < 0;
+    int ka = 0, m;
+    if (leaf) {
+        m = N.hi - N.lo;
+    } else {
+        ka = kout[2 * N.a + side];
+        m = ka + kout[2 * N.b + side];
+    }
+    T *A = reinterpret_cast<T *>(smraw);                 // r x m, ld r
+    T *v = A + (long)r * mcap;                            // r
+    T *nrm2 = v + r;                                      // mcap
+    int *order = reinterpret_cast<int *>(nrm2 + mcap);    // mcap
+    T *L = ws + me.loff;                                  // m x r, ld mcap
+    const T *S = C.S;
+    const long lds = C.lds;
+
+    // ---- local samples
+    for (int idx = threadIdx.x; idx < m * r; idx += ID_NT) {
+        int i = idx % m, j = idx / m;
+        T val;
+        if (leaf) {
+            const T *Ysrc = ws + (side == 0 ? C.yoff : C.zoff);
+            val = Ysrc[(N.lo + i) + (long)C.nb * j];
+        } else {
+            bool fa = i < ka;
+            int child = fa ? N.a : N.b, other = fa ? N.b : N.a, ii = fa ? i : i - ka;
+            const NodeSide cs = nodes[child].s[side];
+            const NodeSide os = nodes[other].s[1 - side];
+            int ko = kout[2 * other + (1 - side)];
+            val = ws[cs.skoff + ii + (long)cs.kcap * j];
+            int gi = iws[cs.skioff + ii];
+            for (int q = 0; q < ko; ++q) {
+                int go = iws[os.skioff + q];
+                T sv = side == 0 ? S[gi + lds * go] : S[go + lds * gi];
+                val -= sv * ws[os.tloff + q + (long)os.kcap * j];
+            }
+        }
+        L[i + (long)mcap * j] = val;
+        A[j + (long)r * i] = val;
+    }
+    for (int c = threadIdx.x; c < m; c += ID_NT) order[c] = c;
+    __syncthreads();
+
+    // ---- column-pivoted QR of A = L^t with the relative rank cut
+    int k = 0;
+    T first = 0;
+    const int kmx = min(r, m);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j = 0; j < kmx; ++j) {
+        for (int c = j + w; c < m; c += ID_NT / 32) {
+            T s = 0;
+            for (int i = j + lane; i < r; i += 32) s += A[i + (long)r * c] * A[i + (long)r * c];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) nrm2[c] = s;
+        }
+        __syncthreads();
+        AM<T> loc{T(-1), INT_MAX};
+        for (int c = j + threadIdx.x; c < m; c += ID_NT)
+            if (nrm2[c] > loc.v || (nrm2[c] == loc.v && c < loc.i)) {
+                loc.v = nrm2[c];
+                loc.i = c;
+            }
+        AM<T> best = blk_argmax(loc, sham);
+        T nrm = sqrt(best.v);
+        if (j == 0) first = nrm;
+        if (first == T(0) || nrm <= tol * first) break;
+        int p = best.i;
+        if (p != j) {
+            for (int i = threadIdx.x; i < r; i += ID_NT) {
+                T t = A[i + (long)r * j];
+                A[i + (long)r * j] = A[i + (long)r * p];
+                A[i + (long)r * p] = t;
+            }
+            if (threadIdx.x == 0) {
+                int t = order[j];
+                order[j] = order[p];
+                order[p] = t;
+            }
+        }
+        __syncthreads();
+        householder_step(A, r, m, j, nrm, v, shs);
+        k = j + 1;
+    }
+    T *Tm = ws + me.toff;
+    solve_T(A, r, m, k, Tm, kcap);
+
+    // ---- exchanges while some |T_ij| > 2 (largest entry, first in row-major order)
+    for (int sw = 0; sw < ID_MAX_SWAPS && k > 0 && k < m; ++sw) {
+        int nc = m - k;
+        AM<T> loc{T(-1), INT_MAX};
+        for (int q = threadIdx.x; q < k * nc; q += ID_NT) {
+            int i = q / nc, jj = q % nc;  // row-major linear index q
+            T a = fabs(Tm[i + (long)kcap * jj]);
+            if (a > loc.v || (a == loc.v && q < loc.i)) {
+                loc.v = a;
+                loc.i = q;
+            }
+        }
+        AM<T> best = blk_argmax(loc, sham);
+        if (best.v <= T(2)) break;
+        if (threadIdx.x == 0) {
+            int i = best.i / nc, jj = best.i % nc;
+            int t = order[i];
+            order[i] = order[k + jj];
+            order[k + jj] = t;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < m * r; idx += ID_NT) {
+            int c = idx / r, i = idx % r;
+            A[i + (long)r * c] = L[order[c] + (long)mcap * i];
+        }
+        __syncthreads();
+        for (int j = 0; j < k; ++j) {
+            T part = 0;
+            for (int i = j + threadIdx.x; i < r; i += ID_NT) part += A[i + (long)r * j] * A[i + (long)r * j];
+            T nn = sqrt(blk_sum(part, shs));
+            householder_step(A, r, m, j, nn, v, shs);
+        }
+        solve_T(A, r, m, k, Tm, kcap);
+    }
+
+    // ---- outputs
+    if (threadIdx.x == 0) {
+        kout[2 * node + side] = k;
+        atomicMax(&front_kmax[N.cf], k);
+    }
+    int *ordg = iws + me.ordoff;
+    int *sk = iws + me.skioff;
+    const NodeSide sa = leaf ? me : nodes[N.a].s[side];
+    const NodeSide sb = leaf ? me : nodes[N.b].s[side];
+    for (int c = threadIdx.x; c < m; c += ID_NT) {
+        ordg[c] = order[c];
+        if (c < k) {
+            int o = order[c];
+            sk[c] = leaf ? N.lo + o : (o < ka ? iws[sa.skioff + o] : iws[sb.skioff + o - ka]);
+        }
+    }
+    T *skel = ws + me.skoff;
+    T *tl = ws + me.tloff;
+    const int strm = side == 0 ? 1 : 0;  // rows compress Psi (stream 1), columns Omega (stream 0)
+    for (int idx = threadIdx.x; idx < k * r; idx += ID_NT) {
+        int i = idx % k, j = idx / k;
+        skel[i + (long)kcap * j] = L[order[i] + (long)mcap * j];
+        auto W = [&](int row) -> T {
+            if (leaf) return (T)rademacher(seed, strm, C.box, N.lo + row, j);
+            return row < ka ? ws[sa.tloff + row + (long)sa.kcap * j]
+                            : ws[sb.tloff + (row - ka) + (long)sb.kcap * j];
+        };
+        T acc = W(order[i]);
+        for (int jj = 0; jj < m - k; ++jj) acc += Tm[i + (long)kcap * jj] * W(order[k + jj]);
+        tl[i + (long)kcap * j] = acc;
+    }
+}
+
+// Tall bases, bottom-up: U^tall (|R| x k, ld |R|) of each node side.
+template <class T>
+__global__ void k_hss_tall(const NodeDev *__restrict__ nodes, const int *__restrict__ work,
+                           const int *__restrict__ kout, T *__restrict__ ws, const int *__restrict__ iws) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int node = work[blockIdx.x] >> 1, side = work[blockIdx.x] & 1;
+    const NodeDev N = nodes[node];
+    const NodeSide me = N.s[side];
+    const int k = kout[2 * node + side];
+    const int R = N.hi - N.lo;
+    const bool leaf = N.a < 0;
+    int ka = 0, m = R;
+    if (!leaf) {
+        ka = kout[2 * N.a + side];
+        m = ka + kout[2 * N.b + side];
+    }
+    int *inv = reinterpret_cast<int *>(smraw);                          // m
+    T *Ul = reinterpret_cast<T *>(smraw + sizeof(int) * ((m + 1) & ~1)); // m x k (ld m)
+    const int *ord = iws + me.ordoff;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) inv[ord[c]] = c;
+    __syncthreads();
+    const T *Tm = ws + me.toff;
+    for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) {
+        int q = idx % m, i = idx / m;
+        int p = inv[q];
+        Ul[q + (long)m * i] = p < k ? T(p == i ? 1 : 0) : Tm[i + (long)me.kcap * (p - k)];
+    }
+    __syncthreads();
+    T *out = ws + me.talloff;
+    if (leaf) {
+        for (int idx = threadIdx.x; idx < R * k; idx += blockDim.x) out[idx] = Ul[idx];
+        return;
+    }
+    const NodeSide sa = nodes[N.a].s[side], sb = nodes[N.b].s[side];
+    const int Ra = nodes[N.a].hi - nodes[N.a].lo, Rb = nodes[N.b].hi - nodes[N.b].lo;
+    const int kb_ = m - ka;
+    const T *Ua = ws + sa.talloff, *Ub = ws + sb.talloff;
+    for (int idx = threadIdx.x; idx < R * k; idx += blockDim.x) {
+        int rho = idx % R, i = idx / R;
+        T acc = 0;
+        if (rho < Ra) {
+            for (int q = 0; q < ka; ++q) acc += Ua[rho + (long)Ra * q] * Ul[q + (long)m * i];
+        } else {
+            int rr = rho - Ra;
+            for (int q = 0; q < kb_; ++q) acc += Ub[rr + (long)Rb * q] * Ul[ka + q + (long)m * i];
+        }
+        out[idx] = acc;
+    }
+}
+
+// One 32 x 32 tile of H per CTA, written into the parent front through fmap.
+template <class T>
+__global__ void k_hss_expand(const ExpandItem *__restrict__ items, const NodeDev *__restrict__ nodes,
+                             const int *__restrict__ kout, const ExpandFront *__restrict__ efs,
+                             const T *__restrict__ ws, const int *__restrict__ iws, T *__restrict__ arena,
+                             T *__restrict__ keep) {
+    __shared__ T Pm[128 * EXP_TILE];
+    const ExpandItem it = items[blockIdx.x];
+    const ExpandFront E = efs[it.cf];
+    const T *S = reinterpret_cast<const T *>(E.S);
+    T *Mp = arena + E.poff;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+    if (it.type == 0) {
+        for (int yy = ty; yy < EXP_TILE; yy += 8) {
+            int i = it.r0 + tx, j = it.c0 + yy;
+            if (i >= it.rhi || j >= it.chi) continue;
+            T val = S[i + E.lds * j];
+            Mp[E.fmap[i] + (long)E.pn * E.fmap[j]] = val;
+            if (E.keep_h >= 0) keep[E.keep_h + i + (long)E.nb * j] = val;
+        }
+        return;
+    }
+    const NodeDev Na = nodes[it.na], Nb = nodes[it.nb];
+    const NodeSide ua = Na.s[0], vb = Nb.s[1];
+    const int ka = kout[2 * it.na + 0], kb_ = kout[2 * it.nb + 1];
+    const int Ra = Na.hi - Na.lo, Rb = Nb.hi - Nb.lo;
+    const T *Ua = ws + ua.talloff, *Vb = ws + vb.talloff;
+    const int *Ja = iws + ua.skioff, *Kb = iws + vb.skioff;
+    // Pm = S(J_a, K_b) V^tall_b(cols of this tile)^t   (ka x 32)
+    for (int idx = threadIdx.x; idx < ka * EXP_TILE; idx += blockDim.x) {
+        int q = idx % ka, jj = idx / ka;
+        int col = it.c0 + jj;
+        T acc = 0;
+        if (col < it.chi) {
+            int gq = Ja[q];
+            for (int q2 = 0; q2 < kb_; ++q2) acc += S[gq + E.lds * Kb[q2]] * Vb[(col - Nb.lo) + (long)Rb * q2];
+        }
+        Pm[q + ka * jj] = acc;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < EXP_TILE; yy += 8) {
+        int i = it.r0 + tx, j = it.c0 + yy;
+        if (i >= it.rhi || j >= it.chi) continue;
+        T acc = 0;
+        for (int q = 0; q < ka; ++q) acc += Ua[(i - Na.lo) + (long)Ra * q] * Pm[q + ka * yy];
+        Mp[E.fmap[i] + (long)E.pn * E.fmap[j]] = acc;
+        if (E.keep_h >= 0) keep[E.keep_h + i + (long)E.nb * j] = acc;
+    }
+}
+
+template <class T>
+int launch_hss_id(const NodeDev *nodes, const int *work, int nwork, const CompFront<T> *cf, T *ws, int *iws,
+                  int *kout, int *front_kmax, T tol, uint64_t seed, size_t smem, cudaStream_t s) {
+    if (nwork == 0) return HSS_OK;
+    static bool configured[2] = {false, false};
+    int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!configured[ti]) {
+        cudaFuncSetAttribute(k_hss_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        configured[ti] = true;
+    }
+    k_hss_id<T><<<nwork, ID_NT, smem, s>>>(nodes, work, cf, ws, iws, kout, front_kmax, tol, seed);
+    HSS_CHECK_LAUNCH("k_hss_id");
+    return HSS_OK;
+}
+
+template <class T>
+int launch_hss_tall(const NodeDev *nodes, const int *work, int nwork, const int *kout, T *ws, int *iws, size_t smem,
+                    cudaStream_t s) {
+    if (nwork == 0) return HSS_OK;
+    static bool configured[2] = {false, false};
+    int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!configured[ti]) {
+        cudaFuncSetAttribute(k_hss_tall<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        configured[ti] = true;
+    }
+    k_hss_tall<T><<<nwork, 256, smem, s>>>(nodes, work, kout, ws, iws);
+    HSS_CHECK_LAUNCH("k_hss_tall");
+    return HSS_OK;
+}
+
+template <class T>
+int launch_hss_expand(const ExpandItem *items, int nitems, const NodeDev *nodes, const int *kout,
+                      const ExpandFront *ef, const T *ws, const int *iws, T *arena, T *keep, cudaStream_t s) {
+    if (nitems == 0) return HSS_OK;
+    k_hss_expand<T><<<nitems, 256, 0, s>>>(items, nodes, kout, ef, ws, iws, arena, keep);
+    HSS_CHECK_LAUNCH("k_hss_expand");
+    return HSS_OK;
+}
+
+#define INST(T)                                                                                                \
+    template int launch_hss_id<T>(const NodeDev *, const int *, int, const CompFront<T> *, T *, int *, int *,  \
+                                  int *, T, uint64_t, size_t, cudaStream_t);                                  \
+    template int launch_hss_tall<T>(const NodeDev *, const int *, int, const int *, T *, int *, size_t,        \
+                                    cudaStream_t);                                                             \
+    template int launch_hss_expand<T>(const ExpandItem *, int, const NodeDev *, const int *, const ExpandFront *, \
+                                      const T *, const int *, T *, T *, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace hssnd

@@ -1,0 +1,140 @@
+// Internal declarations shared by the libhssnd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hssnd.h"
+
+namespace hssnd {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define HSS_CUDA(call)                                     \
+    do {                                                   \
+        cudaError_t _e = (call);                           \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);\
+    } while (0)
+
+#define HSS_CHECK_LAUNCH(what)                                  \
+    do {                                                        \
+        cudaError_t _e = cudaGetLastError();                    \
+        if (_e != cudaSuccess) return cuda_fail(_e, what);      \
+    } while (0)
+
+// Device allocation owned by a handle.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            o.p = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t nbytes);  // returns HSS_OK / HSS_ENOMEM
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+template <class T> int upload(DevBuf &b, const std::vector<T> &v, cudaStream_t s) {
+    int rc = b.alloc(sizeof(T) * (v.size() ? v.size() : 1));
+    if (rc) return rc;
+    if (!v.empty()) HSS_CUDA(cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+    return HSS_OK;
+}
+
+// ---------------------------------------------------------------- tree
+struct HssNode {          // one node of the HSS tree of a front's S (host view)
+    int lo, hi;           // index range inside B^box
+    int a, b;             // children (node ids inside the same front) or -1
+    int depth;            // 0 = root
+};
+
+}  // namespace hssnd
+
+struct hss_tree {
+    int dim = 2, n[3] = {1, 1, 1}, p = 1, bs = 1, ndof = 0, nelem = 0, nbox = 0, maxlev = 0;
+    hss_nd_opts opts{};
+    std::vector<int> level, parent, child0, child1, lohi, pos0, pos1, ni, nb, ioff, boff;
+    std::vector<int> iset, bset, fmap, perm, dfs_elem;
+    std::vector<std::vector<int>> stages;  // stages[s]: boxes of level maxlev - s (deepest first)
+    hssnd::DevBuf d_iset, d_bset, d_fmap;
+    // HSS tree of each box's S over B^box (nodes in post-order, root last)
+    std::vector<std::vector<hssnd::HssNode>> hss;
+};
+
+namespace hssnd {
+
+// ---------------------------------------------------------------- gemm
+// C = alpha * op(A) * op(B) + beta * C on a list of column-major problems.
+// B == nullptr: op(B)(kk, j) is the +-1 test matrix entry of (seed, stream,
+// front, row brow0 + kk, column j) (counter-based SplitMix64 sign).
+// Rows [zr_lo, zr_hi) use beta = 0; columns [skip_lo, skip_hi) are not written.
+template <class T> struct GemmDesc {
+    const T *A;
+    const T *B;
+    T *C;
+    int lda, ldb, ldc;
+    int m, n, k;
+    int transA, transB;
+    T alpha, beta;
+    int zr_lo, zr_hi;
+    int skip_lo, skip_hi;
+    uint64_t seed;
+    int stream, front, brow0;
+};
+
+struct GemmTile {
+    int desc;
+    int tm, tn;   // tile coordinates (units of the tile size)
+};
+
+constexpr int GEMM_TM = 64;
+constexpr int GEMM_TN = 64;
+
+template <class T>
+int gemm_batched(const GemmDesc<T> *d_desc, const GemmTile *d_tiles, int ntiles, cudaStream_t s);
+
+template <class T>
+void gemm_tiles_for(const GemmDesc<T> &d, int desc_index, std::vector<GemmTile> &tiles);
+
+// ---------------------------------------------------------------- device helpers
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// +-1 entry (row, col) of test-matrix stream `stream` of front `front` under `seed`.
+__host__ __device__ inline double rademacher(uint64_t seed, int stream, int front, int row, int col) {
+    uint64_t key = seed ^ ((uint64_t)stream << 62) ^ ((uint64_t)front << 40) ^ ((uint64_t)row << 20) ^
+                   (uint64_t)col;
+    return (splitmix64(key) >> 63) ? -1.0 : 1.0;
+}
+
+inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace hssnd

@@ -1,0 +1,287 @@
+"""ctypes binding of libhssnd.so (the C ABI in include/hssnd.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current stream.  There
+is no CPU fallback: importing this module fails loudly when the library is
+missing, and every call raises HssError on a non-zero return code.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libhssnd.so")
+
+HSS_OK, HSS_EINVAL, HSS_ENOMEM, HSS_ESINGULAR, HSS_ENOCONV, HSS_ETIMEOUT, HSS_ECUDA = range(7)
+SCHEMES = {"box": 0, "hslab": 1, "vslab": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+
+EXPORTED = [
+    "hss_nd_opts_default", "hss_factor_opts_default", "fgmres_opts_default",
+    "nd_order", "hss_tree_info", "hss_tree_export", "hss_factor", "hss_factor_get_info",
+    "hss_factor_export_front", "hss_apply", "hss_spmv", "fgmres_solve", "fgmres_history",
+    "hss_tree_destroy", "hss_factor_destroy", "hss_last_error",
+]
+
+
+class HssError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libhssnd error {code}: {msg}")
+        self.code = code
+
+
+class hss_bsr(C.Structure):
+    _fields_ = [("nb", C.c_int), ("bs", C.c_int), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+class hss_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("p", C.c_int)]
+
+
+class hss_nd_opts(C.Structure):
+    _fields_ = [("leaf_max", C.c_int), ("scheme", C.c_int)]
+
+
+class hss_factor_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("compress", C.c_int), ("r0", C.c_int), ("dr", C.c_int),
+                ("rmax", C.c_int), ("oversample", C.c_int), ("precision", C.c_int),
+                ("seed", C.c_uint64), ("keep_schur", C.c_int)]
+
+
+class fgmres_opts(C.Structure):
+    _fields_ = [("restart", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int)]
+
+
+class fgmres_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("max_iters", C.c_int), ("relres", C.c_double), ("converged", C.c_int)]
+
+
+class hss_tree_desc(C.Structure):
+    _fields_ = [("ndof", C.c_int), ("nbox", C.c_int), ("maxlev", C.c_int), ("iset_len", C.c_int),
+                ("bset_len", C.c_int), ("bs", C.c_int)]
+
+
+class hss_factor_info(C.Structure):
+    _fields_ = [("factor_bytes", C.c_double), ("front_flops", C.c_double), ("executed_flops", C.c_double),
+                ("max_rank", C.c_int), ("max_r", C.c_int), ("rounds", C.c_int), ("nfronts", C.c_int)]
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    ip = C.POINTER(C.c_int)
+    dp = C.POINTER(C.c_double)
+    sig = {
+        "nd_order": (C.c_int, [C.POINTER(hss_mesh), C.POINTER(hss_bsr), C.POINTER(hss_nd_opts), P, C.POINTER(P)]),
+        "hss_tree_info": (C.c_int, [P, C.POINTER(hss_tree_desc)]),
+        "hss_tree_export": (C.c_int, [P] + [ip] * 13),
+        "hss_factor": (C.c_int, [C.POINTER(hss_bsr), P, C.POINTER(hss_factor_opts), P, C.POINTER(P)]),
+        "hss_factor_get_info": (C.c_int, [P, C.POINTER(hss_factor_info)]),
+        "hss_factor_export_front": (C.c_int, [P, C.c_int, dp, dp, ip, ip]),
+        "hss_apply": (C.c_int, [P, C.c_int, P, C.c_int, P, C.c_int, P]),
+        "hss_spmv": (C.c_int, [C.POINTER(hss_bsr), C.c_int, P, C.c_int, P, C.c_int, P]),
+        "fgmres_solve": (C.c_int, [C.POINTER(hss_bsr), P, C.c_int, P, C.c_int, P, C.c_int,
+                                   C.POINTER(fgmres_opts), C.POINTER(fgmres_stats), P]),
+        "fgmres_history": (C.c_int, [C.c_int, dp, C.c_int]),
+        "hss_tree_destroy": (None, [P]),
+        "hss_factor_destroy": (None, [P]),
+        "hss_last_error": (C.c_char_p, []),
+        "hss_nd_opts_default": (None, [C.POINTER(hss_nd_opts)]),
+        "hss_factor_opts_default": (None, [C.POINTER(hss_factor_opts)]),
+        "fgmres_opts_default": (None, [C.POINTER(fgmres_opts)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def _check(rc, allow=()):
+    if rc != HSS_OK and rc not in allow:
+        raise HssError(rc, _lib.hss_last_error().decode())
+    return rc
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+class DeviceBSR:
+    """Block-sparse matrix resident on the GPU (int32 structure, fp64 values)."""
+
+    def __init__(self, nb, bs, row_ptr, col_idx, val, device="cuda"):
+        self.nb, self.bs = int(nb), int(bs)
+        self.row_ptr = torch.as_tensor(np.asarray(row_ptr, dtype=np.int32), device=device)
+        self.col_idx = torch.as_tensor(np.asarray(col_idx, dtype=np.int32), device=device)
+        self.val = torch.as_tensor(np.ascontiguousarray(val, dtype=np.float64).reshape(-1), device=device)
+        self.c = hss_bsr(self.nb, self.bs, self.row_ptr.data_ptr(), self.col_idx.data_ptr(), self.val.data_ptr())
+
+    @classmethod
+    def from_host(cls, A, device="cuda"):
+        return cls(A.nb, A.bs, A.row_ptr, A.col_idx, A.val, device)
+
+    @property
+    def n(self):
+        return self.nb * self.bs
+
+
+def _colmajor(x: torch.Tensor, N: int):
+    """(N,) or (N, k) fp64 CUDA tensor -> contiguous (k, N) storage (column-major N x k)."""
+    if x.dim() == 1:
+        x = x.reshape(N, 1)
+    if x.shape[0] != N:
+        raise ValueError(f"expected {N} rows, got {tuple(x.shape)}")
+    return x.t().contiguous().to(torch.float64), x.shape[1]
+
+
+class Tree:
+    def __init__(self, handle, mesh):
+        self.h = C.c_void_p(handle)
+        self.mesh = mesh
+        d = hss_tree_desc()
+        _check(_lib.hss_tree_info(self.h, C.byref(d)))
+        self.desc = d
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hss_tree_destroy(self.h)
+            self.h = None
+
+    def export(self) -> dict:
+        d = self.desc
+        nb_ = d.nbox
+        arrs = {k: np.zeros(nb_, dtype=np.int32) for k in
+                ("level", "parent", "child0", "child1", "ni", "nb", "ioff", "boff")}
+        arrs["lohi"] = np.zeros(6 * nb_, dtype=np.int32)
+        arrs["iset"] = np.zeros(max(d.iset_len, 1), dtype=np.int32)
+        arrs["bset"] = np.zeros(d.bset_len, dtype=np.int32)
+        arrs["fmap"] = np.zeros(d.bset_len, dtype=np.int32)
+        arrs["perm"] = np.zeros(d.ndof, dtype=np.int32)
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))  # noqa: E731
+        _check(_lib.hss_tree_export(self.h, *[ip(arrs[k]) for k in (
+            "level", "parent", "child0", "child1", "ni", "nb", "ioff", "boff", "lohi", "iset", "bset", "fmap",
+            "perm")]))
+        arrs["iset"] = arrs["iset"][: d.iset_len]
+        arrs["lohi"] = arrs["lohi"].reshape(nb_, 6)
+        return arrs
+
+
+class Factor:
+    def __init__(self, handle, tree, precision):
+        self.h = C.c_void_p(handle)
+        self.tree = tree          # keeps the tree alive
+        self.precision = precision
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hss_factor_destroy(self.h)
+            self.h = None
+
+    def info(self) -> dict:
+        i = hss_factor_info()
+        _check(_lib.hss_factor_get_info(self.h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in hss_factor_info._fields_}
+
+    def export_front(self, box: int):
+        nb_ = int(self.tree.export()["nb"][box])
+        S = np.zeros((nb_, nb_), order="F")
+        H = np.zeros((nb_, nb_), order="F")
+        kmax, r = C.c_int(0), C.c_int(0)
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
+        _check(_lib.hss_factor_export_front(self.h, box, dp(S), dp(H), C.byref(kmax), C.byref(r)))
+        return S, H, kmax.value, r.value
+
+
+def nd_order(mesh, A: DeviceBSR, leaf_max=64, scheme="box", stream=None) -> Tree:
+    """mesh: (dim, (nx, ny[, nz]), p)."""
+    dim, n, p = mesh
+    n3 = list(n) + [1] * (3 - len(n))
+    m = hss_mesh(dim, (C.c_int * 3)(*n3), p)
+    o = hss_nd_opts(leaf_max, SCHEMES[scheme])
+    out = C.c_void_p()
+    _check(_lib.nd_order(C.byref(m), C.byref(A.c), C.byref(o), _stream(stream), C.byref(out)))
+    return Tree(out.value, mesh)
+
+
+def factor_opts(**kw) -> hss_factor_opts:
+    o = hss_factor_opts()
+    _lib.hss_factor_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(o, k, v)
+    return o
+
+
+def hss_factor(A: DeviceBSR, tree: Tree, stream=None, **kw) -> Factor:
+    o = factor_opts(**kw)
+    out = C.c_void_p()
+    _check(_lib.hss_factor(C.byref(A.c), tree.h, C.byref(o), _stream(stream), C.byref(out)))
+    return Factor(out.value, tree, o.precision)
+
+
+def hss_apply(F: Factor, x: torch.Tensor, stream=None) -> torch.Tensor:
+    N = F.tree.desc.ndof
+    xs, k = _colmajor(x, N)
+    ys = torch.empty_like(xs)
+    _check(_lib.hss_apply(F.h, k, _ptr(xs), N, _ptr(ys), N, _stream(stream)))
+    y = ys.t()
+    return y.reshape(N) if x.dim() == 1 else y
+
+
+def hss_apply_raw(F: Factor, nrhs: int, x: torch.Tensor, y: torch.Tensor, ld: int, stream=None):
+    """y = M^-1 x on column-major storage already laid out (no copies)."""
+    _check(_lib.hss_apply(F.h, nrhs, _ptr(x), ld, _ptr(y), ld, _stream(stream)))
+
+
+def hss_spmv(A: DeviceBSR, x: torch.Tensor, stream=None) -> torch.Tensor:
+    N = A.n
+    xs, k = _colmajor(x, N)
+    ys = torch.empty_like(xs)
+    _check(_lib.hss_spmv(C.byref(A.c), k, _ptr(xs), N, _ptr(ys), N, _stream(stream)))
+    y = ys.t()
+    return y.reshape(N) if x.dim() == 1 else y
+
+
+@dataclass
+class SolveStats:
+    iters: int
+    max_iters: int
+    relres: float
+    converged: bool
+
+
+def fgmres_solve(A: DeviceBSR, F: Factor | None, b: torch.Tensor, x0: torch.Tensor | None = None,
+                 restart=30, rtol=1e-8, maxit=1000, stream=None):
+    N = A.n
+    bs_, k = _colmajor(b, N)
+    xs = torch.zeros_like(bs_) if x0 is None else _colmajor(x0, N)[0]
+    o = fgmres_opts(restart, rtol, maxit)
+    st = fgmres_stats()
+    _check(_lib.fgmres_solve(C.byref(A.c), F.h if F is not None else None, k, _ptr(bs_), N, _ptr(xs), N,
+                             C.byref(o), C.byref(st), _stream(stream)), allow=(HSS_ENOCONV,))
+    x = xs.t()
+    return (x.reshape(N) if b.dim() == 1 else x), SolveStats(st.iters, st.max_iters, st.relres, bool(st.converged))
+
+
+def fgmres_history(rhs=0, cap=100000) -> np.ndarray:
+    h = np.zeros(cap)
+    n = _lib.fgmres_history(rhs, h.ctypes.data_as(C.POINTER(C.c_double)), cap)
+    return h[:n]

@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bars: nested-dissection sets, maps and permutation bit-exact; Schur
+complements, HSS approximants and the preconditioner apply within 1e-10
+relative in FP64; FGMRES reaches the same relative residual with iteration
+counts within +-10% (at least +-1).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1508_07798_gb300 import dg_inputs as dg
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def _hss():
+    from paper_1508_07798_gb300 import hssnd
+    return hssnd
+
+
+def _setup(kind, n, p, dim=2, seed=0, leaf=64):
+    if kind == "poisson":
+        mesh = dg.Mesh(dim, tuple(n) + (1,) * (3 - dim), p)
+        A = dg.assemble_sipg(mesh)
+    elif kind == "helm":
+        mesh = dg.Mesh(dim, tuple(n) + (1,) * (3 - dim), p)
+        c = dg.cosine_field(mesh, seed)
+        A = dg.assemble_sipg(mesh, c_elem=c, kappa=dg.helmholtz_kappa(n[0], p))
+    else:
+        mesh = dg.Mesh(3, tuple(n), p)
+        A = dg.assemble_sipg(mesh, a_elem=dg.gaussian_log_field(mesh, seed))
+    return mesh, A
+
+
+ND_CASES = [("poisson", (16, 16), 1, 2, 64), ("poisson", (2, 1), 1, 2, 4), ("poisson", (7, 5), 2, 2, 18),
+            ("helm", (6, 6), 3, 2, 16), ("poisson", (3, 3, 2), 1, 3, 16), ("poisson", (4, 4, 4), 1, 3, 64),
+            ("poisson", (5, 4), 1, 2, 1000), ("helm", (64, 64), 2, 2, 64)]
+
+
+@pytest.mark.parametrize("scheme", ["box", "hslab", "vslab"])
+@pytest.mark.parametrize("kind,n,p,dim,leaf", ND_CASES)
+def test_nd_bit_exact(kind, n, p, dim, leaf, scheme):
+    if scheme != "box" and n[0] > 16:
+        pytest.skip("slab schemes checked on the small meshes")
+    hs = _hss()
+    mesh, A = _setup(kind, n, p, dim)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((dim, tuple(n), p), dA, leaf_max=leaf, scheme=scheme)
+    ex = tree.export()
+    nd = oracle.nd_order(dim, mesh.n, p, A.row_ptr, A.col_idx, leaf_max=leaf, scheme=scheme)
+    assert ex["level"].tolist() == nd["level"].tolist()
+    assert ex["parent"].tolist() == nd["parent"].tolist()
+    assert ex["child0"].tolist() == nd["child"][:, 0].tolist()
+    assert ex["child1"].tolist() == nd["child"][:, 1].tolist()
+    assert np.array_equal(ex["lohi"][:, :3], nd["lo"]) and np.array_equal(ex["lohi"][:, 3:], nd["hi"])
+    assert ex["ni"].tolist() == nd["ni"].tolist() and ex["nb"].tolist() == nd["nb"].tolist()
+    assert np.array_equal(ex["iset"], nd["iset_flat"])
+    assert np.array_equal(ex["bset"], nd["bset_flat"])
+    assert np.array_equal(ex["fmap"], nd["fmap_flat"])
+    assert np.array_equal(ex["perm"], nd["perm"])
+
+
+def test_spmv_matches_scipy():
+    import torch
+    hs = _hss()
+    mesh, A = _setup("helm", (16, 16), 2)
+    dA = hs.DeviceBSR.from_host(A)
+    X = dg.random_rhs(A.n, 3, 5)
+    Y = hs.hss_spmv(dA, torch.as_tensor(X, device="cuda")).cpu().numpy()
+    ref = dg.bsr_to_csr(A) @ X
+    assert np.linalg.norm(Y - ref) <= 1e-14 * np.linalg.norm(ref)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+EXACT = [("poisson", (16, 16), 1, 2, 64), ("helm", (12, 12), 2, 2, 36), ("poisson", (2, 1), 1, 2, 4),
+         ("poisson", (3, 3, 3), 1, 3, 16), ("helm", (9, 7), 3, 2, 32)]
+
+
+@pytest.mark.parametrize("kind,n,p,dim,leaf", EXACT)
+def test_exact_mode_apply_equals_oracle_and_dense_solve(kind, n, p, dim, leaf):
+    import torch
+    hs = _hss()
+    mesh, A = _setup(kind, n, p, dim)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((dim, tuple(n), p), dA, leaf_max=leaf)
+    F = hs.hss_factor(dA, tree, compress=0)
+    B = dg.random_rhs(A.n, 2, 1)
+    Y = hs.hss_apply(F, torch.as_tensor(B, device="cuda")).cpu().numpy()
+    nd = oracle.nd_order(dim, mesh.n, p, A.row_ptr, A.col_idx, leaf_max=leaf)
+    fac = oracle.factor(dg.bsr_to_csr(A), nd, compress=False)
+    assert _rel(Y, oracle.apply(fac, B)) <= TOL
+    Xd = np.linalg.solve(dg.bsr_to_dense(A), B)
+    assert _rel(Y, Xd) <= 1e-9
+
+
+APPROX = [("poisson", (16, 16), 1, 2, 64, 1e-6), ("helm", (16, 16), 2, 2, 64, 1e-4),
+          ("helm", (24, 24), 2, 2, 64, 1e-6), ("poisson", (6, 6, 6), 1, 3, 64, 1e-5)]
+
+
+@pytest.mark.parametrize("kind,n,p,dim,leaf,tol", APPROX)
+def test_fronts_and_apply_match_oracle(kind, n, p, dim, leaf, tol):
+    import torch
+    hs = _hss()
+    mesh, A = _setup(kind, n, p, dim)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((dim, tuple(n), p), dA, leaf_max=leaf)
+    F = hs.hss_factor(dA, tree, tol=tol, seed=3, keep_schur=1)
+    nd = oracle.nd_order(dim, mesh.n, p, A.row_ptr, A.col_idx, leaf_max=leaf)
+    fac = oracle.factor(dg.bsr_to_csr(A), nd, tol=tol, seed=3, rmax=96)
+    logs = {r["box"]: r for r in fac["log"]}
+    compressed = 0
+    for b in range(nd["nbox"]):
+        if nd["nb"][b] == 0:
+            continue
+        S, H, kmax, r = F.export_front(b)
+        assert _rel(S, fac["boxes"][b]["S"]) <= TOL, b
+        rec = logs[b]
+        if rec.get("nnodes", 1) > 1:
+            compressed += 1
+            assert kmax == rec["kmax"] and r == rec["r"], (b, kmax, rec["kmax"], r, rec["r"])
+    assert compressed > 0
+    X = dg.random_rhs(A.n, 2, 7)
+    Y = hs.hss_apply(F, torch.as_tensor(X, device="cuda")).cpu().numpy()
+    assert _rel(Y, oracle.apply(fac, X)) <= TOL
+
+
+def test_hss_approximant_matches_oracle():
+    hs = _hss()
+    mesh, A = _setup("helm", (16, 16), 2)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((2, (16, 16), 2), dA)
+    F = hs.hss_factor(dA, tree, tol=1e-4, seed=1, keep_schur=1)
+    nd = oracle.nd_order(2, mesh.n, 2, A.row_ptr, A.col_idx)
+    fac = oracle.factor(dg.bsr_to_csr(A), nd, tol=1e-4, seed=1, rmax=96, keep_h=True)
+    for b in (0, 1, 2, 3):
+        S, H, kmax, r = F.export_front(b)
+        assert _rel(H, fac["boxes"][b]["H"]) <= TOL
+        assert _rel(H, S) <= 1e-2          # the approximant is close to S
+
+
+SOLVES = [("poisson", (16, 16), 1, 1e-6, 1e-10), ("helm", (32, 32), 2, 1e-4, 1e-8),
+          ("helm", (16, 16), 3, 1e-5, 1e-8)]
+
+
+@pytest.mark.parametrize("kind,n,p,tol,rtol", SOLVES)
+def test_fgmres_matches_oracle(kind, n, p, tol, rtol):
+    import torch
+    hs = _hss()
+    mesh, A = _setup(kind, n, p)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((2, tuple(n), p), dA)
+    F = hs.hss_factor(dA, tree, tol=tol, seed=0)
+    b = dg.point_source_rhs(mesh, 0)[:, 0] if kind == "helm" else dg.random_rhs(A.n, 1, 0)[:, 0]
+    x, st = hs.fgmres_solve(dA, F, torch.as_tensor(b, device="cuda"), rtol=rtol, restart=30)
+    Acsr = dg.bsr_to_csr(A)
+    xr = x.cpu().numpy()
+    assert st.converged and np.linalg.norm(b - Acsr @ xr) <= rtol * np.linalg.norm(b) * 1.0000001
+    nd = oracle.nd_order(2, mesh.n, p, A.row_ptr, A.col_idx)
+    fac = oracle.factor(Acsr, nd, tol=tol, seed=0, rmax=96)
+    xo, info = oracle.fgmres(lambda v: Acsr @ v, lambda v: oracle.apply(fac, v), b, rtol=rtol, restart=30)
+    assert abs(st.iters - info["iters"]) <= max(1, round(0.1 * info["iters"]))
+    assert _rel(xr, xo) <= 1e3 * rtol
+
+
+def test_unpreconditioned_history_matches_oracle():
+    import torch
+    hs = _hss()
+    mesh, A = _setup("poisson", (6, 6), 1)
+    dA = hs.DeviceBSR.from_host(A)
+    b = dg.random_rhs(A.n, 1, 2)[:, 0]
+    x, st = hs.fgmres_solve(dA, None, torch.as_tensor(b, device="cuda"), restart=20, rtol=1e-9, maxit=20)
+    h = hs.fgmres_history(0)
+    Acsr = dg.bsr_to_csr(A)
+    xo, info = oracle.fgmres(lambda v: Acsr @ v, None, b, restart=20, rtol=1e-9, maxit=20)
+    assert len(h) == len(info["hist"]) == 20
+    assert np.allclose(h, info["hist"], rtol=1e-8, atol=1e-15)
+    assert not st.converged
+
+
+def test_multiple_rhs_apply_and_solve():
+    import torch
+    hs = _hss()
+    mesh, A = _setup("helm", (16, 16), 2)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((2, (16, 16), 2), dA)
+    F = hs.hss_factor(dA, tree, tol=1e-4)
+    B = torch.as_tensor(dg.random_rhs(A.n, 5, 3, kind="normal"), device="cuda")
+    Y = hs.hss_apply(F, B)
+    for k in range(5):
+        yk = hs.hss_apply(F, B[:, k].contiguous())
+        assert torch.allclose(Y[:, k], yk, rtol=1e-13, atol=1e-13)
+    X, st = hs.fgmres_solve(dA, F, B, rtol=1e-8)
+    assert st.converged
+    R = B.cpu().numpy() - dg.bsr_to_csr(A) @ X.cpu().numpy()
+    assert np.linalg.norm(R, axis=0).max() <= 1e-8 * np.linalg.norm(B.cpu().numpy(), axis=0).min() * 1.01
+
+
+def test_errors_are_reported():
+    import torch
+    hs = _hss()
+    mesh, A = _setup("poisson", (4, 4), 1)
+    dA = hs.DeviceBSR.from_host(A)
+    with pytest.raises(hs.HssError) as e:
+        hs.nd_order((2, (5, 4), 1), dA)       # mesh and matrix disagree
+    assert e.value.code == hs.HSS_EINVAL
+    tree = hs.nd_order((2, (4, 4), 1), dA, leaf_max=8)
+    with pytest.raises(hs.HssError) as e:
+        hs.hss_factor(dA, tree, rmax=4096)
+    assert e.value.code == hs.HSS_EINVAL
+    # a zero block row makes a front singular
+    A2 = dg.assemble_sipg(mesh)
+    e0 = 5
+    for t in range(A2.row_ptr[e0], A2.row_ptr[e0 + 1]):
+        A2.val[t] = 0.0
+    for e in range(A2.nb):
+        for t in range(A2.row_ptr[e], A2.row_ptr[e + 1]):
+            if A2.col_idx[t] == e0:
+                A2.val[t] = 0.0
+    dA2 = hs.DeviceBSR.from_host(A2)
+    tree2 = hs.nd_order((2, (4, 4), 1), dA2, leaf_max=8)
+    with pytest.raises(hs.HssError) as e:
+        hs.hss_factor(dA2, tree2, compress=0)
+    assert e.value.code == hs.HSS_ESINGULAR
+    # non-convergence returns the iterate and the flag
+    F = hs.hss_factor(dA, tree, compress=1, tol=1e-1)
+    b = torch.as_tensor(dg.random_rhs(A.n, 1, 0)[:, 0], device="cuda")
+    x, st = hs.fgmres_solve(dA, None, b, rtol=1e-14, maxit=2)
+    assert not st.converged and st.iters == 2
