@@ -1,0 +1,375 @@
+"""Benchmark: nested dissection + approximate LDM^t factorization + FGMRES
+solve to 1e-8 relative residual on one GPU per rank.
+
+Workload (one "step" = the whole hot path on one synthetic problem):
+indefinite Helmholtz -Lap u - k^2 c(x) u = f, SIPG DG p=2 on 64x64 quads
+(36,864 dofs, 9x9 blocks), k for 10 dofs per wavelength, c(x) = 1 + 0.3 x
+(mean of 8 random-phase cosines), Gaussian point source, ID tolerance 1e-4,
+FGMRES(30) in FP64 to 1e-8.  Forms: FP64 plain (factor in FP64) and mixed
+(factor in FP32, FP64 Krylov); `value` is the mixed form's time to solution.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: CUDA events on the launching stream, a 256 MB write between timed
+steps flushes L2 (129 MB), max over ranks.  Under torchrun every rank solves
+its own instance (seed = rank): weak scaling, no collective in the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "factor+FGMRES time to 1e-8 rel. residual (mixed vs FP64 plain, 1 GB300); apply GB/s"
+WORKLOAD = "helmholtz_sipg_p2_64x64"
+N_ELEM, P_DEG, TOL, RTOL, RESTART = 64, 2, 1e-4, 1e-8, 30
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", default="fp32,fp64")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_s=d["bf16_tflops_sustained"], src="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_s=1700.0, src="fallback")
+
+
+# FP64 and FP32 SIMT peaks from unit counts and clock: 152 SMs x FMA/clk/SM x 2 x 2.07 GHz.
+# FP32: 128 FMA/clk/SM -> 80.5 TFLOP/s.  FP64: the nominal 1.25 TFLOP/s of GB300.
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_TFLOPS = 1.25
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                smax = float(f[2].split()[0])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problem(seed):
+    from paper_1508_07798_gb300 import dg_inputs as dg
+    mesh, A = dg.helmholtz_2d(N_ELEM, P_DEG, seed)
+    b = dg.point_source_rhs(mesh, seed)[:, 0]
+    return mesh, A, b
+
+
+def bench_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_1508_07798_gb300 import hssnd
+    from paper_1508_07798_gb300 import dg_inputs as dg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    mesh, A, b_host = make_problem(rank)
+    meshdesc = (2, (N_ELEM, N_ELEM), P_DEG)
+    dA = hssnd.DeviceBSR.from_host(A)
+    b = torch.as_tensor(b_host, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    Acsr = dg.bsr_to_csr(A)
+
+    def step(prec):
+        tree = hssnd.nd_order(meshdesc, dA, leaf_max=64)
+        F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec)
+        x, st = hssnd.fgmres_solve(dA, F, b, rtol=RTOL, restart=RESTART)
+        return tree, F, x, st
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    forms = {}
+    launches_total = 0
+    clk = Clocks(dev.index)
+    prof_all = {}
+    for prec in args.forms.split(","):
+        for _ in range(args.warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        barrier()
+        hssnd.profile_reset()
+        hssnd.profile_enable(True)
+        if prec == args.forms.split(",")[0]:
+            clk.start()
+        times = []
+        l0 = hssnd.launch_count()
+        last = None
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            last = step(prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        launches_total += hssnd.launch_count() - l0
+        hssnd.profile_enable(False)
+        prof = hssnd.profile_read()
+        prof_all[prec] = prof
+        tree, F, x, st = last
+        xr = x.cpu().numpy()
+        relres = float(np.linalg.norm(b_host - Acsr @ xr) / np.linalg.norm(b_host))
+        info = F.info()
+        forms[prec] = dict(ms=statistics.mean(times), ms_min=min(times), ms_all=times, iters=st.iters,
+                           relres=relres, converged=bool(st.converged and relres <= RTOL * 1.0001),
+                           factor_bytes=info["factor_bytes"], front_flops=info["front_flops"],
+                           executed_flops=info["executed_flops"], max_rank=info["max_rank"], max_r=info["max_r"])
+    clocks = clk.stop()
+    barrier()
+
+    # ---- apply GB/s: 20 applies of the last factor of each form, L2 flushed between
+    apply = {}
+    pk = peaks()
+    for prec in args.forms.split(","):
+        tree = hssnd.nd_order(meshdesc, dA, leaf_max=64)
+        F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec)
+        N = A.n
+        xv = torch.randn(N, dtype=torch.float64, device=dev)
+        yv = torch.empty_like(xv)
+        for _ in range(3):
+            hssnd.hss_apply_raw(F, 1, xv, yv, N)
+        hssnd.profile_reset()
+        hssnd.profile_enable(True)
+        ts = []
+        for _ in range(20):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hssnd.hss_apply_raw(F, 1, xv, yv, N)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        hssnd.profile_enable(False)
+        pr = hssnd.profile_read()
+        byt = sum(v[2] for k, v in pr.items() if k.startswith("apply"))
+        kms = sum(v[0] for k, v in pr.items() if k.startswith("apply"))
+        per_apply_bytes = byt / 20
+        apply[prec] = dict(ms=statistics.median(ts), bytes=per_apply_bytes,
+                           gbs=per_apply_bytes / (statistics.median(ts) * 1e-3) / 1e9,
+                           kernel_gbs=byt / (kms * 1e-3) / 1e9 if kms > 0 else None)
+        apply[prec]["frac"] = apply[prec]["gbs"] / pk["hbm"]
+
+    # ---- e2e through the C ABI with host buffers: H2D of A and b, solve, D2H of x
+    e2e = None
+    head = args.forms.split(",")[0]
+    rp = torch.as_tensor(A.row_ptr).pin_memory()
+    ci = torch.as_tensor(A.col_idx).pin_memory()
+    va = torch.as_tensor(A.val.reshape(-1)).pin_memory()
+    bh = torch.as_tensor(b_host).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    d_rp = torch.empty_like(rp, device=dev)
+    d_ci = torch.empty_like(ci, device=dev)
+    d_va = torch.empty_like(va, device=dev)
+    d_b = torch.empty_like(bh, device=dev)
+    h2d = rp.numel() * 4 + ci.numel() * 4 + va.numel() * 8 + bh.numel() * 8
+    d2h = xh.numel() * 8
+    ets = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_rp.copy_(rp, non_blocking=True)
+        d_ci.copy_(ci, non_blocking=True)
+        d_va.copy_(va, non_blocking=True)
+        d_b.copy_(bh, non_blocking=True)
+        dA2 = hssnd.DeviceBSR.__new__(hssnd.DeviceBSR)
+        dA2.nb, dA2.bs, dA2.row_ptr, dA2.col_idx, dA2.val = A.nb, A.bs, d_rp, d_ci, d_va
+        dA2.c = hssnd.hss_bsr(A.nb, A.bs, d_rp.data_ptr(), d_ci.data_ptr(), d_va.data_ptr())
+        tree = hssnd.nd_order(meshdesc, dA2, leaf_max=64)
+        F = hssnd.hss_factor(dA2, tree, tol=TOL, precision=head)
+        x, st = hssnd.fgmres_solve(dA2, F, d_b, rtol=RTOL, restart=RESTART)
+        xh.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            ets.append(e0.elapsed_time(e1))
+    e2e = dict(value=statistics.mean(ets), unit="ms", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+
+    # ---- max over ranks
+    value = forms[head]["ms"]
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([value, e2e["value"]], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        value, e2e["value"] = float(tt[0]), float(tt[1])
+
+    # ---- roofline of the dominant kernel of the headline form
+    prof = prof_all[head]
+    tracked = {k: v for k, v in prof.items() if v[2] > 0}
+    dom = max(tracked, key=lambda k: tracked[k][0]) if tracked else max(prof, key=lambda k: prof[k][0])
+    ms, cnt, work = prof[dom]
+    total_ms = sum(v[0] for v in prof.values())
+    if dom.startswith("gemm"):
+        peak = FP32_SIMT_TFLOPS if dom.endswith("f32") else FP64_TFLOPS
+        ach = work / cnt / (ms / cnt * 1e-3) / 1e12
+        roof = dict(kernel=dom, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
+                    peak_source="derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz" if dom.endswith("f32")
+                    else "nominal GB300 FP64 1.25 TFLOP/s")
+    else:
+        ach = work / cnt / (ms / cnt * 1e-3) / 1e9
+        roof = dict(kernel=dom, bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
+                    traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
+                    peak_source=pk["src"])
+    kernels = {k: dict(ms=round(v[0] / args.steps, 4), launches=v[1] // args.steps) for k, v in
+               sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    res = dict(metric=METRIC, value=value, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup,
+               ms_per_step=value, higher_is_better=False, scaling="weak", vs_baseline=None,
+               dtype="f32 factor / f64 Krylov" if head == "fp32" else "f64", data="synthetic",
+               config=dict(workload=WORKLOAD, dofs=A.n, p=P_DEG, mesh=f"{N_ELEM}x{N_ELEM}", id_tol=TOL,
+                           rtol=RTOL, restart=RESTART, leaf_max=64, headline_form=head,
+                           l2="flushed by a 256 MB write before every timed step",
+                           parallelism=f"replicas x{world} (independent instances)"),
+               forms={k: {kk: vv for kk, vv in v.items() if kk != "ms_all"} for k, v in forms.items()},
+               apply=apply, roofline=roof, e2e=e2e, clocks=clocks, gpu_launches=int(launches_total // max(1, len(forms))),
+               kernels_per_step=kernels)
+    return res
+
+
+def cpu_baseline_run(seed=0):
+    """The oracle, as it stands, on one full problem of the workload."""
+    import numpy as np
+    import oracle
+    from paper_1508_07798_gb300 import dg_inputs as dg
+    mesh, A, b = make_problem(seed)
+    Acsr = dg.bsr_to_csr(A)
+    t0 = time.perf_counter()
+    nd = oracle.nd_order(2, mesh.n, P_DEG, A.row_ptr, A.col_idx, leaf_max=64)
+    fac = oracle.factor(Acsr, nd, tol=TOL, seed=0, rmax=96)
+    x, info = oracle.fgmres(lambda v: Acsr @ v, lambda v: oracle.apply(fac, v), b, rtol=RTOL, restart=RESTART)
+    dt = time.perf_counter() - t0
+    return dt * 1e3, info
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((d.get("num_threads", 1) for d in threadpool_info()), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # the reference arm is the CPU oracle (no reference implementation exists)
+        for _ in range(min(args.warmup, 1)):
+            pass
+        ts, its = [], None
+        for _ in range(args.steps):
+            ms, info = cpu_baseline_run(0)
+            ts.append(ms)
+            its = info["iters"]
+        v = statistics.mean(ts)
+        line = dict(metric=METRIC, value=v, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=v, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
+                    data="synthetic", impl="reference",
+                    config=dict(workload=WORKLOAD, dofs=N_ELEM * N_ELEM * (P_DEG + 1) ** 2, id_tol=TOL, rtol=RTOL),
+                    cpu_baseline=dict(kind="oracle", cores=cpu_cores(), value=v, unit="ms",
+                                      sample="one full 36,864-dof solve per step (nd + factor + FGMRES), "
+                                             "warm-up skipped (no state to warm)", iters=its),
+                    e2e=dict(value=v, unit="ms", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    res = bench_ours(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ms, info = cpu_baseline_run(0)
+        res["cpu_baseline"] = dict(value=ms, unit="ms", cores=cpu_cores(), kind="oracle",
+                                   sample="one full 36,864-dof solve (nd + factor + FGMRES), seed 0",
+                                   iters=info["iters"])
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -201,6 +201,22 @@ int fgmres_solve(const hss_bsr *A, const hss_factor_t *f, int nrhs, const double
  * returns the count. */
 int fgmres_history(int rhs, double *hist, int cap);
 
+/* Diagnostics (no counterpart in the paper).
+ * hss_launch_count: number of CUDA kernels the library has launched since it
+ * was loaded (all threads).
+ * hss_profile_enable(1) brackets every subsequent launch with two CUDA events
+ * on its stream, grouped by kernel class; hss_profile_enable(0) stops.
+ * hss_profile_read(-1, ...) returns the number of classes; for idx >= 0 it
+ * fills the class name (HOST buffer of cap bytes), the summed event time in
+ * ms, the launch count and the algorithmic work the library attributes to
+ * those launches (flops for GEMM classes, bytes for apply/SpMV classes, 0 when
+ * not tracked).  Reading synchronizes the pending events.
+ * hss_profile_reset clears the classes. */
+long hss_launch_count(void);
+int hss_profile_enable(int on);
+int hss_profile_reset(void);
+int hss_profile_read(int idx, char *name, int cap, double *total_ms, long *launches, double *work);
+
 void hss_tree_destroy(hss_tree *t);
 void hss_factor_destroy(hss_factor_t *f);
 const char *hss_last_error(void);

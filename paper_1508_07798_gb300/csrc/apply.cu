@@ -12,6 +12,7 @@
 #include "internal.h"
 #include "front.h"
 #include "factor.h"
+#include "prof.h"
 
 namespace hssnd {
 
@@ -133,6 +134,9 @@ int apply_stage(const ApplyStage &st, bool forward, const FrontDev *fr, const T 
     const ApplyTile *tiles = forward ? st.d_fwd : st.d_bwd;
     int nt = forward ? st.nfwd : st.nbwd;
     if (nt == 0) return HSS_OK;
+    double bytes = (forward ? st.fwd_bytes : st.bwd_bytes) * (sizeof(T) / 8.0) +
+                   (forward ? st.fwd_vec : st.bwd_vec) * 8.0 * nrhs;
+    HSS_PROF(forward ? "apply_fwd" : "apply_bwd", s, bytes);
     if (forward) {
         if (nrhs == 1)
             k_apply_fwd<T, 1><<<nt, AP_NT, 0, s>>>(tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs);

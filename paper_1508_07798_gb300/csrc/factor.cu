@@ -79,6 +79,7 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
     std::vector<GemmTile> tiles;
     std::vector<int> job_off(maxsteps + 1), tile_off(maxsteps + 1);
     std::vector<size_t> smem(maxsteps, 0);
+    std::vector<double> step_flops(maxsteps, 0.0);
     for (int st = 0; st < maxsteps; ++st) {
         job_off[st] = (int)jobs.size();
         tile_off[st] = (int)tiles.size();
@@ -91,10 +92,9 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             if (use_smem) smem[st] = std::max(smem[st], need);
             jobs.push_back({f, k0, kbs, use_smem, aoff[f]});
             GemmDesc<T> d{};
-            d.A = nullptr;  // patched on the device side below (pointer arithmetic on arena)
             d.A = arena + fr[f].foff + (long)fr[f].n * k0;
             d.lda = fr[f].n;
-            d.B = nullptr;  // set after the workspace exists
+            d.B = nullptr;  // Aold of this job, set once the workspace exists
             d.C = arena + fr[f].foff;
             d.ldc = fr[f].n;
             d.ldb = kbs;
@@ -109,9 +109,9 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             d.zr_hi = k0 + kbs;
             d.skip_lo = k0;
             d.skip_hi = k0 + kbs;
-            d.front = (int)(aoff[f] & 0x7fffffff);  // temporary: holds the Aold offset
             descs.push_back(d);
             gemm_tiles_for(descs.back(), (int)descs.size() - 1, tiles);
+            step_flops[st] += gemm_flops(d);
         }
     }
     job_off[maxsteps] = (int)jobs.size();
@@ -121,7 +121,6 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
     if ((rc = d_aold.alloc(sizeof(T) * std::max(aold_total, 1L)))) return rc;
     for (size_t i = 0; i < descs.size(); ++i) {
         descs[i].B = d_aold.as<T>() + jobs[i].aoff;
-        descs[i].front = 0;
     }
     if ((rc = upload(d_jobs, jobs, s)) || (rc = upload(d_descs, descs, s)) || (rc = upload(d_tiles, tiles, s)))
         return rc;
@@ -131,7 +130,7 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
                                      piv, status, s)))
             return rc;
         if ((rc = gemm_batched<T>(d_descs.as<GemmDesc<T>>(), d_tiles.as<GemmTile>() + tile_off[st],
-                                  tile_off[st + 1] - tile_off[st], s)))
+                                  tile_off[st + 1] - tile_off[st], s, step_flops[st])))
             return rc;
     }
     HSS_CUDA(cudaStreamSynchronize(s));
@@ -304,8 +303,11 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             DevBuf a, b, c2, d2;
             if ((rc = upload(a, g1, s)) || (rc = upload(b, t1, s)) || (rc = upload(c2, g2, s)) || (rc = upload(d2, t2, s)))
                 return rc;
-            if ((rc = gemm_batched<T>(a.as<GemmDesc<T>>(), b.as<GemmTile>(), (int)t1.size(), s))) return rc;
-            if ((rc = gemm_batched<T>(c2.as<GemmDesc<T>>(), d2.as<GemmTile>(), (int)t2.size(), s))) return rc;
+            double f1 = 0, f2 = 0;
+            for (auto &d : g1) f1 += gemm_flops(d);
+            for (auto &d : g2) f2 += gemm_flops(d);
+            if ((rc = gemm_batched<T>(a.as<GemmDesc<T>>(), b.as<GemmTile>(), (int)t1.size(), s, f1))) return rc;
+            if ((rc = gemm_batched<T>(c2.as<GemmDesc<T>>(), d2.as<GemmTile>(), (int)t2.size(), s, f2))) return rc;
             HSS_CUDA(cudaStreamSynchronize(s));
         }
         // ---- interpolative decompositions, deepest HSS level first
@@ -422,10 +424,15 @@ int build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, DevBuf &&
     as.fronts_buf = std::move(d_fronts);
     as.d_fronts = as.fronts_buf.as<FrontDev>();
     std::vector<ApplyTile> fw, bw;
+    as.fwd_bytes = as.bwd_bytes = as.fwd_vec = as.bwd_vec = 0;
     for (int f = 0; f < (int)fr.size(); ++f) {
         if (fr[f].ni == 0) continue;
         for (int r0 = 0; r0 < fr[f].n; r0 += APPLY_ROWS) fw.push_back({f, r0});
         for (int r0 = 0; r0 < fr[f].ni; r0 += APPLY_ROWS) bw.push_back({f, r0});
+        as.fwd_bytes += 8.0 * fr[f].n * (double)fr[f].ni;
+        as.bwd_bytes += 8.0 * fr[f].ni * (double)fr[f].nb;
+        as.fwd_vec += fr[f].ni + fr[f].ni + 2.0 * fr[f].nb;      // x_I read, t written, x_B read+written
+        as.bwd_vec += fr[f].nb + fr[f].ni + fr[f].ni;           // x_B read, t read, x_I written
     }
     int rc;
     if ((rc = upload(as.fwd_buf, fw, s)) || (rc = upload(as.bwd_buf, bw, s))) return rc;

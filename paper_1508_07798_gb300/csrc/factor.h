@@ -22,6 +22,8 @@ struct ApplyStage {
     FrontDev *d_fronts = nullptr;
     ApplyTile *d_fwd = nullptr, *d_bwd = nullptr;
     int nfwd = 0, nbwd = 0;
+    double fwd_bytes = 0, bwd_bytes = 0;  // factor entries read (x8 bytes in FP64)
+    double fwd_vec = 0, bwd_vec = 0;      // vector entries read + written per right-hand side
 };
 
 struct FrontLog {   // per-front record (rank logging, Sec. 5 empirical cost)

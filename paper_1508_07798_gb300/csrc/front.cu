@@ -17,6 +17,7 @@
 
 #include "internal.h"
 #include "front.h"
+#include "prof.h"
 
 namespace hssnd {
 
@@ -230,10 +231,11 @@ template <class T>
 int launch_scatter_A(const hss_bsr *A, const StageElem *se, int nse, int *elem_slot, const FrontDev *fr, T *arena,
                      cudaStream_t s) {
     if (nse == 0) return HSS_OK;
-    k_set_slots<<<cdiv(nse, 256), 256, 0, s>>>(se, nse, elem_slot, 1);
+    { HSS_PROF("set_slots", s); k_set_slots<<<cdiv(nse, 256), 256, 0, s>>>(se, nse, elem_slot, 1); }
+    { HSS_PROF("scatter_A", s);
     k_scatter_A<T><<<cdiv((long)nse * 32, 256), 256, 0, s>>>(A->row_ptr, A->col_idx, A->val, A->bs, se, nse,
-                                                             elem_slot, fr, arena);
-    k_set_slots<<<cdiv(nse, 256), 256, 0, s>>>(se, nse, elem_slot, 0);
+                                                             elem_slot, fr, arena); }
+    { HSS_PROF("set_slots", s); k_set_slots<<<cdiv(nse, 256), 256, 0, s>>>(se, nse, elem_slot, 0); }
     HSS_CHECK_LAUNCH("k_scatter_A");
     return HSS_OK;
 }
@@ -248,6 +250,7 @@ int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev
         cudaFuncSetAttribute(k_gj_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX);
         configured[ti] = true;
     }
+    HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s);
     k_gj_panel<T><<<njobs, PANEL_NT, smem, s>>>(jobs, fr, arena, aold, piv, status);
     HSS_CHECK_LAUNCH("k_gj_panel");
     return HSS_OK;
@@ -256,6 +259,7 @@ int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev
 int launch_iperm(const FrontDev *fr, int nf, const int *iset, const int *piv, int *iperm, int *scratch,
                  cudaStream_t s) {
     if (nf == 0) return HSS_OK;
+    HSS_PROF("iperm", s);
     k_iperm<<<cdiv(nf, 128), 128, 0, s>>>(fr, nf, iset, piv, iperm, scratch);
     HSS_CHECK_LAUNCH("k_iperm");
     return HSS_OK;

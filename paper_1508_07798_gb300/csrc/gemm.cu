@@ -5,6 +5,7 @@
 // generated in registers (never stored), and the leaf-local sample
 // corrections of the HSS construction.
 #include "internal.h"
+#include "prof.h"
 
 namespace hssnd {
 
@@ -105,8 +106,9 @@ __global__ void __launch_bounds__(GT) k_gemm(const GemmDesc<T> *__restrict__ des
 }
 
 template <class T>
-int gemm_batched(const GemmDesc<T> *d_desc, const GemmTile *d_tiles, int ntiles, cudaStream_t s) {
+int gemm_batched(const GemmDesc<T> *d_desc, const GemmTile *d_tiles, int ntiles, cudaStream_t s, double flops) {
     if (ntiles <= 0) return HSS_OK;
+    HSS_PROF(sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", s, flops);
     k_gemm<T><<<ntiles, GT, 0, s>>>(d_desc, d_tiles);
     HSS_CHECK_LAUNCH("k_gemm");
     return HSS_OK;
@@ -123,8 +125,8 @@ void gemm_tiles_for(const GemmDesc<T> &d, int desc_index, std::vector<GemmTile> 
     }
 }
 
-template int gemm_batched<double>(const GemmDesc<double> *, const GemmTile *, int, cudaStream_t);
-template int gemm_batched<float>(const GemmDesc<float> *, const GemmTile *, int, cudaStream_t);
+template int gemm_batched<double>(const GemmDesc<double> *, const GemmTile *, int, cudaStream_t, double);
+template int gemm_batched<float>(const GemmDesc<float> *, const GemmTile *, int, cudaStream_t, double);
 template void gemm_tiles_for<double>(const GemmDesc<double> &, int, std::vector<GemmTile> &);
 template void gemm_tiles_for<float>(const GemmDesc<float> &, int, std::vector<GemmTile> &);
 

@@ -16,6 +16,7 @@
 #include <climits>
 
 #include "hss.h"
+#include "prof.h"
 
 namespace hssnd {
 
@@ -378,6 +379,7 @@ int launch_hss_id(const NodeDev *nodes, const int *work, int nwork, const CompFr
         cudaFuncSetAttribute(k_hss_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         configured[ti] = true;
     }
+    HSS_PROF("hss_id", s);
     k_hss_id<T><<<nwork, ID_NT, smem, s>>>(nodes, work, cf, ws, iws, kout, front_kmax, tol, seed);
     HSS_CHECK_LAUNCH("k_hss_id");
     return HSS_OK;
@@ -393,6 +395,7 @@ int launch_hss_tall(const NodeDev *nodes, const int *work, int nwork, const int 
         cudaFuncSetAttribute(k_hss_tall<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         configured[ti] = true;
     }
+    HSS_PROF("hss_tall", s);
     k_hss_tall<T><<<nwork, 256, smem, s>>>(nodes, work, kout, ws, iws);
     HSS_CHECK_LAUNCH("k_hss_tall");
     return HSS_OK;
@@ -402,6 +405,7 @@ template <class T>
 int launch_hss_expand(const ExpandItem *items, int nitems, const NodeDev *nodes, const int *kout,
                       const ExpandFront *ef, const T *ws, const int *iws, T *arena, T *keep, cudaStream_t s) {
     if (nitems == 0) return HSS_OK;
+    HSS_PROF("hss_expand", s);
     k_hss_expand<T><<<nitems, 256, 0, s>>>(items, nodes, kout, ef, ws, iws, arena, keep);
     HSS_CHECK_LAUNCH("k_hss_expand");
     return HSS_OK;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -115,7 +116,15 @@ constexpr int GEMM_TM = 64;
 constexpr int GEMM_TN = 64;
 
 template <class T>
-int gemm_batched(const GemmDesc<T> *d_desc, const GemmTile *d_tiles, int ntiles, cudaStream_t s);
+int gemm_batched(const GemmDesc<T> *d_desc, const GemmTile *d_tiles, int ntiles, cudaStream_t s,
+                 double flops = 0.0);
+
+// 2 m n k of the written part of a problem
+template <class T> double gemm_flops(const GemmDesc<T> &d) {
+    int ncols = d.n;
+    if (d.skip_hi > d.skip_lo) ncols -= std::max(0, std::min(d.n, d.skip_hi) - std::max(0, d.skip_lo));
+    return 2.0 * d.m * (double)ncols * d.k;
+}
 
 template <class T>
 void gemm_tiles_for(const GemmDesc<T> &d, int desc_index, std::vector<GemmTile> &tiles);

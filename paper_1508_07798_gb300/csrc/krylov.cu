@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "factor.h"
+#include "prof.h"
 
 namespace hssnd {
 
@@ -155,11 +156,26 @@ __global__ void k_init_g(double *__restrict__ g, int m, const double *__restrict
     for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = i == 0 ? beta[0] : 0.0;
 }
 
+static double spmv_bytes(const hss_bsr *A, int nrhs) {
+    // block values and column indices once, row pointers, x read and y written per right-hand side;
+    // computed only while profiling, the block count cached per matrix
+    if (!prof_enabled()) return 0.0;
+    static const int *cached_ptr = nullptr;
+    static int cached_nnzb = 0;
+    if (cached_ptr != A->row_ptr) {
+        cudaMemcpy(&cached_nnzb, A->row_ptr + A->nb, sizeof(int), cudaMemcpyDeviceToHost);
+        cached_ptr = A->row_ptr;
+    }
+    int nnzb = cached_nnzb;
+    double N = (double)A->nb * A->bs;
+    return (double)nnzb * A->bs * A->bs * 8.0 + nnzb * 4.0 + (A->nb + 1) * 4.0 + 2.0 * N * 8.0 * nrhs;
+}
+
 int spmv(const hss_bsr *A, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s) {
     long N = (long)A->nb * A->bs;
     long tot = N * nrhs;
     if (tot == 0) return HSS_OK;
-    k_spmv<<<cdiv(tot, KRY_NT), KRY_NT, 0, s>>>(A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy, nrhs);
+    { HSS_PROF("spmv", s, spmv_bytes(A, nrhs)); k_spmv<<<cdiv(tot, KRY_NT), KRY_NT, 0, s>>>(A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy, nrhs); }
     HSS_CHECK_LAUNCH("k_spmv");
     return HSS_OK;
 }
@@ -187,8 +203,8 @@ static thread_local std::vector<std::vector<double>> g_hist;
 
 // sum_i v_i w_i into out[0] (deterministic two-pass)
 static int dot1(const double *v, const double *w, long N, double *part, double *out, int acc, cudaStream_t s) {
-    k_dots<<<DOT_BLOCKS, KRY_NT, 0, s>>>(v, N, 1, w, N, part);
-    k_dots_final<<<1, 32, 0, s>>>(part, DOT_BLOCKS, 1, out, acc);
+    { HSS_PROF("dots", s); k_dots<<<DOT_BLOCKS, KRY_NT, 0, s>>>(v, N, 1, w, N, part); }
+    { HSS_PROF("dots_final", s); k_dots_final<<<1, 32, 0, s>>>(part, DOT_BLOCKS, 1, out, acc); }
     HSS_CHECK_LAUNCH("dot");
     return HSS_OK;
 }
@@ -204,7 +220,7 @@ static int fgmres_one(const hss_bsr *A, const hss_factor_t *f, const double *b, 
     double host[2];
     // ||b||
     if ((rc = dot1(b, b, N, part, sc + 0, 0, s))) return rc;
-    k_sqrt_into<<<1, 32, 0, s>>>(sc + 0, sc + 1);
+    { HSS_PROF("sqrt_into", s); k_sqrt_into<<<1, 32, 0, s>>>(sc + 0, sc + 1); }
     HSS_CUDA(cudaMemcpyAsync(host, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     HSS_CUDA(cudaStreamSynchronize(s));
     const double bnorm = host[0];
@@ -219,9 +235,9 @@ static int fgmres_one(const hss_bsr *A, const hss_factor_t *f, const double *b, 
     while (true) {
         // r = b - A x, beta = ||r||
         if ((rc = spmv(A, 1, x, N, r, N, s))) return rc;
-        k_resid<<<gb, KRY_NT, 0, s>>>(b, r, N);
+        { HSS_PROF("resid", s); k_resid<<<gb, KRY_NT, 0, s>>>(b, r, N); }
         if ((rc = dot1(r, r, N, part, sc + 2, 0, s))) return rc;
-        k_sqrt_into<<<1, 32, 0, s>>>(sc + 2, sc + 3);
+        { HSS_PROF("sqrt_into", s); k_sqrt_into<<<1, 32, 0, s>>>(sc + 2, sc + 3); }
         HSS_CUDA(cudaMemcpyAsync(host, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
         HSS_CUDA(cudaStreamSynchronize(s));
         double beta = host[0];
@@ -231,8 +247,8 @@ static int fgmres_one(const hss_bsr *A, const hss_factor_t *f, const double *b, 
             return HSS_OK;
         }
         if (iters >= o.maxit) return HSS_OK;
-        k_scale_by<<<gb, KRY_NT, 0, s>>>(r, sc + 3, V, N);
-        k_init_g<<<1, 64, 0, s>>>(K.g.as<double>(), m, sc + 3);
+        { HSS_PROF("scale_by", s); k_scale_by<<<gb, KRY_NT, 0, s>>>(r, sc + 3, V, N); }
+        { HSS_PROF("init_g", s); k_init_g<<<1, 64, 0, s>>>(K.g.as<double>(), m, sc + 3); }
         HSS_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (m + 1) * m, s));
         int jend = 0;
         for (int j = 0; j < m; ++j) {
@@ -246,16 +262,16 @@ static int fgmres_one(const hss_bsr *A, const hss_factor_t *f, const double *b, 
             double *hcol = H + (long)(m + 1) * j;
             // classical Gram-Schmidt, twice
             for (int pass = 0; pass < 2; ++pass) {
-                k_dots<<<gb, KRY_NT, 0, s>>>(V, N, j + 1, w, N, part);
-                k_dots_final<<<1, KRY_MAXM, 0, s>>>(part, gb, j + 1, pass ? K.y.as<double>() : hcol, 0);
-                k_sub_Vh<<<gb, KRY_NT, 0, s>>>(V, N, j + 1, pass ? K.y.as<double>() : hcol, w, N);
+                { HSS_PROF("dots", s); k_dots<<<gb, KRY_NT, 0, s>>>(V, N, j + 1, w, N, part); }
+                { HSS_PROF("dots_final", s); k_dots_final<<<1, KRY_MAXM, 0, s>>>(part, gb, j + 1, pass ? K.y.as<double>() : hcol, 0); }
+                { HSS_PROF("sub_Vh", s); k_sub_Vh<<<gb, KRY_NT, 0, s>>>(V, N, j + 1, pass ? K.y.as<double>() : hcol, w, N); }
             }
             // h += h2 (the second-pass coefficients, read as a one-block partial sum)
-            k_dots_final<<<1, KRY_MAXM, 0, s>>>(K.y.as<double>(), 1, j + 1, hcol, 1);
+            { HSS_PROF("dots_final", s); k_dots_final<<<1, KRY_MAXM, 0, s>>>(K.y.as<double>(), 1, j + 1, hcol, 1); }
             if ((rc = dot1(w, w, N, part, sc + 4, 0, s))) return rc;
-            k_sqrt_into<<<1, 32, 0, s>>>(sc + 4, hcol + j + 1);
-            k_scale_by<<<gb, KRY_NT, 0, s>>>(w, hcol + j + 1, V + N * (j + 1), N);
-            k_givens<<<1, 32, 0, s>>>(H, m, j, K.cs.as<double>(), K.sn.as<double>(), K.g.as<double>(), sc + 5);
+            { HSS_PROF("sqrt_into", s); k_sqrt_into<<<1, 32, 0, s>>>(sc + 4, hcol + j + 1); }
+            { HSS_PROF("scale_by", s); k_scale_by<<<gb, KRY_NT, 0, s>>>(w, hcol + j + 1, V + N * (j + 1), N); }
+            { HSS_PROF("givens", s); k_givens<<<1, 32, 0, s>>>(H, m, j, K.cs.as<double>(), K.sn.as<double>(), K.g.as<double>(), sc + 5); }
             HSS_CHECK_LAUNCH("arnoldi step");
             HSS_CUDA(cudaMemcpyAsync(host, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
             HSS_CUDA(cudaStreamSynchronize(s));
@@ -265,8 +281,8 @@ static int fgmres_one(const hss_bsr *A, const hss_factor_t *f, const double *b, 
             hist.push_back(est);
             if (est <= o.rtol || iters >= o.maxit || !(est == est)) break;
         }
-        k_backsolve<<<1, 32, 0, s>>>(H, m, jend, K.g.as<double>(), K.y.as<double>());
-        k_update_x<<<gb, KRY_NT, 0, s>>>(Z, N, jend, K.y.as<double>(), x, N);
+        { HSS_PROF("backsolve", s); k_backsolve<<<1, 32, 0, s>>>(H, m, jend, K.g.as<double>(), K.y.as<double>()); }
+        { HSS_PROF("update_x", s); k_update_x<<<gb, KRY_NT, 0, s>>>(Z, N, jend, K.y.as<double>(), x, N); }
         HSS_CHECK_LAUNCH("fgmres update");
     }
 }

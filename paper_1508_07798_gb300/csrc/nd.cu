@@ -9,6 +9,7 @@
 #include <deque>
 
 #include "internal.h"
+#include "prof.h"
 
 namespace hssnd {
 
@@ -405,12 +406,15 @@ extern "C" int nd_order(const hss_mesh *mesh, const hss_bsr *A, const hss_nd_opt
         cudaMemsetAsync(d_err.p, 0, sizeof(int), s) != cudaSuccess)
         return fail(cuda_fail(cudaGetLastError(), "nd_order memset"));
     int nt = 256;
+    { HSS_PROF("nd_ancestors", s);
     k_nd_ancestors<<<cdiv(nelem, nt), nt, 0, s>>>(d_box.as<NdBoxDev>(), n[0], n[1], (int)nelem, maxlev,
-                                                   d_anc.as<int>(), d_dfs.as<int>());
+                                                   d_anc.as<int>(), d_dfs.as<int>()); }
+    { HSS_PROF("nd_flags", s);
     k_nd_flags<<<cdiv(nelem, nt), nt, 0, s>>>(A->row_ptr, A->col_idx, (int)nelem, maxlev, d_anc.as<int>(),
-                                               d_flag.as<unsigned>(), d_err.as<int>());
+                                               d_flag.as<unsigned>(), d_err.as<int>()); }
     int *cntB = d_cnt.as<int>(), *cntI = cntB + nbox;
-    k_nd_count<<<nbox, ND_NT, 0, s>>>(d_box.as<NdBoxDev>(), d_dfs.as<int>(), d_flag.as<unsigned>(), cntB, cntI);
+    { HSS_PROF("nd_count", s);
+    k_nd_count<<<nbox, ND_NT, 0, s>>>(d_box.as<NdBoxDev>(), d_dfs.as<int>(), d_flag.as<unsigned>(), cntB, cntI); }
     {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(cuda_fail(e, "nd_order kernels"));
@@ -448,9 +452,10 @@ extern "C" int nd_order(const hss_mesh *mesh, const hss_bsr *A, const hss_nd_opt
     if (cudaMemcpyAsync(d_off.p, hoff.data(), sizeof(int) * 4 * nbox, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return fail(cuda_fail(cudaGetLastError(), "nd_order offsets"));
     int *dio = d_off.as<int>();
+    { HSS_PROF("nd_emit", s);
     k_nd_emit<<<nbox, ND_NT, 0, s>>>(d_box.as<NdBoxDev>(), d_dfs.as<int>(), d_flag.as<unsigned>(), bs, dio,
                                       dio + nbox, dio + 2 * nbox, dio + 3 * nbox, t->d_iset.as<int>(),
-                                      t->d_bset.as<int>(), t->d_fmap.as<int>());
+                                      t->d_bset.as<int>(), t->d_fmap.as<int>()); }
     {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(cuda_fail(e, "k_nd_emit"));

@@ -1,0 +1,127 @@
+// Launch counter and per-kernel-class event timing (diagnostics API of hssnd.h).
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "prof.h"
+
+namespace hssnd {
+
+namespace {
+struct Rec {
+    cudaEvent_t a, b;
+    int cls;
+};
+struct ClassStat {
+    std::string name;
+    double total_ms = 0.0;
+    long launches = 0;
+    double work = 0.0;
+};
+std::mutex g_mu;
+std::atomic<long> g_launches{0};
+bool g_on = false;
+std::vector<ClassStat> g_cls;
+std::vector<Rec> g_pending;
+std::vector<cudaEvent_t> g_pool;
+
+int class_of(const char *name) {
+    for (size_t i = 0; i < g_cls.size(); ++i)
+        if (g_cls[i].name == name) return (int)i;
+    g_cls.push_back({name});
+    return (int)g_cls.size() - 1;
+}
+
+cudaEvent_t get_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void drain_locked() {
+    for (auto &r : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess)
+            g_cls[r.cls].total_ms += ms;
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_pending.clear();
+}
+}  // namespace
+
+bool prof_enabled() { return g_on; }
+
+ProfScope::ProfScope(const char *name, cudaStream_t stream, double work) : cls(-1), s(stream), slot(-1) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!g_on) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cls = class_of(name);
+    g_cls[cls].launches++;
+    g_cls[cls].work += work;
+    Rec r{get_event(), get_event(), cls};
+    cudaEventRecord(r.a, s);
+    g_pending.push_back(r);
+    slot = (int)g_pending.size() - 1;
+    if (g_pending.size() > 4096) {
+        // keep memory bounded: settle the finished records except ours
+        Rec mine = g_pending.back();
+        g_pending.pop_back();
+        drain_locked();
+        g_pending.push_back(mine);
+        slot = 0;
+    }
+}
+
+ProfScope::~ProfScope() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (slot < (int)g_pending.size()) cudaEventRecord(g_pending[slot].b, s);
+}
+
+}  // namespace hssnd
+
+using namespace hssnd;
+
+extern "C" long hss_launch_count(void) { return g_launches.load(); }
+
+extern "C" int hss_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!on) drain_locked();
+    g_on = on != 0;
+    return HSS_OK;
+}
+
+extern "C" int hss_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    drain_locked();
+    g_cls.clear();
+    return HSS_OK;
+}
+
+extern "C" int hss_profile_read(int idx, char *name, int cap, double *total_ms, long *launches, double *work) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    drain_locked();
+    if (idx < 0) return (int)g_cls.size();
+    if (idx >= (int)g_cls.size()) {
+        set_error("hss_profile_read: no such kernel class");
+        return HSS_EINVAL;
+    }
+    const ClassStat &c = g_cls[idx];
+    if (name && cap > 0) {
+        std::strncpy(name, c.name.c_str(), cap - 1);
+        name[cap - 1] = 0;
+    }
+    if (total_ms) *total_ms = c.total_ms;
+    if (launches) *launches = c.launches;
+    if (work) *work = c.work;
+    return HSS_OK;
+}

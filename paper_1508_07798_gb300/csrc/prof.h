@@ -1,0 +1,23 @@
+// Launch accounting and optional per-kernel-class CUDA-event timing.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace hssnd {
+
+// Every kernel launch of the library goes through one ProfScope: it counts
+// the launch and, while profiling is enabled, brackets it with two events on
+// the launching stream.  `work` is the algorithmic work the caller attributes
+// to the launch (flops or bytes, by kernel class).
+struct ProfScope {
+    int cls;
+    cudaStream_t s;
+    int slot;
+    ProfScope(const char *name, cudaStream_t stream, double work = 0.0);
+    ~ProfScope();
+};
+
+bool prof_enabled();
+
+}  // namespace hssnd
+
+#define HSS_PROF(name, stream, ...) ::hssnd::ProfScope _prof_scope_(name, stream, ##__VA_ARGS__)

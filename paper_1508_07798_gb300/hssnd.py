@@ -26,6 +26,7 @@ EXPORTED = [
     "nd_order", "hss_tree_info", "hss_tree_export", "hss_factor", "hss_factor_get_info",
     "hss_factor_export_front", "hss_apply", "hss_spmv", "fgmres_solve", "fgmres_history",
     "hss_tree_destroy", "hss_factor_destroy", "hss_last_error",
+    "hss_launch_count", "hss_profile_enable", "hss_profile_reset", "hss_profile_read",
 ]
 
 
@@ -97,6 +98,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hss_nd_opts_default": (None, [C.POINTER(hss_nd_opts)]),
         "hss_factor_opts_default": (None, [C.POINTER(hss_factor_opts)]),
         "fgmres_opts_default": (None, [C.POINTER(fgmres_opts)]),
+        "hss_launch_count": (C.c_long, []),
+        "hss_profile_enable": (C.c_int, [C.c_int]),
+        "hss_profile_reset": (C.c_int, []),
+        "hss_profile_read": (C.c_int, [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_long), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -285,3 +291,27 @@ def fgmres_history(rhs=0, cap=100000) -> np.ndarray:
     h = np.zeros(cap)
     n = _lib.fgmres_history(rhs, h.ctypes.data_as(C.POINTER(C.c_double)), cap)
     return h[:n]
+
+
+def launch_count() -> int:
+    return int(_lib.hss_launch_count())
+
+
+def profile_enable(on: bool = True):
+    _check(_lib.hss_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(_lib.hss_profile_reset())
+
+
+def profile_read() -> dict:
+    """{kernel class: (total_ms, launches, work)} of the events recorded so far."""
+    n = _lib.hss_profile_read(-1, None, 0, None, None, None)
+    out = {}
+    for i in range(n):
+        name = C.create_string_buffer(64)
+        ms, cnt, work = C.c_double(), C.c_long(), C.c_double()
+        _check(_lib.hss_profile_read(i, name, 64, C.byref(ms), C.byref(cnt), C.byref(work)))
+        out[name.value.decode()] = (ms.value, cnt.value, work.value)
+    return out
