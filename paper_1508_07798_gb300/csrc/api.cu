@@ -1,5 +1,6 @@
 // Error state, option defaults and small shared host utilities of libhssnd.
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 
 #include "internal.h"
@@ -29,6 +30,64 @@ int DevBuf::alloc(size_t nbytes) {
     }
     bytes = nbytes;
     return HSS_OK;
+}
+
+Work::~Work() {
+    cudaStreamSynchronize(s);
+    chunks.clear();
+    if (hpin) cudaFreeHost(hpin);
+    for (void *p : old_pins) cudaFreeHost(p);
+}
+
+int Work::dalloc_bytes(size_t bytes, void **out) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (chunks.empty() || cur + bytes > chunks.back().bytes) {
+        size_t want = std::max(bytes, std::max((size_t)(16u << 20), chunks.empty() ? 0 : 2 * chunks.back().bytes));
+        DevBuf b;
+        int rc = b.alloc(want);
+        if (rc) return rc;
+        chunks.push_back(std::move(b));
+        cur = 0;
+    }
+    *out = static_cast<char *>(chunks.back().p) + cur;
+    cur += bytes;
+    return HSS_OK;
+}
+
+int Work::stage_bytes(const void *src, size_t bytes, void **dev) {
+    int rc = dalloc_bytes(bytes, dev);
+    if (rc || bytes == 0) return rc;
+    size_t need = (bytes + 255) & ~(size_t)255;
+    if (hused + need > hcap) {
+        if (hpin) old_pins.push_back(hpin);   // copies in flight may still read it
+        hcap = std::max(need, std::max((size_t)(1u << 20), 2 * hcap));
+        hused = 0;
+        if (cudaMallocHost(&hpin, hcap) != cudaSuccess) {
+            hpin = nullptr;
+            hcap = 0;
+            return cuda_fail(cudaGetLastError(), "cudaMallocHost");
+        }
+    }
+    void *h = static_cast<char *>(hpin) + hused;
+    std::memcpy(h, src, bytes);
+    hused += need;
+    cudaError_t e = cudaMemcpyAsync(*dev, h, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "upload");
+    return HSS_OK;
+}
+
+void Work::reset() {
+    if (chunks.size() > 1) {
+        size_t total = 0;
+        for (auto &c : chunks) total += c.bytes;
+        chunks.clear();
+        DevBuf b;
+        if (b.alloc(total) == HSS_OK) chunks.push_back(std::move(b));
+    }
+    cur = 0;
+    hused = 0;
+    for (void *p : old_pins) cudaFreeHost(p);
+    old_pins.clear();
 }
 
 }  // namespace hssnd

@@ -14,40 +14,56 @@
 #include "factor.h"
 #include "prof.h"
 
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
+
 namespace hssnd {
 
 constexpr int AP_NT = 256;
 constexpr int AP_RG = AP_NT / APPLY_ROWS;   // column groups per CTA
 constexpr int AP_ZC = 1024;                  // z entries staged per chunk (per right-hand side block)
 
-template <class T, int RB>
-__global__ void __launch_bounds__(AP_NT) k_apply_fwd(const ApplyTile *__restrict__ tiles, const FrontDev *__restrict__ fr,
-                                                   const T *__restrict__ arena, const int *__restrict__ iperm,
-                                                   const int *__restrict__ ilist, const int *__restrict__ blist,
-                                                   double *__restrict__ w, long ldw, double *__restrict__ tv, long ldt,
-                                                   int nrhs) {
+// One cluster of `cs` CTAs per row tile of one front; CTA rank r multiplies the
+// tile's rows by its 1/cs share of the columns, the partial sums meet in the
+// rank-0 CTA's registers through distributed shared memory (fixed order).
+//   FWD: y = [F_ii^-1 P^t ; -F_bi F_ii^-1 P^t] x(Iperm)  ->  t = y[0,ni), x_B += y[ni,n)
+//   BWD: x_I = t - W x_B
+template <class T, int RB, bool FWD>
+__global__ void __launch_bounds__(AP_NT) k_apply(const ApplyTile *__restrict__ tiles, const FrontDev *__restrict__ fr,
+                                               const T *__restrict__ arena, const int *__restrict__ iperm,
+                                               const int *__restrict__ ilist, const int *__restrict__ blist,
+                                               double *__restrict__ w, long ldw, double *__restrict__ tv, long ldt,
+                                               int nrhs) {
     __shared__ double zs[AP_ZC * RB];
     __shared__ double red[AP_RG][APPLY_ROWS][RB];
-    const ApplyTile tl = tiles[blockIdx.x];
+    __shared__ double part[RB][APPLY_ROWS];
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = (int)cl.num_blocks(), crank = (int)cl.block_rank();
+    const ApplyTile tl = tiles[blockIdx.x / cs];
     const FrontDev F = fr[tl.front];
     const T *M = arena + F.foff;
+    const int ncols = FWD ? F.ni : F.nb, colbase = FWD ? 0 : F.ni, nrows = FWD ? F.n : F.ni;
+    const int chunk = (ncols + cs - 1) / cs;
+    const int c_lo = min(ncols, crank * chunk), c_hi = min(ncols, c_lo + chunk);
     const int tx = threadIdx.x % APPLY_ROWS, ty = threadIdx.x / APPLY_ROWS;
     const int i = tl.row0 + tx;
     for (int rb0 = 0; rb0 < nrhs; rb0 += RB) {
         double acc[RB];
 #pragma unroll
         for (int q = 0; q < RB; ++q) acc[q] = 0.0;
-        for (int c0 = 0; c0 < F.ni; c0 += AP_ZC) {
-            int cn = min(AP_ZC, F.ni - c0);
+        for (int c0 = c_lo; c0 < c_hi; c0 += AP_ZC) {
+            const int cn = min(AP_ZC, c_hi - c0);
             __syncthreads();
             for (int idx = threadIdx.x; idx < cn * RB; idx += AP_NT) {
                 int c = idx % cn, q = idx / cn;
                 int rr = rb0 + q;
-                zs[c + AP_ZC * q] = rr < nrhs ? w[iperm[F.iperm_off + c0 + c] + ldw * rr] : 0.0;
+                int dof = FWD ? iperm[F.iperm_off + c0 + c] : blist[F.bset_off + c0 + c];
+                zs[c + AP_ZC * q] = rr < nrhs ? w[dof + ldw * rr] : 0.0;
             }
             __syncthreads();
-            if (i < F.n) {
-                const T *col = M + i + (long)F.n * c0;
+            if (i < nrows) {
+                const T *col = M + i + (long)F.n * (colbase + c0);
+#pragma unroll 8
                 for (int c = ty; c < cn; c += AP_RG) {
                     double m = (double)col[(long)F.n * c];
 #pragma unroll
@@ -58,73 +74,55 @@ __global__ void __launch_bounds__(AP_NT) k_apply_fwd(const ApplyTile *__restrict
 #pragma unroll
         for (int q = 0; q < RB; ++q) red[ty][tx][q] = acc[q];
         __syncthreads();
-        if (ty == 0 && i < F.n) {
+        if (ty == 0) {
+#pragma unroll
+            for (int q = 0; q < RB; ++q) {
+                double y = 0.0;
+                for (int g = 0; g < AP_RG; ++g) y += red[g][tx][q];
+                part[q][tx] = y;
+            }
+        }
+        cl.sync();
+        if (crank == 0 && ty == 0 && i < nrows) {
 #pragma unroll
             for (int q = 0; q < RB; ++q) {
                 int rr = rb0 + q;
                 if (rr >= nrhs) break;
                 double y = 0.0;
-                for (int g = 0; g < AP_RG; ++g) y += red[g][tx][q];
-                if (i < F.ni)
-                    tv[ilist[F.iset_off + i] + ldt * rr] = y;
-                else
-                    w[blist[F.bset_off + i - F.ni] + ldw * rr] += y;
+                for (int r = 0; r < cs; ++r) y += cl.map_shared_rank(&part[q][0], r)[tx];
+                if (FWD) {
+                    if (i < F.ni)
+                        tv[ilist[F.iset_off + i] + ldt * rr] = y;
+                    else
+                        w[blist[F.bset_off + i - F.ni] + ldw * rr] += y;
+                } else {
+                    int dof = ilist[F.iset_off + i];
+                    w[dof + ldw * rr] = tv[dof + ldt * rr] - y;
+                }
             }
         }
-        __syncthreads();
+        cl.sync();
     }
 }
 
-template <class T, int RB>
-__global__ void __launch_bounds__(AP_NT) k_apply_bwd(const ApplyTile *__restrict__ tiles, const FrontDev *__restrict__ fr,
-                                                   const T *__restrict__ arena, const int *__restrict__ ilist,
-                                                   const int *__restrict__ blist, double *__restrict__ w, long ldw,
-                                                   const double *__restrict__ tv, long ldt, int nrhs) {
-    __shared__ double zs[AP_ZC * RB];
-    __shared__ double red[AP_RG][APPLY_ROWS][RB];
-    const ApplyTile tl = tiles[blockIdx.x];
-    const FrontDev F = fr[tl.front];
-    const T *M = arena + F.foff;
-    const int tx = threadIdx.x % APPLY_ROWS, ty = threadIdx.x / APPLY_ROWS;
-    const int i = tl.row0 + tx;
-    for (int rb0 = 0; rb0 < nrhs; rb0 += RB) {
-        double acc[RB];
-#pragma unroll
-        for (int q = 0; q < RB; ++q) acc[q] = 0.0;
-        for (int c0 = 0; c0 < F.nb; c0 += AP_ZC) {
-            int cn = min(AP_ZC, F.nb - c0);
-            __syncthreads();
-            for (int idx = threadIdx.x; idx < cn * RB; idx += AP_NT) {
-                int c = idx % cn, q = idx / cn;
-                int rr = rb0 + q;
-                zs[c + AP_ZC * q] = rr < nrhs ? w[blist[F.bset_off + c0 + c] + ldw * rr] : 0.0;
-            }
-            __syncthreads();
-            if (i < F.ni) {
-                const T *col = M + i + (long)F.n * (F.ni + c0);
-                for (int c = ty; c < cn; c += AP_RG) {
-                    double m = (double)col[(long)F.n * c];
-#pragma unroll
-                    for (int q = 0; q < RB; ++q) acc[q] = fma(m, zs[c + AP_ZC * q], acc[q]);
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < RB; ++q) red[ty][tx][q] = acc[q];
-        __syncthreads();
-        if (ty == 0 && i < F.ni) {
-#pragma unroll
-            for (int q = 0; q < RB; ++q) {
-                int rr = rb0 + q;
-                if (rr >= nrhs) break;
-                double y = 0.0;
-                for (int g = 0; g < AP_RG; ++g) y += red[g][tx][q];
-                int dof = ilist[F.iset_off + i];
-                w[dof + ldw * rr] = tv[dof + ldt * rr] - y;
-            }
-        }
-        __syncthreads();
-    }
+template <class T, int RB, bool FWD>
+static cudaError_t launch_apply(int ntiles, int cs, cudaStream_t s, const ApplyTile *tiles, const FrontDev *fr,
+                                const T *arena, const int *iperm, const int *ilist, const int *blist, double *w,
+                                long ldw, double *tv, long ldt, int nrhs) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ntiles * cs);
+    cfg.blockDim = dim3(AP_NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_apply<T, RB, FWD>, tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt,
+                              nrhs);
 }
 
 template <class T>
@@ -133,22 +131,19 @@ int apply_stage(const ApplyStage &st, bool forward, const FrontDev *fr, const T 
                 cudaStream_t s) {
     const ApplyTile *tiles = forward ? st.d_fwd : st.d_bwd;
     int nt = forward ? st.nfwd : st.nbwd;
+    int cs = forward ? st.cs_fwd : st.cs_bwd;
     if (nt == 0) return HSS_OK;
     double bytes = (forward ? st.fwd_bytes : st.bwd_bytes) * (sizeof(T) / 8.0) +
                    (forward ? st.fwd_vec : st.bwd_vec) * 8.0 * nrhs;
     HSS_PROF(forward ? "apply_fwd" : "apply_bwd", s, bytes);
-    if (forward) {
-        if (nrhs == 1)
-            k_apply_fwd<T, 1><<<nt, AP_NT, 0, s>>>(tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs);
-        else
-            k_apply_fwd<T, 4><<<nt, AP_NT, 0, s>>>(tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs);
-    } else {
-        if (nrhs == 1)
-            k_apply_bwd<T, 1><<<nt, AP_NT, 0, s>>>(tiles, fr, arena, ilist, blist, w, ldw, tv, ldt, nrhs);
-        else
-            k_apply_bwd<T, 4><<<nt, AP_NT, 0, s>>>(tiles, fr, arena, ilist, blist, w, ldw, tv, ldt, nrhs);
-    }
-    HSS_CHECK_LAUNCH("k_apply");
+    cudaError_t e;
+    if (forward)
+        e = nrhs == 1 ? launch_apply<T, 1, true>(nt, cs, s, tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs)
+                      : launch_apply<T, 4, true>(nt, cs, s, tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs);
+    else
+        e = nrhs == 1 ? launch_apply<T, 1, false>(nt, cs, s, tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs)
+                      : launch_apply<T, 4, false>(nt, cs, s, tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs);
+    if (e != cudaSuccess) return cuda_fail(e, "k_apply launch");
     return HSS_OK;
 }
 

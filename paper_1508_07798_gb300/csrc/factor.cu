@@ -32,7 +32,7 @@ template <class T> struct StageCtx {
 template <class T>
 int assemble_stage(const hss_bsr *A, const hss_tree *t, const std::vector<FrontDev> &fr, const FrontDev *d_fr,
                    const std::vector<std::vector<int>> &dofs, const std::vector<std::vector<int>> &sides,
-                   int *elem_slot, T *arena, cudaStream_t s) {
+                   int *elem_slot, T *arena, Work &W, cudaStream_t s) {
     std::vector<StageElem> se;
     int bs = t->bs;
     for (size_t f = 0; f < fr.size(); ++f) {
@@ -40,26 +40,22 @@ int assemble_stage(const hss_bsr *A, const hss_tree *t, const std::vector<FrontD
         for (size_t pos = 0; pos < d.size(); pos += bs) se.push_back({d[pos] / bs, (int)f, (int)pos, sides[f][pos / bs]});
     }
     if (se.empty()) return HSS_OK;
-    DevBuf d_se;
+    StageElem *d_se;
     int rc;
-    if ((rc = upload(d_se, se, s))) return rc;
-    rc = launch_scatter_A<T>(A, d_se.as<StageElem>(), (int)se.size(), elem_slot, d_fr, arena, s);
-    if (rc) return rc;
-    // d_se must stay alive until the kernels ran
-    HSS_CUDA(cudaStreamSynchronize(s));
-    return HSS_OK;
+    if ((rc = W.up(se, &d_se))) return rc;
+    return launch_scatter_A<T>(A, d_se, (int)se.size(), elem_slot, d_fr, arena, s);
 }
 
 template <class T> int choose_kb(int ni) {
     for (int kb = PANEL_KB_MAX; kb >= 8; kb /= 2)
-        if ((long)ni * kb * (long)sizeof(T) <= PANEL_SMEM_MAX) return kb;
+        if ((long)ni * kb * (long)sizeof(T) + (long)ni * 4 <= PANEL_SMEM_MAX) return kb;
     return PANEL_KB_MAX;  // global-memory panel
 }
 
 // Blocked Gauss-Jordan sweep over the I pivots of every front of a stage.
 template <class T>
-int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *arena, int *piv, int *status,
-                    double &exec_flops, cudaStream_t s) {
+int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *arena, int *piv, int *rperm,
+                    const int *ilist, int *iperm, int *status, double &exec_flops, Work &W, cudaStream_t s) {
     int nf = (int)fr.size();
     std::vector<int> kb(nf), nsteps(nf);
     std::vector<long> aoff(nf);
@@ -87,9 +83,10 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             if (st >= nsteps[f]) continue;
             int k0 = st * kb[f];
             int kbs = std::min(kb[f], fr[f].ni - k0);
-            size_t need = (size_t)(fr[f].ni - k0) * kbs * sizeof(T);
+            size_t hT = (size_t)(fr[f].ni - k0);
+            size_t need = hT * kbs * sizeof(T) + hT * sizeof(int);
             int use_smem = need <= (size_t)PANEL_SMEM_MAX;
-            if (use_smem) smem[st] = std::max(smem[st], need);
+            smem[st] = std::max(smem[st], use_smem ? need : hT * sizeof(int));
             jobs.push_back({f, k0, kbs, use_smem, aoff[f]});
             GemmDesc<T> d{};
             d.A = arena + fr[f].foff + (long)fr[f].n * k0;
@@ -116,24 +113,23 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
     }
     job_off[maxsteps] = (int)jobs.size();
     tile_off[maxsteps] = (int)tiles.size();
-    DevBuf d_aold, d_jobs, d_descs, d_tiles;
+    T *d_aold;
+    PanelJob *d_jobs;
+    GemmDesc<T> *d_descs;
+    GemmTile *d_tiles;
     int rc;
-    if ((rc = d_aold.alloc(sizeof(T) * std::max(aold_total, 1L)))) return rc;
-    for (size_t i = 0; i < descs.size(); ++i) {
-        descs[i].B = d_aold.as<T>() + jobs[i].aoff;
-    }
-    if ((rc = upload(d_jobs, jobs, s)) || (rc = upload(d_descs, descs, s)) || (rc = upload(d_tiles, tiles, s)))
-        return rc;
+    if ((rc = W.dalloc(aold_total, &d_aold))) return rc;
+    for (size_t i = 0; i < descs.size(); ++i) descs[i].B = d_aold + jobs[i].aoff;
+    if ((rc = W.up(jobs, &d_jobs)) || (rc = W.up(descs, &d_descs)) || (rc = W.up(tiles, &d_tiles))) return rc;
     for (int st = 0; st < maxsteps; ++st) {
         int nj = job_off[st + 1] - job_off[st];
-        if ((rc = launch_gj_panel<T>(d_jobs.as<PanelJob>() + job_off[st], nj, smem[st], d_fr, arena, d_aold.as<T>(),
-                                     piv, status, s)))
+        if ((rc = launch_gj_panel<T>(d_jobs + job_off[st], nj, smem[st], d_fr, arena, d_aold, piv, rperm, ilist,
+                                     iperm, status, s)))
             return rc;
-        if ((rc = gemm_batched<T>(d_descs.as<GemmDesc<T>>(), d_tiles.as<GemmTile>() + tile_off[st],
-                                  tile_off[st + 1] - tile_off[st], s, step_flops[st])))
+        if ((rc = gemm_batched<T>(d_descs, d_tiles + tile_off[st], tile_off[st + 1] - tile_off[st], s,
+                                  step_flops[st])))
             return rc;
     }
-    HSS_CUDA(cudaStreamSynchronize(s));
     return HSS_OK;
 }
 
@@ -149,7 +145,7 @@ template <class T>
 int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vector<FrontDev> &fr,
                    const std::vector<int> &boxes, const std::vector<long> &poff, const std::vector<int> &pn,
                    const std::vector<long> &keep_h, T *arena, T *keep, int *status_dev, int nstatus,
-                   std::vector<FrontLog> &logv, hss_factor_t *F, cudaStream_t s) {
+                   std::vector<FrontLog> &logv, hss_factor_t *F, Work &W, cudaStream_t s) {
     int nf = (int)fr.size();
     int rc;
     std::vector<ExpandFront> ef(nf);
@@ -163,8 +159,8 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         ef[f].pn = pn[f];
         ef[f].keep_h = keep_h[f];
     }
-    DevBuf d_ef;
-    if ((rc = upload(d_ef, ef, s))) return rc;
+    ExpandFront *d_ef;
+    if ((rc = W.up(ef, &d_ef))) return rc;
 
     std::vector<RoundFront> active;
     std::vector<ExpandItem> plain_items;
@@ -182,12 +178,11 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         }
     }
     if (!plain_items.empty()) {
-        DevBuf d_items;
-        if ((rc = upload(d_items, plain_items, s))) return rc;
-        if ((rc = launch_hss_expand<T>(d_items.as<ExpandItem>(), (int)plain_items.size(), nullptr, nullptr,
-                                       d_ef.as<ExpandFront>(), nullptr, nullptr, arena, keep, s)))
+        ExpandItem *d_items;
+        if ((rc = W.up(plain_items, &d_items))) return rc;
+        if ((rc = launch_hss_expand<T>(d_items, (int)plain_items.size(), nullptr, nullptr, d_ef, nullptr, nullptr,
+                                       arena, keep, s)))
             return rc;
-        HSS_CUDA(cudaStreamSynchronize(s));
     }
 
     while (!active.empty()) {
@@ -240,14 +235,15 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         }
         node_base[nc] = (int)nodes.size();
         int nn = (int)nodes.size();
-        DevBuf d_ws, d_iws, d_nodes, d_cfs, d_kout, d_fk;
-        if ((rc = d_ws.alloc(sizeof(T) * std::max(wsz, 1L))) || (rc = d_iws.alloc(sizeof(int) * std::max(isz, 1L))) ||
-            (rc = upload(d_nodes, nodes, s)) || (rc = upload(d_cfs, cfs, s)) ||
-            (rc = d_kout.alloc(sizeof(int) * 2 * nn)) || (rc = d_fk.alloc(sizeof(int) * nc)))
+        T *ws;
+        int *d_iws, *d_kout, *d_fk;
+        NodeDev *d_nodes;
+        CompFront<T> *d_cfs;
+        if ((rc = W.dalloc(wsz, &ws)) || (rc = W.dalloc(isz, &d_iws)) || (rc = W.up(nodes, &d_nodes)) ||
+            (rc = W.up(cfs, &d_cfs)) || (rc = W.dalloc(2 * nn, &d_kout)) || (rc = W.dalloc(nc, &d_fk)))
             return rc;
-        HSS_CUDA(cudaMemsetAsync(d_kout.p, 0, sizeof(int) * 2 * nn, s));
-        HSS_CUDA(cudaMemsetAsync(d_fk.p, 0, sizeof(int) * nc, s));
-        T *ws = d_ws.as<T>();
+        HSS_CUDA(cudaMemsetAsync(d_kout, 0, sizeof(int) * 2 * nn, s));
+        HSS_CUDA(cudaMemsetAsync(d_fk, 0, sizeof(int) * nc, s));
         // ---- sampling Y = S Omega, Z = S^t Psi, then the leaf corrections
         std::vector<GemmDesc<T>> g1, g2;
         std::vector<GemmTile> t1, t2;
@@ -300,15 +296,14 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             }
         }
         {
-            DevBuf a, b, c2, d2;
-            if ((rc = upload(a, g1, s)) || (rc = upload(b, t1, s)) || (rc = upload(c2, g2, s)) || (rc = upload(d2, t2, s)))
-                return rc;
+            GemmDesc<T> *a, *c2;
+            GemmTile *b, *d2;
+            if ((rc = W.up(g1, &a)) || (rc = W.up(t1, &b)) || (rc = W.up(g2, &c2)) || (rc = W.up(t2, &d2))) return rc;
             double f1 = 0, f2 = 0;
             for (auto &d : g1) f1 += gemm_flops(d);
             for (auto &d : g2) f2 += gemm_flops(d);
-            if ((rc = gemm_batched<T>(a.as<GemmDesc<T>>(), b.as<GemmTile>(), (int)t1.size(), s, f1))) return rc;
-            if ((rc = gemm_batched<T>(c2.as<GemmDesc<T>>(), d2.as<GemmTile>(), (int)t2.size(), s, f2))) return rc;
-            HSS_CUDA(cudaStreamSynchronize(s));
+            if ((rc = gemm_batched<T>(a, b, (int)t1.size(), s, f1))) return rc;
+            if ((rc = gemm_batched<T>(c2, d2, (int)t2.size(), s, f2))) return rc;
         }
         // ---- interpolative decompositions, deepest HSS level first
         int maxd = 0;
@@ -332,18 +327,16 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             idsmem[dpt] = std::max(idsmem[dpt], sizeof(T) * ((size_t)r * mcap + r + mcap) + sizeof(int) * mcap + 16);
             tallsmem[dpt] = std::max(tallsmem[dpt], sizeof(int) * (mcap + 2) + sizeof(T) * (size_t)mcap * kcap + 16);
         }
-        std::vector<DevBuf> wbufs(maxd + 1);
         for (int dpt = maxd; dpt >= 1; --dpt) {
             if (work[dpt].empty()) continue;
-            if ((rc = upload(wbufs[dpt], work[dpt], s))) return rc;
-            if ((rc = launch_hss_id<T>(d_nodes.as<NodeDev>(), wbufs[dpt].as<int>(), (int)work[dpt].size(),
-                                       d_cfs.as<CompFront<T>>(), ws, d_iws.as<int>(), d_kout.as<int>(),
-                                       d_fk.as<int>(), (T)o.tol, o.seed, idsmem[dpt], s)))
+            int *d_work;
+            if ((rc = W.up(work[dpt], &d_work))) return rc;
+            if ((rc = launch_hss_id<T>(d_nodes, d_work, (int)work[dpt].size(), d_cfs, ws, d_iws, d_kout, d_fk,
+                                       (T)o.tol, o.seed, idsmem[dpt], s)))
                 return rc;
         }
-        std::vector<int> hk(2 * nn), hfk(nc);
-        HSS_CUDA(cudaMemcpyAsync(hk.data(), d_kout.p, sizeof(int) * 2 * nn, cudaMemcpyDeviceToHost, s));
-        HSS_CUDA(cudaMemcpyAsync(hfk.data(), d_fk.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+        std::vector<int> hfk(nc);
+        HSS_CUDA(cudaMemcpyAsync(hfk.data(), d_fk, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
         HSS_CUDA(cudaStreamSynchronize(s));
         // ---- decide: fronts whose rank reached r - oversample sample again, wider
         std::vector<RoundFront> next;
@@ -364,12 +357,10 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             for (int x : work[dpt])
                 if (done[nodes[x >> 1].cf]) wk.push_back(x);
             if (wk.empty()) continue;
-            DevBuf d_wk;
-            if ((rc = upload(d_wk, wk, s))) return rc;
-            if ((rc = launch_hss_tall<T>(d_nodes.as<NodeDev>(), d_wk.as<int>(), (int)wk.size(), d_kout.as<int>(), ws,
-                                         d_iws.as<int>(), tallsmem[dpt], s)))
+            int *d_wk;
+            if ((rc = W.up(wk, &d_wk))) return rc;
+            if ((rc = launch_hss_tall<T>(d_nodes, d_wk, (int)wk.size(), d_kout, ws, d_iws, tallsmem[dpt], s)))
                 return rc;
-            HSS_CUDA(cudaStreamSynchronize(s));
         }
         std::vector<ExpandItem> items;
         for (int c = 0; c < nc; ++c) {
@@ -394,13 +385,11 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             }
         }
         if (!items.empty()) {
-            DevBuf d_items;
-            if ((rc = upload(d_items, items, s))) return rc;
-            if ((rc = launch_hss_expand<T>(d_items.as<ExpandItem>(), (int)items.size(), d_nodes.as<NodeDev>(),
-                                           d_kout.as<int>(), d_ef.as<ExpandFront>(), ws, d_iws.as<int>(), arena,
-                                           keep, s)))
+            ExpandItem *d_items;
+            if ((rc = W.up(items, &d_items))) return rc;
+            if ((rc = launch_hss_expand<T>(d_items, (int)items.size(), d_nodes, d_kout, d_ef, ws, d_iws, arena, keep,
+                                           s)))
                 return rc;
-            HSS_CUDA(cudaStreamSynchronize(s));
         }
         active.swap(next);
     }
@@ -434,6 +423,19 @@ int build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, DevBuf &&
         as.fwd_vec += fr[f].ni + fr[f].ni + 2.0 * fr[f].nb;      // x_I read, t written, x_B read+written
         as.bwd_vec += fr[f].nb + fr[f].ni + fr[f].ni;           // x_B read, t read, x_I written
     }
+    // split the columns of the widest front over a cluster of up to 8 CTAs (about 256 columns each)
+    int maxc_f = 0, maxc_b = 0;
+    for (const auto &d : fr) {
+        if (d.ni == 0) continue;
+        maxc_f = std::max(maxc_f, d.ni);
+        maxc_b = std::max(maxc_b, d.nb);
+    }
+    auto csz = [](int cols) {
+        int c = (cols + 255) / 256;
+        return c <= 1 ? 1 : c <= 2 ? 2 : c <= 4 ? 4 : 8;
+    };
+    as.cs_fwd = csz(maxc_f);
+    as.cs_bwd = csz(maxc_b);
     int rc;
     if ((rc = upload(as.fwd_buf, fw, s)) || (rc = upload(as.bwd_buf, bw, s))) return rc;
     as.d_fwd = as.fwd_buf.as<ApplyTile>();
@@ -483,6 +485,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         if ((rc = F->keep.alloc(sizeof(T) * std::max(ks, 1L)))) return rc;
     }
     T *keep = F->keep.as<T>();
+    Work W(s);
     F->factor_bytes = 0;
     F->front_flops = 0;
     F->exec_flops = 0;
@@ -534,23 +537,15 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             F->front_flops += 2.0 / 3.0 * ni * ni * ni + 2.0 * ni * ni * nb + 2.0 * nb * nb * ni;
             F->factor_bytes += sizeof(T) * (ni * (ni + nb) + ni * nb);
         }
-        DevBuf d_fr, d_status;
-        if ((rc = upload(d_fr, fr, s)) || (rc = d_status.alloc(sizeof(int) * fr.size()))) return rc;
-        HSS_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int) * fr.size(), s));
-        if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, s))) return rc;
-        if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_status.as<int>(),
-                                     F->exec_flops, s)))
+        W.reset();   // the stream is idle: the previous stage ended with a readback
+        DevBuf d_fr;
+        int *d_status;
+        if ((rc = upload(d_fr, fr, s)) || (rc = W.dalloc(fr.size(), &d_status))) return rc;
+        HSS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int) * fr.size(), s));
+        if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
             return rc;
-        std::vector<int> hst(fr.size());
-        HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status.p, sizeof(int) * fr.size(), cudaMemcpyDeviceToHost, s));
-        HSS_CUDA(cudaStreamSynchronize(s));
-        for (size_t f = 0; f < fr.size(); ++f)
-            if (hst[f]) {
-                set_error("hss_factor: zero pivot in the front of box " + std::to_string(boxes[f]));
-                return HSS_ESINGULAR;
-            }
-        if ((rc = launch_iperm(d_fr.as<FrontDev>(), (int)fr.size(), t->d_iset.as<int>(), d_piv.as<int>(),
-                               F->d_iperm.as<int>(), d_scratch.as<int>(), s)))
+        if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
+                                     t->d_iset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, W, s)))
             return rc;
         if (o.keep_schur)
             for (size_t f = 0; f < fr.size(); ++f) {
@@ -560,9 +555,17 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
                                            arena + d.foff + d.ni + (long)d.n * d.ni, sizeof(T) * d.n,
                                            sizeof(T) * d.nb, d.nb, cudaMemcpyDeviceToDevice, s));
             }
-        if ((rc = compress_stage<T>(t, o, fr, boxes, poff, pn, keeph, arena, keep, d_status.as<int>(),
-                                    (int)fr.size(), F->log, F, s)))
+        if ((rc = compress_stage<T>(t, o, fr, boxes, poff, pn, keeph, arena, keep, d_status, (int)fr.size(), F->log,
+                                    F, W, s)))
             return rc;
+        std::vector<int> hst(fr.size());
+        HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status, sizeof(int) * fr.size(), cudaMemcpyDeviceToHost, s));
+        HSS_CUDA(cudaStreamSynchronize(s));
+        for (size_t f = 0; f < fr.size(); ++f)
+            if (hst[f]) {
+                set_error("hss_factor: zero pivot in the front of box " + std::to_string(boxes[f]));
+                return HSS_ESINGULAR;
+            }
         F->apply.emplace_back();
         if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), false, s))) return rc;
     }
@@ -584,23 +587,23 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         dofs[0] = topset;
         sides[0].assign(ntop / t->bs, 1);
         for (int q = 0; q < t->nb[0] / t->bs; ++q) sides[0][q] = 0;
-        DevBuf d_fr, d_status;
-        if ((rc = upload(d_fr, fr, s)) || (rc = d_status.alloc(sizeof(int)))) return rc;
-        HSS_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), s));
-        if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, s))) return rc;
-        if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_status.as<int>(),
-                                     F->exec_flops, s)))
+        W.reset();
+        DevBuf d_fr;
+        int *d_status;
+        if ((rc = upload(d_fr, fr, s)) || (rc = W.dalloc(1, &d_status))) return rc;
+        HSS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+        if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
+            return rc;
+        if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
+                                     F->d_topset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, W, s)))
             return rc;
         int hst = 0;
-        HSS_CUDA(cudaMemcpyAsync(&hst, d_status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        HSS_CUDA(cudaMemcpyAsync(&hst, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         HSS_CUDA(cudaStreamSynchronize(s));
         if (hst) {
             set_error("hss_factor: zero pivot in the top block");
             return HSS_ESINGULAR;
         }
-        if ((rc = launch_iperm(d_fr.as<FrontDev>(), 1, F->d_topset.as<int>(), d_piv.as<int>(), F->d_iperm.as<int>(),
-                               d_scratch.as<int>(), s)))
-            return rc;
         F->front_flops += 2.0 / 3.0 * (double)ntop * ntop * ntop;
         F->factor_bytes += sizeof(T) * (double)ntop * ntop;
         F->apply.emplace_back();

@@ -22,6 +22,7 @@ struct ApplyStage {
     FrontDev *d_fronts = nullptr;
     ApplyTile *d_fwd = nullptr, *d_bwd = nullptr;
     int nfwd = 0, nbwd = 0;
+    int cs_fwd = 1, cs_bwd = 1;           // cluster size (column split) of the two sweeps
     double fwd_bytes = 0, bwd_bytes = 0;  // factor entries read (x8 bytes in FP64)
     double fwd_vec = 0, bwd_vec = 0;      // vector entries read + written per right-hand side
 };

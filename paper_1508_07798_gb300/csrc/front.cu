@@ -89,16 +89,23 @@ template <class T> __device__ ArgMax<T> block_argmax(ArgMax<T> x, ArgMax<T> *sh)
 // One CTA per front with an active panel [k0, k0+kb) of its I columns.
 // 1. Gauss-Jordan on the tall panel rows [k0, ni) x panel columns, with row
 //    pivoting inside [k0+j, ni) (in shared memory when it fits);
-// 2. the pivot row swaps applied to the columns outside the panel;
+// 2. the pivot row swaps applied to the columns outside the panel, and to the
+//    running row permutation rperm (position -> original I row);
 // 3. Aold = pivot rows, all columns (input of the trailing update);
-// 4. rows outside [k0, ni): F(i, P) = -F(i, P) X with X = F(P,P)^-1.
+// 4. rows outside [k0, ni): F(i, P) = -F(i, P) X with X = F(P,P)^-1;
+// 5. last panel of a front: the apply's gather list iperm[j] = I[rperm[j]]
+//    (the sweep leaves F_ii^-1 P^t, so F_ii^-1 x = (F_ii^-1 P^t)(P x)).
 template <class T>
 __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restrict__ jobs, const FrontDev *__restrict__ fr,
                                                     T *__restrict__ arena, T *__restrict__ aold_ws,
-                                                    int *__restrict__ piv, int *__restrict__ status) {
+                                                    int *__restrict__ piv, int *__restrict__ rperm,
+                                                    const int *__restrict__ ilist, int *__restrict__ iperm,
+                                                    int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ ArgMax<T> red[PANEL_NT / 32];
     __shared__ T Xs[PANEL_KB_MAX * PANEL_KB_MAX];
+    __shared__ T rowj[PANEL_KB_MAX];
+    __shared__ int swp[PANEL_KB_MAX];
     const PanelJob J = jobs[blockIdx.x];
     const FrontDev F = fr[J.front];
     T *M = arena + F.foff;
@@ -107,17 +114,20 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
     const int hT = ni - k0;
     T *P;
     long ldp;
+    int *rp;   // rperm[k0 .. ni) in shared memory
     if (J.smem) {
         P = reinterpret_cast<T *>(smraw);
         ldp = hT;
-        for (int q = threadIdx.x; q < hT * kb; q += PANEL_NT) {
-            int i = q % hT, c = q / hT;
-            P[i + ldp * c] = M[(k0 + i) + ld * (k0 + c)];
-        }
+        rp = reinterpret_cast<int *>(smraw + sizeof(T) * (size_t)hT * kb);
+        for (int c = 0; c < kb; ++c)
+            for (int i = threadIdx.x; i < hT; i += PANEL_NT) P[i + ldp * c] = M[(k0 + i) + ld * (k0 + c)];
     } else {
         P = M + k0 + ld * k0;
         ldp = ld;
+        rp = reinterpret_cast<int *>(smraw);
     }
+    int *rglob = rperm + F.ioff;
+    for (int i = threadIdx.x; i < hT; i += PANEL_NT) rp[i] = k0 == 0 ? i : rglob[k0 + i];
     __syncthreads();
     int *pv = piv + F.ioff;
     for (int j = 0; j < kb; ++j) {
@@ -141,22 +151,29 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
                 P[j + ldp * c] = P[p + ldp * c];
                 P[p + ldp * c] = tmp;
             }
-        if (threadIdx.x == 0) pv[k0 + j] = k0 + p;
-        __syncthreads();
-        T piv_v = P[j + ldp * j];
-        T dinv = piv_v != T(0) ? T(1) / piv_v : T(0);
-        // eliminate column j from every other panel row
-        for (int q = threadIdx.x; q < hT * kb; q += PANEL_NT) {
-            int i = q % hT, c = q / hT;
-            if (i == j || c == j) continue;
-            P[i + ldp * c] -= P[i + ldp * j] * (P[j + ldp * c] * dinv);
+        if (threadIdx.x == 0) {
+            pv[k0 + j] = k0 + p;
+            swp[j] = p;
+            int t = rp[j];
+            rp[j] = rp[p];
+            rp[p] = t;
         }
         __syncthreads();
-        for (int c = threadIdx.x; c < kb; c += PANEL_NT)
-            if (c != j) P[j + ldp * c] *= dinv;
-        for (int i = threadIdx.x; i < hT; i += PANEL_NT)
-            if (i != j) P[i + ldp * j] = -P[i + ldp * j] * dinv;
-        if (threadIdx.x == 0) P[j + ldp * j] = dinv;
+        const T dinv = P[j + ldp * j] != T(0) ? T(1) / P[j + ldp * j] : T(0);
+        for (int c = threadIdx.x; c < kb; c += PANEL_NT) rowj[c] = (c == j) ? T(0) : P[j + ldp * c] * dinv;
+        __syncthreads();
+        // eliminate column j from every other panel row (one thread per row)
+        for (int i = threadIdx.x; i < hT; i += PANEL_NT) {
+            if (i == j) continue;
+            const T a = P[i + ldp * j];
+            if (a != T(0)) {
+#pragma unroll 8
+                for (int c = 0; c < kb; ++c) P[i + ldp * c] -= a * rowj[c];
+            }
+            P[i + ldp * j] = -a * dinv;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < kb; c += PANEL_NT) P[j + ldp * c] = (c == j) ? dinv : rowj[c];
         __syncthreads();
     }
     // X = inverse of the pivot block, kept for the rows outside the panel
@@ -164,26 +181,25 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
         int i = q % kb, c = q / kb;
         Xs[i + kb * c] = P[i + ldp * c];
     }
-    if (J.smem) {
-        for (int q = threadIdx.x; q < hT * kb; q += PANEL_NT) {
-            int i = q % hT, c = q / hT;
-            M[(k0 + i) + ld * (k0 + c)] = P[i + ldp * c];
+    if (J.smem)
+        for (int c = 0; c < kb; ++c)
+            for (int i = threadIdx.x; i < hT; i += PANEL_NT) M[(k0 + i) + ld * (k0 + c)] = P[i + ldp * c];
+    for (int i = threadIdx.x; i < hT; i += PANEL_NT) rglob[k0 + i] = rp[i];
+    __syncthreads();
+    // row swaps on the columns outside the panel, in pivot order (one thread per column)
+    for (int c = threadIdx.x; c < n; c += PANEL_NT) {
+        if (c >= k0 && c < k0 + kb) continue;
+        T *col = M + ld * c + k0;
+        for (int j = 0; j < kb; ++j) {
+            int p = swp[j];
+            if (p != j) {
+                T tmp = col[j];
+                col[j] = col[p];
+                col[p] = tmp;
+            }
         }
     }
     __syncthreads();
-    // row swaps on the columns outside the panel, in pivot order
-    for (int j = 0; j < kb; ++j) {
-        int p = pv[k0 + j];
-        if (p != k0 + j) {
-            for (int c = threadIdx.x; c < n; c += PANEL_NT) {
-                if (c >= k0 && c < k0 + kb) continue;
-                T tmp = M[(k0 + j) + ld * c];
-                M[(k0 + j) + ld * c] = M[p + ld * c];
-                M[p + ld * c] = tmp;
-            }
-        }
-        __syncthreads();
-    }
     // Aold: the (swapped) pivot rows over all columns
     T *Ao = aold_ws + J.aoff;
     for (int q = threadIdx.x; q < kb * n; q += PANEL_NT) {
@@ -195,35 +211,25 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
     for (int r = threadIdx.x; r < nout; r += PANEL_NT) {
         int i = r < k0 ? r : r + hT;
         T old[PANEL_KB_MAX];
-#pragma unroll 8
-        for (int s = 0; s < kb; ++s) old[s] = M[i + ld * (k0 + s)];
+#pragma unroll
+        for (int s = 0; s < PANEL_KB_MAX; ++s)
+            if (s < kb) old[s] = M[i + ld * (k0 + s)];
         for (int c = 0; c < kb; ++c) {
             T acc = T(0);
-#pragma unroll 8
-            for (int s = 0; s < kb; ++s) acc = fma(old[s], Xs[s + kb * c], acc);
+#pragma unroll
+            for (int s = 0; s < PANEL_KB_MAX; ++s)
+                if (s < kb) acc = fma(old[s], Xs[s + kb * c], acc);
             M[i + ld * (k0 + c)] = -acc;
         }
     }
-}
-
-// After the last panel: the gather list that applies F_ii^-1 to x_I in the
-// original order.  The sweep produced F_ii^-1 P^t; column idx[c] of it is
-// column c of F_ii^-1 where idx replays the swaps in reverse order, so
-// x_perm[idx[c]] = x[c], i.e. iperm[idx[c]] = I[c].
-__global__ void k_iperm(const FrontDev *__restrict__ fr, int nf, const int *__restrict__ iset,
-                        const int *__restrict__ piv, int *__restrict__ iperm, int *__restrict__ scratch) {
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nf) return;
-    const FrontDev F = fr[f];
-    int *idx = scratch + F.ioff;
-    for (int c = 0; c < F.ni; ++c) idx[c] = c;
-    for (int j = F.ni - 1; j >= 0; --j) {
-        int p = piv[F.ioff + j];
-        int t = idx[j];
-        idx[j] = idx[p];
-        idx[p] = t;
+    // last panel: gather list of the apply
+    if (k0 + kb == ni) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < ni; j += PANEL_NT) {
+            int r = j < k0 ? rglob[j] : rp[j - k0];
+            iperm[F.iperm_off + j] = ilist[F.iset_off + r];
+        }
     }
-    for (int c = 0; c < F.ni; ++c) iperm[F.iperm_off + idx[c]] = iset[F.iset_off + c];
 }
 
 // ---------------------------------------------------------------- launchers
@@ -242,7 +248,7 @@ int launch_scatter_A(const hss_bsr *A, const StageElem *se, int nse, int *elem_s
 
 template <class T>
 int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *aold, int *piv,
-                    int *status, cudaStream_t s) {
+                    int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s) {
     if (njobs == 0) return HSS_OK;
     static bool configured[2] = {false, false};
     int ti = sizeof(T) == 8 ? 0 : 1;
@@ -251,17 +257,8 @@ int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev
         configured[ti] = true;
     }
     HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s);
-    k_gj_panel<T><<<njobs, PANEL_NT, smem, s>>>(jobs, fr, arena, aold, piv, status);
+    k_gj_panel<T><<<njobs, PANEL_NT, smem, s>>>(jobs, fr, arena, aold, piv, rperm, ilist, iperm, status);
     HSS_CHECK_LAUNCH("k_gj_panel");
-    return HSS_OK;
-}
-
-int launch_iperm(const FrontDev *fr, int nf, const int *iset, const int *piv, int *iperm, int *scratch,
-                 cudaStream_t s) {
-    if (nf == 0) return HSS_OK;
-    HSS_PROF("iperm", s);
-    k_iperm<<<cdiv(nf, 128), 128, 0, s>>>(fr, nf, iset, piv, iperm, scratch);
-    HSS_CHECK_LAUNCH("k_iperm");
     return HSS_OK;
 }
 
@@ -269,9 +266,9 @@ template int launch_scatter_A<double>(const hss_bsr *, const StageElem *, int, i
                                       cudaStream_t);
 template int launch_scatter_A<float>(const hss_bsr *, const StageElem *, int, int *, const FrontDev *, float *,
                                      cudaStream_t);
-template int launch_gj_panel<double>(const PanelJob *, int, size_t, const FrontDev *, double *, double *, int *, int *,
-                                     cudaStream_t);
+template int launch_gj_panel<double>(const PanelJob *, int, size_t, const FrontDev *, double *, double *, int *,
+                                     int *, const int *, int *, int *, cudaStream_t);
 template int launch_gj_panel<float>(const PanelJob *, int, size_t, const FrontDev *, float *, float *, int *, int *,
-                                    cudaStream_t);
+                                    const int *, int *, int *, cudaStream_t);
 
 }  // namespace hssnd

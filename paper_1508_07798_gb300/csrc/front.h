@@ -40,8 +40,6 @@ int launch_scatter_A(const hss_bsr *A, const StageElem *se, int nse, int *elem_s
                      cudaStream_t s);
 template <class T>
 int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *aold, int *piv,
-                    int *status, cudaStream_t s);
-int launch_iperm(const FrontDev *fr, int nf, const int *iset, const int *piv, int *iperm, int *scratch,
-                 cudaStream_t s);
+                    int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s);
 
 }  // namespace hssnd

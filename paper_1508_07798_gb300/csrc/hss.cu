@@ -35,18 +35,13 @@ template <class T> __device__ AM<T> blk_argmax(AM<T> x, AM<T> *sh) {
         }
     }
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();   // previous readers of sh are done
     if (lane == 0) sh[w] = x;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        AM<T> b = sh[0];
-        for (int k = 1; k < ID_NT / 32; ++k)
-            if (sh[k].v > b.v || (sh[k].v == b.v && sh[k].i < b.i)) b = sh[k];
-        sh[0] = b;
-    }
-    __syncthreads();
-    AM<T> r = sh[0];
-    __syncthreads();
-    return r;
+    AM<T> b = sh[0];
+    for (int k = 1; k < ID_NT / 32; ++k)
+        if (sh[k].v > b.v || (sh[k].v == b.v && sh[k].i < b.i)) b = sh[k];
+    return b;
 }
 
 template <class T> __device__ T blk_sum(T x, T *sh) {
@@ -86,19 +81,6 @@ template <class T> __device__ void householder_step(T *A, int r, int m, int j, T
     }
     __syncthreads();
     for (int i = j + threadIdx.x; i < r; i += ID_NT) A[i + (long)r * j] = (i == j) ? alpha : T(0);
-    __syncthreads();
-}
-
-// T = R11^-1 R12 by back substitution, one thread per column of R12.
-template <class T> __device__ void solve_T(const T *A, int r, int m, int k, T *Tm, int kcap) {
-    for (int c = k + threadIdx.x; c < m; c += ID_NT) {
-        T *tc = Tm + (long)kcap * (c - k);
-        for (int i = k - 1; i >= 0; --i) {
-            T t = A[i + (long)r * c];
-            for (int l = i + 1; l < k; ++l) t -= A[i + (long)r * l] * tc[l];
-            tc[i] = t / A[i + (long)r * i];
-        }
-    }
     __syncthreads();
 }
 
@@ -158,56 +140,91 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
     for (int c = threadIdx.x; c < m; c += ID_NT) order[c] = c;
     __syncthreads();
 
-    // ---- column-pivoted QR of A = L^t with the relative rank cut
+    // ---- column-pivoted QR of A = L^t with the relative rank cut; trailing
+    // column norms are recomputed (not downdated) by the warp that updates
+    // the column
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int c = w; c < m; c += ID_NT / 32) {
+        T sq = 0;
+        for (int i = lane; i < r; i += 32) sq += A[i + (long)r * c] * A[i + (long)r * c];
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) nrm2[c] = sq;
+    }
     int k = 0;
     T first = 0;
     const int kmx = min(r, m);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int j = 0; j < kmx; ++j) {
-        for (int c = j + w; c < m; c += ID_NT / 32) {
-            T s = 0;
-            for (int i = j + lane; i < r; i += 32) s += A[i + (long)r * c] * A[i + (long)r * c];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) nrm2[c] = s;
-        }
-        __syncthreads();
         AM<T> loc{T(-1), INT_MAX};
+        __syncthreads();
         for (int c = j + threadIdx.x; c < m; c += ID_NT)
             if (nrm2[c] > loc.v || (nrm2[c] == loc.v && c < loc.i)) {
                 loc.v = nrm2[c];
                 loc.i = c;
             }
         AM<T> best = blk_argmax(loc, sham);
-        T nrm = sqrt(best.v);
+        const T nn2 = best.v;
+        const T nrm = sqrt(nn2);
         if (j == 0) first = nrm;
         if (first == T(0) || nrm <= tol * first) break;
-        int p = best.i;
-        if (p != j) {
+        const int p = best.i;
+        // every thread has read nrm2 and order before the barrier inside blk_argmax
+        if (threadIdx.x == 0 && p != j) {
+            int t = order[j];
+            order[j] = order[p];
+            order[p] = t;
+            nrm2[p] = nrm2[j];
+        }
+        if (p != j)
             for (int i = threadIdx.x; i < r; i += ID_NT) {
                 T t = A[i + (long)r * j];
                 A[i + (long)r * j] = A[i + (long)r * p];
                 A[i + (long)r * p] = t;
             }
-            if (threadIdx.x == 0) {
-                int t = order[j];
-                order[j] = order[p];
-                order[p] = t;
+        __syncthreads();
+        const T x0 = A[j + (long)r * j];
+        const T alpha = (x0 != T(0)) ? -copysign(nrm, x0) : -nrm;
+        const T vn = (x0 - alpha) * (x0 - alpha) + (nn2 - x0 * x0);
+        for (int i = j + threadIdx.x; i < r; i += ID_NT) v[i] = (i == j) ? x0 - alpha : A[i + (long)r * j];
+        __syncthreads();
+        for (int c = j + 1 + w; c < m; c += ID_NT / 32) {
+            T d = 0;
+            for (int i = j + lane; i < r; i += 32) d += v[i] * A[i + (long)r * c];
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            const T coef = vn > T(0) ? T(2) * d / vn : T(0);
+            T sq = 0;
+            for (int i = j + lane; i < r; i += 32) {
+                T a = A[i + (long)r * c] - coef * v[i];
+                A[i + (long)r * c] = a;
+                if (i > j) sq += a * a;
+            }
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (lane == 0) nrm2[c] = sq;
+        }
+        for (int i = j + threadIdx.x; i < r; i += ID_NT) A[i + (long)r * j] = (i == j) ? alpha : T(0);
+        k = j + 1;
+    }
+    __syncthreads();
+    // T = R11^-1 R12 in place (one thread per column of R12)
+    auto solve_T_inplace = [&]() {
+        for (int c = k + threadIdx.x; c < m; c += ID_NT) {
+            T *col = A + (long)r * c;
+            for (int i = k - 1; i >= 0; --i) {
+                T t = col[i];
+                for (int l = i + 1; l < k; ++l) t -= A[i + (long)r * l] * col[l];
+                col[i] = t / A[i + (long)r * i];
             }
         }
         __syncthreads();
-        householder_step(A, r, m, j, nrm, v, shs);
-        k = j + 1;
-    }
-    T *Tm = ws + me.toff;
-    solve_T(A, r, m, k, Tm, kcap);
+    };
+    solve_T_inplace();
 
     // ---- exchanges while some |T_ij| > 2 (largest entry, first in row-major order)
     for (int sw = 0; sw < ID_MAX_SWAPS && k > 0 && k < m; ++sw) {
-        int nc = m - k;
+        const int nc = m - k;
         AM<T> loc{T(-1), INT_MAX};
         for (int q = threadIdx.x; q < k * nc; q += ID_NT) {
             int i = q / nc, jj = q % nc;  // row-major linear index q
-            T a = fabs(Tm[i + (long)kcap * jj]);
+            T a = fabs(A[i + (long)r * (k + jj)]);
             if (a > loc.v || (a == loc.v && q < loc.i)) {
                 loc.v = a;
                 loc.i = q;
@@ -215,6 +232,7 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
         }
         AM<T> best = blk_argmax(loc, sham);
         if (best.v <= T(2)) break;
+        __syncthreads();
         if (threadIdx.x == 0) {
             int i = best.i / nc, jj = best.i % nc;
             int t = order[i];
@@ -233,10 +251,15 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
             T nn = sqrt(blk_sum(part, shs));
             householder_step(A, r, m, j, nn, v, shs);
         }
-        solve_T(A, r, m, k, Tm, kcap);
+        solve_T_inplace();
     }
 
     // ---- outputs
+    T *Tm = ws + me.toff;
+    for (int idx = threadIdx.x; idx < k * (m - k); idx += ID_NT) {
+        int i = idx % k, jj = idx / k;
+        Tm[i + (long)kcap * jj] = A[i + (long)r * (k + jj)];
+    }
     if (threadIdx.x == 0) {
         kout[2 * node + side] = k;
         atomicMax(&front_kmax[N.cf], k);
@@ -252,19 +275,29 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
             sk[c] = leaf ? N.lo + o : (o < ka ? iws[sa.skioff + o] : iws[sb.skioff + o - ka]);
         }
     }
+    __syncthreads();
+    // the local test matrix W (m x r) replaces A in shared memory:
+    // rows compress Psi (stream 1), columns Omega (stream 0)
+    T *Wl = A;
+    const int strm = side == 0 ? 1 : 0;
+    for (int idx = threadIdx.x; idx < m * r; idx += ID_NT) {
+        int row = idx % m, j = idx / m;
+        T val;
+        if (leaf)
+            val = (T)rademacher(seed, strm, C.box, N.lo + row, j);
+        else
+            val = row < ka ? ws[sa.tloff + row + (long)sa.kcap * j] : ws[sb.tloff + (row - ka) + (long)sb.kcap * j];
+        Wl[row + (long)m * j] = val;
+    }
+    __syncthreads();
     T *skel = ws + me.skoff;
     T *tl = ws + me.tloff;
-    const int strm = side == 0 ? 1 : 0;  // rows compress Psi (stream 1), columns Omega (stream 0)
     for (int idx = threadIdx.x; idx < k * r; idx += ID_NT) {
         int i = idx % k, j = idx / k;
         skel[i + (long)kcap * j] = L[order[i] + (long)mcap * j];
-        auto W = [&](int row) -> T {
-            if (leaf) return (T)rademacher(seed, strm, C.box, N.lo + row, j);
-            return row < ka ? ws[sa.tloff + row + (long)sa.kcap * j]
-                            : ws[sb.tloff + (row - ka) + (long)sb.kcap * j];
-        };
-        T acc = W(order[i]);
-        for (int jj = 0; jj < m - k; ++jj) acc += Tm[i + (long)kcap * jj] * W(order[k + jj]);
+        const T *wc = Wl + (long)m * j;
+        T acc = wc[order[i]];
+        for (int jj = 0; jj < m - k; ++jj) acc += Tm[i + (long)kcap * jj] * wc[order[k + jj]];
         tl[i + (long)kcap * j] = acc;
     }
 }

@@ -66,6 +66,37 @@ template <class T> int upload(DevBuf &b, const std::vector<T> &v, cudaStream_t s
     return HSS_OK;
 }
 
+// Scratch of one library call: a device bump allocator and a pinned host
+// staging buffer for uploads.  Nothing is freed until reset() (stream idle)
+// or destruction, so kernels may use the memory until the next sync point.
+struct Work {
+    cudaStream_t s = nullptr;
+    std::vector<DevBuf> chunks;
+    size_t cur = 0;
+    void *hpin = nullptr;
+    size_t hcap = 0, hused = 0;
+    std::vector<void *> old_pins;
+    explicit Work(cudaStream_t st) : s(st) {}
+    Work(const Work &) = delete;
+    Work &operator=(const Work &) = delete;
+    ~Work();
+    int dalloc_bytes(size_t bytes, void **out);
+    template <class T> int dalloc(size_t n, T **out) {
+        void *p;
+        int rc = dalloc_bytes(sizeof(T) * (n ? n : 1), &p);
+        *out = static_cast<T *>(p);
+        return rc;
+    }
+    int stage_bytes(const void *src, size_t bytes, void **dev);
+    template <class T> int up(const std::vector<T> &v, T **out) {
+        void *p;
+        int rc = stage_bytes(v.data(), sizeof(T) * v.size(), &p);
+        *out = static_cast<T *>(p);
+        return rc;
+    }
+    void reset();   // the stream must be idle
+};
+
 // ---------------------------------------------------------------- tree
 struct HssNode {          // one node of the HSS tree of a front's S (host view)
     int lo, hi;           // index range inside B^box

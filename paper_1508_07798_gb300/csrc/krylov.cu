@@ -65,14 +65,15 @@ __global__ void k_dots(const double *__restrict__ V, long ldv, int nq, const dou
     }
 }
 
-// out[q] (= or +=) sum of the partials, q < nq, in a fixed order.
+// out[q] (= or +=) sum of the partials, q < nq, one warp per q, fixed order.
 __global__ void k_dots_final(const double *__restrict__ partial, int nblk, int nq, double *__restrict__ out,
                              int accumulate) {
-    int q = threadIdx.x;
+    int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (q >= nq) return;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[(long)b * KRY_MAXM + q];
-    out[q] = accumulate ? out[q] + s : s;
+    for (int b = lane; b < nblk; b += 32) s += partial[(long)b * KRY_MAXM + q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[q] = accumulate ? out[q] + s : s;
 }
 
 // w -= V(:, 0:nq) h
@@ -263,11 +264,11 @@ static int fgmres_one(const hss_bsr *A, const hss_factor_t *f, const double *b, 
             // classical Gram-Schmidt, twice
             for (int pass = 0; pass < 2; ++pass) {
                 { HSS_PROF("dots", s); k_dots<<<gb, KRY_NT, 0, s>>>(V, N, j + 1, w, N, part); }
-                { HSS_PROF("dots_final", s); k_dots_final<<<1, KRY_MAXM, 0, s>>>(part, gb, j + 1, pass ? K.y.as<double>() : hcol, 0); }
+                { HSS_PROF("dots_final", s); k_dots_final<<<1, 32 * (j + 1), 0, s>>>(part, gb, j + 1, pass ? K.y.as<double>() : hcol, 0); }
                 { HSS_PROF("sub_Vh", s); k_sub_Vh<<<gb, KRY_NT, 0, s>>>(V, N, j + 1, pass ? K.y.as<double>() : hcol, w, N); }
             }
             // h += h2 (the second-pass coefficients, read as a one-block partial sum)
-            { HSS_PROF("dots_final", s); k_dots_final<<<1, KRY_MAXM, 0, s>>>(K.y.as<double>(), 1, j + 1, hcol, 1); }
+            { HSS_PROF("dots_final", s); k_dots_final<<<1, 32 * (j + 1), 0, s>>>(K.y.as<double>(), 1, j + 1, hcol, 1); }
             if ((rc = dot1(w, w, N, part, sc + 4, 0, s))) return rc;
             { HSS_PROF("sqrt_into", s); k_sqrt_into<<<1, 32, 0, s>>>(sc + 4, hcol + j + 1); }
             { HSS_PROF("scale_by", s); k_scale_by<<<gb, KRY_NT, 0, s>>>(w, hcol + j + 1, V + N * (j + 1), N); }
