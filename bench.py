@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--forms", default="fp32,fp64")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps only (no apply loop, no host-buffer run): for profiling")
     return ap.parse_args()
 
 
@@ -187,6 +189,10 @@ def bench_ours(args, rank, world):
                            executed_flops=info["executed_flops"], max_rank=info["max_rank"], max_r=info["max_r"])
     clocks = clk.stop()
     barrier()
+    if args.quick:
+        return dict(metric=METRIC, quick=True, forms={k: {kk: vv for kk, vv in v.items() if kk != "ms_all"}
+                                                      for k, v in forms.items()},
+                    gpu_launches=int(launches_total // max(1, len(forms))))
 
     # ---- apply GB/s: 20 applies of the last factor of each form, L2 flushed between
     apply = {}
@@ -285,8 +291,8 @@ def bench_ours(args, rank, world):
         roof = dict(kernel=dom, bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
                     traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
                     peak_source=pk["src"])
-    kernels = {k: dict(ms=round(v[0] / args.steps, 4), launches=v[1] // args.steps) for k, v in
-               sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    kernels = {form: {k: dict(ms=round(v[0] / args.steps, 4), launches=v[1] // args.steps) for k, v in
+                      sorted(pf.items(), key=lambda kv: -kv[1][0])} for form, pf in prof_all.items()}
     res = dict(metric=METRIC, value=value, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup,
                ms_per_step=value, higher_is_better=False, scaling="weak", vs_baseline=None,
                dtype="f32 factor / f64 Krylov" if head == "fp32" else "f64", data="synthetic",
@@ -358,7 +364,7 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     res = bench_ours(args, rank, world)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         ms, info = cpu_baseline_run(0)
         res["cpu_baseline"] = dict(value=ms, unit="ms", cores=cpu_cores(), kind="oracle",
                                    sample="one full 36,864-dof solve (nd + factor + FGMRES), seed 0",

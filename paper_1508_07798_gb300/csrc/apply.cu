@@ -32,8 +32,12 @@ template <class T, int RB, bool FWD>
 __global__ void __launch_bounds__(AP_NT) k_apply(const ApplyTile *__restrict__ tiles, const FrontDev *__restrict__ fr,
                                                const T *__restrict__ arena, const int *__restrict__ iperm,
                                                const int *__restrict__ ilist, const int *__restrict__ blist,
-                                               double *__restrict__ w, long ldw, double *__restrict__ tv, long ldt,
-                                               int nrhs) {
+                                               const ApplyParams *__restrict__ prm) {
+    double *__restrict__ w = prm->w;
+    const long ldw = prm->ldw;
+    double *__restrict__ tv = prm->tv;
+    const long ldt = prm->ldt;
+    const int nrhs = prm->nrhs;
     __shared__ double zs[AP_ZC * RB];
     __shared__ double red[AP_RG][APPLY_ROWS][RB];
     __shared__ double part[RB][APPLY_ROWS];
@@ -105,10 +109,26 @@ __global__ void __launch_bounds__(AP_NT) k_apply(const ApplyTile *__restrict__ t
     }
 }
 
+__global__ void k_apply_set(ApplyParams *d, ApplyParams v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *d = v;
+}
+
+// w = x (every right-hand side), skipped when they alias
+__global__ void k_apply_copyin(const ApplyParams *__restrict__ prm, long N) {
+    const double *x = prm->x;
+    double *w = prm->w;
+    if (x == w) return;
+    long tot = N * prm->nrhs;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += (long)gridDim.x * blockDim.x) {
+        long r = g / N, i = g % N;
+        w[i + prm->ldw * r] = x[i + prm->ldx * r];
+    }
+}
+
 template <class T, int RB, bool FWD>
 static cudaError_t launch_apply(int ntiles, int cs, cudaStream_t s, const ApplyTile *tiles, const FrontDev *fr,
-                                const T *arena, const int *iperm, const int *ilist, const int *blist, double *w,
-                                long ldw, double *tv, long ldt, int nrhs) {
+                                const T *arena, const int *iperm, const int *ilist, const int *blist,
+                                const ApplyParams *prm) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ntiles * cs);
     cfg.blockDim = dim3(AP_NT);
@@ -121,52 +141,55 @@ static cudaError_t launch_apply(int ntiles, int cs, cudaStream_t s, const ApplyT
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_apply<T, RB, FWD>, tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt,
-                              nrhs);
+    return cudaLaunchKernelEx(&cfg, k_apply<T, RB, FWD>, tiles, fr, arena, iperm, ilist, blist, prm);
 }
 
-template <class T>
-int apply_stage(const ApplyStage &st, bool forward, const FrontDev *fr, const T *arena, const int *iperm,
-                const int *ilist, const int *blist, double *w, long ldw, double *tv, long ldt, int nrhs,
-                cudaStream_t s) {
-    const ApplyTile *tiles = forward ? st.d_fwd : st.d_bwd;
-    int nt = forward ? st.nfwd : st.nbwd;
-    int cs = forward ? st.cs_fwd : st.cs_bwd;
-    if (nt == 0) return HSS_OK;
-    double bytes = (forward ? st.fwd_bytes : st.bwd_bytes) * (sizeof(T) / 8.0) +
-                   (forward ? st.fwd_vec : st.bwd_vec) * 8.0 * nrhs;
-    HSS_PROF(forward ? "apply_fwd" : "apply_bwd", s, bytes);
-    cudaError_t e;
-    if (forward)
-        e = nrhs == 1 ? launch_apply<T, 1, true>(nt, cs, s, tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs)
-                      : launch_apply<T, 4, true>(nt, cs, s, tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs);
-    else
-        e = nrhs == 1 ? launch_apply<T, 1, false>(nt, cs, s, tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs)
-                      : launch_apply<T, 4, false>(nt, cs, s, tiles, fr, arena, iperm, ilist, blist, w, ldw, tv, ldt, nrhs);
-    if (e != cudaSuccess) return cuda_fail(e, "k_apply launch");
+// The whole sweep (copy-in, forward levels, top block, backward levels) as
+// one kernel sequence on stream s; parameters come from f->d_aparams.
+template <class T, int RB> static int record_sweep(const hss_factor_t *f, cudaStream_t s, int &nk) {
+    const T *arena = f->arena_ptr<T>();
+    const ApplyParams *prm = f->d_aparams.as<ApplyParams>();
+    nk = 0;
+    k_apply_copyin<<<2 * 152, 256, 0, s>>>(prm, f->ndof);
+    ++nk;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool fwd = pass == 0;
+        for (size_t q = 0; q < f->apply.size(); ++q) {
+            const ApplyStage &st = fwd ? f->apply[q] : f->apply[f->apply.size() - 1 - q];
+            const int *ilist = st.top ? f->d_topset.as<int>() : f->tree->d_iset.as<int>();
+            const int nt = fwd ? st.nfwd : st.nbwd;
+            if (nt == 0) continue;
+            cudaError_t e = fwd ? launch_apply<T, RB, true>(nt, st.cs_fwd, s, st.d_fwd, st.d_fronts, arena,
+                                                              f->d_iperm.as<int>(), ilist, f->tree->d_bset.as<int>(), prm)
+                                : launch_apply<T, RB, false>(nt, st.cs_bwd, s, st.d_bwd, st.d_fronts, arena,
+                                                               f->d_iperm.as<int>(), ilist, f->tree->d_bset.as<int>(), prm);
+            if (e != cudaSuccess) return cuda_fail(e, "k_apply launch");
+            ++nk;
+        }
+    }
+    HSS_CHECK_LAUNCH("apply sweep");
     return HSS_OK;
 }
 
-template <class T> static int apply_impl(const hss_factor_t *f, int nrhs, double *y, long ldy, cudaStream_t s) {
-    const T *arena = f->arena_ptr<T>();
-    double *tv = f->tvec.as<double>();
-    long ldt = f->ndof;
-    int rc;
-    // forward: stages deepest first, then the top block
-    for (size_t k = 0; k < f->apply.size(); ++k) {
-        const ApplyStage &st = f->apply[k];
-        const int *ilist = st.top ? f->d_topset.as<int>() : f->tree->d_iset.as<int>();
-        if ((rc = apply_stage<T>(st, true, st.d_fronts, arena, f->d_iperm.as<int>(), ilist, f->tree->d_bset.as<int>(),
-                                 y, ldy, tv, ldt, nrhs, s)))
-            return rc;
+template <class T> static int build_graph(hss_factor_t *f, int slot) {
+    cudaStream_t cs;
+    HSS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    int rc = HSS_OK;
+    prof_set_capture(true);
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        int nk = 0;
+        rc = slot == 0 ? record_sweep<T, 1>(f, cs, nk) : record_sweep<T, 4>(f, cs, nk);
+        e = cudaStreamEndCapture(cs, &g);
+        f->graph_kernels[slot] = nk;
     }
-    for (size_t k = f->apply.size(); k-- > 0;) {
-        const ApplyStage &st = f->apply[k];
-        const int *ilist = st.top ? f->d_topset.as<int>() : f->tree->d_iset.as<int>();
-        if ((rc = apply_stage<T>(st, false, st.d_fronts, arena, f->d_iperm.as<int>(), ilist, f->tree->d_bset.as<int>(),
-                                 y, ldy, tv, ldt, nrhs, s)))
-            return rc;
-    }
+    prof_set_capture(false);
+    if (e == cudaSuccess && rc == HSS_OK) e = cudaGraphInstantiate(&f->gexec[slot], g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "apply graph");
     return HSS_OK;
 }
 
@@ -174,12 +197,19 @@ int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, dou
     hss_factor_t *mf = const_cast<hss_factor_t *>(f);
     int rc;
     if ((rc = mf->tvec.alloc(sizeof(double) * (size_t)f->ndof * nrhs))) return rc;
-    if (x != y) {
-        HSS_CUDA(cudaMemcpy2DAsync(y, sizeof(double) * ldy, x, sizeof(double) * ldx, sizeof(double) * f->ndof, nrhs,
-                                   cudaMemcpyDeviceToDevice, s));
+    if ((rc = mf->d_aparams.alloc(sizeof(ApplyParams)))) return rc;
+    const int slot = nrhs == 1 ? 0 : 1;
+    if (!f->gexec[slot]) {
+        rc = f->precision == HSS_FP32 ? build_graph<float>(mf, slot) : build_graph<double>(mf, slot);
+        if (rc) return rc;
     }
-    if (f->precision == HSS_FP32) return apply_impl<float>(f, nrhs, y, ldy, s);
-    return apply_impl<double>(f, nrhs, y, ldy, s);
+    ApplyParams pv{x, ldx, y, ldy, mf->tvec.as<double>(), (long)f->ndof, nrhs};
+    HSS_PROF("apply", s, f->apply_bytes(nrhs));
+    prof_add_launches(f->graph_kernels[slot]);
+    k_apply_set<<<1, 32, 0, s>>>(mf->d_aparams.as<ApplyParams>(), pv);
+    HSS_CHECK_LAUNCH("k_apply_set");
+    HSS_CUDA(cudaGraphLaunch(f->gexec[slot], s));
+    return HSS_OK;
 }
 
 }  // namespace hssnd

@@ -53,16 +53,26 @@ template <class T> int choose_kb(int ni) {
 }
 
 // Blocked Gauss-Jordan sweep over the I pivots of every front of a stage.
+// Per panel step: the panel kernels (register-resident where the panel fits,
+// shared/global memory otherwise), the post-panel tiles, the trailing GEMM.
 template <class T>
 int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *arena, int *piv, int *rperm,
                     const int *ilist, int *iperm, int *status, double &exec_flops, Work &W, cudaStream_t s) {
     int nf = (int)fr.size();
-    std::vector<int> kb(nf), nsteps(nf);
+    std::vector<int> kb(nf), nsteps(nf), isreg(nf), Rf(nf);
     std::vector<long> aoff(nf);
     long aold_total = 0;
     int maxsteps = 0;
     for (int f = 0; f < nf; ++f) {
+        isreg[f] = 0;
         kb[f] = choose_kb<T>(fr[f].ni);
+        for (int k = PANEL_KB_MAX; k >= 8; k /= 2)
+            if (fr[f].ni > 0 && panel_reg_fits(k, fr[f].ni, (int)sizeof(T))) {
+                kb[f] = k;
+                isreg[f] = 1;
+                break;
+            }
+        Rf[f] = cdiv(std::max(fr[f].ni, 1), PANEL_NT);
         nsteps[f] = fr[f].ni > 0 ? cdiv(fr[f].ni, kb[f]) : 0;
         aoff[f] = aold_total;
         aold_total += (long)kb[f] * fr[f].n;
@@ -70,24 +80,58 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         exec_flops += 2.0 * fr[f].n * (double)fr[f].n * fr[f].ni;
     }
     if (maxsteps == 0) return HSS_OK;
+    struct Group {
+        int off, cnt, reg, kb, rows;
+        size_t smem;
+    };
     std::vector<PanelJob> jobs;
     std::vector<GemmDesc<T>> descs;
     std::vector<GemmTile> tiles;
-    std::vector<int> job_off(maxsteps + 1), tile_off(maxsteps + 1);
-    std::vector<size_t> smem(maxsteps, 0);
+    std::vector<PanelTile> ptiles;
+    std::vector<std::vector<Group>> groups(maxsteps);
+    std::vector<int> tile_off(maxsteps + 1), ptile_off(maxsteps + 1);
+    long xtotal = 0, mtotal = 0;
     std::vector<double> step_flops(maxsteps, 0.0);
     for (int st = 0; st < maxsteps; ++st) {
-        job_off[st] = (int)jobs.size();
         tile_off[st] = (int)tiles.size();
-        for (int f = 0; f < nf; ++f) {
-            if (st >= nsteps[f]) continue;
+        ptile_off[st] = (int)ptiles.size();
+        std::vector<int> act;
+        for (int f = 0; f < nf; ++f)
+            if (st < nsteps[f]) act.push_back(f);
+        // register panels grouped by (kb, R), then the memory panels
+        std::stable_sort(act.begin(), act.end(), [&](int a, int b) {
+            if (isreg[a] != isreg[b]) return isreg[a] > isreg[b];
+            if (kb[a] != kb[b]) return kb[a] < kb[b];
+            return Rf[a] < Rf[b];
+        });
+        for (int f : act) {
             int k0 = st * kb[f];
             int kbs = std::min(kb[f], fr[f].ni - k0);
             size_t hT = (size_t)(fr[f].ni - k0);
-            size_t need = hT * kbs * sizeof(T) + hT * sizeof(int);
-            int use_smem = need <= (size_t)PANEL_SMEM_MAX;
-            smem[st] = std::max(smem[st], use_smem ? need : hT * sizeof(int));
-            jobs.push_back({f, k0, kbs, use_smem, aoff[f]});
+            int use_smem = 0;
+            size_t need = 0;
+            if (isreg[f]) {
+                use_smem = 2;
+                need = 3 * hT * sizeof(int);
+            } else {
+                need = hT * kbs * sizeof(T) + hT * sizeof(int);
+                use_smem = need <= (size_t)PANEL_SMEM_MAX;
+                if (!use_smem) need = hT * sizeof(int);
+            }
+            auto &gs = groups[st];
+            if (gs.empty() || gs.back().reg != isreg[f] || (isreg[f] && (gs.back().kb != kb[f] ||
+                                                                         cdiv(gs.back().rows, PANEL_NT) != Rf[f])))
+                gs.push_back({(int)jobs.size(), 0, isreg[f], kb[f], Rf[f] * PANEL_NT, 0});
+            gs.back().cnt++;
+            gs.back().smem = std::max(gs.back().smem, need);
+            int jid = (int)jobs.size();
+            jobs.push_back({f, k0, kbs, use_smem, aoff[f], xtotal, mtotal});
+            xtotal += (long)kbs * kbs;
+            mtotal += 1 + 4 * PANEL_KB_MAX;
+            for (int c0 = 0; c0 < fr[f].n; c0 += 32)
+                if (!(c0 >= k0 && c0 + 32 <= k0 + kbs)) ptiles.push_back({jid, 0, c0});
+            int nout = fr[f].n - (fr[f].ni - k0);
+            for (int r0 = 0; r0 < nout; r0 += 64) ptiles.push_back({jid, 1, r0});
             GemmDesc<T> d{};
             d.A = arena + fr[f].foff + (long)fr[f].n * k0;
             d.lda = fr[f].n;
@@ -111,20 +155,33 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             step_flops[st] += gemm_flops(d);
         }
     }
-    job_off[maxsteps] = (int)jobs.size();
     tile_off[maxsteps] = (int)tiles.size();
-    T *d_aold;
+    ptile_off[maxsteps] = (int)ptiles.size();
+    T *d_aold, *d_x;
+    int *d_mv;
     PanelJob *d_jobs;
     GemmDesc<T> *d_descs;
     GemmTile *d_tiles;
+    PanelTile *d_ptiles;
     int rc;
-    if ((rc = W.dalloc(aold_total, &d_aold))) return rc;
+    if ((rc = W.dalloc(aold_total, &d_aold)) || (rc = W.dalloc(xtotal, &d_x)) || (rc = W.dalloc(mtotal, &d_mv)))
+        return rc;
     for (size_t i = 0; i < descs.size(); ++i) descs[i].B = d_aold + jobs[i].aoff;
-    if ((rc = W.up(jobs, &d_jobs)) || (rc = W.up(descs, &d_descs)) || (rc = W.up(tiles, &d_tiles))) return rc;
+    if ((rc = W.up(jobs, &d_jobs)) || (rc = W.up(descs, &d_descs)) || (rc = W.up(tiles, &d_tiles)) ||
+        (rc = W.up(ptiles, &d_ptiles)))
+        return rc;
     for (int st = 0; st < maxsteps; ++st) {
-        int nj = job_off[st + 1] - job_off[st];
-        if ((rc = launch_gj_panel<T>(d_jobs + job_off[st], nj, smem[st], d_fr, arena, d_aold, piv, rperm, ilist,
-                                     iperm, status, s)))
+        for (const Group &g : groups[st]) {
+            if (g.reg)
+                rc = launch_gj_panel_reg<T>(d_jobs + g.off, g.cnt, g.kb, g.rows, d_fr, arena, d_x, d_mv, piv, rperm,
+                                            ilist, iperm, status, s);
+            else
+                rc = launch_gj_panel<T>(d_jobs + g.off, g.cnt, g.smem, d_fr, arena, d_x, d_mv, piv, rperm, ilist,
+                                        iperm, status, s);
+            if (rc) return rc;
+        }
+        if ((rc = launch_gj_post<T>(d_ptiles + ptile_off[st], ptile_off[st + 1] - ptile_off[st], d_jobs, d_fr, arena,
+                                    d_aold, d_x, d_mv, s)))
             return rc;
         if ((rc = gemm_batched<T>(d_descs, d_tiles + tile_off[st], tile_off[st + 1] - tile_off[st], s,
                                   step_flops[st])))
@@ -181,7 +238,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         ExpandItem *d_items;
         if ((rc = W.up(plain_items, &d_items))) return rc;
         if ((rc = launch_hss_expand<T>(d_items, (int)plain_items.size(), nullptr, nullptr, d_ef, nullptr, nullptr,
-                                       arena, keep, s)))
+                                       arena, keep, 0, s)))
             return rc;
     }
 
@@ -324,7 +381,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             int mcap = nodes[i].s[0].mcap, kcap = nodes[i].s[0].kcap;
             work[dpt].push_back(2 * i);
             work[dpt].push_back(2 * i + 1);
-            idsmem[dpt] = std::max(idsmem[dpt], sizeof(T) * ((size_t)r * mcap + r + mcap) + sizeof(int) * mcap + 16);
+            idsmem[dpt] = std::max(idsmem[dpt], sizeof(T) * ((size_t)(r + 1) * mcap + r + mcap) + sizeof(int) * mcap + 16);
             tallsmem[dpt] = std::max(tallsmem[dpt], sizeof(int) * (mcap + 2) + sizeof(T) * (size_t)mcap * kcap + 16);
         }
         for (int dpt = maxd; dpt >= 1; --dpt) {
@@ -363,8 +420,10 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
                 return rc;
         }
         std::vector<ExpandItem> items;
+        int kmax_done = 0;
         for (int c = 0; c < nc; ++c) {
             if (!done[c]) continue;
+            kmax_done = std::max(kmax_done, hfk[c]);
             int f = active[c].f;
             for (int i = node_base[c]; i < node_base[c + 1]; ++i) {
                 const NodeDev &N = nodes[i];
@@ -388,7 +447,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             ExpandItem *d_items;
             if ((rc = W.up(items, &d_items))) return rc;
             if ((rc = launch_hss_expand<T>(d_items, (int)items.size(), d_nodes, d_kout, d_ef, ws, d_iws, arena, keep,
-                                           s)))
+                                           kmax_done, s)))
                 return rc;
         }
         active.swap(next);

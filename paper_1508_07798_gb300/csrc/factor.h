@@ -27,6 +27,18 @@ struct ApplyStage {
     double fwd_vec = 0, bwd_vec = 0;      // vector entries read + written per right-hand side
 };
 
+// Vector arguments of one apply, read by the sweep kernels from device memory
+// (so that one captured graph serves every call).
+struct ApplyParams {
+    const double *x;
+    long ldx;
+    double *w;
+    long ldw;
+    double *tv;
+    long ldt;
+    int nrhs;
+};
+
 struct FrontLog {   // per-front record (rank logging, Sec. 5 empirical cost)
     int box, level, ni, nb, r, rounds, kmax, nnodes;
 };
@@ -51,5 +63,21 @@ struct hss_factor_t {
     int ntop = 0;
     double factor_bytes = 0, front_flops = 0, exec_flops = 0;
     int max_rank = 0, max_r = 0, rounds = 0;
+    // captured apply sweeps (slot 0: one right-hand side, slot 1: blocks of 4)
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int graph_kernels[2] = {0, 0};
+    hssnd::DevBuf d_aparams;
     template <class T> T *arena_ptr() const { return arena.as<T>(); }
+    // algorithmic bytes of one apply: factor entries once, vector traffic per right-hand side
+    double apply_bytes(int nrhs) const {
+        double b = 0;
+        for (const auto &st : apply)
+            b += (st.fwd_bytes + st.bwd_bytes) * (precision == HSS_FP32 ? 0.5 : 1.0) +
+                 (st.fwd_vec + st.bwd_vec) * 8.0 * nrhs;
+        return b + 2.0 * 8.0 * ndof * nrhs;   // copy-in
+    }
+    ~hss_factor_t() {
+        for (auto &g : gexec)
+            if (g) cudaGraphExecDestroy(g);
+    }
 };

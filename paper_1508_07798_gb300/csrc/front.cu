@@ -97,13 +97,12 @@ template <class T> __device__ ArgMax<T> block_argmax(ArgMax<T> x, ArgMax<T> *sh)
 //    (the sweep leaves F_ii^-1 P^t, so F_ii^-1 x = (F_ii^-1 P^t)(P x)).
 template <class T>
 __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restrict__ jobs, const FrontDev *__restrict__ fr,
-                                                    T *__restrict__ arena, T *__restrict__ aold_ws,
-                                                    int *__restrict__ piv, int *__restrict__ rperm,
-                                                    const int *__restrict__ ilist, int *__restrict__ iperm,
-                                                    int *__restrict__ status) {
+                                                    T *__restrict__ arena, T *__restrict__ xws,
+                                                    int *__restrict__ mws, int *__restrict__ piv,
+                                                    int *__restrict__ rperm, const int *__restrict__ ilist,
+                                                    int *__restrict__ iperm, int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ ArgMax<T> red[PANEL_NT / 32];
-    __shared__ T Xs[PANEL_KB_MAX * PANEL_KB_MAX];
     __shared__ T rowj[PANEL_KB_MAX];
     __shared__ int swp[PANEL_KB_MAX];
     const PanelJob J = jobs[blockIdx.x];
@@ -119,8 +118,20 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
         P = reinterpret_cast<T *>(smraw);
         ldp = hT;
         rp = reinterpret_cast<int *>(smraw + sizeof(T) * (size_t)hT * kb);
-        for (int c = 0; c < kb; ++c)
-            for (int i = threadIdx.x; i < hT; i += PANEL_NT) P[i + ldp * c] = M[(k0 + i) + ld * (k0 + c)];
+        const int tot = hT * kb;
+        for (int q0 = threadIdx.x; q0 < tot; q0 += PANEL_NT * 8) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                int q = q0 + u * PANEL_NT;
+                v[u] = q < tot ? M[(k0 + q % hT) + ld * (k0 + q / hT)] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                int q = q0 + u * PANEL_NT;
+                if (q < tot) P[(q % hT) + ldp * (q / hT)] = v[u];
+            }
+        }
     } else {
         P = M + k0 + ld * k0;
         ldp = ld;
@@ -130,27 +141,30 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
     for (int i = threadIdx.x; i < hT; i += PANEL_NT) rp[i] = k0 == 0 ? i : rglob[k0 + i];
     __syncthreads();
     int *pv = piv + F.ioff;
-    for (int j = 0; j < kb; ++j) {
-        ArgMax<T> loc{T(-1), 0x7fffffff};
-        for (int i = j + threadIdx.x; i < hT; i += PANEL_NT) {
-            T a = fabs(P[i + ldp * j]);
-            if (a > loc.v || (a == loc.v && i < loc.i)) {
-                loc.v = a;
-                loc.i = i;
-            }
+    // candidates of the first pivot column
+    ArgMax<T> loc{T(-1), 0x7fffffff};
+    for (int i = threadIdx.x; i < hT; i += PANEL_NT) {
+        T a = fabs(P[i]);
+        if (a > loc.v) {
+            loc.v = a;
+            loc.i = i;
         }
+    }
+    for (int j = 0; j < kb; ++j) {
+        // 1. pivot: largest |P(i, j)| over i >= j, ties to the lowest row
         ArgMax<T> best = block_argmax(loc, red);
         int p = best.i;
         if (best.v == T(0)) {
             if (threadIdx.x == 0) atomicExch(&status[J.front], 1);
             p = j;
         }
-        if (p != j)
-            for (int c = threadIdx.x; c < kb; c += PANEL_NT) {
-                T tmp = P[j + ldp * c];
-                P[j + ldp * c] = P[p + ldp * c];
-                P[p + ldp * c] = tmp;
-            }
+        // 2. swap rows j and p inside the panel; the pivot row goes to rowj
+        for (int c = threadIdx.x; c < kb; c += PANEL_NT) {
+            T pj = P[p + ldp * c];
+            if (p != j) P[p + ldp * c] = P[j + ldp * c];
+            P[j + ldp * c] = pj;
+            rowj[c] = pj;
+        }
         if (threadIdx.x == 0) {
             pv[k0 + j] = k0 + p;
             swp[j] = p;
@@ -159,69 +173,105 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
             rp[p] = t;
         }
         __syncthreads();
-        const T dinv = P[j + ldp * j] != T(0) ? T(1) / P[j + ldp * j] : T(0);
-        for (int c = threadIdx.x; c < kb; c += PANEL_NT) rowj[c] = (c == j) ? T(0) : P[j + ldp * c] * dinv;
-        __syncthreads();
-        // eliminate column j from every other panel row (one thread per row)
+        // 3. eliminate column j from every other row, finish row j, and gather
+        //    the candidates of column j+1 (rows > j) on the way
+        const T dinv = rowj[j] != T(0) ? T(1) / rowj[j] : T(0);
+        loc = ArgMax<T>{T(-1), 0x7fffffff};
         for (int i = threadIdx.x; i < hT; i += PANEL_NT) {
-            if (i == j) continue;
+            if (i == j) {
+                for (int c = 0; c < kb; ++c) P[j + ldp * c] = (c == j) ? dinv : rowj[c] * dinv;
+                continue;
+            }
             const T a = P[i + ldp * j];
             if (a != T(0)) {
+                const T ad = a * dinv;
 #pragma unroll 8
-                for (int c = 0; c < kb; ++c) P[i + ldp * c] -= a * rowj[c];
+                for (int c = 0; c < kb; ++c) P[i + ldp * c] -= ad * rowj[c];
+                P[i + ldp * j] = -ad;
             }
-            P[i + ldp * j] = -a * dinv;
+            if (i > j && j + 1 < kb) {
+                T v2 = fabs(P[i + ldp * (j + 1)]);
+                if (v2 > loc.v) {
+                    loc.v = v2;
+                    loc.i = i;
+                }
+            }
         }
-        __syncthreads();
-        for (int c = threadIdx.x; c < kb; c += PANEL_NT) P[j + ldp * c] = (c == j) ? dinv : rowj[c];
-        __syncthreads();
+        // the barrier inside the next block_argmax orders these writes
     }
-    // X = inverse of the pivot block, kept for the rows outside the panel
+    __syncthreads();
+    // X = inverse of the pivot block, for the rows outside the panel
+    T *Xg = xws + J.xoff;
     for (int q = threadIdx.x; q < kb * kb; q += PANEL_NT) {
         int i = q % kb, c = q / kb;
-        Xs[i + kb * c] = P[i + ldp * c];
+        Xg[q] = P[i + ldp * c];
     }
-    if (J.smem)
-        for (int c = 0; c < kb; ++c)
-            for (int i = threadIdx.x; i < hT; i += PANEL_NT) M[(k0 + i) + ld * (k0 + c)] = P[i + ldp * c];
-    for (int i = threadIdx.x; i < hT; i += PANEL_NT) rglob[k0 + i] = rp[i];
-    __syncthreads();
-    // row swaps on the columns outside the panel, in pivot order (one thread per column)
-    for (int c = threadIdx.x; c < n; c += PANEL_NT) {
-        if (c >= k0 && c < k0 + kb) continue;
-        T *col = M + ld * c + k0;
-        for (int j = 0; j < kb; ++j) {
-            int p = swp[j];
-            if (p != j) {
-                T tmp = col[j];
-                col[j] = col[p];
-                col[p] = tmp;
+    if (J.smem) {
+        // write the panel back, eight loads in flight per thread
+        const int tot = hT * kb;
+        for (int q0 = threadIdx.x; q0 < tot; q0 += PANEL_NT * 8) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                int q = q0 + u * PANEL_NT;
+                v[u] = q < tot ? P[(q % hT) + ldp * (q / hT)] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                int q = q0 + u * PANEL_NT;
+                if (q < tot) M[(k0 + q % hT) + ld * (k0 + q / hT)] = v[u];
             }
         }
     }
-    __syncthreads();
-    // Aold: the (swapped) pivot rows over all columns
-    T *Ao = aold_ws + J.aoff;
-    for (int q = threadIdx.x; q < kb * n; q += PANEL_NT) {
-        int i = q % kb, c = q / kb;
-        Ao[i + (long)kb * c] = M[(k0 + i) + ld * c];
+    for (int i = threadIdx.x; i < hT; i += PANEL_NT) rglob[k0 + i] = rp[i];
+    // the panel's swaps compose to a permutation that moves at most 2 kb rows:
+    // moves[0] = count, moves[1..64] = destinations, moves[65..128] = sources.
+    // q (position -> source position) lives in shared memory for the touched
+    // positions only: slot t < kb is position t, slot kb + j is position swp[j].
+    __shared__ int qpos[2 * PANEL_KB_MAX], qsrc[2 * PANEL_KB_MAX];
+    __shared__ int nmv;
+    if (threadIdx.x < 2 * kb) {
+        int x = threadIdx.x < kb ? threadIdx.x : swp[threadIdx.x - kb];
+        qpos[threadIdx.x] = x;
+        qsrc[threadIdx.x] = x;
     }
-    // rows outside [k0, ni): F(i, P) <- -F(i, P) X
-    int nout = n - hT;
-    for (int r = threadIdx.x; r < nout; r += PANEL_NT) {
-        int i = r < k0 ? r : r + hT;
-        T old[PANEL_KB_MAX];
-#pragma unroll
-        for (int s = 0; s < PANEL_KB_MAX; ++s)
-            if (s < kb) old[s] = M[i + ld * (k0 + s)];
-        for (int c = 0; c < kb; ++c) {
-            T acc = T(0);
-#pragma unroll
-            for (int s = 0; s < PANEL_KB_MAX; ++s)
-                if (s < kb) acc = fma(old[s], Xs[s + kb * c], acc);
-            M[i + ld * (k0 + c)] = -acc;
+    if (threadIdx.x == 0) nmv = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // slot of position x: x < kb -> x; otherwise the first kb + j with swp[j] == x
+        auto slot = [&](int x) {
+            if (x < kb) return x;
+            for (int j = 0; j < kb; ++j)
+                if (swp[j] == x) return kb + j;
+            return -1;
+        };
+        for (int j = 0; j < kb; ++j) {
+            int pj = swp[j];
+            if (pj == j) continue;
+            int a = j, b = slot(pj);
+            int t = qsrc[a];
+            qsrc[a] = qsrc[b];
+            qsrc[b] = t;
         }
     }
+    __syncthreads();
+    int *mv = mws + J.moff;
+    if (threadIdx.x < 2 * kb) {
+        int t = threadIdx.x;
+        int x = qpos[t];
+        // keep the first slot of each position only
+        bool first = t < kb || x >= kb;
+        if (t >= kb)
+            for (int j = 0; j < t - kb; ++j)
+                if (swp[j] == x) first = false;
+        if (first && qsrc[t] != x) {
+            int m = atomicAdd(&nmv, 1);
+            mv[1 + m] = x;
+            mv[1 + 2 * PANEL_KB_MAX + m] = qsrc[t];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mv[0] = nmv;
     // last panel: gather list of the apply
     if (k0 + kb == ni) {
         __syncthreads();
@@ -230,6 +280,200 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
             iperm[F.iperm_off + j] = ilist[F.iset_off + r];
         }
     }
+}
+
+// Register-resident panel: thread t owns panel rows t, t + NT, ... (R rows of
+// KB values each) for the whole panel, so the 32 pivot steps touch no shared
+// memory besides the pivot row.  Rows are not moved while pivoting: pos[]
+// (row -> position) and posinv[] (position -> row) replay the interchanges of
+// partial pivoting exactly (the search runs over rows not yet pivoted, ties to
+// the lowest position), and every row is written once, to its final position.
+template <class T, int KB, int R>
+__global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__restrict__ jobs,
+                                                        const FrontDev *__restrict__ fr, T *__restrict__ arena,
+                                                        T *__restrict__ xws, int *__restrict__ mws,
+                                                        int *__restrict__ piv, int *__restrict__ rperm,
+                                                        const int *__restrict__ ilist, int *__restrict__ iperm,
+                                                        int *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ ArgMax<T> red[PANEL_NT / 32];
+    __shared__ T rowj[KB];
+    __shared__ int nmv;
+    const PanelJob J = jobs[blockIdx.x];
+    const FrontDev F = fr[J.front];
+    T *M = arena + F.foff;
+    const long ld = F.n;
+    const int k0 = J.k0, kb = J.kb, ni = F.ni;
+    const int hT = ni - k0;
+    int *pos = reinterpret_cast<int *>(smraw);   // hT
+    int *posinv = pos + hT;                       // hT
+    int *rp = posinv + hT;                        // hT: position -> original I row
+    int *rglob = rperm + F.ioff;
+    T reg[R][KB];
+    bool done[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int i = threadIdx.x + PANEL_NT * q;
+        done[q] = false;
+#pragma unroll
+        for (int c = 0; c < KB; ++c) reg[q][c] = (i < hT && c < kb) ? M[(k0 + i) + ld * (k0 + c)] : T(0);
+    }
+    for (int i = threadIdx.x; i < hT; i += PANEL_NT) {
+        pos[i] = i;
+        posinv[i] = i;
+        rp[i] = k0 == 0 ? i : rglob[k0 + i];
+    }
+    if (threadIdx.x == 0) nmv = 0;
+    __syncthreads();
+    int *pv = piv + F.ioff;
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+        if (j >= kb) break;
+        // 1. pivot among the rows not yet pivoted: largest |value|, lowest position on ties
+        ArgMax<T> loc{T(-1), 0x7fffffff};
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = threadIdx.x + PANEL_NT * q;
+            if (i < hT && !done[q]) {
+                const T v = fabs(reg[q][j]);
+                const int p = pos[i];
+                if (v > loc.v || (v == loc.v && p < loc.i)) {
+                    loc.v = v;
+                    loc.i = p;
+                }
+            }
+        }
+        const ArgMax<T> best = block_argmax(loc, red);
+        int p = best.i;
+        if (best.v == T(0)) {
+            if (threadIdx.x == 0) atomicExch(&status[J.front], 1);
+            p = j;
+        }
+        const int x = posinv[p];   // row of the pivot
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (threadIdx.x + PANEL_NT * q == x) {
+#pragma unroll
+                for (int c = 0; c < KB; ++c) rowj[c] = reg[q][c];
+                done[q] = true;
+            }
+        if (threadIdx.x == 0) {
+            const int y = posinv[j];   // row at position j trades places with the pivot
+            posinv[j] = x;
+            posinv[p] = y;
+            pos[x] = j;
+            pos[y] = p;
+            const int t = rp[j];
+            rp[j] = rp[p];
+            rp[p] = t;
+            pv[k0 + j] = k0 + p;
+        }
+        __syncthreads();
+        // 2. Gauss-Jordan step in registers
+        const T dinv = rowj[j] != T(0) ? T(1) / rowj[j] : T(0);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = threadIdx.x + PANEL_NT * q;
+            if (i >= hT) continue;
+            if (i == x) {
+#pragma unroll
+                for (int c = 0; c < KB; ++c) reg[q][c] = (c == j) ? dinv : rowj[c] * dinv;
+            } else {
+                const T ad = reg[q][j] * dinv;
+#pragma unroll
+                for (int c = 0; c < KB; ++c) reg[q][c] -= ad * rowj[c];
+                reg[q][j] = -ad;
+            }
+        }
+        // the barriers inside the next block_argmax order rowj and pos updates
+    }
+    __syncthreads();
+    // 3. every row to its final position; the pivot block also to X
+    T *Xg = xws + J.xoff;
+    int *mv = mws + J.moff;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int i = threadIdx.x + PANEL_NT * q;
+        if (i >= hT) continue;
+        const int r = pos[i];
+#pragma unroll
+        for (int c = 0; c < KB; ++c)
+            if (c < kb) M[(k0 + r) + ld * (k0 + c)] = reg[q][c];
+        if (r < kb) {
+#pragma unroll
+            for (int c = 0; c < KB; ++c)
+                if (c < kb) Xg[r + kb * c] = reg[q][c];
+        }
+        if (r != i) {   // the other columns move the same way (k_gj_post)
+            int m = atomicAdd(&nmv, 1);
+            mv[1 + m] = r;
+            mv[1 + 2 * PANEL_KB_MAX + m] = i;
+        }
+    }
+    for (int i = threadIdx.x; i < hT; i += PANEL_NT) rglob[k0 + i] = rp[i];
+    __syncthreads();
+    if (threadIdx.x == 0) mv[0] = nmv;
+    if (k0 + kb == ni)
+        for (int j = threadIdx.x; j < ni; j += PANEL_NT) {
+            int r = j < k0 ? rglob[j] : rp[j - k0];
+            iperm[F.iperm_off + j] = ilist[F.iset_off + r];
+        }
+}
+
+// Work that follows a panel, spread over many CTAs:
+//   type 0 (32 columns outside the panel): apply the panel's row moves, then
+//          copy the (moved) pivot rows into Aold, the B operand of the update;
+//   type 1 (64 rows outside [k0, ni)): F(i, P) <- -F(i, P) X.
+template <class T>
+__global__ void __launch_bounds__(256) k_gj_post(const PanelTile *__restrict__ tiles, const PanelJob *__restrict__ jobs,
+                                             const FrontDev *__restrict__ fr, T *__restrict__ arena,
+                                             T *__restrict__ aold_ws, const T *__restrict__ xws,
+                                             const int *__restrict__ mws) {
+    __shared__ T Xs[PANEL_KB_MAX * PANEL_KB_MAX];
+    __shared__ T old[64][PANEL_KB_MAX + 1];
+    const PanelTile tl = tiles[blockIdx.x];
+    const PanelJob J = jobs[tl.job];
+    const FrontDev F = fr[J.front];
+    T *M = arena + F.foff;
+    const long ld = F.n;
+    const int k0 = J.k0, kb = J.kb, n = F.n, hT = F.ni - k0;
+    if (tl.type == 0) {
+        const int *mv = mws + J.moff;
+        const int nm = mv[0];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        T *Ao = aold_ws + J.aoff;
+        for (int cc = wid; cc < 32; cc += 8) {
+            const int c = tl.start + cc;
+            if (c >= n || (c >= k0 && c < k0 + kb)) continue;
+            T *col = M + ld * c + k0;
+            if (nm > 0) {
+                T v0 = lane < nm ? col[mv[1 + 2 * PANEL_KB_MAX + lane]] : T(0);
+                T v1 = lane + 32 < nm ? col[mv[1 + 2 * PANEL_KB_MAX + lane + 32]] : T(0);
+                __syncwarp();
+                if (lane < nm) col[mv[1 + lane]] = v0;
+                if (lane + 32 < nm) col[mv[1 + lane + 32]] = v1;
+                __syncwarp();
+            }
+            if (lane < kb) Ao[lane + (long)kb * c] = col[lane];
+        }
+        return;
+    }
+    // type 1
+    const T *Xg = xws + J.xoff;
+    for (int q = threadIdx.x; q < kb * kb; q += 256) Xs[q] = Xg[q];
+    const int nout = n - hT;
+    const int rr = threadIdx.x & 63, cg4 = threadIdx.x >> 6;   // 64 rows x 4 column groups
+    const int r = tl.start + rr;
+    const int i = r < k0 ? r : r + hT;
+    if (r < nout)
+        for (int s2 = cg4; s2 < kb; s2 += 4) old[rr][s2] = M[i + ld * (k0 + s2)];
+    __syncthreads();
+    if (r < nout)
+        for (int c = cg4; c < kb; c += 4) {
+            T acc = T(0);
+            for (int s2 = 0; s2 < kb; ++s2) acc = fma(old[rr][s2], Xs[s2 + kb * c], acc);
+            M[i + ld * (k0 + c)] = -acc;
+        }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -247,8 +491,61 @@ int launch_scatter_A(const hss_bsr *A, const StageElem *se, int nse, int *elem_s
 }
 
 template <class T>
-int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *aold, int *piv,
-                    int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s) {
+int launch_gj_post(const PanelTile *tiles, int ntiles, const PanelJob *jobs, const FrontDev *fr, T *arena, T *aold,
+                   const T *xws, const int *mws, cudaStream_t s) {
+    if (ntiles == 0) return HSS_OK;
+    HSS_PROF(sizeof(T) == 8 ? "gj_post_f64" : "gj_post_f32", s);
+    k_gj_post<T><<<ntiles, 256, 0, s>>>(tiles, jobs, fr, arena, aold, xws, mws);
+    HSS_CHECK_LAUNCH("k_gj_post");
+    return HSS_OK;
+}
+
+template <class T, int KB, int R>
+static cudaError_t launch_reg(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws,
+                              int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status,
+                              cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_gj_panel_reg<T, KB, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX);
+        configured = true;
+    }
+    k_gj_panel_reg<T, KB, R><<<njobs, PANEL_NT, smem, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
+    return cudaGetLastError();
+}
+
+// Register panel for kb <= KB and rows <= R * PANEL_NT: returns false when no
+// instantiation covers (kb, rows).
+template <class T>
+int launch_gj_panel_reg(const PanelJob *jobs, int njobs, int kb, int rows, const FrontDev *fr, T *arena, T *xws,
+                        int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s) {
+    if (njobs == 0) return HSS_OK;
+    HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s);
+    const int R = cdiv(rows, PANEL_NT);
+    const size_t smem = sizeof(int) * 3 * (size_t)rows;
+    cudaError_t e = cudaErrorInvalidValue;
+#define REG(KB_, R_)                                                                                              \
+    else if (kb <= KB_ && R <= R_) e = launch_reg<T, KB_, R_>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, \
+                                                              ilist, iperm, status, s);
+    if (false) {
+    }
+    REG(8, 1) REG(16, 1) REG(32, 1) REG(8, 2) REG(16, 2) REG(32, 2) REG(8, 3) REG(16, 3)
+    REG(32, 3) REG(8, 4) REG(16, 4) REG(8, 6) REG(16, 6) REG(8, 8) REG(8, 12)
+#undef REG
+    if (e != cudaSuccess) return cuda_fail(e, "k_gj_panel_reg");
+    return HSS_OK;
+}
+
+bool panel_reg_fits(int kb, int rows, int tsize) {
+    const int R = cdiv(rows, PANEL_NT);
+    // register budget of the panel rows: R * kb values of tsize bytes <= 96 32-bit registers
+    if (R * kb * (tsize / 4) > 96) return false;
+    if (3L * rows * 4 > PANEL_SMEM_MAX) return false;
+    return (kb <= 32 && R <= 3) || (kb <= 16 && R <= 6) || (kb <= 8 && R <= 12);
+}
+
+template <class T>
+int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws, int *mws,
+                    int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s) {
     if (njobs == 0) return HSS_OK;
     static bool configured[2] = {false, false};
     int ti = sizeof(T) == 8 ? 0 : 1;
@@ -257,7 +554,7 @@ int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev
         configured[ti] = true;
     }
     HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s);
-    k_gj_panel<T><<<njobs, PANEL_NT, smem, s>>>(jobs, fr, arena, aold, piv, rperm, ilist, iperm, status);
+    k_gj_panel<T><<<njobs, PANEL_NT, smem, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
     HSS_CHECK_LAUNCH("k_gj_panel");
     return HSS_OK;
 }
@@ -267,8 +564,16 @@ template int launch_scatter_A<double>(const hss_bsr *, const StageElem *, int, i
 template int launch_scatter_A<float>(const hss_bsr *, const StageElem *, int, int *, const FrontDev *, float *,
                                      cudaStream_t);
 template int launch_gj_panel<double>(const PanelJob *, int, size_t, const FrontDev *, double *, double *, int *,
-                                     int *, const int *, int *, int *, cudaStream_t);
+                                     int *, int *, const int *, int *, int *, cudaStream_t);
 template int launch_gj_panel<float>(const PanelJob *, int, size_t, const FrontDev *, float *, float *, int *, int *,
-                                    const int *, int *, int *, cudaStream_t);
+                                    int *, const int *, int *, int *, cudaStream_t);
+template int launch_gj_panel_reg<double>(const PanelJob *, int, int, int, const FrontDev *, double *, double *,
+                                         int *, int *, int *, const int *, int *, int *, cudaStream_t);
+template int launch_gj_panel_reg<float>(const PanelJob *, int, int, int, const FrontDev *, float *, float *, int *,
+                                        int *, int *, const int *, int *, int *, cudaStream_t);
+template int launch_gj_post<double>(const PanelTile *, int, const PanelJob *, const FrontDev *, double *, double *,
+                                    const double *, const int *, cudaStream_t);
+template int launch_gj_post<float>(const PanelTile *, int, const PanelJob *, const FrontDev *, float *, float *,
+                                   const float *, const int *, cudaStream_t);
 
 }  // namespace hssnd

@@ -33,13 +33,29 @@ struct PanelJob {
     int k0, kb;
     int smem;         // 1: panel in shared memory
     long aoff;        // offset of this job's Aold (kb x n) in the workspace
+    long xoff;        // offset of the pivot-block inverse X (kb x kb)
+    long moff;        // offset of the row-move list (1 + 4 * PANEL_KB_MAX ints)
+};
+
+// A tile of the post-panel work (see k_gj_post).
+struct PanelTile {
+    int job;
+    int type;         // 0: 32 columns outside the panel; 1: 64 rows outside [k0, ni)
+    int start;
 };
 
 template <class T>
 int launch_scatter_A(const hss_bsr *A, const StageElem *se, int nse, int *elem_slot, const FrontDev *fr, T *arena,
                      cudaStream_t s);
 template <class T>
-int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *aold, int *piv,
-                    int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s);
+int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws, int *mws,
+                    int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s);
+template <class T>
+int launch_gj_panel_reg(const PanelJob *jobs, int njobs, int kb, int rows, const FrontDev *fr, T *arena, T *xws,
+                        int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s);
+bool panel_reg_fits(int kb, int rows, int tsize);
+template <class T>
+int launch_gj_post(const PanelTile *tiles, int ntiles, const PanelJob *jobs, const FrontDev *fr, T *arena, T *aold,
+                   const T *xws, const int *mws, cudaStream_t s);
 
 }  // namespace hssnd

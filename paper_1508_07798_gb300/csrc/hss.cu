@@ -60,11 +60,11 @@ template <class T> __device__ T blk_sum(T x, T *sh) {
     return r;
 }
 
-// Householder step j on A (r x m, ld r), columns >= j; returns R_jj.
-template <class T> __device__ void householder_step(T *A, int r, int m, int j, T nrm, T *v, T *shs) {
-    T x0 = A[j + (long)r * j];
+// Householder step j on A (r x m, leading dimension lda), columns >= j.
+template <class T> __device__ void householder_step(T *A, int r, int lda, int m, int j, T nrm, T *v, T *shs) {
+    T x0 = A[j + (long)lda * j];
     T alpha = (x0 != T(0)) ? -copysign(nrm, x0) : -nrm;
-    for (int i = j + threadIdx.x; i < r; i += ID_NT) v[i] = (i == j) ? x0 - alpha : A[i + (long)r * j];
+    for (int i = j + threadIdx.x; i < r; i += ID_NT) v[i] = (i == j) ? x0 - alpha : A[i + (long)lda * j];
     __syncthreads();
     T part = 0;
     for (int i = j + threadIdx.x; i < r; i += ID_NT) part += v[i] * v[i];
@@ -73,14 +73,14 @@ template <class T> __device__ void householder_step(T *A, int r, int m, int j, T
     if (vn > T(0)) {
         for (int c = j + 1 + w; c < m; c += ID_NT / 32) {
             T d = 0;
-            for (int i = j + lane; i < r; i += 32) d += v[i] * A[i + (long)r * c];
+            for (int i = j + lane; i < r; i += 32) d += v[i] * A[i + (long)lda * c];
             for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
             T coef = T(2) * d / vn;
-            for (int i = j + lane; i < r; i += 32) A[i + (long)r * c] -= coef * v[i];
+            for (int i = j + lane; i < r; i += 32) A[i + (long)lda * c] -= coef * v[i];
         }
     }
     __syncthreads();
-    for (int i = j + threadIdx.x; i < r; i += ID_NT) A[i + (long)r * j] = (i == j) ? alpha : T(0);
+    for (int i = j + threadIdx.x; i < r; i += ID_NT) A[i + (long)lda * j] = (i == j) ? alpha : T(0);
     __syncthreads();
 }
 
@@ -105,8 +105,9 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
         ka = kout[2 * N.a + side];
         m = ka + kout[2 * N.b + side];
     }
-    T *A = reinterpret_cast<T *>(smraw);                 // r x m, ld r
-    T *v = A + (long)r * mcap;                            // r
+    const int lda = r + 1;                                 // odd: column-wise access is conflict free
+    T *A = reinterpret_cast<T *>(smraw);                 // r x m, ld lda
+    T *v = A + (long)lda * mcap;                          // r
     T *nrm2 = v + r;                                      // mcap
     int *order = reinterpret_cast<int *>(nrm2 + mcap);    // mcap
     T *L = ws + me.loff;                                  // m x r, ld mcap
@@ -114,28 +115,53 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
     const long lds = C.lds;
 
     // ---- local samples
-    for (int idx = threadIdx.x; idx < m * r; idx += ID_NT) {
-        int i = idx % m, j = idx / m;
-        T val;
-        if (leaf) {
-            const T *Ysrc = ws + (side == 0 ? C.yoff : C.zoff);
-            val = Ysrc[(N.lo + i) + (long)C.nb * j];
-        } else {
-            bool fa = i < ka;
-            int child = fa ? N.a : N.b, other = fa ? N.b : N.a, ii = fa ? i : i - ka;
-            const NodeSide cs = nodes[child].s[side];
-            const NodeSide os = nodes[other].s[1 - side];
-            int ko = kout[2 * other + (1 - side)];
-            val = ws[cs.skoff + ii + (long)cs.kcap * j];
-            int gi = iws[cs.skioff + ii];
-            for (int q = 0; q < ko; ++q) {
-                int go = iws[os.skioff + q];
-                T sv = side == 0 ? S[gi + lds * go] : S[go + lds * gi];
-                val -= sv * ws[os.tloff + q + (long)os.kcap * j];
-            }
+    if (leaf) {
+        const T *Ysrc = ws + (side == 0 ? C.yoff : C.zoff);
+        for (int idx = threadIdx.x; idx < m * r; idx += ID_NT) {
+            int i = idx % m, j = idx / m;
+            L[i + (long)mcap * j] = Ysrc[(N.lo + i) + (long)C.nb * j];
         }
-        L[i + (long)mcap * j] = val;
-        A[j + (long)r * i] = val;
+        __syncthreads();   // L is read below under a different thread mapping
+    } else {
+        // coupling blocks staged in shared memory (A's space is free until the QR):
+        //   rows: S(J_a, K_b) and S(J_b, K_a); columns: S(J_b, K_a)^t and S(J_a, K_b)^t
+        const NodeSide ca = nodes[N.a].s[side], cb = nodes[N.b].s[side];
+        const NodeSide oa = nodes[N.a].s[1 - side], ob = nodes[N.b].s[1 - side];
+        const int kb_ = m - ka;
+        const int koa = kout[2 * N.a + (1 - side)], kob = kout[2 * N.b + (1 - side)];
+        T *Ba = A;                       // ka x kob (ld ka)
+        T *Bb = A + (long)ka * kob;      // kb x koa (ld kb)
+        for (int idx = threadIdx.x; idx < ka * kob; idx += ID_NT) {
+            int i = idx % ka, q = idx / ka;
+            int gi = iws[ca.skioff + i], go = iws[ob.skioff + q];
+            Ba[idx] = side == 0 ? S[gi + lds * go] : S[go + lds * gi];
+        }
+        for (int idx = threadIdx.x; idx < kb_ * koa; idx += ID_NT) {
+            int i = idx % kb_, q = idx / kb_;
+            int gi = iws[cb.skioff + i], go = iws[oa.skioff + q];
+            Bb[idx] = side == 0 ? S[gi + lds * go] : S[go + lds * gi];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < m * r; idx += ID_NT) {
+            int i = idx % m, j = idx / m;
+            T val;
+            if (i < ka) {
+                val = ws[ca.skoff + i + (long)ca.kcap * j];
+                const T *tl = ws + ob.tloff + (long)ob.kcap * j;
+                for (int q = 0; q < kob; ++q) val -= Ba[i + ka * q] * tl[q];
+            } else {
+                int ii = i - ka;
+                val = ws[cb.skoff + ii + (long)cb.kcap * j];
+                const T *tl = ws + oa.tloff + (long)oa.kcap * j;
+                for (int q = 0; q < koa; ++q) val -= Bb[ii + kb_ * q] * tl[q];
+            }
+            L[i + (long)mcap * j] = val;
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < m * r; idx += ID_NT) {
+        int j = idx % r, i = idx / r;
+        A[j + (long)lda * i] = L[i + (long)mcap * j];
     }
     for (int c = threadIdx.x; c < m; c += ID_NT) order[c] = c;
     __syncthreads();
@@ -146,7 +172,7 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int c = w; c < m; c += ID_NT / 32) {
         T sq = 0;
-        for (int i = lane; i < r; i += 32) sq += A[i + (long)r * c] * A[i + (long)r * c];
+        for (int i = lane; i < r; i += 32) sq += A[i + (long)lda * c] * A[i + (long)lda * c];
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
         if (lane == 0) nrm2[c] = sq;
     }
@@ -176,42 +202,42 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
         }
         if (p != j)
             for (int i = threadIdx.x; i < r; i += ID_NT) {
-                T t = A[i + (long)r * j];
-                A[i + (long)r * j] = A[i + (long)r * p];
-                A[i + (long)r * p] = t;
+                T t = A[i + (long)lda * j];
+                A[i + (long)lda * j] = A[i + (long)lda * p];
+                A[i + (long)lda * p] = t;
             }
         __syncthreads();
-        const T x0 = A[j + (long)r * j];
+        const T x0 = A[j + (long)lda * j];
         const T alpha = (x0 != T(0)) ? -copysign(nrm, x0) : -nrm;
         const T vn = (x0 - alpha) * (x0 - alpha) + (nn2 - x0 * x0);
-        for (int i = j + threadIdx.x; i < r; i += ID_NT) v[i] = (i == j) ? x0 - alpha : A[i + (long)r * j];
+        for (int i = j + threadIdx.x; i < r; i += ID_NT) v[i] = (i == j) ? x0 - alpha : A[i + (long)lda * j];
         __syncthreads();
         for (int c = j + 1 + w; c < m; c += ID_NT / 32) {
             T d = 0;
-            for (int i = j + lane; i < r; i += 32) d += v[i] * A[i + (long)r * c];
+            for (int i = j + lane; i < r; i += 32) d += v[i] * A[i + (long)lda * c];
             for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
             const T coef = vn > T(0) ? T(2) * d / vn : T(0);
             T sq = 0;
             for (int i = j + lane; i < r; i += 32) {
-                T a = A[i + (long)r * c] - coef * v[i];
-                A[i + (long)r * c] = a;
+                T a = A[i + (long)lda * c] - coef * v[i];
+                A[i + (long)lda * c] = a;
                 if (i > j) sq += a * a;
             }
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
             if (lane == 0) nrm2[c] = sq;
         }
-        for (int i = j + threadIdx.x; i < r; i += ID_NT) A[i + (long)r * j] = (i == j) ? alpha : T(0);
+        for (int i = j + threadIdx.x; i < r; i += ID_NT) A[i + (long)lda * j] = (i == j) ? alpha : T(0);
         k = j + 1;
     }
     __syncthreads();
     // T = R11^-1 R12 in place (one thread per column of R12)
     auto solve_T_inplace = [&]() {
         for (int c = k + threadIdx.x; c < m; c += ID_NT) {
-            T *col = A + (long)r * c;
+            T *col = A + (long)lda * c;
             for (int i = k - 1; i >= 0; --i) {
                 T t = col[i];
-                for (int l = i + 1; l < k; ++l) t -= A[i + (long)r * l] * col[l];
-                col[i] = t / A[i + (long)r * i];
+                for (int l = i + 1; l < k; ++l) t -= A[i + (long)lda * l] * col[l];
+                col[i] = t / A[i + (long)lda * i];
             }
         }
         __syncthreads();
@@ -224,7 +250,7 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
         AM<T> loc{T(-1), INT_MAX};
         for (int q = threadIdx.x; q < k * nc; q += ID_NT) {
             int i = q / nc, jj = q % nc;  // row-major linear index q
-            T a = fabs(A[i + (long)r * (k + jj)]);
+            T a = fabs(A[i + (long)lda * (k + jj)]);
             if (a > loc.v || (a == loc.v && q < loc.i)) {
                 loc.v = a;
                 loc.i = q;
@@ -242,14 +268,14 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
         __syncthreads();
         for (int idx = threadIdx.x; idx < m * r; idx += ID_NT) {
             int c = idx / r, i = idx % r;
-            A[i + (long)r * c] = L[order[c] + (long)mcap * i];
+            A[i + (long)lda * c] = L[order[c] + (long)mcap * i];
         }
         __syncthreads();
         for (int j = 0; j < k; ++j) {
             T part = 0;
-            for (int i = j + threadIdx.x; i < r; i += ID_NT) part += A[i + (long)r * j] * A[i + (long)r * j];
+            for (int i = j + threadIdx.x; i < r; i += ID_NT) part += A[i + (long)lda * j] * A[i + (long)lda * j];
             T nn = sqrt(blk_sum(part, shs));
-            householder_step(A, r, m, j, nn, v, shs);
+            householder_step(A, r, lda, m, j, nn, v, shs);
         }
         solve_T_inplace();
     }
@@ -258,7 +284,7 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
     T *Tm = ws + me.toff;
     for (int idx = threadIdx.x; idx < k * (m - k); idx += ID_NT) {
         int i = idx % k, jj = idx / k;
-        Tm[i + (long)kcap * jj] = A[i + (long)r * (k + jj)];
+        Tm[i + (long)kcap * jj] = A[i + (long)lda * (k + jj)];
     }
     if (threadIdx.x == 0) {
         kout[2 * node + side] = k;
@@ -358,6 +384,7 @@ __global__ void k_hss_expand(const ExpandItem *__restrict__ items, const NodeDev
                              const int *__restrict__ kout, const ExpandFront *__restrict__ efs,
                              const T *__restrict__ ws, const int *__restrict__ iws, T *__restrict__ arena,
                              T *__restrict__ keep) {
+    extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ T Pm[128 * EXP_TILE];
     const ExpandItem it = items[blockIdx.x];
     const ExpandFront E = efs[it.cf];
@@ -380,15 +407,23 @@ __global__ void k_hss_expand(const ExpandItem *__restrict__ items, const NodeDev
     const int Ra = Na.hi - Na.lo, Rb = Nb.hi - Nb.lo;
     const T *Ua = ws + ua.talloff, *Vb = ws + vb.talloff;
     const int *Ja = iws + ua.skioff, *Kb = iws + vb.skioff;
+    T *Sab = reinterpret_cast<T *>(smraw);          // ka x kb (ld ka)
+    T *Vt = Sab + (long)ka * kb_;                   // 32 x kb (ld 32)
+    for (int idx = threadIdx.x; idx < ka * kb_; idx += blockDim.x) {
+        int q = idx % ka, q2 = idx / ka;
+        Sab[idx] = S[Ja[q] + E.lds * Kb[q2]];
+    }
+    for (int idx = threadIdx.x; idx < EXP_TILE * kb_; idx += blockDim.x) {
+        int jj = idx % EXP_TILE, q2 = idx / EXP_TILE;
+        int col = it.c0 + jj;
+        Vt[idx] = col < it.chi ? Vb[(col - Nb.lo) + (long)Rb * q2] : T(0);
+    }
+    __syncthreads();
     // Pm = S(J_a, K_b) V^tall_b(cols of this tile)^t   (ka x 32)
     for (int idx = threadIdx.x; idx < ka * EXP_TILE; idx += blockDim.x) {
         int q = idx % ka, jj = idx / ka;
-        int col = it.c0 + jj;
         T acc = 0;
-        if (col < it.chi) {
-            int gq = Ja[q];
-            for (int q2 = 0; q2 < kb_; ++q2) acc += S[gq + E.lds * Kb[q2]] * Vb[(col - Nb.lo) + (long)Rb * q2];
-        }
+        for (int q2 = 0; q2 < kb_; ++q2) acc += Sab[q + ka * q2] * Vt[jj + EXP_TILE * q2];
         Pm[q + ka * jj] = acc;
     }
     __syncthreads();
@@ -436,10 +471,19 @@ int launch_hss_tall(const NodeDev *nodes, const int *work, int nwork, const int 
 
 template <class T>
 int launch_hss_expand(const ExpandItem *items, int nitems, const NodeDev *nodes, const int *kout,
-                      const ExpandFront *ef, const T *ws, const int *iws, T *arena, T *keep, cudaStream_t s) {
+                      const ExpandFront *ef, const T *ws, const int *iws, T *arena, T *keep, int kmax,
+                      cudaStream_t s) {
     if (nitems == 0) return HSS_OK;
     HSS_PROF("hss_expand", s);
-    k_hss_expand<T><<<nitems, 256, 0, s>>>(items, nodes, kout, ef, ws, iws, arena, keep);
+    static bool configured[2] = {false, false};
+    int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!configured[ti]) {
+        cudaFuncSetAttribute(k_hss_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        configured[ti] = true;
+    }
+    // S(J_a,K_b) (kmax x kmax) and a 32 x kmax tile of V^tall
+    size_t smem = sizeof(T) * (size_t)(kmax * kmax + EXP_TILE * kmax);
+    k_hss_expand<T><<<nitems, 256, smem, s>>>(items, nodes, kout, ef, ws, iws, arena, keep);
     HSS_CHECK_LAUNCH("k_hss_expand");
     return HSS_OK;
 }
@@ -450,7 +494,7 @@ int launch_hss_expand(const ExpandItem *items, int nitems, const NodeDev *nodes,
     template int launch_hss_tall<T>(const NodeDev *, const int *, int, const int *, T *, int *, size_t,        \
                                     cudaStream_t);                                                             \
     template int launch_hss_expand<T>(const ExpandItem *, int, const NodeDev *, const int *, const ExpandFront *, \
-                                      const T *, const int *, T *, T *, cudaStream_t);
+                                      const T *, const int *, T *, T *, int, cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

@@ -64,6 +64,7 @@ int launch_hss_tall(const NodeDev *nodes, const int *work, int nwork, const int 
                     cudaStream_t s);
 template <class T>
 int launch_hss_expand(const ExpandItem *items, int nitems, const NodeDev *nodes, const int *kout,
-                      const ExpandFront *ef, const T *ws, const int *iws, T *arena, T *keep, cudaStream_t s);
+                      const ExpandFront *ef, const T *ws, const int *iws, T *arena, T *keep, int kmax,
+                      cudaStream_t s);
 
 }  // namespace hssnd

@@ -58,9 +58,14 @@ void drain_locked() {
 }
 }  // namespace
 
+thread_local bool g_capturing = false;
+
 bool prof_enabled() { return g_on; }
+void prof_set_capture(bool on) { g_capturing = on; }
+void prof_add_launches(long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 ProfScope::ProfScope(const char *name, cudaStream_t stream, double work) : cls(-1), s(stream), slot(-1) {
+    if (g_capturing) return;
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_on) return;
     std::lock_guard<std::mutex> lk(g_mu);

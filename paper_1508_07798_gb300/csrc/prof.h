@@ -17,6 +17,8 @@ struct ProfScope {
 };
 
 bool prof_enabled();
+void prof_set_capture(bool on);     // while a graph is being captured, scopes record nothing
+void prof_add_launches(long n);     // kernels executed by a graph launch
 
 }  // namespace hssnd
 
