@@ -14,98 +14,100 @@
 #include "factor.h"
 #include "prof.h"
 
-#include <cooperative_groups.h>
-namespace cg = cooperative_groups;
+#include <algorithm>
 
 namespace hssnd {
 
 constexpr int AP_NT = 256;
-constexpr int AP_RG = AP_NT / APPLY_ROWS;   // column groups per CTA
-constexpr int AP_ZC = 1024;                  // z entries staged per chunk (per right-hand side block)
+constexpr int AP_WPB = AP_NT / 32;   // warps (work items) per CTA
 
-// One cluster of `cs` CTAs per row tile of one front; CTA rank r multiplies the
-// tile's rows by its 1/cs share of the columns, the partial sums meet in the
-// rank-0 CTA's registers through distributed shared memory (fixed order).
+// One warp per work item = (front, 32-row tile, column chunk of at most
+// APPLY_CHUNK columns).  Lane l owns row row0 + l; x is gathered one value per
+// lane and broadcast by shuffles; 32 matrix loads per lane are in flight per
+// group of 32 columns.  A tile split over several chunks writes partial sums;
+// the last warp to finish (atomic ticket) adds them in chunk order and writes
+// the result, so the sum order is fixed.  No barrier, no waiting.
 //   FWD: y = [F_ii^-1 P^t ; -F_bi F_ii^-1 P^t] x(Iperm)  ->  t = y[0,ni), x_B += y[ni,n)
 //   BWD: x_I = t - W x_B
 template <class T, int RB, bool FWD>
-__global__ void __launch_bounds__(AP_NT) k_apply(const ApplyTile *__restrict__ tiles, const FrontDev *__restrict__ fr,
-                                               const T *__restrict__ arena, const int *__restrict__ iperm,
-                                               const int *__restrict__ ilist, const int *__restrict__ blist,
-                                               const ApplyParams *__restrict__ prm) {
+__global__ void __launch_bounds__(AP_NT) k_apply(const ApplyItem *__restrict__ items, int nitems,
+                                               const FrontDev *__restrict__ fr, const T *__restrict__ arena,
+                                               const int *__restrict__ iperm, const int *__restrict__ ilist,
+                                               const int *__restrict__ blist, const ApplyParams *__restrict__ prm,
+                                               double *__restrict__ part, int *__restrict__ tickets) {
+    const int lane = threadIdx.x & 31;
+    const int item = blockIdx.x * AP_WPB + (threadIdx.x >> 5);
+    if (item >= nitems) return;   // whole warps leave together
     double *__restrict__ w = prm->w;
     const long ldw = prm->ldw;
     double *__restrict__ tv = prm->tv;
     const long ldt = prm->ldt;
-    const int nrhs = prm->nrhs;
-    __shared__ double zs[AP_ZC * RB];
-    __shared__ double red[AP_RG][APPLY_ROWS][RB];
-    __shared__ double part[RB][APPLY_ROWS];
-    cg::cluster_group cl = cg::this_cluster();
-    const int cs = (int)cl.num_blocks(), crank = (int)cl.block_rank();
-    const ApplyTile tl = tiles[blockIdx.x / cs];
-    const FrontDev F = fr[tl.front];
+    const int nrhs = prm->nrhs;   // <= RB
+    const ApplyItem it = items[item];
+    const FrontDev F = fr[it.front];
     const T *M = arena + F.foff;
-    const int ncols = FWD ? F.ni : F.nb, colbase = FWD ? 0 : F.ni, nrows = FWD ? F.n : F.ni;
-    const int chunk = (ncols + cs - 1) / cs;
-    const int c_lo = min(ncols, crank * chunk), c_hi = min(ncols, c_lo + chunk);
-    const int tx = threadIdx.x % APPLY_ROWS, ty = threadIdx.x / APPLY_ROWS;
-    const int i = tl.row0 + tx;
-    for (int rb0 = 0; rb0 < nrhs; rb0 += RB) {
-        double acc[RB];
+    const int colbase = FWD ? 0 : F.ni, nrows = FWD ? F.n : F.ni;
+    const int i = it.row0 + lane;
+    const bool rowok = i < nrows;
+    // arithmetic in the factor's precision (FP32 factors: FP32 products and sums;
+    // GB300's FP64 pipe is a small fraction of its FP32 rate)
+    T acc[RB];
 #pragma unroll
-        for (int q = 0; q < RB; ++q) acc[q] = 0.0;
-        for (int c0 = c_lo; c0 < c_hi; c0 += AP_ZC) {
-            const int cn = min(AP_ZC, c_hi - c0);
-            __syncthreads();
-            for (int idx = threadIdx.x; idx < cn * RB; idx += AP_NT) {
-                int c = idx % cn, q = idx / cn;
-                int rr = rb0 + q;
-                int dof = FWD ? iperm[F.iperm_off + c0 + c] : blist[F.bset_off + c0 + c];
-                zs[c + AP_ZC * q] = rr < nrhs ? w[dof + ldw * rr] : 0.0;
-            }
-            __syncthreads();
-            if (i < nrows) {
-                const T *col = M + i + (long)F.n * (colbase + c0);
-#pragma unroll 8
-                for (int c = ty; c < cn; c += AP_RG) {
-                    double m = (double)col[(long)F.n * c];
+    for (int r = 0; r < RB; ++r) acc[r] = T(0);
+    for (int cg = it.c0; cg < it.c1; cg += 32) {
+        const int c = cg + lane;
+        T z[RB];
+        if (c < it.c1) {
+            const int dof = FWD ? iperm[F.iperm_off + c] : blist[F.bset_off + c];
 #pragma unroll
-                    for (int q = 0; q < RB; ++q) acc[q] = fma(m, zs[c + AP_ZC * q], acc[q]);
-                }
-            }
+            for (int r = 0; r < RB; ++r) z[r] = r < nrhs ? (T)w[dof + ldw * r] : T(0);
+        } else {
+#pragma unroll
+            for (int r = 0; r < RB; ++r) z[r] = T(0);
         }
+        T m[32];
+        const T *col = M + i + (long)F.n * (colbase + cg);
 #pragma unroll
-        for (int q = 0; q < RB; ++q) red[ty][tx][q] = acc[q];
-        __syncthreads();
-        if (ty == 0) {
+        for (int q = 0; q < 32; ++q) m[q] = (rowok && cg + q < it.c1) ? col[(long)F.n * q] : T(0);
 #pragma unroll
-            for (int q = 0; q < RB; ++q) {
-                double y = 0.0;
-                for (int g = 0; g < AP_RG; ++g) y += red[g][tx][q];
-                part[q][tx] = y;
-            }
+        for (int q = 0; q < 32; ++q) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r) acc[r] = fma(m[q], __shfl_sync(0xffffffffu, z[r], q), acc[r]);
         }
-        cl.sync();
-        if (crank == 0 && ty == 0 && i < nrows) {
+    }
+    if (it.nchunk > 1) {
+        T *mine = reinterpret_cast<T *>(part) + (long)item * 32 * RB;
 #pragma unroll
-            for (int q = 0; q < RB; ++q) {
-                int rr = rb0 + q;
-                if (rr >= nrhs) break;
-                double y = 0.0;
-                for (int r = 0; r < cs; ++r) y += cl.map_shared_rank(&part[q][0], r)[tx];
-                if (FWD) {
-                    if (i < F.ni)
-                        tv[ilist[F.iset_off + i] + ldt * rr] = y;
-                    else
-                        w[blist[F.bset_off + i - F.ni] + ldw * rr] += y;
-                } else {
-                    int dof = ilist[F.iset_off + i];
-                    w[dof + ldw * rr] = tv[dof + ldt * rr] - y;
-                }
-            }
+        for (int r = 0; r < RB; ++r) mine[r * 32 + lane] = acc[r];
+        __threadfence();
+        int ticket = 0;
+        if (lane == 0) ticket = atomicAdd(&tickets[it.tile], 1);
+        ticket = __shfl_sync(0xffffffffu, ticket, 0);
+        if (ticket != it.nchunk - 1) return;
+        __threadfence();
+        const T *first = reinterpret_cast<const T *>(part) + (long)it.first * 32 * RB;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            T y = T(0);
+            for (int ch = 0; ch < it.nchunk; ++ch) y += __ldcg(first + (long)ch * 32 * RB + r * 32 + lane);
+            acc[r] = y;
         }
-        cl.sync();
+        if (lane == 0) tickets[it.tile] = 0;   // ready for the next apply
+    }
+    if (!rowok) return;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        if (r >= nrhs) break;
+        const double y = (double)acc[r];
+        if (FWD) {
+            if (i < F.ni)
+                tv[ilist[F.iset_off + i] + ldt * r] = y;
+            else
+                w[blist[F.bset_off + i - F.ni] + ldw * r] += y;
+        } else {
+            const int dof = ilist[F.iset_off + i];
+            w[dof + ldw * r] = tv[dof + ldt * r] - y;
+        }
     }
 }
 
@@ -125,25 +127,6 @@ __global__ void k_apply_copyin(const ApplyParams *__restrict__ prm, long N) {
     }
 }
 
-template <class T, int RB, bool FWD>
-static cudaError_t launch_apply(int ntiles, int cs, cudaStream_t s, const ApplyTile *tiles, const FrontDev *fr,
-                                const T *arena, const int *iperm, const int *ilist, const int *blist,
-                                const ApplyParams *prm) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ntiles * cs);
-    cfg.blockDim = dim3(AP_NT);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_apply<T, RB, FWD>, tiles, fr, arena, iperm, ilist, blist, prm);
-}
-
 // The whole sweep (copy-in, forward levels, top block, backward levels) as
 // one kernel sequence on stream s; parameters come from f->d_aparams.
 template <class T, int RB> static int record_sweep(const hss_factor_t *f, cudaStream_t s, int &nk) {
@@ -159,11 +142,17 @@ template <class T, int RB> static int record_sweep(const hss_factor_t *f, cudaSt
             const int *ilist = st.top ? f->d_topset.as<int>() : f->tree->d_iset.as<int>();
             const int nt = fwd ? st.nfwd : st.nbwd;
             if (nt == 0) continue;
-            cudaError_t e = fwd ? launch_apply<T, RB, true>(nt, st.cs_fwd, s, st.d_fwd, st.d_fronts, arena,
-                                                              f->d_iperm.as<int>(), ilist, f->tree->d_bset.as<int>(), prm)
-                                : launch_apply<T, RB, false>(nt, st.cs_bwd, s, st.d_bwd, st.d_fronts, arena,
-                                                               f->d_iperm.as<int>(), ilist, f->tree->d_bset.as<int>(), prm);
-            if (e != cudaSuccess) return cuda_fail(e, "k_apply launch");
+            const ApplyItem *itm = fwd ? st.d_fwd : st.d_bwd;
+            double *part = f->d_apart.as<double>() + (fwd ? st.part_fwd : st.part_bwd) * 32 * 4;
+            int *tk = f->d_tickets.as<int>() + (fwd ? st.tk_fwd : st.tk_bwd);
+            if (fwd)
+                k_apply<T, RB, true><<<cdiv(nt, AP_WPB), AP_NT, 0, s>>>(itm, nt, st.d_fronts, arena,
+                                                                        f->d_iperm.as<int>(), ilist,
+                                                                        f->tree->d_bset.as<int>(), prm, part, tk);
+            else
+                k_apply<T, RB, false><<<cdiv(nt, AP_WPB), AP_NT, 0, s>>>(itm, nt, st.d_fronts, arena,
+                                                                         f->d_iperm.as<int>(), ilist,
+                                                                         f->tree->d_bset.as<int>(), prm, part, tk);
             ++nk;
         }
     }
@@ -196,19 +185,22 @@ template <class T> static int build_graph(hss_factor_t *f, int slot) {
 int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s) {
     hss_factor_t *mf = const_cast<hss_factor_t *>(f);
     int rc;
-    if ((rc = mf->tvec.alloc(sizeof(double) * (size_t)f->ndof * nrhs))) return rc;
+    if ((rc = mf->tvec.alloc(sizeof(double) * (size_t)f->ndof * std::min(nrhs, 4)))) return rc;
     if ((rc = mf->d_aparams.alloc(sizeof(ApplyParams)))) return rc;
     const int slot = nrhs == 1 ? 0 : 1;
     if (!f->gexec[slot]) {
         rc = f->precision == HSS_FP32 ? build_graph<float>(mf, slot) : build_graph<double>(mf, slot);
         if (rc) return rc;
     }
-    ApplyParams pv{x, ldx, y, ldy, mf->tvec.as<double>(), (long)f->ndof, nrhs};
     HSS_PROF("apply", s, f->apply_bytes(nrhs));
-    prof_add_launches(f->graph_kernels[slot]);
-    k_apply_set<<<1, 32, 0, s>>>(mf->d_aparams.as<ApplyParams>(), pv);
-    HSS_CHECK_LAUNCH("k_apply_set");
-    HSS_CUDA(cudaGraphLaunch(f->gexec[slot], s));
+    for (int k = 0; k < nrhs; k += 4) {   // one sweep per block of up to 4 right-hand sides
+        ApplyParams pv{x + ldx * k, ldx, y + ldy * k, ldy, mf->tvec.as<double>(), (long)f->ndof,
+                       std::min(4, nrhs - k)};
+        prof_add_launches(f->graph_kernels[slot]);
+        k_apply_set<<<1, 32, 0, s>>>(mf->d_aparams.as<ApplyParams>(), pv);
+        HSS_CHECK_LAUNCH("k_apply_set");
+        HSS_CUDA(cudaGraphLaunch(f->gexec[slot], s));
+    }
     return HSS_OK;
 }
 

@@ -466,41 +466,48 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
 }
 
 template <class T>
-int build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, DevBuf &&d_fronts, bool top, cudaStream_t s) {
+int build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, DevBuf &&d_fronts, bool top, long &part_total,
+                      int &tk_total, cudaStream_t s) {
     as.top = top;
     as.nfronts = (int)fr.size();
     as.fronts_buf = std::move(d_fronts);
     as.d_fronts = as.fronts_buf.as<FrontDev>();
-    std::vector<ApplyTile> fw, bw;
+    std::vector<ApplyItem> items[2];
+    int tiles[2] = {0, 0};
     as.fwd_bytes = as.bwd_bytes = as.fwd_vec = as.bwd_vec = 0;
     for (int f = 0; f < (int)fr.size(); ++f) {
         if (fr[f].ni == 0) continue;
-        for (int r0 = 0; r0 < fr[f].n; r0 += APPLY_ROWS) fw.push_back({f, r0});
-        for (int r0 = 0; r0 < fr[f].ni; r0 += APPLY_ROWS) bw.push_back({f, r0});
+        for (int pass = 0; pass < 2; ++pass) {
+            const int nrows = pass == 0 ? fr[f].n : fr[f].ni;
+            const int ncols = pass == 0 ? fr[f].ni : fr[f].nb;
+            const int nch = std::max(1, cdiv(ncols, APPLY_CHUNK));
+            for (int r0 = 0; r0 < nrows; r0 += 32) {
+                const int first = (int)items[pass].size();
+                const int tile = nch > 1 ? tiles[pass]++ : -1;
+                for (int ch = 0; ch < nch; ++ch)
+                    items[pass].push_back({f, r0, std::min(ncols, ch * APPLY_CHUNK),
+                                           std::min(ncols, (ch + 1) * APPLY_CHUNK), tile, first, nch});
+            }
+        }
         as.fwd_bytes += 8.0 * fr[f].n * (double)fr[f].ni;
         as.bwd_bytes += 8.0 * fr[f].ni * (double)fr[f].nb;
         as.fwd_vec += fr[f].ni + fr[f].ni + 2.0 * fr[f].nb;      // x_I read, t written, x_B read+written
         as.bwd_vec += fr[f].nb + fr[f].ni + fr[f].ni;           // x_B read, t read, x_I written
     }
-    // split the columns of the widest front over a cluster of up to 8 CTAs (about 256 columns each)
-    int maxc_f = 0, maxc_b = 0;
-    for (const auto &d : fr) {
-        if (d.ni == 0) continue;
-        maxc_f = std::max(maxc_f, d.ni);
-        maxc_b = std::max(maxc_b, d.nb);
-    }
-    auto csz = [](int cols) {
-        int c = (cols + 255) / 256;
-        return c <= 1 ? 1 : c <= 2 ? 2 : c <= 4 ? 4 : 8;
-    };
-    as.cs_fwd = csz(maxc_f);
-    as.cs_bwd = csz(maxc_b);
+    as.part_fwd = part_total;
+    part_total += (long)items[0].size();
+    as.part_bwd = part_total;
+    part_total += (long)items[1].size();
+    as.tk_fwd = tk_total;
+    tk_total += tiles[0];
+    as.tk_bwd = tk_total;
+    tk_total += tiles[1];
     int rc;
-    if ((rc = upload(as.fwd_buf, fw, s)) || (rc = upload(as.bwd_buf, bw, s))) return rc;
-    as.d_fwd = as.fwd_buf.as<ApplyTile>();
-    as.d_bwd = as.bwd_buf.as<ApplyTile>();
-    as.nfwd = (int)fw.size();
-    as.nbwd = (int)bw.size();
+    if ((rc = upload(as.fwd_buf, items[0], s)) || (rc = upload(as.bwd_buf, items[1], s))) return rc;
+    as.d_fwd = as.fwd_buf.as<ApplyItem>();
+    as.d_bwd = as.bwd_buf.as<ApplyItem>();
+    as.nfwd = (int)items[0].size();
+    as.nbwd = (int)items[1].size();
     return HSS_OK;
 }
 
@@ -545,6 +552,8 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     }
     T *keep = F->keep.as<T>();
     Work W(s);
+    long part_total = 0;
+    int tk_total = 0;
     F->factor_bytes = 0;
     F->front_flops = 0;
     F->exec_flops = 0;
@@ -626,7 +635,8 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
                 return HSS_ESINGULAR;
             }
         F->apply.emplace_back();
-        if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), false, s))) return rc;
+        if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), false, part_total, tk_total, s)))
+            return rc;
     }
     // ---- top block A^(0): cross couplings from A, then full Gauss-Jordan inversion
     {
@@ -666,7 +676,14 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         F->front_flops += 2.0 / 3.0 * (double)ntop * ntop * ntop;
         F->factor_bytes += sizeof(T) * (double)ntop * ntop;
         F->apply.emplace_back();
-        if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), true, s))) return rc;
+        if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), true, part_total, tk_total, s)))
+            return rc;
+    }
+    {
+        if ((rc = F->d_apart.alloc(sizeof(double) * 32 * 4 * std::max(part_total, 1L))) ||
+            (rc = F->d_tickets.alloc(sizeof(int) * std::max(tk_total, 1))))
+            return rc;
+        HSS_CUDA(cudaMemsetAsync(F->d_tickets.p, 0, sizeof(int) * std::max(tk_total, 1), s));
     }
     HSS_CUDA(cudaStreamSynchronize(s));
     return HSS_OK;

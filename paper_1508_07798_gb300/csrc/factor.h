@@ -7,11 +7,17 @@
 
 namespace hssnd {
 
-constexpr int APPLY_ROWS = 64;
+constexpr int APPLY_ROWS = 32;
 
-struct ApplyTile {
-    int front;   // stage-local front index
-    int row0;
+constexpr int APPLY_CHUNK = 64;   // columns per warp work item of the apply
+
+struct ApplyItem {
+    int front;        // stage-local front index
+    int row0;         // first of the 32 rows
+    int c0, c1;       // column range of this item
+    int tile;         // row-tile index inside the stage (ticket slot)
+    int first;        // item index of the tile's first chunk
+    int nchunk;       // chunks of this tile
 };
 
 // Per level (and the top block): fronts and the row tiles of the apply.
@@ -20,9 +26,10 @@ struct ApplyStage {
     int nfronts = 0;
     DevBuf fronts_buf, fwd_buf, bwd_buf;
     FrontDev *d_fronts = nullptr;
-    ApplyTile *d_fwd = nullptr, *d_bwd = nullptr;
-    int nfwd = 0, nbwd = 0;
-    int cs_fwd = 1, cs_bwd = 1;           // cluster size (column split) of the two sweeps
+    ApplyItem *d_fwd = nullptr, *d_bwd = nullptr;
+    int nfwd = 0, nbwd = 0;               // work items (warps) of the two sweeps
+    long part_fwd = 0, part_bwd = 0;      // offsets (in items) into the partial-sum buffer
+    int tk_fwd = 0, tk_bwd = 0;           // offsets into the ticket array
     double fwd_bytes = 0, bwd_bytes = 0;  // factor entries read (x8 bytes in FP64)
     double fwd_vec = 0, bwd_vec = 0;      // vector entries read + written per right-hand side
 };
@@ -67,6 +74,8 @@ struct hss_factor_t {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_kernels[2] = {0, 0};
     hssnd::DevBuf d_aparams;
+    hssnd::DevBuf d_apart;       // partial sums of split apply tiles (items x 32 x 4)
+    hssnd::DevBuf d_tickets;     // one ticket counter per split tile
     template <class T> T *arena_ptr() const { return arena.as<T>(); }
     // algorithmic bytes of one apply: factor entries once, vector traffic per right-hand side
     double apply_bytes(int nrhs) const {

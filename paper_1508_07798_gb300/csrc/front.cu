@@ -56,34 +56,35 @@ __global__ void k_set_slots(const StageElem *__restrict__ se, int nse, int *__re
 }
 
 // ---------------------------------------------------------------- GJ panel
+// Argmax over non-negative magnitudes by their IEEE bit patterns (monotonic
+// for v >= 0; -1 = no candidate), so no floating-point compare is spent on the
+// reduction (FP64 compares run on GB300's narrow FP64 pipe).
 template <class T> struct ArgMax {
-    T v;
+    long long v;
     int i;
 };
+__device__ __forceinline__ long long mag_key(float a) { return (long long)(__float_as_int(a) & 0x7fffffff); }
+__device__ __forceinline__ long long mag_key(double a) { return __double_as_longlong(a) & 0x7fffffffffffffffLL; }
 
+// Block-wide argmax (largest |v|, ties to the lowest index) with one barrier:
+// every thread reduces the per-warp results itself.  The caller guarantees a
+// barrier between two calls (so nobody still reads sh when it is rewritten).
 template <class T> __device__ ArgMax<T> block_argmax(ArgMax<T> x, ArgMax<T> *sh) {
-    // largest |v|, ties to the lowest index
     for (int o = 16; o > 0; o >>= 1) {
-        T v2 = __shfl_down_sync(0xffffffffu, x.v, o);
+        long long v2 = __shfl_down_sync(0xffffffffu, x.v, o);
         int i2 = __shfl_down_sync(0xffffffffu, x.i, o);
         if (v2 > x.v || (v2 == x.v && i2 < x.i)) {
             x.v = v2;
             x.i = i2;
         }
     }
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) sh[w] = x;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        ArgMax<T> b = sh[0];
-        for (int k = 1; k < nw; ++k)
-            if (sh[k].v > b.v || (sh[k].v == b.v && sh[k].i < b.i)) b = sh[k];
-        sh[0] = b;
-    }
-    __syncthreads();
-    ArgMax<T> r = sh[0];
-    __syncthreads();
-    return r;
+    ArgMax<T> b = sh[0];
+    for (int k = 1; k < nw; ++k)
+        if (sh[k].v > b.v || (sh[k].v == b.v && sh[k].i < b.i)) b = sh[k];
+    return b;
 }
 
 // One CTA per front with an active panel [k0, k0+kb) of its I columns.
@@ -142,9 +143,9 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
     __syncthreads();
     int *pv = piv + F.ioff;
     // candidates of the first pivot column
-    ArgMax<T> loc{T(-1), 0x7fffffff};
+    ArgMax<T> loc{-1LL, 0x7fffffff};
     for (int i = threadIdx.x; i < hT; i += PANEL_NT) {
-        T a = fabs(P[i]);
+        long long a = mag_key(P[i]);
         if (a > loc.v) {
             loc.v = a;
             loc.i = i;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
         // 1. pivot: largest |P(i, j)| over i >= j, ties to the lowest row
         ArgMax<T> best = block_argmax(loc, red);
         int p = best.i;
-        if (best.v == T(0)) {
+        if (best.v <= 0) {
             if (threadIdx.x == 0) atomicExch(&status[J.front], 1);
             p = j;
         }
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
         // 3. eliminate column j from every other row, finish row j, and gather
         //    the candidates of column j+1 (rows > j) on the way
         const T dinv = rowj[j] != T(0) ? T(1) / rowj[j] : T(0);
-        loc = ArgMax<T>{T(-1), 0x7fffffff};
+        loc = ArgMax<T>{-1LL, 0x7fffffff};
         for (int i = threadIdx.x; i < hT; i += PANEL_NT) {
             if (i == j) {
                 for (int c = 0; c < kb; ++c) P[j + ldp * c] = (c == j) ? dinv : rowj[c] * dinv;
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
                 P[i + ldp * j] = -ad;
             }
             if (i > j && j + 1 < kb) {
-                T v2 = fabs(P[i + ldp * (j + 1)]);
+                long long v2 = mag_key(P[i + ldp * (j + 1)]);
                 if (v2 > loc.v) {
                     loc.v = v2;
                     loc.i = i;
@@ -326,30 +327,34 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__res
     if (threadIdx.x == 0) nmv = 0;
     __syncthreads();
     int *pv = piv + F.ioff;
+    // candidates of the first column
+    ArgMax<T> loc{-1LL, 0x7fffffff};
 #pragma unroll
-    for (int j = 0; j < KB; ++j) {
-        if (j >= kb) break;
-        // 1. pivot among the rows not yet pivoted: largest |value|, lowest position on ties
-        ArgMax<T> loc{T(-1), 0x7fffffff};
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int i = threadIdx.x + PANEL_NT * q;
-            if (i < hT && !done[q]) {
-                const T v = fabs(reg[q][j]);
-                const int p = pos[i];
-                if (v > loc.v || (v == loc.v && p < loc.i)) {
-                    loc.v = v;
-                    loc.i = p;
-                }
+    for (int q = 0; q < R; ++q) {
+        const int i = threadIdx.x + PANEL_NT * q;
+        if (i < hT) {
+            const long long v = mag_key(reg[q][0]);
+            if (v > loc.v || (v == loc.v && i < loc.i)) {
+                loc.v = v;
+                loc.i = i;
             }
         }
+    }
+    // Pivot loop, not unrolled (the unrolled body overflows the instruction
+    // cache): each row's registers rotate left by one per step, so the active
+    // column always sits in register 0; after kb steps register c holds
+    // column (kb + c) mod KB.
+#pragma unroll 1
+    for (int j = 0; j < kb; ++j) {
+        // 1. pivot among the rows not yet pivoted: largest |value|, lowest position on ties
         const ArgMax<T> best = block_argmax(loc, red);
         int p = best.i;
-        if (best.v == T(0)) {
+        if (best.v <= 0) {
             if (threadIdx.x == 0) atomicExch(&status[J.front], 1);
             p = j;
         }
         const int x = posinv[p];   // row of the pivot
+        const int y = posinv[j];   // row at position j: trades places with the pivot
 #pragma unroll
         for (int q = 0; q < R; ++q)
             if (threadIdx.x + PANEL_NT * q == x) {
@@ -357,8 +362,8 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__res
                 for (int c = 0; c < KB; ++c) rowj[c] = reg[q][c];
                 done[q] = true;
             }
+        __syncthreads();   // every thread has read posinv; rowj is complete
         if (threadIdx.x == 0) {
-            const int y = posinv[j];   // row at position j trades places with the pivot
             posinv[j] = x;
             posinv[p] = y;
             pos[x] = j;
@@ -368,27 +373,40 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__res
             rp[p] = t;
             pv[k0 + j] = k0 + p;
         }
-        __syncthreads();
-        // 2. Gauss-Jordan step in registers
-        const T dinv = rowj[j] != T(0) ? T(1) / rowj[j] : T(0);
+        // 2. Gauss-Jordan step in registers, then rotate; candidates of the next column
+        const T dinv = rowj[0] != T(0) ? T(1) / rowj[0] : T(0);
+        loc = ArgMax<T>{-1LL, 0x7fffffff};
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int i = threadIdx.x + PANEL_NT * q;
             if (i >= hT) continue;
+            T head;
             if (i == x) {
 #pragma unroll
-                for (int c = 0; c < KB; ++c) reg[q][c] = (c == j) ? dinv : rowj[c] * dinv;
+                for (int c = 1; c < KB; ++c) reg[q][c] = rowj[c] * dinv;
+                head = dinv;
             } else {
-                const T ad = reg[q][j] * dinv;
+                const T ad = reg[q][0] * dinv;
 #pragma unroll
-                for (int c = 0; c < KB; ++c) reg[q][c] -= ad * rowj[c];
-                reg[q][j] = -ad;
+                for (int c = 1; c < KB; ++c) reg[q][c] -= ad * rowj[c];
+                head = -ad;
+            }
+#pragma unroll
+            for (int c = 0; c + 1 < KB; ++c) reg[q][c] = reg[q][c + 1];
+            reg[q][KB - 1] = head;
+            if (!done[q]) {
+                const long long v = mag_key(reg[q][0]);
+                const int ps = (i == y) ? p : pos[i];
+                if (v > loc.v || (v == loc.v && ps < loc.i)) {
+                    loc.v = v;
+                    loc.i = ps;
+                }
             }
         }
-        // the barriers inside the next block_argmax order rowj and pos updates
     }
     __syncthreads();
-    // 3. every row to its final position; the pivot block also to X
+    // 3. every row to its final position (register c holds column (kb + c) mod KB);
+    //    the pivot block also to X
     T *Xg = xws + J.xoff;
     int *mv = mws + J.moff;
 #pragma unroll
@@ -397,12 +415,12 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__res
         if (i >= hT) continue;
         const int r = pos[i];
 #pragma unroll
-        for (int c = 0; c < KB; ++c)
-            if (c < kb) M[(k0 + r) + ld * (k0 + c)] = reg[q][c];
-        if (r < kb) {
-#pragma unroll
-            for (int c = 0; c < KB; ++c)
-                if (c < kb) Xg[r + kb * c] = reg[q][c];
+        for (int c = 0; c < KB; ++c) {
+            const int col = (kb + c) % KB;
+            if (col < kb) {
+                M[(k0 + r) + ld * (k0 + col)] = reg[q][c];
+                if (r < kb) Xg[r + kb * col] = reg[q][c];
+            }
         }
         if (r != i) {   // the other columns move the same way (k_gj_post)
             int m = atomicAdd(&nmv, 1);

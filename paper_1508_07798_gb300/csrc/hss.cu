@@ -20,14 +20,22 @@
 
 namespace hssnd {
 
+// Argmax over non-negative values by their IEEE bit patterns (monotonic for
+// v >= 0; -1 = no candidate): integer compares only.
 template <class T> struct AM {
-    T v;
+    long long v;
     int i;
 };
+__device__ __forceinline__ long long nn_key(float a) { return (long long)(unsigned)__float_as_int(a); }
+__device__ __forceinline__ long long nn_key(double a) { return __double_as_longlong(a); }
+__device__ __forceinline__ long long abs_key(float a) { return (long long)(__float_as_int(a) & 0x7fffffff); }
+__device__ __forceinline__ long long abs_key(double a) { return __double_as_longlong(a) & 0x7fffffffffffffffLL; }
+__device__ __forceinline__ float key_val(long long k, float) { return __int_as_float((int)k); }
+__device__ __forceinline__ double key_val(long long k, double) { return __longlong_as_double(k); }
 
 template <class T> __device__ AM<T> blk_argmax(AM<T> x, AM<T> *sh) {
     for (int o = 16; o > 0; o >>= 1) {
-        T v2 = __shfl_down_sync(0xffffffffu, x.v, o);
+        long long v2 = __shfl_down_sync(0xffffffffu, x.v, o);
         int i2 = __shfl_down_sync(0xffffffffu, x.i, o);
         if (v2 > x.v || (v2 == x.v && i2 < x.i)) {
             x.v = v2;
@@ -180,15 +188,17 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
     T first = 0;
     const int kmx = min(r, m);
     for (int j = 0; j < kmx; ++j) {
-        AM<T> loc{T(-1), INT_MAX};
+        AM<T> loc{-1LL, INT_MAX};
         __syncthreads();
-        for (int c = j + threadIdx.x; c < m; c += ID_NT)
-            if (nrm2[c] > loc.v || (nrm2[c] == loc.v && c < loc.i)) {
-                loc.v = nrm2[c];
+        for (int c = j + threadIdx.x; c < m; c += ID_NT) {
+            const long long kc = nn_key(nrm2[c]);
+            if (kc > loc.v || (kc == loc.v && c < loc.i)) {
+                loc.v = kc;
                 loc.i = c;
             }
+        }
         AM<T> best = blk_argmax(loc, sham);
-        const T nn2 = best.v;
+        const T nn2 = key_val(best.v, T(0));
         const T nrm = sqrt(nn2);
         if (j == 0) first = nrm;
         if (first == T(0) || nrm <= tol * first) break;
@@ -247,17 +257,17 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
     // ---- exchanges while some |T_ij| > 2 (largest entry, first in row-major order)
     for (int sw = 0; sw < ID_MAX_SWAPS && k > 0 && k < m; ++sw) {
         const int nc = m - k;
-        AM<T> loc{T(-1), INT_MAX};
+        AM<T> loc{-1LL, INT_MAX};
         for (int q = threadIdx.x; q < k * nc; q += ID_NT) {
             int i = q / nc, jj = q % nc;  // row-major linear index q
-            T a = fabs(A[i + (long)lda * (k + jj)]);
+            const long long a = abs_key(A[i + (long)lda * (k + jj)]);
             if (a > loc.v || (a == loc.v && q < loc.i)) {
                 loc.v = a;
                 loc.i = q;
             }
         }
         AM<T> best = blk_argmax(loc, sham);
-        if (best.v <= T(2)) break;
+        if (key_val(best.v, T(0)) <= T(2)) break;
         __syncthreads();
         if (threadIdx.x == 0) {
             int i = best.i / nc, jj = best.i % nc;
