@@ -88,6 +88,9 @@ typedef struct hss_factor_opts {
     int precision;          /* HSS_FP64 (default) or HSS_FP32 (mixed form) */
     uint64_t seed;          /* seed of the +-1 test matrices; default 0 */
     int keep_schur;         /* 1: keep a copy of every front's S and H for hss_factor_export_front */
+    int tensor_cores;       /* FP32 form only: 0 (default) SIMT FMA; 1 tcgen05 TF32 with the three-product
+                               hi/lo split (FP32 accuracy) for products with K >= 128 (the sampling
+                               products); 2 the same with a single TF32 product */
 } hss_factor_opts;
 
 typedef struct fgmres_opts {
@@ -180,6 +183,14 @@ int hss_factor_export_front(const hss_factor_t *f, int box, double *S, double *H
  * Errors: HSS_EINVAL, HSS_ENOMEM (workspace for a larger nrhs), HSS_ECUDA. */
 int hss_apply(const hss_factor_t *f, int nrhs, const double *x, int ldx, double *y, int ldy,
               void *stream);
+
+/* C = alpha A B + beta C in FP32, DEVICE column-major m x k, k x n, m x n
+ * (the GEMM of the FP32 form, exposed for testing and reuse).  engine: 0 SIMT
+ * FMA; 1 tcgen05 TF32 with the three-product hi/lo split; 2 tcgen05 single
+ * TF32.  No counterpart in the paper (a building block of eq. (32)'s update).
+ * Synchronizes `stream`; HSS_ETIMEOUT if a bounded tensor-core wait expired. */
+int hss_gemm_f32(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+                 float alpha, float beta, int engine, void *stream);
 
 /* y = A x for nrhs columns (DEVICE, column-major).  Asynchronous. */
 int hss_spmv(const hss_bsr *A, int nrhs, const double *x, int ldx, double *y, int ldy,

@@ -113,6 +113,7 @@ void hss_factor_opts_default(hss_factor_opts *o) {
     o->precision = HSS_FP64;
     o->seed = 0;
     o->keep_schur = 0;
+    o->tensor_cores = 0;
 }
 
 void fgmres_opts_default(fgmres_opts *o) {

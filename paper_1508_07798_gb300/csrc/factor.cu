@@ -12,6 +12,7 @@
 // status) to decide sample growth and to size the expansion.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 
 #include "factor.h"
@@ -46,6 +47,40 @@ int assemble_stage(const hss_bsr *A, const hss_tree *t, const std::vector<FrontD
     return launch_scatter_A<T>(A, d_se, (int)se.size(), elem_slot, d_fr, arena, s);
 }
 
+// GEMM engine of a factorization: SIMT FMA, or (FP32 form) tcgen05 TF32
+// tensor cores for problems of at least one 128-row tile.
+struct Engine {
+    int tc = 0;          // 0 SIMT; 1 TF32 with hi/lo split; 2 single TF32
+    int *err = nullptr;  // set by a tensor-core kernel whose bounded wait expired
+};
+
+// Tensor cores pay off for long contractions only: the Gauss-Jordan trailing
+// updates (K = panel width <= 32) are memory bound per 128 x 128 tile and ran
+// 2.4x slower on tcgen05 than the 64 x 64 SIMT tiles (fewer, heavier CTAs), so
+// they stay on FMA; the sampling products (K = |B|) go to the tensor cores.
+template <class T> bool use_tc(const Engine &e, const GemmDesc<T> &d) {
+    return std::is_same<T, float>::value && e.tc != 0 && d.m >= 128 && d.n >= 32 && d.k >= 128;
+}
+
+template <class T> void tiles_for(const Engine &e, const GemmDesc<T> &d, int idx, std::vector<GemmTile> &t) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (use_tc(e, d)) {
+            gemm_tc_tiles_for(d, idx, t);
+            return;
+        }
+    }
+    gemm_tiles_for(d, idx, t);
+}
+
+template <class T>
+int run_gemm(const Engine &e, bool tc, const GemmDesc<T> *dd, const GemmTile *dt, int n, cudaStream_t s,
+             double flops) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (tc) return gemm_tc(dd, dt, n, e.tc == 1 ? 1 : 0, e.err, s, flops);
+    }
+    return gemm_batched<T>(dd, dt, n, s, flops);
+}
+
 template <class T> int choose_kb(int ni) {
     for (int kb = PANEL_KB_MAX; kb >= 8; kb /= 2)
         if ((long)ni * kb * (long)sizeof(T) + (long)ni * 4 <= PANEL_SMEM_MAX) return kb;
@@ -57,7 +92,8 @@ template <class T> int choose_kb(int ni) {
 // shared/global memory otherwise), the post-panel tiles, the trailing GEMM.
 template <class T>
 int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *arena, int *piv, int *rperm,
-                    const int *ilist, int *iperm, int *status, double &exec_flops, Work &W, cudaStream_t s) {
+                    const int *ilist, int *iperm, int *status, double &exec_flops, const Engine &eng, Work &W,
+                    cudaStream_t s) {
     int nf = (int)fr.size();
     std::vector<int> kb(nf), nsteps(nf), isreg(nf), Rf(nf);
     std::vector<long> aoff(nf);
@@ -86,14 +122,15 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
     };
     std::vector<PanelJob> jobs;
     std::vector<GemmDesc<T>> descs;
-    std::vector<GemmTile> tiles;
+    std::vector<GemmTile> tiles, ttiles;   // SIMT and tensor-core tiles
     std::vector<PanelTile> ptiles;
     std::vector<std::vector<Group>> groups(maxsteps);
-    std::vector<int> tile_off(maxsteps + 1), ptile_off(maxsteps + 1);
+    std::vector<int> tile_off(maxsteps + 1), ttile_off(maxsteps + 1), ptile_off(maxsteps + 1);
     long xtotal = 0, mtotal = 0;
-    std::vector<double> step_flops(maxsteps, 0.0);
+    std::vector<double> step_flops(maxsteps, 0.0), tstep_flops(maxsteps, 0.0);
     for (int st = 0; st < maxsteps; ++st) {
         tile_off[st] = (int)tiles.size();
+        ttile_off[st] = (int)ttiles.size();
         ptile_off[st] = (int)ptiles.size();
         std::vector<int> act;
         for (int f = 0; f < nf; ++f)
@@ -151,24 +188,30 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             d.skip_lo = k0;
             d.skip_hi = k0 + kbs;
             descs.push_back(d);
-            gemm_tiles_for(descs.back(), (int)descs.size() - 1, tiles);
-            step_flops[st] += gemm_flops(d);
+            if (use_tc(eng, d)) {
+                tiles_for(eng, descs.back(), (int)descs.size() - 1, ttiles);
+                tstep_flops[st] += gemm_flops(d);
+            } else {
+                gemm_tiles_for(descs.back(), (int)descs.size() - 1, tiles);
+                step_flops[st] += gemm_flops(d);
+            }
         }
     }
     tile_off[maxsteps] = (int)tiles.size();
+    ttile_off[maxsteps] = (int)ttiles.size();
     ptile_off[maxsteps] = (int)ptiles.size();
     T *d_aold, *d_x;
     int *d_mv;
     PanelJob *d_jobs;
     GemmDesc<T> *d_descs;
-    GemmTile *d_tiles;
+    GemmTile *d_tiles, *d_ttiles;
     PanelTile *d_ptiles;
     int rc;
     if ((rc = W.dalloc(aold_total, &d_aold)) || (rc = W.dalloc(xtotal, &d_x)) || (rc = W.dalloc(mtotal, &d_mv)))
         return rc;
     for (size_t i = 0; i < descs.size(); ++i) descs[i].B = d_aold + jobs[i].aoff;
     if ((rc = W.up(jobs, &d_jobs)) || (rc = W.up(descs, &d_descs)) || (rc = W.up(tiles, &d_tiles)) ||
-        (rc = W.up(ptiles, &d_ptiles)))
+        (rc = W.up(ttiles, &d_ttiles)) || (rc = W.up(ptiles, &d_ptiles)))
         return rc;
     for (int st = 0; st < maxsteps; ++st) {
         for (const Group &g : groups[st]) {
@@ -186,6 +229,9 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         if ((rc = gemm_batched<T>(d_descs, d_tiles + tile_off[st], tile_off[st + 1] - tile_off[st], s,
                                   step_flops[st])))
             return rc;
+        if ((rc = run_gemm<T>(eng, true, d_descs, d_ttiles + ttile_off[st], ttile_off[st + 1] - ttile_off[st], s,
+                              tstep_flops[st])))
+            return rc;
     }
     return HSS_OK;
 }
@@ -202,7 +248,7 @@ template <class T>
 int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vector<FrontDev> &fr,
                    const std::vector<int> &boxes, const std::vector<long> &poff, const std::vector<int> &pn,
                    const std::vector<long> &keep_h, T *arena, T *keep, int *status_dev, int nstatus,
-                   std::vector<FrontLog> &logv, hss_factor_t *F, Work &W, cudaStream_t s) {
+                   std::vector<FrontLog> &logv, hss_factor_t *F, const Engine &eng, Work &W, cudaStream_t s) {
     int nf = (int)fr.size();
     int rc;
     std::vector<ExpandFront> ef(nf);
@@ -303,7 +349,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         HSS_CUDA(cudaMemsetAsync(d_fk, 0, sizeof(int) * nc, s));
         // ---- sampling Y = S Omega, Z = S^t Psi, then the leaf corrections
         std::vector<GemmDesc<T>> g1, g2;
-        std::vector<GemmTile> t1, t2;
+        std::vector<GemmTile> t1, t1c, t2;   // sampling (SIMT / tensor cores), leaf corrections
         for (int c = 0; c < nc; ++c) {
             GemmDesc<T> d{};
             d.A = cfs[c].S;
@@ -324,12 +370,14 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             d.transA = 0;
             d.stream = 0;
             g1.push_back(d);
-            gemm_tiles_for(g1.back(), (int)g1.size() - 1, t1);
+            if (use_tc(eng, d)) tiles_for(eng, g1.back(), (int)g1.size() - 1, t1c);
+            else gemm_tiles_for(g1.back(), (int)g1.size() - 1, t1);
             d.C = ws + cfs[c].zoff;
             d.transA = 1;
             d.stream = 1;
             g1.push_back(d);
-            gemm_tiles_for(g1.back(), (int)g1.size() - 1, t1);
+            if (use_tc(eng, d)) tiles_for(eng, g1.back(), (int)g1.size() - 1, t1c);
+            else gemm_tiles_for(g1.back(), (int)g1.size() - 1, t1);
             for (int i = node_base[c]; i < node_base[c + 1]; ++i) {
                 if (nodes[i].a >= 0) continue;
                 int lo = nodes[i].lo, m = nodes[i].hi - nodes[i].lo;
@@ -354,12 +402,15 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         }
         {
             GemmDesc<T> *a, *c2;
-            GemmTile *b, *d2;
-            if ((rc = W.up(g1, &a)) || (rc = W.up(t1, &b)) || (rc = W.up(g2, &c2)) || (rc = W.up(t2, &d2))) return rc;
-            double f1 = 0, f2 = 0;
-            for (auto &d : g1) f1 += gemm_flops(d);
+            GemmTile *b, *bc, *d2;
+            if ((rc = W.up(g1, &a)) || (rc = W.up(t1, &b)) || (rc = W.up(t1c, &bc)) || (rc = W.up(g2, &c2)) ||
+                (rc = W.up(t2, &d2)))
+                return rc;
+            double f1 = 0, f1c = 0, f2 = 0;
+            for (auto &d : g1) (use_tc(eng, d) ? f1c : f1) += gemm_flops(d);
             for (auto &d : g2) f2 += gemm_flops(d);
             if ((rc = gemm_batched<T>(a, b, (int)t1.size(), s, f1))) return rc;
+            if ((rc = run_gemm<T>(eng, true, a, bc, (int)t1c.size(), s, f1c))) return rc;
             if ((rc = gemm_batched<T>(c2, d2, (int)t2.size(), s, f2))) return rc;
         }
         // ---- interpolative decompositions, deepest HSS level first
@@ -552,6 +603,21 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     }
     T *keep = F->keep.as<T>();
     Work W(s);
+    DevBuf d_tcerr;
+    if ((rc = d_tcerr.alloc(sizeof(int)))) return rc;
+    HSS_CUDA(cudaMemsetAsync(d_tcerr.p, 0, sizeof(int), s));
+    Engine eng;
+    eng.tc = std::is_same<T, float>::value ? o.tensor_cores : 0;
+    eng.err = d_tcerr.as<int>();
+    auto check_tc = [&]() -> int {
+        int h = 0;
+        HSS_CUDA(cudaMemcpy(&h, d_tcerr.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (h) {
+            set_error("hss_factor: a bounded tensor-core wait expired");
+            return HSS_ETIMEOUT;
+        }
+        return HSS_OK;
+    };
     long part_total = 0;
     int tk_total = 0;
     F->factor_bytes = 0;
@@ -613,7 +679,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
             return rc;
         if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
-                                     t->d_iset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, W, s)))
+                                     t->d_iset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, eng, W, s)))
             return rc;
         if (o.keep_schur)
             for (size_t f = 0; f < fr.size(); ++f) {
@@ -624,7 +690,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
                                            sizeof(T) * d.nb, d.nb, cudaMemcpyDeviceToDevice, s));
             }
         if ((rc = compress_stage<T>(t, o, fr, boxes, poff, pn, keeph, arena, keep, d_status, (int)fr.size(), F->log,
-                                    F, W, s)))
+                                    F, eng, W, s)))
             return rc;
         std::vector<int> hst(fr.size());
         HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status, sizeof(int) * fr.size(), cudaMemcpyDeviceToHost, s));
@@ -634,6 +700,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
                 set_error("hss_factor: zero pivot in the front of box " + std::to_string(boxes[f]));
                 return HSS_ESINGULAR;
             }
+        if ((rc = check_tc())) return rc;
         F->apply.emplace_back();
         if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), false, part_total, tk_total, s)))
             return rc;
@@ -664,7 +731,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
             return rc;
         if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
-                                     F->d_topset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, W, s)))
+                                     F->d_topset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, eng, W, s)))
             return rc;
         int hst = 0;
         HSS_CUDA(cudaMemcpyAsync(&hst, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -673,6 +740,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             set_error("hss_factor: zero pivot in the top block");
             return HSS_ESINGULAR;
         }
+        if ((rc = check_tc())) return rc;
         F->front_flops += 2.0 / 3.0 * (double)ntop * ntop * ntop;
         F->factor_bytes += sizeof(T) * (double)ntop * ntop;
         F->apply.emplace_back();

@@ -150,6 +150,13 @@ template <class T>
 int gemm_batched(const GemmDesc<T> *d_desc, const GemmTile *d_tiles, int ntiles, cudaStream_t s,
                  double flops = 0.0);
 
+// Tensor-core (tcgen05, TF32) GEMM of the FP32 form: split = 1 uses the
+// three-product hi/lo split (FP32 accuracy), 0 a single TF32 product.  err is
+// set when a bounded wait expires.
+int gemm_tc(const GemmDesc<float> *d_desc, const GemmTile *d_tiles, int ntiles, int split, int *err, cudaStream_t s,
+            double flops);
+void gemm_tc_tiles_for(const GemmDesc<float> &d, int desc_index, std::vector<GemmTile> &tiles);
+
 // 2 m n k of the written part of a problem
 template <class T> double gemm_flops(const GemmDesc<T> &d) {
     int ncols = d.n;

@@ -26,7 +26,7 @@ EXPORTED = [
     "nd_order", "hss_tree_info", "hss_tree_export", "hss_factor", "hss_factor_get_info",
     "hss_factor_export_front", "hss_apply", "hss_spmv", "fgmres_solve", "fgmres_history",
     "hss_tree_destroy", "hss_factor_destroy", "hss_last_error",
-    "hss_launch_count", "hss_profile_enable", "hss_profile_reset", "hss_profile_read",
+    "hss_launch_count", "hss_profile_enable", "hss_profile_reset", "hss_profile_read", "hss_gemm_f32",
 ]
 
 
@@ -52,7 +52,7 @@ class hss_nd_opts(C.Structure):
 class hss_factor_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("compress", C.c_int), ("r0", C.c_int), ("dr", C.c_int),
                 ("rmax", C.c_int), ("oversample", C.c_int), ("precision", C.c_int),
-                ("seed", C.c_uint64), ("keep_schur", C.c_int)]
+                ("seed", C.c_uint64), ("keep_schur", C.c_int), ("tensor_cores", C.c_int)]
 
 
 class fgmres_opts(C.Structure):
@@ -99,6 +99,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hss_factor_opts_default": (None, [C.POINTER(hss_factor_opts)]),
         "fgmres_opts_default": (None, [C.POINTER(fgmres_opts)]),
         "hss_launch_count": (C.c_long, []),
+        "hss_gemm_f32": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.c_int, P, C.c_int, C.c_float,
+                                   C.c_float, C.c_int, P]),
         "hss_profile_enable": (C.c_int, [C.c_int]),
         "hss_profile_reset": (C.c_int, []),
         "hss_profile_read": (C.c_int, [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
@@ -315,3 +317,19 @@ def profile_read() -> dict:
         _check(_lib.hss_profile_read(i, name, 64, C.byref(ms), C.byref(cnt), C.byref(work)))
         out[name.value.decode()] = (ms.value, cnt.value, work.value)
     return out
+
+
+def gemm_f32(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, alpha=1.0, beta=0.0, engine=1,
+             stream=None) -> torch.Tensor:
+    """C = alpha A B + beta C on FP32 CUDA tensors (row-major torch tensors are
+    handled as their column-major transposes: C^t = B^t A^t)."""
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2
+    if C is None:
+        C = torch.zeros(m, n, dtype=torch.float32, device=A.device)
+    At, Bt, Ct = A.contiguous(), B.contiguous(), C
+    assert Ct.is_contiguous()
+    # row-major (m x n) C is column-major (n x m) C^t = B^t A^t
+    _check(_lib.hss_gemm_f32(n, m, k, _ptr(Bt), n, _ptr(At), k, _ptr(Ct), n, alpha, beta, engine, _stream(stream)))
+    return Ct

@@ -232,3 +232,55 @@ def test_errors_are_reported():
     b = torch.as_tensor(dg.random_rhs(A.n, 1, 0)[:, 0], device="cuda")
     x, st = hs.fgmres_solve(dA, None, b, rtol=1e-14, maxit=2)
     assert not st.converged and st.iters == 2
+
+
+@pytest.mark.parametrize("m,n,k", [(300, 200, 70), (128, 128, 32), (513, 77, 257), (64, 300, 5), (1, 1, 1)])
+def test_gemm_f32_engines(m, n, k):
+    """The FP32 GEMM engines against an FP64 product: SIMT FMA and tcgen05
+    TF32 with the hi/lo split at FP32 accuracy, single TF32 at TF32 accuracy."""
+    import torch
+    hs = _hss()
+    g = torch.Generator(device="cpu").manual_seed(m * 7 + n)
+    A = torch.randn(m, k, generator=g).cuda()
+    B = torch.randn(k, n, generator=g).cuda()
+    C0 = torch.randn(m, n, generator=g).cuda()
+    ref = (A.double() @ B.double()) * 0.5 + C0.double() * 2.0
+    scale = (A.double().abs() @ B.double().abs()).max().item() + 1.0
+    for engine, tol in ((0, 2e-6), (1, 2e-6), (2, 2e-3)):
+        C = C0.clone()
+        hs.gemm_f32(A, B, C, alpha=0.5, beta=2.0, engine=engine)
+        torch.cuda.synchronize()
+        err = (C.double() - ref).abs().max().item() / scale
+        assert err <= tol, (engine, err)
+
+
+def test_fp32_form_tensor_cores_match_simt():
+    """The FP32 form with tcgen05 GEMMs (TF32 hi/lo split) against the same form
+    with SIMT FMA GEMMs.  With compression off (pure arithmetic), both FP32
+    Schur complements stay within the same order of the FP64 ones; with
+    compression on, both solves converge alike."""
+    import torch
+    hs = _hss()
+    mesh, A = _setup("helm", (32, 32), 2)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((2, (32, 32), 2), dA)
+    F64 = hs.hss_factor(dA, tree, compress=0, keep_schur=1)
+    Ft = hs.hss_factor(dA, tree, compress=0, precision="fp32", tensor_cores=1, keep_schur=1)
+    Fs = hs.hss_factor(dA, tree, compress=0, precision="fp32", tensor_cores=0, keep_schur=1)
+    ex = tree.export()
+    big = [b for b in range(len(ex["nb"])) if ex["ni"][b] + ex["nb"][b] >= 128 and ex["nb"][b] > 0]
+    assert big
+    for b in big:
+        S64, _, _, _ = F64.export_front(b)
+        St, _, _, _ = Ft.export_front(b)
+        Ss, _, _, _ = Fs.export_front(b)
+        et, es = _rel(St, S64), _rel(Ss, S64)
+        # the split drops the lo*lo product and the tensor core's internal sums are
+        # not single-rounded FMAs: a few times the FMA-chain error, same order
+        assert et <= 10.0 * es + 1e-6 and et <= 1e-2, (b, et, es)
+    Ftc = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=1)
+    Fsi = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=0)
+    bvec = torch.as_tensor(dg.point_source_rhs(mesh, 0)[:, 0], device="cuda")
+    xt, st = hs.fgmres_solve(dA, Ftc, bvec, rtol=1e-8)
+    xs, ss = hs.fgmres_solve(dA, Fsi, bvec, rtol=1e-8)
+    assert st.converged and ss.converged and abs(st.iters - ss.iters) <= 2

@@ -41,7 +41,7 @@ def test_binding_lists_every_symbol():
 def test_option_defaults_without_gpu(lib):
     from paper_1508_07798_gb300 import hssnd
     o = hssnd.factor_opts()
-    assert o.tol == 1e-6 and o.r0 == 32 and o.oversample == 10 and o.compress == 1
+    assert o.tol == 1e-6 and o.r0 == 32 and o.oversample == 10 and o.compress == 1 and o.tensor_cores == 0
     f = hssnd.fgmres_opts()
     hssnd._lib.fgmres_opts_default(ctypes.byref(f))
     assert f.restart == 30 and f.rtol == 1e-8
