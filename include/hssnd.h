@@ -192,6 +192,37 @@ int hss_apply(const hss_factor_t *f, int nrhs, const double *x, int ldx, double 
 int hss_gemm_f32(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
                  float alpha, float beta, int engine, void *stream);
 
+/* hss_gemm_f32 without any memory allocation.  No counterpart in the paper.
+ * Same arguments, layout, engines and result as hss_gemm_f32; the difference
+ * is where the launch records live: hss_gemm_f32 puts its GEMM descriptor,
+ * tile list and tensor-core timeout flag in workspace it allocates per call,
+ * this variant keeps them in one fixed device array inside the library
+ * (256-byte aligned, 512 + 12 * HSS_GEMM_STATIC_MAX_TILES bytes, about
+ * 193 KB), so it calls no allocator of any kind (no cudaMalloc/cudaFree, no
+ * pinned host buffer, no allocating library routine).  It is for callers
+ * that may not allocate: code that runs while a memory pool or allocator is
+ * being trimmed or rebuilt (an allocation there re-enters it), code with a
+ * fixed device-memory budget that must leave the heap untouched, and code
+ * that must not block the device, which freeing workspace does.
+ * Limit: the product is cut into tiles (64 x 64 for engine 0, 128 x 128 for
+ * engines 1 and 2) and at most HSS_GEMM_STATIC_MAX_TILES tiles fit, e.g.
+ * m = n = 8192 with engine 0, 16384 with engines 1 and 2; a larger m x n
+ * returns HSS_EINVAL with the tile count in hss_last_error().
+ * Nothing in the scratch has to start at zero: each call writes the
+ * descriptor, tile list and a cleared timeout flag on `stream` before the
+ * GEMM reads them.  There is one array per device: two calls that overlap in
+ * time (on different streams or host threads) race on it and give undefined
+ * results; callers serialize them.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, which can load the module);
+ * a caller that wants that setup out of a timed or restricted region makes
+ * one small call first.  The optional event timing of hss_profile_enable
+ * creates CUDA events: leave it off where nothing may be allocated.
+ * Synchronizes `stream`; HSS_ETIMEOUT if a bounded tensor-core wait expired,
+ * HSS_ECUDA if the address lookup or a launch failed. */
+#define HSS_GEMM_STATIC_MAX_TILES 16384
+int hss_gemm_f32_static(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C,
+                        int ldc, float alpha, float beta, int engine, void *stream);
+
 /* y = A x for nrhs columns (DEVICE, column-major).  Asynchronous. */
 int hss_spmv(const hss_bsr *A, int nrhs, const double *x, int ldx, double *y, int ldy,
              void *stream);

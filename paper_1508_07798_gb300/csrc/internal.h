@@ -145,6 +145,8 @@ struct GemmTile {
 
 constexpr int GEMM_TM = 64;
 constexpr int GEMM_TN = 64;
+constexpr int GEMM_TC_TM = 128;   // tile of the tcgen05 GEMM (one MMA M x N)
+constexpr int GEMM_TC_TN = 128;
 
 template <class T>
 int gemm_batched(const GemmDesc<T> *d_desc, const GemmTile *d_tiles, int ntiles, cudaStream_t s,

@@ -20,8 +20,8 @@ namespace hssnd {
 
 namespace {
 
-constexpr int TC_M = 128;
-constexpr int TC_N = 128;
+constexpr int TC_M = GEMM_TC_TM;
+constexpr int TC_N = GEMM_TC_TN;
 constexpr int TC_K = 32;            // K per staged chunk
 constexpr int TC_NT = 128;          // threads per CTA
 constexpr uint32_t TC_LBO = 128;    // bytes between core matrices along K

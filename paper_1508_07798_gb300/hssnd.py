@@ -27,6 +27,7 @@ EXPORTED = [
     "hss_factor_export_front", "hss_apply", "hss_spmv", "fgmres_solve", "fgmres_history",
     "hss_tree_destroy", "hss_factor_destroy", "hss_last_error",
     "hss_launch_count", "hss_profile_enable", "hss_profile_reset", "hss_profile_read", "hss_gemm_f32",
+    "hss_gemm_f32_static",
 ]
 
 
@@ -101,6 +102,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hss_launch_count": (C.c_long, []),
         "hss_gemm_f32": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.c_int, P, C.c_int, C.c_float,
                                    C.c_float, C.c_int, P]),
+        "hss_gemm_f32_static": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.c_int, P, C.c_int,
+                                          C.c_float, C.c_float, C.c_int, P]),
         "hss_profile_enable": (C.c_int, [C.c_int]),
         "hss_profile_reset": (C.c_int, []),
         "hss_profile_read": (C.c_int, [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
@@ -333,3 +336,20 @@ def gemm_f32(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, al
     # row-major (m x n) C is column-major (n x m) C^t = B^t A^t
     _check(_lib.hss_gemm_f32(n, m, k, _ptr(Bt), n, _ptr(At), k, _ptr(Ct), n, alpha, beta, engine, _stream(stream)))
     return Ct
+
+
+GEMM_STATIC_MAX_TILES = 16384
+
+
+def gemm_f32_static(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, alpha=1.0, beta=0.0, engine=1,
+                    stream=None) -> torch.Tensor:
+    """gemm_f32 through hss_gemm_f32_static (launch records in the library's
+    fixed device array, no allocation in the call).  C must be given: this
+    wrapper allocates nothing either."""
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2 and C.shape == (m, n)
+    assert A.is_contiguous() and B.is_contiguous() and C.is_contiguous()
+    _check(_lib.hss_gemm_f32_static(n, m, k, _ptr(B), n, _ptr(A), k, _ptr(C), n, alpha, beta, engine,
+                                    _stream(stream)))
+    return C
