@@ -158,7 +158,10 @@ int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_factor_opts *op
 
 /* Statistics of a factorization (host): stored factor bytes, algorithmic
  * flops of the front eliminations (2/3 ni^3 + 2 ni^2 nb + 2 nb^2 ni summed),
- * sample rounds, largest HSS rank and sample width. */
+ * sample rounds, largest HSS rank and sample width, and the number of fronts
+ * that kept their Schur complement S uncompressed because the sample width
+ * reached opts.rmax while some rank still exceeded r - oversample (Theorem 1
+ * needs k + p samples for its error bound). */
 typedef struct hss_factor_info {
     double factor_bytes;
     double front_flops;
@@ -167,6 +170,7 @@ typedef struct hss_factor_info {
     int max_r;
     int rounds;
     int nfronts;
+    int capped_fronts;
 } hss_factor_info;
 int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info);
 

@@ -63,7 +63,7 @@ def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=
         if compress and B.size > 0:
             nodes = hss_tree_for_front(nd, b)
             Hs, rep = hss_compress(S, nodes, tol, seed, b, r0=r0, dr=dr, oversample=oversample, rmax=rmax)
-            rec.update(r=rep["r"], rounds=rep["rounds"],
+            rec.update(r=rep["r"], rounds=rep["rounds"], capped=rep.get("capped", False),
                        kmax=max(list(rep["krow"].values()) + list(rep["kcol"].values()) + [0]),
                        nnodes=len(nodes), rep=rep)
         else:

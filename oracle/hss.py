@@ -26,7 +26,10 @@ Readings where the paper is silent:
     at 32 and grows by 32 (whole front redone, earlier columns kept) while some
     node's rank exceeds r - 10 and r < n (and, when a cap rmax is given, while
     r + 32 <= rmax);
-  * the ID tolerance is relative per ID (see idecomp.py).
+  * the ID tolerance is relative per ID (see idecomp.py);
+  * when the cap rmax stops the growth while some rank still exceeds r - 10,
+    Theorem 1's error bound (which needs k + p samples) does not apply, and
+    the front keeps S itself (H = S, rep["capped"] = True).
 The approximant is returned expanded to a dense matrix H (the parent front is
 built from H, eq. (32)), together with the representation and its ranks.
 """
@@ -79,7 +82,8 @@ def hss_tree_for_front(nd, box):
 def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rmax=None):
     """Randomized HSS approximant of S.  Returns (H, rep) with H dense.
 
-    rmax (optional) caps the sample width: growth stops once r + dr > rmax."""
+    rmax (optional) caps the sample width: growth stops once r + dr > rmax,
+    and a front whose ranks still need more samples then returns H = S."""
     S = np.asarray(S, dtype=np.float64)
     n = S.shape[0]
     root = len(nodes) - 1
@@ -120,10 +124,16 @@ def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rma
             st[t] = dict(U=U, V=V, J=rows[Jl], K=cols[Kl], Yskel=Yl[Jl], Zskel=Zl[Kl],
                          Omt=V.T @ Oml, Pst=U.T @ Psl, swaps=iu["swaps"] + iv["swaps"])
         kmax = max(max(st[t]["U"].shape[1], st[t]["V"].shape[1]) for t in order)
-        if kmax > r - oversample and r < n and (rmax is None or r + dr <= rmax):
+        short_of_samples = kmax > r - oversample and r < n
+        if short_of_samples and (rmax is None or r + dr <= rmax):
             r += dr
             continue
         break
+    if short_of_samples:
+        return S.copy(), dict(r=r, rounds=rounds, nodes=nodes, capped=True,
+                              krow={t: st[t]["U"].shape[1] for t in order},
+                              kcol={t: st[t]["V"].shape[1] for t in order},
+                              swaps=sum(st[t]["swaps"] for t in order))
 
     # expansion: U^tall / V^tall bottom-up, then the dense blocks
     Ut, Vt = {}, {}
@@ -147,7 +157,7 @@ def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rma
             Rb = slice(nodes[b]["lo"], nodes[b]["hi"])
             H[Ra, Rb] = Ut[a] @ S[np.ix_(st[a]["J"], st[b]["K"])] @ Vt[b].T
             H[Rb, Ra] = Ut[b] @ S[np.ix_(st[b]["J"], st[a]["K"])] @ Vt[a].T
-    rep = dict(r=r, rounds=rounds, nodes=nodes,
+    rep = dict(r=r, rounds=rounds, nodes=nodes, capped=False,
                krow={t: st[t]["U"].shape[1] for t in order},
                kcol={t: st[t]["V"].shape[1] for t in order},
                J={t: st[t]["J"] for t in order}, K={t: st[t]["K"] for t in order},

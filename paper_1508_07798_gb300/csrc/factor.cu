@@ -268,6 +268,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
     std::vector<RoundFront> active;
     std::vector<ExpandItem> plain_items;
     std::vector<int> rounds(nf, 0), kmax(nf, 0), rfin(nf, 0);
+    std::vector<char> capped(nf, 0);
     for (int f = 0; f < nf; ++f) {
         int b = boxes[f];
         if (fr[f].nb == 0) continue;
@@ -447,23 +448,30 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         HSS_CUDA(cudaMemcpyAsync(hfk.data(), d_fk, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
         HSS_CUDA(cudaStreamSynchronize(s));
         // ---- decide: fronts whose rank reached r - oversample sample again, wider
+        // A front whose rank still needs more samples when the cap rmax stops
+        // the growth has no oversampling margin left: Theorem 1's error bound
+        // (l = k + p samples) does not hold, so it keeps S itself (H = S).
         std::vector<RoundFront> next;
-        std::vector<char> done(nc, 0);
+        std::vector<char> done(nc, 0), dense(nc, 0);
         for (int c = 0; c < nc; ++c) {
             int f = active[c].f, r = active[c].r;
             rounds[f]++;
             kmax[f] = hfk[c];
             rfin[f] = r;
-            if (hfk[c] > r - o.oversample && r < fr[f].nb && r + o.dr <= o.rmax)
+            const bool short_of_samples = hfk[c] > r - o.oversample && r < fr[f].nb;
+            if (short_of_samples && r + o.dr <= o.rmax) {
                 next.push_back({f, r + o.dr});
-            else
+            } else {
                 done[c] = 1;
+                dense[c] = short_of_samples;
+                capped[f] = short_of_samples;
+            }
         }
         // ---- expansion of the finished fronts: tall bases, then H tiles
         for (int dpt = maxd; dpt >= 1; --dpt) {
             std::vector<int> wk;
             for (int x : work[dpt])
-                if (done[nodes[x >> 1].cf]) wk.push_back(x);
+                if (done[nodes[x >> 1].cf] && !dense[nodes[x >> 1].cf]) wk.push_back(x);
             if (wk.empty()) continue;
             int *d_wk;
             if ((rc = W.up(wk, &d_wk))) return rc;
@@ -474,8 +482,14 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         int kmax_done = 0;
         for (int c = 0; c < nc; ++c) {
             if (!done[c]) continue;
-            kmax_done = std::max(kmax_done, hfk[c]);
             int f = active[c].f;
+            if (dense[c]) {
+                for (int r0 = 0; r0 < fr[f].nb; r0 += EXP_TILE)
+                    for (int c0 = 0; c0 < fr[f].nb; c0 += EXP_TILE)
+                        items.push_back({0, f, -1, -1, r0, c0, 0, fr[f].nb, 0, fr[f].nb});
+                continue;
+            }
+            kmax_done = std::max(kmax_done, hfk[c]);
             for (int i = node_base[c]; i < node_base[c + 1]; ++i) {
                 const NodeDev &N = nodes[i];
                 if (N.a < 0) {
@@ -510,6 +524,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         F->max_rank = std::max(F->max_rank, kmax[f]);
         F->max_r = std::max(F->max_r, rfin[f]);
         F->rounds = std::max(F->rounds, rounds[f]);
+        F->capped_fronts += capped[f];
     }
     (void)status_dev;
     (void)nstatus;
@@ -805,6 +820,7 @@ extern "C" int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info)
     info->max_r = f->max_r;
     info->rounds = f->rounds;
     info->nfronts = (int)f->log.size();
+    info->capped_fronts = f->capped_fronts;
     return HSS_OK;
 }
 

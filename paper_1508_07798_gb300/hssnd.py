@@ -71,7 +71,8 @@ class hss_tree_desc(C.Structure):
 
 class hss_factor_info(C.Structure):
     _fields_ = [("factor_bytes", C.c_double), ("front_flops", C.c_double), ("executed_flops", C.c_double),
-                ("max_rank", C.c_int), ("max_r", C.c_int), ("rounds", C.c_int), ("nfronts", C.c_int)]
+                ("max_rank", C.c_int), ("max_r", C.c_int), ("rounds", C.c_int), ("nfronts", C.c_int),
+                ("capped_fronts", C.c_int)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:

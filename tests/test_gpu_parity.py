@@ -144,6 +144,33 @@ def test_hss_approximant_matches_oracle():
         assert _rel(H, S) <= 1e-2          # the approximant is close to S
 
 
+def test_capped_sample_width_keeps_s_like_oracle():
+    """With the sample width capped at 32 and a tight tolerance, fronts whose
+    ranks exceed r - 10 keep S (H = S) on both sides; the rest are compressed
+    as usual.  Same fronts, same H, same count."""
+    import torch
+    hs = _hss()
+    mesh, A = _setup("helm", (16, 16), 2)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((2, (16, 16), 2), dA)
+    F = hs.hss_factor(dA, tree, tol=1e-9, seed=2, rmax=32, keep_schur=1)
+    nd = oracle.nd_order(2, mesh.n, 2, A.row_ptr, A.col_idx)
+    fac = oracle.factor(dg.bsr_to_csr(A), nd, tol=1e-9, seed=2, rmax=32, keep_h=True)
+    capped = [r["box"] for r in fac["log"] if r.get("capped")]
+    assert 0 < len(capped) < sum(1 for r in fac["log"] if r.get("nnodes", 1) > 1)
+    assert F.info()["capped_fronts"] == len(capped)
+    for b in range(nd["nbox"]):
+        if nd["nb"][b] == 0:
+            continue
+        S, H, kmax, r = F.export_front(b)
+        assert _rel(H, fac["boxes"][b]["H"]) <= TOL, b
+        if b in capped:
+            assert np.array_equal(H, S), b
+    X = dg.random_rhs(A.n, 1, 4)
+    Y = hs.hss_apply(F, torch.as_tensor(X, device="cuda")).cpu().numpy()
+    assert _rel(Y, oracle.apply(fac, X)) <= TOL
+
+
 SOLVES = [("poisson", (16, 16), 1, 1e-6, 1e-10), ("helm", (32, 32), 2, 1e-4, 1e-8),
           ("helm", (16, 16), 3, 1e-5, 1e-8)]
 

@@ -169,3 +169,22 @@ def test_single_node_is_identity():
     nodes = [dict(lo=0, hi=20, children=[], depth=0)]
     H, rep = hss_compress(S, nodes, 1e-4, 0, 0)
     assert np.array_equal(H, S)
+
+
+def test_hss_capped_width_keeps_s():
+    """Rank 30 needs r >= 40 samples (k + p, Theorem 1).  With the width
+    capped at 32 the bound does not hold: the front keeps S exactly.  With
+    room to grow (cap 64), the same matrix is recovered by the HSS build."""
+    n = 256
+    nodes = _nodes_binary(n, 64)
+    S = _hss_by_construction(nodes, 30, np.random.default_rng(4))
+    H, rep = hss_compress(S, nodes, 1e-12, seed=0, front_id=0, rmax=32)
+    assert rep["capped"] and rep["r"] == 32 and rep["rounds"] == 1
+    assert np.array_equal(H, S)
+    H2, rep2 = hss_compress(S, nodes, 1e-12, seed=0, front_id=0, rmax=64)
+    assert not rep2["capped"] and rep2["r"] == 64
+    assert not np.array_equal(H2, S) and np.linalg.norm(H2 - S) <= 1e-8 * np.linalg.norm(S)
+    # a low-rank matrix never reaches the cap
+    S3 = _hss_by_construction(nodes, 4, np.random.default_rng(5))
+    H3, rep3 = hss_compress(S3, nodes, 1e-12, seed=0, front_id=0, rmax=32)
+    assert not rep3["capped"] and np.linalg.norm(H3 - S3) <= 1e-9 * np.linalg.norm(S3)
