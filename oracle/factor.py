@@ -27,6 +27,32 @@ def csr_from_bsr(nb, bs, row_ptr, col_idx, val):
     return M.tocsr()
 
 
+def box_schur(A_csr, nd, b):
+    """Exact Schur complement of box b onto its boundary set B^b: the box's
+    dofs are the I sets of its whole subtree plus B^b, and S = F_bb -
+    F_bi F_ii^-1 F_ib with F = A(box, box) (Sec. 3, block elimination of the
+    box interior).  It equals the S that Algorithm 2 forms at b whenever no
+    Schur complement below b was approximated (compression off, or every
+    descendant kept its S), so boxes of a large problem can be checked one
+    at a time.  Rows and columns follow the stored order of B^b."""
+    A = A_csr.tocsr()
+    stack, inner = [int(b)], []
+    while stack:
+        c = stack.pop()
+        inner.append(nd["iset"][c])
+        if not nd["is_leaf"][c]:
+            stack.extend(int(x) for x in nd["child"][c])
+    I = np.concatenate(inner) if inner else np.zeros(0, dtype=np.int64)
+    B = nd["bset"][b]
+    idx = np.concatenate([I, B])
+    F = A[idx][:, idx].toarray()
+    ni = I.size
+    if ni == 0:
+        return F[ni:, ni:].copy()
+    W = sla.lu_solve(sla.lu_factor(F[:ni, :ni]), F[:ni, ni:])
+    return F[ni:, ni:] - F[ni:, :ni] @ W
+
+
 def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=10, rmax=None,
            keep_h=False):
     """Returns a dict with the per-box factors, the top block LU and logs.

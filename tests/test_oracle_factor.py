@@ -61,6 +61,34 @@ def test_schur_is_inverse_of_trailing_block_of_front_inverse():
     assert checked > 5
 
 
+def test_box_schur_at_leaves_is_inverse_of_trailing_block_of_leaf_inverse():
+    """The one-box Schur complement used for sampled checks of large problems,
+    at leaves: the trailing block of A(leaf, leaf)^-1 is S^-1 (Sec. 3)."""
+    mesh, A, nd, Acsr = _setup(2, (12, 12), 1, 36, "helm")   # 3 x 3-element leaves: one interior element
+    leaves = [b for b in range(nd["nbox"]) if nd["is_leaf"][b] and nd["ni"][b] > 0 and nd["nb"][b] > 0]
+    assert len(leaves) >= 4
+    for b in leaves[:6]:
+        S = oracle.box_schur(Acsr, nd, b)
+        idx = np.concatenate([nd["iset"][b], nd["bset"][b]])
+        Finv = np.linalg.inv(Acsr[idx][:, idx].toarray())
+        Sref = np.linalg.inv(Finv[nd["ni"][b]:, nd["ni"][b]:])
+        assert np.linalg.norm(S - Sref) <= 1e-10 * np.linalg.norm(Sref)
+
+
+@pytest.mark.parametrize("dim,n,p,leaf,kind", [(2, (8, 8), 2, 36, "helm"), (3, (4, 4, 4), 1, 64, "poisson")])
+def test_box_schur_equals_exact_factor_schur(dim, n, p, leaf, kind):
+    """With compression off, Algorithm 2's S at every box equals the Schur
+    complement of the box interior taken from A in one step."""
+    mesh, A, nd, Acsr = _setup(dim, n, p, leaf, kind)
+    fac = oracle.factor(Acsr, nd, compress=False)
+    for b in range(nd["nbox"]):
+        if nd["nb"][b] == 0:
+            continue
+        S = oracle.box_schur(Acsr, nd, b)
+        ref = fac["boxes"][b]["S"]
+        assert np.linalg.norm(S - ref) <= 1e-10 * np.linalg.norm(ref), b
+
+
 def test_front_assembly_from_children_and_A():
     """eq. (32): a parent front holds H of each child on its diagonal blocks and
     the original couplings A(B^mu, B^nu) across."""
