@@ -242,6 +242,47 @@ int hss_spmv(const hss_bsr *A, int nrhs, const double *x, int ldx, double *y, in
 int fgmres_solve(const hss_bsr *A, const hss_factor_t *f, int nrhs, const double *b, int ldb,
                  double *x, int ldx, const fgmres_opts *opts, fgmres_stats *stats, void *stream);
 
+/* ---- Batched form: many independent problems in one pass over the levels.
+ * The paper treats one problem; Algorithm 2 runs unchanged per instance and
+ * only the scheduling is shared.  All instances must have the same block size
+ * bs (group instances by dim and p).
+ *
+ * nd_order_batched: orders every instance as nd_order does and returns one
+ * forest: the instances' boxes, elements and dofs are concatenated in instance
+ * order (instance i's dof d is forest dof D_i + d, D_i the sum of the earlier
+ * instances' dof counts), and tree level l holds level l of every instance.
+ * meshes and As are HOST arrays of ninst entries (As' pointers are device
+ * pointers).  Synchronizes `stream`.  Errors: as nd_order (the failing
+ * instance is named in hss_last_error), HSS_EINVAL when block sizes differ. */
+int nd_order_batched(int ninst, const hss_mesh *meshes, const hss_bsr *As, const hss_nd_opts *opts,
+                     void *stream, hss_tree **out);
+
+/* hss_factor_batched: Algorithm 2 on every instance of a forest, one tree
+ * level of all instances at a time (each elimination, sampling, ID and
+ * expansion launch covers the fronts of every instance at that level).  Each
+ * instance keeps its own top block A^(0) (eq. (36)) and its test matrices are
+ * counted by the instance's own box ids, so instance i's part of the factor
+ * is the one hss_factor computes for instance i alone.  The factor keeps a
+ * device copy of the block-diagonal union of As (HOST array of ninst
+ * matrices).  hss_apply on the result applies every instance's
+ * preconditioner to a forest vector; hss_factor_export_front takes forest box
+ * ids.  Synchronizes `stream`.  Errors: as hss_factor. */
+int hss_factor_batched(int ninst, const hss_bsr *As, const hss_tree *forest, const hss_factor_opts *opts,
+                       void *stream, hss_factor_t **out);
+
+/* fgmres_solve_batched: the FGMRES(restart) of fgmres_solve for every
+ * (instance, right-hand side) pair of a batched factor, each an independent
+ * Krylov process with its own Hessenberg matrix, rotations, stopping test and
+ * restarts, all advanced in lock step so that an Arnoldi step costs one
+ * hss_apply and one SpMV over the whole batch (processes that have stopped
+ * are masked).  b, x: DEVICE forest vectors, ndof x nrhs column-major
+ * (ldb, ldx >= ndof); x holds x0 on entry and the solutions on return.
+ * stats: HOST array of ninst entries (per instance, over its right-hand
+ * sides), may be NULL.  Synchronizes `stream` once per Arnoldi step.
+ * Returns HSS_ENOCONV when a process reached maxit first. */
+int fgmres_solve_batched(const hss_factor_t *f, int nrhs, const double *b, int ldb, double *x, int ldx,
+                         const fgmres_opts *opts, fgmres_stats *stats, void *stream);
+
 /* Convergence history of the last fgmres_solve on this thread: Arnoldi residual
  * estimates |g_{j+1}|/||b|| of right-hand side `rhs` (HOST, up to cap values);
  * returns the count. */

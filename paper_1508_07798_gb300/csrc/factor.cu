@@ -13,10 +13,12 @@
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
+#include <cstdint>
 #include <cstring>
 
 #include "factor.h"
 #include "hss.h"
+#include "prof.h"
 
 namespace hssnd {
 
@@ -303,7 +305,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             cfs[c].lds = d.n;
             cfs[c].nb = d.nb;
             cfs[c].r = r;
-            cfs[c].box = boxes[active[c].f];
+            cfs[c].box = t->box_local[boxes[active[c].f]];
             cfs[c].yoff = wsz;
             wsz += (long)d.nb * r;
             cfs[c].zoff = wsz;
@@ -588,15 +590,25 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         foff[b] = total;
         total += (n * n + 31) / 32 * 32;
     }
-    const int ntop = t->nb[0] + t->nb[1];
-    const long foff_top = total;
-    total += (long)ntop * ntop;
+    // one top block A^(0) per instance (a plain tree is a forest of one)
+    const int ninst = t->ninst;
+    std::vector<int> ntop_i(ninst), top_off(ninst + 1, 0);
+    std::vector<long> foff_top(ninst);
+    std::vector<int> topset;
+    for (int i = 0; i < ninst; ++i) {
+        const int b0 = t->inst_top[i];
+        ntop_i[i] = t->nb[b0] + t->nb[b0 + 1];
+        foff_top[i] = total;
+        total += ((long)ntop_i[i] * ntop_i[i] + 31) / 32 * 32;
+        top_off[i + 1] = top_off[i] + ntop_i[i];
+        topset.insert(topset.end(), t->bset.begin() + t->boff[b0], t->bset.begin() + t->boff[b0 + 2]);
+    }
+    const int ntop = top_off[ninst];
     F->ntop = ntop;
     if ((rc = F->arena.alloc(sizeof(T) * std::max(total, 1L)))) return rc;
     HSS_CUDA(cudaMemsetAsync(F->arena.p, 0, sizeof(T) * total, s));
     T *arena = F->arena_ptr<T>();
     const int ilen = t->ioff[nbox];
-    std::vector<int> topset(t->bset.begin() + t->boff[0], t->bset.begin() + t->boff[2]);
     DevBuf d_piv, d_scratch, d_slot;
     if ((rc = upload(F->d_topset, topset, s)) || (rc = F->d_iperm.alloc(sizeof(int) * (ilen + ntop + 1))) ||
         (rc = d_piv.alloc(sizeof(int) * (ilen + ntop + 1))) || (rc = d_scratch.alloc(sizeof(int) * (ilen + ntop + 1))) ||
@@ -679,8 +691,8 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             fr.push_back(front_of(b));
             front_dofs(b, dofs[f], sides[f]);
             int par = t->parent[b];
-            poff[f] = par >= 0 ? foff[par] : foff_top;
-            pn[f] = par >= 0 ? t->ni[par] + t->nb[par] : ntop;
+            poff[f] = par >= 0 ? foff[par] : foff_top[t->box_inst[b]];
+            pn[f] = par >= 0 ? t->ni[par] + t->nb[par] : ntop_i[t->box_inst[b]];
             keeph[f] = F->keep_h[b];
             const double ni = fr.back().ni, nb = fr.back().nb;
             F->front_flops += 2.0 / 3.0 * ni * ni * ni + 2.0 * ni * ni * nb + 2.0 * nb * nb * ni;
@@ -720,44 +732,51 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), false, part_total, tk_total, s)))
             return rc;
     }
-    // ---- top block A^(0): cross couplings from A, then full Gauss-Jordan inversion
+    // ---- top blocks A^(0): cross couplings from A, then full Gauss-Jordan inversion
     {
-        FrontDev top{};
-        top.foff = foff_top;
-        top.n = ntop;
-        top.ni = ntop;
-        top.nb = 0;
-        top.ioff = ilen;
-        top.iset_off = 0;
-        top.iperm_off = ilen;
-        top.bset_off = 0;
-        top.leaf = 0;
-        top.box = -1;
-        std::vector<FrontDev> fr = {top};
-        std::vector<std::vector<int>> dofs(1), sides(1);
-        dofs[0] = topset;
-        sides[0].assign(ntop / t->bs, 1);
-        for (int q = 0; q < t->nb[0] / t->bs; ++q) sides[0][q] = 0;
+        std::vector<FrontDev> fr(ninst);
+        std::vector<std::vector<int>> dofs(ninst), sides(ninst);
+        for (int i = 0; i < ninst; ++i) {
+            FrontDev &top = fr[i];
+            top = FrontDev{};
+            top.foff = foff_top[i];
+            top.n = ntop_i[i];
+            top.ni = ntop_i[i];
+            top.nb = 0;
+            top.ioff = ilen + top_off[i];
+            top.iset_off = top_off[i];
+            top.iperm_off = ilen + top_off[i];
+            top.bset_off = 0;
+            top.leaf = 0;
+            top.box = -1 - i;
+            dofs[i].assign(topset.begin() + top_off[i], topset.begin() + top_off[i + 1]);
+            sides[i].assign(ntop_i[i] / t->bs, 1);
+            for (int q = 0; q < t->nb[t->inst_top[i]] / t->bs; ++q) sides[i][q] = 0;
+        }
         W.reset();
         DevBuf d_fr;
         int *d_status;
-        if ((rc = upload(d_fr, fr, s)) || (rc = W.dalloc(1, &d_status))) return rc;
-        HSS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+        if ((rc = upload(d_fr, fr, s)) || (rc = W.dalloc(ninst, &d_status))) return rc;
+        HSS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int) * ninst, s));
         if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
             return rc;
         if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
                                      F->d_topset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, eng, W, s)))
             return rc;
-        int hst = 0;
-        HSS_CUDA(cudaMemcpyAsync(&hst, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        std::vector<int> hst(ninst);
+        HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status, sizeof(int) * ninst, cudaMemcpyDeviceToHost, s));
         HSS_CUDA(cudaStreamSynchronize(s));
-        if (hst) {
-            set_error("hss_factor: zero pivot in the top block");
-            return HSS_ESINGULAR;
-        }
+        for (int i = 0; i < ninst; ++i)
+            if (hst[i]) {
+                set_error(ninst == 1 ? std::string("hss_factor: zero pivot in the top block")
+                                     : "hss_factor: zero pivot in the top block of instance " + std::to_string(i));
+                return HSS_ESINGULAR;
+            }
         if ((rc = check_tc())) return rc;
-        F->front_flops += 2.0 / 3.0 * (double)ntop * ntop * ntop;
-        F->factor_bytes += sizeof(T) * (double)ntop * ntop;
+        for (int i = 0; i < ninst; ++i) {
+            F->front_flops += 2.0 / 3.0 * (double)ntop_i[i] * ntop_i[i] * ntop_i[i];
+            F->factor_bytes += sizeof(T) * (double)ntop_i[i] * ntop_i[i];
+        }
         F->apply.emplace_back();
         if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), true, part_total, tk_total, s)))
             return rc;
@@ -776,6 +795,109 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
 }  // namespace hssnd
 
 using namespace hssnd;
+
+namespace hssnd {
+// dst[i] = src[i] + add (row pointers and column indices of one instance moved
+// into the block-diagonal union)
+__global__ void k_shift_index(const int *__restrict__ src, int n, int add, int *__restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i] + add;
+}
+}  // namespace hssnd
+
+static int check_factor_opts(const hss_factor_opts &o, const char *who) {
+    if (!(o.tol >= 0) || o.r0 < 1 || o.dr < 1 || o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 ||
+        (o.precision != HSS_FP64 && o.precision != HSS_FP32)) {
+        set_error(std::string(who) + ": options out of range (rmax <= 128)");
+        return HSS_EINVAL;
+    }
+    return HSS_OK;
+}
+
+extern "C" int hss_factor_batched(int ninst, const hss_bsr *As, const hss_tree *forest, const hss_factor_opts *opts,
+                                  void *stream, hss_factor_t **out) {
+    if (!As || !forest || !out || ninst < 1) {
+        set_error("hss_factor_batched: null argument or ninst < 1");
+        return HSS_EINVAL;
+    }
+    *out = nullptr;
+    hss_factor_opts o;
+    hss_factor_opts_default(&o);
+    if (opts) o = *opts;
+    int rc;
+    if ((rc = check_factor_opts(o, "hss_factor_batched"))) return rc;
+    if (forest->ninst != ninst) {
+        set_error("hss_factor_batched: the tree is not a forest of ninst instances (use nd_order_batched)");
+        return HSS_EINVAL;
+    }
+    const int bs = forest->bs;
+    for (int i = 0; i < ninst; ++i)
+        if (As[i].bs != bs || As[i].nb != forest->inst_elem[i + 1] - forest->inst_elem[i] || !As[i].row_ptr ||
+            !As[i].col_idx || !As[i].val) {
+            set_error("hss_factor_batched: matrix " + std::to_string(i) + " does not match its tree");
+            return HSS_EINVAL;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int> nnz(ninst);
+    for (int i = 0; i < ninst; ++i)
+        HSS_CUDA(cudaMemcpyAsync(&nnz[i], As[i].row_ptr + As[i].nb, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSS_CUDA(cudaStreamSynchronize(s));
+    long nnz_tot = 0;
+    for (int v : nnz) nnz_tot += v;
+    if (nnz_tot > INT32_MAX) {
+        set_error("hss_factor_batched: more than 2^31 blocks in the union");
+        return HSS_EINVAL;
+    }
+    hss_factor_t *F = new hss_factor_t();
+    const int nelem = forest->nelem;
+    if ((rc = F->b_row.alloc(sizeof(int) * (nelem + 1))) || (rc = F->b_col.alloc(sizeof(int) * std::max(nnz_tot, 1L))) ||
+        (rc = F->b_val.alloc(sizeof(double) * std::max(nnz_tot, 1L) * bs * bs))) {
+        delete F;
+        return rc;
+    }
+    int *row = F->b_row.as<int>(), *col = F->b_col.as<int>();
+    double *val = F->b_val.as<double>();
+    long off = 0;
+    for (int i = 0; i < ninst; ++i) {
+        const int e0 = forest->inst_elem[i];
+        if (As[i].nb > 0) {
+            HSS_PROF("shift_index", s);
+            k_shift_index<<<cdiv(As[i].nb, 256), 256, 0, s>>>(As[i].row_ptr, As[i].nb, (int)off, row + e0);
+        }
+        if (nnz[i] > 0) {
+            {
+                HSS_PROF("shift_index", s);
+                k_shift_index<<<std::min(cdiv(nnz[i], 256), 1024), 256, 0, s>>>(As[i].col_idx, nnz[i], e0, col + off);
+            }
+            if (cudaMemcpyAsync(val + off * bs * bs, As[i].val, sizeof(double) * (size_t)nnz[i] * bs * bs,
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                delete F;
+                return cuda_fail(cudaGetLastError(), "hss_factor_batched: copy of the block values");
+            }
+        }
+        off += nnz[i];
+    }
+    const int last = (int)nnz_tot;
+    if (cudaMemcpyAsync(row + nelem, &last, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        delete F;
+        return cuda_fail(cudaGetLastError(), "hss_factor_batched: block-diagonal union");
+    }
+    F->batched = 1;
+    F->bA = hss_bsr{nelem, bs, row, col, val};
+    F->tree = forest;
+    F->ndof = forest->ndof;
+    F->precision = o.precision;
+    F->opts = o;
+    rc = o.precision == HSS_FP32 ? factor_impl<float>(&F->bA, forest, o, s, F)
+                                 : factor_impl<double>(&F->bA, forest, o, s, F);
+    if (rc) {
+        cudaStreamSynchronize(s);
+        delete F;
+        return rc;
+    }
+    *out = F;
+    return HSS_OK;
+}
 
 extern "C" int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_factor_opts *opts, void *stream,
                           hss_factor_t **out) {

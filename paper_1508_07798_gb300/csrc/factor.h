@@ -51,6 +51,7 @@ struct FrontLog {   // per-front record (rank logging, Sec. 5 empirical cost)
 };
 
 int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);
+int spmv(const hss_bsr *A, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);
 
 }  // namespace hssnd
 
@@ -77,6 +78,11 @@ struct hss_factor_t {
     hssnd::DevBuf d_aparams;
     hssnd::DevBuf d_apart;       // partial sums of split apply tiles (items x 32 x 4)
     hssnd::DevBuf d_tickets;     // one ticket counter per split tile
+    // batched factor (hss_factor_batched): device copy of the block-diagonal
+    // union of the instances' matrices, used by the batched solver
+    int batched = 0;
+    hss_bsr bA{};
+    hssnd::DevBuf b_row, b_col, b_val;
     template <class T> T *arena_ptr() const { return arena.as<T>(); }
     // algorithmic bytes of one apply: factor entries once, vector traffic per right-hand side
     double apply_bytes(int nrhs) const {

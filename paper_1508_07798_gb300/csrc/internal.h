@@ -115,6 +115,14 @@ struct hss_tree {
     hssnd::DevBuf d_iset, d_bset, d_fmap;
     // HSS tree of each box's S over B^box (nodes in post-order, root last)
     std::vector<std::vector<hssnd::HssNode>> hss;
+    // A forest of independent instances (nd_order_batched) concatenates the
+    // instances' boxes, dofs and elements; nd_order makes a forest of one.
+    int ninst = 1;
+    std::vector<int> inst_top;     // first level-1 box of each instance (its sibling is inst_top + 1)
+    std::vector<int> inst_dof;     // first dof of each instance, ninst + 1 entries
+    std::vector<int> inst_elem;    // first element of each instance, ninst + 1 entries
+    std::vector<int> box_inst;     // instance of each box
+    std::vector<int> box_local;    // box id inside its instance (counter of the test matrices)
 };
 
 namespace hssnd {

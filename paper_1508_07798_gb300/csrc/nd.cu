@@ -485,7 +485,107 @@ extern "C" int nd_order(const hss_mesh *mesh, const hss_bsr *A, const hss_nd_opt
     for (int b = 0; b < 2; ++b)
         t->perm.insert(t->perm.end(), t->bset.begin() + t->boff[b], t->bset.begin() + t->boff[b + 1]);
     build_hss_trees(t);
+    t->ninst = 1;
+    t->inst_top = {0};
+    t->inst_dof = {0, t->ndof};
+    t->inst_elem = {0, t->nelem};
+    t->box_inst.assign(nbox, 0);
+    t->box_local.resize(nbox);
+    for (int b = 0; b < nbox; ++b) t->box_local[b] = b;
     *out = t;
+    return HSS_OK;
+}
+
+extern "C" int nd_order_batched(int ninst, const hss_mesh *meshes, const hss_bsr *As, const hss_nd_opts *opts,
+                                void *stream, hss_tree **out) {
+    if (!meshes || !As || !out || ninst < 1) {
+        set_error("nd_order_batched: null argument or ninst < 1");
+        return HSS_EINVAL;
+    }
+    *out = nullptr;
+    std::vector<hss_tree *> parts(ninst, nullptr);
+    auto drop = [&](int rc) {
+        for (auto *q : parts) delete q;
+        return rc;
+    };
+    for (int i = 0; i < ninst; ++i) {
+        int rc = nd_order(meshes + i, As + i, opts, stream, &parts[i]);
+        if (rc) {
+            set_error("nd_order_batched: instance " + std::to_string(i) + ": " + hss_last_error());
+            return drop(rc);
+        }
+        if (parts[i]->bs != parts[0]->bs) {
+            set_error("nd_order_batched: instances must share the block size (instance " + std::to_string(i) + ")");
+            return drop(HSS_EINVAL);
+        }
+    }
+    hss_tree *F = new hss_tree;
+    const hss_tree &P0 = *parts[0];
+    F->dim = P0.dim;
+    std::copy(P0.n, P0.n + 3, F->n);
+    F->p = P0.p;
+    F->bs = P0.bs;
+    F->opts = P0.opts;
+    F->ninst = ninst;
+    F->ioff.push_back(0);
+    F->boff.push_back(0);
+    int dof0 = 0, elem0 = 0, box0 = 0;
+    for (int i = 0; i < ninst; ++i) {
+        const hss_tree &P = *parts[i];
+        const int ib = (int)F->iset.size(), bb = (int)F->bset.size();
+        F->inst_top.push_back(box0);
+        F->inst_dof.push_back(dof0);
+        F->inst_elem.push_back(elem0);
+        F->maxlev = std::max(F->maxlev, P.maxlev);
+        for (int b = 0; b < P.nbox; ++b) {
+            F->level.push_back(P.level[b]);
+            F->parent.push_back(P.parent[b] < 0 ? -1 : P.parent[b] + box0);
+            F->child0.push_back(P.child0[b] < 0 ? -1 : P.child0[b] + box0);
+            F->child1.push_back(P.child1[b] < 0 ? -1 : P.child1[b] + box0);
+            F->lohi.insert(F->lohi.end(), P.lohi.begin() + 6 * b, P.lohi.begin() + 6 * b + 6);
+            F->pos0.push_back(P.pos0[b] + dof0);
+            F->pos1.push_back(P.pos1[b] + dof0);
+            F->ni.push_back(P.ni[b]);
+            F->nb.push_back(P.nb[b]);
+            F->ioff.push_back(ib + P.ioff[b + 1]);
+            F->boff.push_back(bb + P.boff[b + 1]);
+            F->hss.push_back(P.hss[b]);
+            F->box_inst.push_back(i);
+            F->box_local.push_back(b);
+        }
+        for (int v : P.iset) F->iset.push_back(v + dof0);
+        for (int v : P.bset) F->bset.push_back(v + dof0);
+        F->fmap.insert(F->fmap.end(), P.fmap.begin(), P.fmap.end());
+        for (int v : P.perm) F->perm.push_back(v + dof0);
+        for (int v : P.dfs_elem) F->dfs_elem.push_back(v + elem0);
+        dof0 += P.ndof;
+        elem0 += P.nelem;
+        box0 += P.nbox;
+    }
+    F->inst_dof.push_back(dof0);
+    F->inst_elem.push_back(elem0);
+    F->ndof = dof0;
+    F->nelem = elem0;
+    F->nbox = box0;
+    for (int lev = F->maxlev; lev >= 1; --lev) {
+        std::vector<int> st;
+        for (int b = 0; b < F->nbox; ++b)
+            if (F->level[b] == lev) st.push_back(b);
+        F->stages.push_back(st);
+    }
+    drop(0);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = upload(F->d_iset, F->iset.empty() ? std::vector<int>{0} : F->iset, s)) ||
+        (rc = upload(F->d_bset, F->bset, s)) || (rc = upload(F->d_fmap, F->fmap, s))) {
+        delete F;
+        return rc;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        delete F;
+        return cuda_fail(cudaGetLastError(), "nd_order_batched upload");
+    }
+    *out = F;
     return HSS_OK;
 }
 

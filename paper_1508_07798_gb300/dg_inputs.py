@@ -325,6 +325,28 @@ def point_source_rhs(mesh: Mesh, seed: int) -> np.ndarray:
     return np.asfortranarray(b.reshape(-1, 1))
 
 
+def batched_instances(count: int, master_seed: int = 0, n_range=(16, 64), p_set=(1, 2, 3),
+                      ops=("poisson", "helmholtz")):
+    """Independent problems of the batched workload: per instance i the seed
+    splitmix64(master_seed + i) draws the mesh size n ~ U{n_range}, the degree
+    p from p_set and the operator (Bernoulli 1/2 over ops); Helmholtz takes
+    10 dofs per wavelength and c(x) per cosine_field, Poisson a = 1.  Returns
+    a list of dicts (mesh, A, kind, seed)."""
+    out = []
+    for i in range(count):
+        sd = splitmix64(master_seed + i)
+        n = n_range[0] + int(sd % (n_range[1] - n_range[0] + 1))
+        p = p_set[int((sd >> 16) % len(p_set))]
+        kind = ops[int((sd >> 32) % len(ops))]
+        seed = int((sd >> 40) & 0xFFFF)
+        if kind == "poisson":
+            mesh, A = poisson_2d(n, p)
+        else:
+            mesh, A = helmholtz_2d(n, p, seed)
+        out.append(dict(mesh=mesh, A=A, kind=kind, seed=seed))
+    return out
+
+
 def bsr_to_csr(A: BSR):
     """scipy CSR copy of the block matrix (row-major blocks)."""
     import scipy.sparse as sp

@@ -27,7 +27,7 @@ EXPORTED = [
     "hss_factor_export_front", "hss_apply", "hss_spmv", "fgmres_solve", "fgmres_history",
     "hss_tree_destroy", "hss_factor_destroy", "hss_last_error",
     "hss_launch_count", "hss_profile_enable", "hss_profile_reset", "hss_profile_read", "hss_gemm_f32",
-    "hss_gemm_f32_static",
+    "hss_gemm_f32_static", "nd_order_batched", "hss_factor_batched", "fgmres_solve_batched",
 ]
 
 
@@ -105,6 +105,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                    C.c_float, C.c_int, P]),
         "hss_gemm_f32_static": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.c_int, P, C.c_int,
                                           C.c_float, C.c_float, C.c_int, P]),
+        "nd_order_batched": (C.c_int, [C.c_int, C.POINTER(hss_mesh), C.POINTER(hss_bsr), C.POINTER(hss_nd_opts), P,
+                                       C.POINTER(P)]),
+        "hss_factor_batched": (C.c_int, [C.c_int, C.POINTER(hss_bsr), P, C.POINTER(hss_factor_opts), P,
+                                         C.POINTER(P)]),
+        "fgmres_solve_batched": (C.c_int, [P, C.c_int, P, C.c_int, P, C.c_int, C.POINTER(fgmres_opts),
+                                           C.POINTER(fgmres_stats), P]),
         "hss_profile_enable": (C.c_int, [C.c_int]),
         "hss_profile_reset": (C.c_int, []),
         "hss_profile_read": (C.c_int, [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
@@ -167,6 +173,7 @@ class Tree:
     def __init__(self, handle, mesh):
         self.h = C.c_void_p(handle)
         self.mesh = mesh
+        self.ninst = 1
         d = hss_tree_desc()
         _check(_lib.hss_tree_info(self.h, C.byref(d)))
         self.desc = d
@@ -291,6 +298,54 @@ def fgmres_solve(A: DeviceBSR, F: Factor | None, b: torch.Tensor, x0: torch.Tens
                              C.byref(o), C.byref(st), _stream(stream)), allow=(HSS_ENOCONV,))
     x = xs.t()
     return (x.reshape(N) if b.dim() == 1 else x), SolveStats(st.iters, st.max_iters, st.relres, bool(st.converged))
+
+
+def _mesh_struct(mesh):
+    dim, n, p = mesh
+    n3 = list(n) + [1] * (3 - len(n))
+    return hss_mesh(dim, (C.c_int * 3)(*n3), p)
+
+
+def nd_order_batched(meshes, As, leaf_max=64, scheme="box", stream=None) -> Tree:
+    """Forest of independent instances (same block size).  The returned tree
+    carries `inst_dof`: the first forest dof of each instance (ninst + 1)."""
+    k = len(meshes)
+    assert k == len(As) and k >= 1
+    ms = (hss_mesh * k)(*[_mesh_struct(m) for m in meshes])
+    bs = (hss_bsr * k)(*[A.c for A in As])
+    o = hss_nd_opts(leaf_max, SCHEMES[scheme])
+    out = C.c_void_p()
+    _check(_lib.nd_order_batched(k, ms, bs, C.byref(o), _stream(stream), C.byref(out)))
+    t = Tree(out.value, list(meshes))
+    t.ninst = k
+    t.inst_dof = np.concatenate([[0], np.cumsum([A.n for A in As])]).astype(np.int64)
+    return t
+
+
+def hss_factor_batched(As, forest: Tree, stream=None, **kw) -> Factor:
+    o = factor_opts(**kw)
+    k = len(As)
+    bs = (hss_bsr * k)(*[A.c for A in As])
+    out = C.c_void_p()
+    _check(_lib.hss_factor_batched(k, bs, forest.h, C.byref(o), _stream(stream), C.byref(out)))
+    return Factor(out.value, forest, o.precision)
+
+
+def fgmres_solve_batched(F: Factor, B: torch.Tensor, x0: torch.Tensor | None = None, restart=30, rtol=1e-8,
+                         maxit=1000, stream=None):
+    """B: forest right-hand sides (ndof,) or (ndof, nrhs).  Returns X and one
+    SolveStats per instance."""
+    N = F.tree.desc.ndof
+    bs_, k = _colmajor(B, N)
+    xs = torch.zeros_like(bs_) if x0 is None else _colmajor(x0, N)[0]
+    o = fgmres_opts(restart, rtol, maxit)
+    ninst = F.tree.ninst
+    st = (fgmres_stats * ninst)()
+    _check(_lib.fgmres_solve_batched(F.h, k, _ptr(bs_), N, _ptr(xs), N, C.byref(o), st, _stream(stream)),
+           allow=(HSS_ENOCONV,))
+    x = xs.t()
+    stats = [SolveStats(s_.iters, s_.max_iters, s_.relres, bool(s_.converged)) for s_ in st]
+    return (x.reshape(N) if B.dim() == 1 else x), stats
 
 
 def fgmres_history(rhs=0, cap=100000) -> np.ndarray:

@@ -1,0 +1,170 @@
+"""Batched form through the C ABI: a forest of independent instances factored
+one level of all instances at a time, and solved by lock-step FGMRES.
+
+Per instance the batched path computes what the single-instance path
+computes: the forest's sets are the instances' sets shifted by the dof
+offsets, every front's S and H equal the single-instance ones exactly (same
+kernels, same per-front arithmetic, test matrices counted by the instance's
+own box ids), the apply equals the per-instance applies, and each (instance,
+right-hand side) process converges to the same true residual with the
+single-instance iteration count within +-10% (at least +-1).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1508_07798_gb300 import dg_inputs as dg
+
+pytestmark = pytest.mark.gpu
+
+
+def _hss():
+    from paper_1508_07798_gb300 import hssnd
+    return hssnd
+
+
+def _instances(specs):
+    out = []
+    for kind, n, p, seed in specs:
+        mesh, A = dg.helmholtz_2d(n, p, seed) if kind == "helm" else dg.poisson_2d(n, p)
+        out.append((mesh, A))
+    return out
+
+
+SPECS = [("helm", 12, 2, 1), ("poisson", 9, 2, 0), ("helm", 16, 2, 2), ("poisson", 5, 2, 0), ("helm", 7, 2, 3)]
+
+
+def test_forest_equals_single_instances_fronts_apply_solve():
+    import torch
+    hs = _hss()
+    inst = _instances(SPECS)
+    dAs = [hs.DeviceBSR.from_host(A) for _, A in inst]
+    meshes = [(2, (m.n[0], m.n[1]), m.p) for m, _ in inst]
+    forest = hs.nd_order_batched(meshes, dAs)
+    ex = forest.export()
+    off = forest.inst_dof
+    box0 = 0
+    singles = []
+    for i, ((mesh, A), dA) in enumerate(zip(inst, dAs)):
+        t = hs.nd_order(meshes[i], dA)
+        e = t.export()
+        nb_ = len(e["level"])
+        sl = slice(box0, box0 + nb_)
+        assert np.array_equal(ex["level"][sl], e["level"])
+        assert np.array_equal(ex["ni"][sl], e["ni"]) and np.array_equal(ex["nb"][sl], e["nb"])
+        par = ex["parent"][sl]
+        assert np.array_equal(np.where(par >= 0, par - box0, -1), e["parent"])
+        ib0, bb0 = ex["ioff"][box0], ex["boff"][box0]
+        assert np.array_equal(ex["iset"][ib0:ib0 + len(e["iset"])], e["iset"] + off[i])
+        assert np.array_equal(ex["bset"][bb0:bb0 + len(e["bset"])], e["bset"] + off[i])
+        assert np.array_equal(ex["fmap"][bb0:bb0 + len(e["fmap"])], e["fmap"])
+        singles.append((t, box0, nb_))
+        box0 += nb_
+    FB = hs.hss_factor_batched(dAs, forest, tol=1e-6, seed=4, keep_schur=1)
+    Fs = []
+    compressed = 0
+    for i, (t, b0, nb_) in enumerate(singles):
+        F = hs.hss_factor(dAs[i], t, tol=1e-6, seed=4, keep_schur=1)
+        Fs.append(F)
+        e = t.export()
+        for b in range(nb_):
+            if e["nb"][b] == 0:
+                continue
+            S1, H1, k1, r1 = F.export_front(b)
+            S2, H2, k2, r2 = FB.export_front(b0 + b)
+            assert np.array_equal(S1, S2) and np.array_equal(H1, H2) and (k1, r1) == (k2, r2), (i, b)
+            compressed += r1 > 0
+    assert compressed > 0
+    # apply: the forest vector is the instances' vectors stacked
+    N = int(off[-1])
+    X = torch.as_tensor(dg.random_rhs(N, 3, 9), device="cuda")
+    YB = hs.hss_apply(FB, X)
+    for i, F in enumerate(Fs):
+        Yi = hs.hss_apply(F, X[off[i]:off[i + 1]].contiguous())
+        assert torch.equal(YB[off[i]:off[i + 1]], Yi), i
+    # lock-step FGMRES: every (instance, rhs) process as in the single solve
+    B = torch.as_tensor(dg.random_rhs(N, 3, 5, kind="normal"), device="cuda")
+    XB, stB = hs.fgmres_solve_batched(FB, B, rtol=1e-9)
+    assert len(stB) == len(inst) and all(s_.converged for s_ in stB)
+    for i, (F, (mesh, A)) in enumerate(zip(Fs, inst)):
+        Bi = B[off[i]:off[i + 1]].contiguous()
+        Xi, sti = hs.fgmres_solve(dAs[i], F, Bi, rtol=1e-9)
+        Acsr = dg.bsr_to_csr(A)
+        xb = XB[off[i]:off[i + 1]].cpu().numpy()
+        bi = Bi.cpu().numpy()
+        res = np.linalg.norm(bi - Acsr @ xb, axis=0) / np.linalg.norm(bi, axis=0)
+        assert res.max() <= 1e-9 * (1 + 1e-6), (i, res)
+        assert abs(stB[i].iters - sti.iters) <= max(3, round(0.1 * sti.iters)), (i, stB[i].iters, sti.iters)
+        assert abs(stB[i].max_iters - sti.max_iters) <= max(1, round(0.1 * sti.max_iters)), i
+
+
+def test_forest_apply_matches_oracle_per_instance():
+    import torch
+    hs = _hss()
+    inst = _instances([("poisson", 8, 1, 0), ("helm", 10, 1, 6), ("poisson", 3, 1, 0)])
+    dAs = [hs.DeviceBSR.from_host(A) for _, A in inst]
+    meshes = [(2, (m.n[0], m.n[1]), m.p) for m, _ in inst]
+    forest = hs.nd_order_batched(meshes, dAs, leaf_max=16)
+    FB = hs.hss_factor_batched(dAs, forest, tol=1e-6, seed=1)
+    off = forest.inst_dof
+    X = dg.random_rhs(int(off[-1]), 2, 3)
+    Y = hs.hss_apply(FB, torch.as_tensor(X, device="cuda")).cpu().numpy()
+    for i, (mesh, A) in enumerate(inst):
+        nd = oracle.nd_order(2, mesh.n, mesh.p, A.row_ptr, A.col_idx, leaf_max=16)
+        fac = oracle.factor(dg.bsr_to_csr(A), nd, tol=1e-6, seed=1, rmax=96)
+        ref = oracle.apply(fac, X[off[i]:off[i + 1]])
+        got = Y[off[i]:off[i + 1]]
+        assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref), i
+
+
+def test_batched_mixed_workload_fp32_solves():
+    """A scaled-down batched workload (same generator, smaller meshes): one
+    forest per block size, FP32 factors, 4 right-hand sides per instance."""
+    import torch
+    hs = _hss()
+    inst = dg.batched_instances(18, master_seed=3, n_range=(8, 24))
+    groups = {}
+    for d in inst:
+        groups.setdefault(d["mesh"].p, []).append(d)
+    assert len(groups) >= 2
+    for p, ds in sorted(groups.items()):
+        dAs = [hs.DeviceBSR.from_host(d["A"]) for d in ds]
+        meshes = [(2, (d["mesh"].n[0], d["mesh"].n[1]), p) for d in ds]
+        forest = hs.nd_order_batched(meshes, dAs)
+        F = hs.hss_factor_batched(dAs, forest, tol=1e-6, precision="fp32")
+        off = forest.inst_dof
+        B = torch.as_tensor(dg.random_rhs(int(off[-1]), 4, p, kind="normal"), device="cuda")
+        X, st = hs.fgmres_solve_batched(F, B, rtol=1e-8)
+        assert all(s_.converged for s_ in st), p
+        for i, d in enumerate(ds):
+            Acsr = dg.bsr_to_csr(d["A"])
+            xb = X[off[i]:off[i + 1]].cpu().numpy()
+            bi = B[off[i]:off[i + 1]].cpu().numpy()
+            res = np.linalg.norm(bi - Acsr @ xb, axis=0) / np.linalg.norm(bi, axis=0)
+            assert res.max() <= 1e-8 * (1 + 1e-6), (p, i, res)
+
+
+def test_batched_errors():
+    import torch
+    hs = _hss()
+    (m1, A1), (m2, A2) = _instances([("poisson", 4, 1, 0), ("poisson", 4, 2, 0)])
+    d1, d2 = hs.DeviceBSR.from_host(A1), hs.DeviceBSR.from_host(A2)
+    with pytest.raises(hs.HssError) as e:
+        hs.nd_order_batched([(2, (4, 4), 1), (2, (4, 4), 2)], [d1, d2])
+    assert e.value.code == hs.HSS_EINVAL
+    t = hs.nd_order((2, (4, 4), 1), d1)
+    F = hs.hss_factor(d1, t)
+    with pytest.raises(hs.HssError) as e:
+        hs.fgmres_solve_batched(F, torch.zeros(A1.n, dtype=torch.float64, device="cuda"))
+    assert e.value.code == hs.HSS_EINVAL
+    forest = hs.nd_order_batched([(2, (4, 4), 1)] * 2, [d1, d1])
+    with pytest.raises(hs.HssError) as e:
+        hs.hss_factor_batched([d1], forest)
+    assert e.value.code == hs.HSS_EINVAL
+    # a zero right-hand side for one process: x = 0 there, the others solve
+    FB = hs.hss_factor_batched([d1, d1], forest)
+    B = torch.as_tensor(dg.random_rhs(2 * A1.n, 1, 0), device="cuda")
+    B[:A1.n] = 0
+    X, st = hs.fgmres_solve_batched(FB, B)
+    assert st[0].converged and st[0].iters == 0 and st[1].converged
+    assert torch.count_nonzero(X[:A1.n]) == 0
