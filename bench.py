@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--forms", default="fp32,fp64")
+    ap.add_argument("--workload", default="helmholtz64", choices=["helmholtz64", "batched256"],
+                    help="helmholtz64: the timed workload (default); batched256: 256 independent "
+                         "instances x 32 right-hand sides through the batched form (its own JSON line)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no apply loop, no host-buffer run): for profiling")
     return ap.parse_args()
@@ -60,6 +63,28 @@ def peaks():
 # FP32: 128 FMA/clk/SM -> 80.5 TFLOP/s.  FP64: the nominal 1.25 TFLOP/s of GB300.
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_TFLOPS = 1.25
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
+    when there is none or the kernel's source changed since the capture."""
+    import hashlib
+    files = {"gemm_f32": ("profiles/k_gemm_f32_dram_helmholtz64_p2.md", "paper_1508_07798_gb300/csrc/gemm.cu")}
+    if kernel not in files:
+        return None
+    summary, src = (os.path.join(ROOT, f) for f in files[kernel])
+    try:
+        kv = {}
+        for line in open(summary):
+            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "kernel_source_sha256_prefix"):
+                k, v = line.split(":", 1)
+                kv[k] = v.strip()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if not sha.startswith(kv["kernel_source_sha256_prefix"]):
+            return None
+        return int(kv["traffic_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 class Clocks:
@@ -292,7 +317,7 @@ def bench_ours(args, rank, world):
         peak = FP32_SIMT_TFLOPS if dom.endswith("f32") else FP64_TFLOPS
         ach = work / cnt / (ms / cnt * 1e-3) / 1e12
         roof = dict(kernel=dom, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                    traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
+                    traffic=profiled_traffic(dom), launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
                     peak_source="derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz" if dom.endswith("f32")
                     else "nominal GB300 FP64 1.25 TFLOP/s")
     else:
@@ -313,6 +338,159 @@ def bench_ours(args, rank, world):
                apply=apply, roofline=roof, e2e=e2e, clocks=clocks, gpu_launches=int(launches_total // max(1, len(forms))),
                kernels_per_step=kernels)
     return res
+
+
+BATCH_COUNT, BATCH_RHS, BATCH_TOL = 256, 32, 1e-6
+
+
+def bench_batched(args, rank, world):
+    """256 independent instances (meshes 16..64 per side, p in {1,2,3}, Poisson
+    or Helmholtz drawn per instance), 32 N(0,1) right-hand sides each, FP32
+    factors, FP64 FGMRES to 1e-8.  One step = nd_order_batched +
+    hss_factor_batched + fgmres_solve_batched for each block-size group."""
+    import numpy as np
+    import torch
+    from paper_1508_07798_gb300 import hssnd
+    from paper_1508_07798_gb300 import dg_inputs as dg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    inst = dg.batched_instances(BATCH_COUNT, master_seed=rank)
+    groups = {}
+    for d in inst:
+        groups.setdefault(d["mesh"].p, []).append(d)
+    G = []
+    for p, ds in sorted(groups.items()):
+        dAs = [hssnd.DeviceBSR.from_host(d["A"]) for d in ds]
+        meshes = [(2, (d["mesh"].n[0], d["mesh"].n[1]), p) for d in ds]
+        N = sum(A.n for A in dAs)
+        Bh = dg.random_rhs(N, BATCH_RHS, 1000 * rank + p, kind="normal")
+        G.append(dict(p=p, ds=ds, dAs=dAs, meshes=meshes, N=N, Bh=Bh, B=torch.as_tensor(Bh, device=dev)))
+    dofs = sum(g["N"] for g in G)
+
+    def step():
+        out = []
+        for g in G:
+            forest = hssnd.nd_order_batched(g["meshes"], g["dAs"])
+            F = hssnd.hss_factor_batched(g["dAs"], forest, tol=BATCH_TOL, precision="fp32")
+            X, st = hssnd.fgmres_solve_batched(F, g["B"], rtol=RTOL, restart=RESTART)
+            out.append((forest, F, X, st))
+        return out
+
+    def timed(n):
+        ts, last = [], None
+        for _ in range(n):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ts, last
+
+    for _ in range(args.warmup):
+        step()
+    clk = Clocks(dev.index)
+    clk.start()
+    l0 = hssnd.launch_count()
+    times, last = timed(args.steps)
+    launches = (hssnd.launch_count() - l0) // args.steps
+    clocks = clk.stop()
+    hssnd.profile_reset()
+    hssnd.profile_enable(True)
+    timed(1)
+    hssnd.profile_enable(False)
+    prof = hssnd.profile_read()
+    # true residuals of every (instance, rhs) on the CPU, per-group statistics
+    worst, conv, iters, groups_out = 0.0, True, [], []
+    for g, (forest, F, X, st) in zip(G, last):
+        off = forest.inst_dof
+        Xh = X.cpu().numpy()
+        for i, d in enumerate(g["ds"]):
+            Acsr = dg.bsr_to_csr(d["A"])
+            bi, xi = g["Bh"][off[i]:off[i + 1]], Xh[off[i]:off[i + 1]]
+            worst = max(worst, float((np.linalg.norm(bi - Acsr @ xi, axis=0) / np.linalg.norm(bi, axis=0)).max()))
+        conv = conv and all(s_.converged for s_ in st)
+        iters += [s_.max_iters for s_ in st]
+        info = F.info()
+        groups_out.append(dict(p=g["p"], instances=len(g["ds"]), dofs=g["N"], factor_bytes=info["factor_bytes"],
+                               front_flops=info["front_flops"], capped_fronts=info["capped_fronts"],
+                               max_rank=info["max_rank"]))
+    # the same instances one at a time through the single-instance calls, once
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for g in G:
+        off = np.concatenate([[0], np.cumsum([A.n for A in g["dAs"]])])
+        for i, (A, m) in enumerate(zip(g["dAs"], g["meshes"])):
+            t = hssnd.nd_order(m, A)
+            F = hssnd.hss_factor(A, t, tol=BATCH_TOL, precision="fp32")
+            hssnd.fgmres_solve(A, F, g["B"][off[i]:off[i + 1]], rtol=RTOL, restart=RESTART)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sequential_ms = e0.elapsed_time(e1)
+    # e2e: host copies of every matrix and right-hand side in, solutions out
+    pinned = []
+    h2d = d2h = 0
+    for g in G:
+        for d in g["ds"]:
+            A = d["A"]
+            for arr in (A.row_ptr, A.col_idx, A.val.reshape(-1)):
+                t = torch.as_tensor(arr).pin_memory()
+                pinned.append((t, torch.empty_like(t, device=dev)))
+                h2d += t.numel() * t.element_size()
+        bt = torch.as_tensor(g["Bh"]).pin_memory()
+        pinned.append((bt, torch.empty_like(bt, device=dev)))
+        h2d += bt.numel() * 8
+        d2h += bt.numel() * 8
+    xh = [torch.empty(g["Bh"].shape, dtype=torch.float64).pin_memory() for g in G]
+    ets = []
+    for it in range(1 + args.steps):
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for hsrc, ddst in pinned:
+            ddst.copy_(hsrc, non_blocking=True)
+        out = step()
+        for k, (_, _, X, _) in enumerate(out):
+            xh[k].copy_(X, non_blocking=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 1:
+            ets.append(a0.elapsed_time(a1))
+    kernels = {k: dict(ms=round(v[0], 3), launches=v[1]) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    tracked = {k: v for k, v in prof.items() if v[2] > 0}
+    dom = max(tracked, key=lambda k: tracked[k][0])
+    ms, cnt, work = prof[dom]
+    pk = peaks()
+    if dom.startswith("gemm"):
+        ach = work / (ms * 1e-3) / 1e12
+        roof = dict(kernel=dom, bound="alu", achieved=ach, peak=FP32_SIMT_TFLOPS, unit="TFLOP/s",
+                    frac=ach / FP32_SIMT_TFLOPS, traffic=None, launches=cnt,
+                    share=ms / sum(v[0] for v in prof.values()),
+                    peak_source="derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz")
+    else:
+        ach = work / (ms * 1e-3) / 1e9
+        roof = dict(kernel=dom, bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
+                    traffic=None, launches=cnt, share=ms / sum(v[0] for v in prof.values()), peak_source=pk["src"])
+    value = statistics.mean(times)
+    return dict(metric=METRIC, value=value, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=value, higher_is_better=False, scaling="weak", vs_baseline=None,
+                dtype="f32 factor / f64 Krylov", data="synthetic",
+                config=dict(workload="batched_256_instances_32rhs", instances=BATCH_COUNT, rhs=BATCH_RHS, dofs=dofs,
+                            id_tol=BATCH_TOL, rtol=RTOL, restart=RESTART, groups=groups_out,
+                            l2="inputs larger than L2 (A and the Krylov blocks take tens of GB)",
+                            parallelism=f"replicas x{world} (independent batches)"),
+                converged=bool(conv and worst <= RTOL * 1.0001), worst_true_relres=worst,
+                max_iters=max(iters), sequential_ms=sequential_ms,
+                roofline=roof, e2e=dict(value=statistics.mean(ets), unit="ms", h2d_bytes_per_step=int(h2d),
+                                        d2h_bytes_per_step=int(d2h)),
+                clocks=clocks, gpu_launches=int(launches), kernels_instrumented_step=kernels)
 
 
 def cpu_baseline_run(seed=0):
@@ -372,6 +550,15 @@ def main():
         dist.init_process_group("nccl")
     import __graft_entry__
     __graft_entry__.build()
+    if args.workload == "batched256":
+        res = bench_batched(args, rank, world)
+        if rank == 0:
+            print(json.dumps(res))
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     res = bench_ours(args, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         ms, info = cpu_baseline_run(0)

@@ -219,7 +219,9 @@ class Factor:
         return {k: getattr(i, k) for k, _ in hss_factor_info._fields_}
 
     def export_front(self, box: int):
-        nb_ = int(self.tree.export()["nb"][box])
+        if getattr(self, "_nb", None) is None:
+            self._nb = self.tree.export()["nb"]
+        nb_ = int(self._nb[box])
         S = np.zeros((nb_, nb_), order="F")
         H = np.zeros((nb_, nb_), order="F")
         kmax, r = C.c_int(0), C.c_int(0)
