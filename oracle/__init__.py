@@ -16,6 +16,8 @@ FP64, with no blocking, fusion or reordering beyond what the paper states:
   factor.py    Algorithm 2 (leaf elimination, eq. (32) merge, eq. (36) top block)
   apply.py     the inverse factorization M^-t D^-1 L^-1 (end of Sec. 4.2)
   fgmres.py    restarted flexible GMRES with right preconditioning
+  mlp.py       rank-prediction MLP of the learned-rank form (not in the paper):
+               forward, loss gradient, Adam, standardisation
 
 Pins (tests/test_oracle_*.py): exact LDM^t with compression off equals a dense
 LU solve; GMRES converges in one iteration then; ID error within the strong
@@ -31,3 +33,4 @@ from .factor import factor, box_schur         # noqa: F401
 from .apply import apply                      # noqa: F401
 from .fgmres import fgmres                    # noqa: F401
 from .rademacher import rademacher            # noqa: F401
+from . import mlp                             # noqa: F401
