@@ -91,6 +91,9 @@ typedef struct hss_factor_opts {
     int tensor_cores;       /* FP32 form only: 0 (default) SIMT FMA; 1 tcgen05 TF32 with the three-product
                                hi/lo split (FP32 accuracy) for products with K >= 128 (the sampling
                                products); 2 the same with a single TF32 product */
+    const int *r_init;      /* HOST array of one initial sample width per box (NULL, the default: r0 for
+                               every front), e.g. from hss_rank_model_predict; the adaptive growth by dr
+                               still applies whenever a rank exceeds r - oversample */
 } hss_factor_opts;
 
 typedef struct fgmres_opts {
@@ -282,6 +285,60 @@ int hss_factor_batched(int ninst, const hss_bsr *As, const hss_tree *forest, con
  * Returns HSS_ENOCONV when a process reached maxit first. */
 int fgmres_solve_batched(const hss_factor_t *f, int nrhs, const double *b, int ldb, double *x, int ldx,
                          const fgmres_opts *opts, fgmres_stats *stats, void *stream);
+
+/* ---- Learned sample widths (no counterpart in the paper: Theorem 1 needs
+ * k + p samples and the paper grows the width until the ranks fit).  A small
+ * MLP predicts each front's largest HSS rank k before sampling, so the first
+ * sampling round usually suffices; the adaptive growth remains the fallback
+ * whenever a rank exceeds r - oversample (the oversampling margin that
+ * Theorem 1's bound needs).
+ *
+ * Features per box (hss_rank_features, HOST out, nbox x 6 row-major):
+ * log(1 + |B|), tree level, kappa * h, p, mean and variance of c over the
+ * box's elements (c_elem: HOST array per element, NULL meaning c = 1).
+ * Network: standardised features -> three ReLU layers of 64 -> one output,
+ * the standardised log(1 + k).  Parameters (HSS_RANK_NPARAMS floats, layout
+ * W1 (64 x 6, row per unit), b1, W2 (64 x 64), b2, W3 (64 x 64), b3, W4 (64),
+ * b4) and the standardisation (14 floats: feature means[6], standard
+ * deviations[6], target mean, target standard deviation). */
+#define HSS_RANK_FEATURES 6
+#define HSS_RANK_HIDDEN 64
+#define HSS_RANK_NPARAMS 8833
+typedef struct hss_rank_model hss_rank_model;
+int hss_rank_features(const hss_tree *t, const double *c_elem, double kappa_h, float *feat);
+/* New model: weights uniform in +-sqrt(6 / fan_in) from the counter hash of
+ * `seed`, biases 0, identity standardisation. */
+int hss_rank_model_create(uint64_t seed, hss_rank_model **out);
+void hss_rank_model_destroy(hss_rank_model *m);
+/* Copy the parameters / standardisation out (HOST; either may be NULL) or in
+ * (setting parameters also clears the Adam state). */
+int hss_rank_model_get(const hss_rank_model *m, float *params, float *norm);
+int hss_rank_model_set(hss_rank_model *m, const float *params, const float *norm);
+/* Standardisation from n training samples: feat DEVICE n x 6 row-major,
+ * target DEVICE n values of log(1 + k).  Means and population standard
+ * deviations (1 where zero).  Synchronizes `stream`. */
+int hss_rank_model_fit_norm(hss_rank_model *m, int n, const float *feat, const float *target, void *stream);
+/* Mean squared error over n samples and its gradient (HOST, NPARAMS floats;
+ * either may be NULL) at the current parameters.  Synchronizes `stream`. */
+int hss_rank_model_loss_grad(hss_rank_model *m, int n, const float *feat, const float *target, float *loss,
+                             float *grad, void *stream);
+/* Adam (lr, 0.9, 0.999, 1e-8) for `epochs` passes over the data in minibatches
+ * of `batch` samples, order per epoch from the counter hash of `seed`; the
+ * final mean squared error over all samples goes to *final_loss (may be NULL).
+ * FP32 forward and backward kernels on the device. */
+int hss_rank_model_train(hss_rank_model *m, int n, const float *feat, const float *target, int epochs, int batch,
+                         float lr, uint64_t seed, float *final_loss, void *stream);
+/* BF16 inference for n feature rows (DEVICE): pred = predicted log(1 + k)
+ * (DEVICE, n floats); r (DEVICE, n ints, may be NULL) = the sample width
+ * covering k + oversample, rounded up to a multiple of 8, within [16, rmax].
+ * Asynchronous. */
+int hss_rank_model_predict(hss_rank_model *m, int n, const float *feat, int oversample, int rmax, float *pred,
+                           int *r, void *stream);
+/* Per-front record of a factorization (HOST arrays of at least cap entries,
+ * any may be NULL): box id, largest node rank, final sample width, sampling
+ * rounds; fronts with a single-node HSS tree (not compressed) report r = 0.
+ * Returns the number of records (all fronts with |B| > 0), -1 for a null handle. */
+int hss_factor_export_log(const hss_factor_t *f, int cap, int *box, int *kmax, int *r, int *rounds);
 
 /* Convergence history of the last fgmres_solve on this thread: Arnoldi residual
  * estimates |g_{j+1}|/||b|| of right-hand side `rhs` (HOST, up to cap values);

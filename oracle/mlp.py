@@ -106,6 +106,29 @@ def adam_step(theta, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+def bf16_round(a):
+    """Round to the nearest bfloat16 (8-bit significand), ties to even,
+    returned as float64: the float32 bit pattern with the low 16 bits rounded
+    off."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(theta, X, norm):
+    """The network with weights, standardised features and activations
+    rounded to bfloat16 (inference form); sums in FP64.  Returns log(1 + k)."""
+    P = {k: bf16_round(v) for k, v in unpack(theta).items()}
+    mu, sd = np.asarray(norm[0], dtype=np.float32), np.asarray(norm[1], dtype=np.float32)
+    Xh = bf16_round((np.asarray(X, dtype=np.float32) - mu) / sd)
+    h1 = bf16_round(np.maximum(Xh @ P["W1"].T + P["b1"], 0.0))
+    h2 = bf16_round(np.maximum(h1 @ P["W2"].T + P["b2"], 0.0))
+    h3 = bf16_round(np.maximum(h2 @ P["W3"].T + P["b3"], 0.0))
+    y = h3 @ P["W4"] + P["b4"][0]
+    return norm[2] + norm[3] * y
+
+
 def predicted_rank(theta, X, norm):
     """k = exp(tmu + tsd * y) - 1, the predicted largest rank (real-valued)."""
     y, _ = forward(theta, X, norm)

@@ -276,7 +276,8 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         if (fr[f].nb == 0) continue;
         bool comp = o.compress && t->hss[b].size() > 1;
         if (comp) {
-            active.push_back({f, std::min(o.r0, o.rmax)});
+            const int r_first = o.r_init ? std::max(1, std::min(o.r_init[b], o.rmax)) : std::min(o.r0, o.rmax);
+            active.push_back({f, r_first});
         } else {
             for (int r0 = 0; r0 < fr[f].nb; r0 += EXP_TILE)
                 for (int c0 = 0; c0 < fr[f].nb; c0 += EXP_TILE)
@@ -944,6 +945,25 @@ extern "C" int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info)
     info->nfronts = (int)f->log.size();
     info->capped_fronts = f->capped_fronts;
     return HSS_OK;
+}
+
+extern "C" int hss_factor_export_log(const hss_factor_t *f, int cap, int *box, int *kmax, int *r, int *rounds) {
+    if (!f || cap < 0) {
+        set_error("hss_factor_export_log: invalid argument");
+        return -1;
+    }
+    int n = 0;
+    for (const auto &lg : f->log) {
+        if (lg.nb == 0) continue;
+        if (n < cap) {
+            if (box) box[n] = lg.box;
+            if (kmax) kmax[n] = lg.kmax;
+            if (r) r[n] = lg.r;
+            if (rounds) rounds[n] = lg.rounds;
+        }
+        ++n;
+    }
+    return n;
 }
 
 extern "C" int hss_factor_export_front(const hss_factor_t *f, int box, double *S, double *H, int *kmax, int *r) {

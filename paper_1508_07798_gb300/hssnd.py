@@ -28,6 +28,9 @@ EXPORTED = [
     "hss_tree_destroy", "hss_factor_destroy", "hss_last_error",
     "hss_launch_count", "hss_profile_enable", "hss_profile_reset", "hss_profile_read", "hss_gemm_f32",
     "hss_gemm_f32_static", "nd_order_batched", "hss_factor_batched", "fgmres_solve_batched",
+    "hss_rank_features", "hss_rank_model_create", "hss_rank_model_destroy", "hss_rank_model_get",
+    "hss_rank_model_set", "hss_rank_model_fit_norm", "hss_rank_model_loss_grad", "hss_rank_model_train",
+    "hss_rank_model_predict", "hss_factor_export_log",
 ]
 
 
@@ -53,7 +56,7 @@ class hss_nd_opts(C.Structure):
 class hss_factor_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("compress", C.c_int), ("r0", C.c_int), ("dr", C.c_int),
                 ("rmax", C.c_int), ("oversample", C.c_int), ("precision", C.c_int),
-                ("seed", C.c_uint64), ("keep_schur", C.c_int), ("tensor_cores", C.c_int)]
+                ("seed", C.c_uint64), ("keep_schur", C.c_int), ("tensor_cores", C.c_int), ("r_init", C.c_void_p)]
 
 
 class fgmres_opts(C.Structure):
@@ -111,6 +114,17 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                          C.POINTER(P)]),
         "fgmres_solve_batched": (C.c_int, [P, C.c_int, P, C.c_int, P, C.c_int, C.POINTER(fgmres_opts),
                                            C.POINTER(fgmres_stats), P]),
+        "hss_rank_features": (C.c_int, [P, P, C.c_double, P]),
+        "hss_rank_model_create": (C.c_int, [C.c_uint64, C.POINTER(P)]),
+        "hss_rank_model_destroy": (None, [P]),
+        "hss_rank_model_get": (C.c_int, [P, P, P]),
+        "hss_rank_model_set": (C.c_int, [P, P, P]),
+        "hss_rank_model_fit_norm": (C.c_int, [P, C.c_int, P, P, P]),
+        "hss_rank_model_loss_grad": (C.c_int, [P, C.c_int, P, P, C.POINTER(C.c_float), P, P]),
+        "hss_rank_model_train": (C.c_int, [P, C.c_int, P, P, C.c_int, C.c_int, C.c_float, C.c_uint64,
+                                           C.POINTER(C.c_float), P]),
+        "hss_rank_model_predict": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int, P, P, P]),
+        "hss_factor_export_log": (C.c_int, [P, C.c_int, ip, ip, ip, ip]),
         "hss_profile_enable": (C.c_int, [C.c_int]),
         "hss_profile_reset": (C.c_int, []),
         "hss_profile_read": (C.c_int, [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
@@ -218,6 +232,13 @@ class Factor:
         _check(_lib.hss_factor_get_info(self.h, C.byref(i)))
         return {k: getattr(i, k) for k, _ in hss_factor_info._fields_}
 
+    def export_log(self) -> dict:
+        n = _lib.hss_factor_export_log(self.h, 0, None, None, None, None)
+        arrs = {k: np.zeros(max(n, 1), dtype=np.int32) for k in ("box", "kmax", "r", "rounds")}
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))  # noqa: E731
+        _lib.hss_factor_export_log(self.h, n, *[ip(arrs[k]) for k in ("box", "kmax", "r", "rounds")])
+        return {k: v[:n] for k, v in arrs.items()}
+
     def export_front(self, box: int):
         if getattr(self, "_nb", None) is None:
             self._nb = self.tree.export()["nb"]
@@ -252,7 +273,12 @@ def factor_opts(**kw) -> hss_factor_opts:
 
 
 def hss_factor(A: DeviceBSR, tree: Tree, stream=None, **kw) -> Factor:
+    r_init = kw.pop("r_init", None)
     o = factor_opts(**kw)
+    if r_init is not None:
+        r_init = np.ascontiguousarray(r_init, dtype=np.int32)
+        assert r_init.size == tree.desc.nbox
+        o.r_init = r_init.ctypes.data
     out = C.c_void_p()
     _check(_lib.hss_factor(C.byref(A.c), tree.h, C.byref(o), _stream(stream), C.byref(out)))
     return Factor(out.value, tree, o.precision)
@@ -348,6 +374,79 @@ def fgmres_solve_batched(F: Factor, B: torch.Tensor, x0: torch.Tensor | None = N
     x = xs.t()
     stats = [SolveStats(s_.iters, s_.max_iters, s_.relres, bool(s_.converged)) for s_ in st]
     return (x.reshape(N) if B.dim() == 1 else x), stats
+
+
+RANK_NPARAMS = 8833
+
+
+def rank_features(tree: Tree, c_elem=None, kappa_h=0.0) -> np.ndarray:
+    """(nbox, 6) float32 features of every box (HOST)."""
+    out = np.zeros((tree.desc.nbox, 6), dtype=np.float32)
+    c = None if c_elem is None else np.ascontiguousarray(c_elem, dtype=np.float64)
+    _check(_lib.hss_rank_features(tree.h, None if c is None else c.ctypes.data, float(kappa_h), out.ctypes.data))
+    return out
+
+
+class RankModel:
+    """MLP predicting each front's largest HSS rank (FP32 training kernels,
+    BF16 inference kernel)."""
+
+    def __init__(self, seed=0):
+        out = C.c_void_p()
+        _check(_lib.hss_rank_model_create(seed, C.byref(out)))
+        self.h = out
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hss_rank_model_destroy(self.h)
+            self.h = None
+
+    def get(self):
+        th = np.zeros(RANK_NPARAMS, dtype=np.float32)
+        nm = np.zeros(14, dtype=np.float32)
+        _check(_lib.hss_rank_model_get(self.h, th.ctypes.data, nm.ctypes.data))
+        return th, nm
+
+    def set(self, params=None, norm=None):
+        th = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        nm = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        _check(_lib.hss_rank_model_set(self.h, None if th is None else th.ctypes.data,
+                                       None if nm is None else nm.ctypes.data))
+
+    @staticmethod
+    def _dev(feat, target=None):
+        f = torch.as_tensor(np.ascontiguousarray(feat, dtype=np.float32), device="cuda").contiguous()
+        t = None if target is None else torch.as_tensor(np.ascontiguousarray(target, dtype=np.float32),
+                                                        device="cuda").contiguous()
+        return f, t
+
+    def fit_norm(self, feat, target, stream=None):
+        f, t = self._dev(feat, target)
+        _check(_lib.hss_rank_model_fit_norm(self.h, f.shape[0], _ptr(f), _ptr(t), _stream(stream)))
+
+    def loss_grad(self, feat, target, stream=None):
+        f, t = self._dev(feat, target)
+        loss = C.c_float()
+        g = np.zeros(RANK_NPARAMS, dtype=np.float32)
+        _check(_lib.hss_rank_model_loss_grad(self.h, f.shape[0], _ptr(f), _ptr(t), C.byref(loss), g.ctypes.data,
+                                             _stream(stream)))
+        return loss.value, g
+
+    def train(self, feat, target, epochs=200, batch=256, lr=1e-3, seed=0, stream=None):
+        f, t = self._dev(feat, target)
+        loss = C.c_float()
+        _check(_lib.hss_rank_model_train(self.h, f.shape[0], _ptr(f), _ptr(t), epochs, batch, lr, seed,
+                                         C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def predict(self, feat, oversample=10, rmax=96, stream=None):
+        f, _ = self._dev(feat)
+        n = f.shape[0]
+        pred = torch.empty(n, dtype=torch.float32, device="cuda")
+        r = torch.empty(n, dtype=torch.int32, device="cuda")
+        _check(_lib.hss_rank_model_predict(self.h, n, _ptr(f), oversample, rmax, _ptr(pred), _ptr(r),
+                                           _stream(stream)))
+        return pred.cpu().numpy(), r.cpu().numpy()
 
 
 def fgmres_history(rhs=0, cap=100000) -> np.ndarray:

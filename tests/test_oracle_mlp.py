@@ -90,3 +90,22 @@ def test_adam_fits_a_representable_target():
         loss, g = mlp.loss_grad(th, X, t, norm)
         th, m, v = mlp.adam_step(th, g, m, v, s, lr=3e-3)
     assert loss < 0.02 * l0 and loss < 0.02
+
+
+def test_bf16_rounding_matches_library_conversion():
+    """The oracle's bfloat16 rounding equals PyTorch's CPU conversion."""
+    import torch
+    rng = np.random.default_rng(10)
+    a = np.concatenate([rng.normal(0, 1, 5000), rng.normal(0, 1e-3, 500), [0.0, -0.0, 1.0, 3.0, 1.0 + 2 ** -8]])
+    a = a.astype(np.float32)
+    ref = torch.as_tensor(a).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16_round(a), ref)
+
+
+def test_bf16_forward_close_to_fp64_forward():
+    X, t = _data(64, 11)
+    norm = mlp.standardisation(X, t)
+    th = _theta(12, 0.2)
+    y64, _ = mlp.forward(th, X, norm)
+    yb = mlp.forward_bf16(th, X, norm)
+    assert np.abs(yb - (norm[2] + norm[3] * y64)).max() <= 0.05 * norm[3] * max(1.0, np.abs(y64).max())
