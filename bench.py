@@ -5,8 +5,11 @@ Workload (one "step" = the whole hot path on one synthetic problem):
 indefinite Helmholtz -Lap u - k^2 c(x) u = f, SIPG DG p=2 on 64x64 quads
 (36,864 dofs, 9x9 blocks), k for 10 dofs per wavelength, c(x) = 1 + 0.3 x
 (mean of 8 random-phase cosines), Gaussian point source, ID tolerance 1e-4,
-FGMRES(30) in FP64 to 1e-8.  Forms: FP64 plain (factor in FP64) and mixed
-(factor in FP32, FP64 Krylov); `value` is the mixed form's time to solution.
+FGMRES(30) in FP64 to 1e-8.  Forms: FP64 plain (factor in FP64), mixed
+(factor in FP32, FP64 Krylov) and mixed with learned sample widths (an MLP
+trained before timing on the ranks of adaptive runs; the timed step includes
+its BF16 inference); `value` is the first form's time to solution (default:
+the learned mixed form).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -41,7 +44,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="fp32,fp64")
+    ap.add_argument("--forms", default="fp32_learned,fp32,fp64",
+                    help="fp32_learned: FP32 factor with learned sample widths (headline); fp32: FP32 "
+                         "factor, adaptive widths; fp64: plain FP64 factor")
     ap.add_argument("--workload", default="helmholtz64", choices=["helmholtz64", "batched256"],
                     help="helmholtz64: the timed workload (default); batched256: 256 independent "
                          "instances x 32 right-hand sides through the batched form (its own JSON line)")
@@ -163,9 +168,35 @@ def bench_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     Acsr = dg.bsr_to_csr(A)
 
+    # learned sample widths: the model is trained once, before any timing, on
+    # the ranks of adaptive runs of the method (Helmholtz 64 x 64, p in
+    # {1, 2, 3}, seeds 100..115, the same ID tolerance); the timed step then
+    # includes the box features, the BF16 inference and the width read-back
+    model = None
+    learned_info = None
+    c_elem = dg.cosine_field(mesh, rank)
+    kappa_h = dg.helmholtz_kappa(N_ELEM, P_DEG) / N_ELEM
+    if "fp32_learned" in args.forms.split(","):
+        from paper_1508_07798_gb300 import ranks
+        probs = []
+        for p_ in (1, 2, 3):
+            for sd in range(100, 116):
+                m_, A_ = dg.helmholtz_2d(N_ELEM, p_, sd)
+                probs.append(((2, (N_ELEM, N_ELEM), p_), A_, dg.cosine_field(m_, sd),
+                              dg.helmholtz_kappa(N_ELEM, p_) / N_ELEM))
+        Xt, tt = ranks.training_set(probs, tol=TOL)
+        model = hssnd.RankModel(seed=1)
+        model.fit_norm(Xt, tt)
+        train_loss = model.train(Xt, tt, epochs=60, batch=256, lr=2e-3, seed=3)
+        learned_info = dict(train_samples=int(len(tt)), train_loss=train_loss)
+
     def step(prec):
         tree = hssnd.nd_order(meshdesc, dA, leaf_max=64)
-        F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec)
+        if prec == "fp32_learned":
+            r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h))[1]
+            F = hssnd.hss_factor(dA, tree, tol=TOL, precision="fp32", r_init=r0)
+        else:
+            F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec)
         x, st = hssnd.fgmres_solve(dA, F, b, rtol=RTOL, restart=RESTART)
         return tree, F, x, st
 
@@ -220,6 +251,7 @@ def bench_ours(args, rank, world):
                            relres=relres, converged=bool(st.converged and relres <= RTOL * 1.0001),
                            factor_bytes=info["factor_bytes"], front_flops=info["front_flops"],
                            executed_flops=info["executed_flops"], max_rank=info["max_rank"], max_r=info["max_r"],
+                           sampling_rounds=int(F.export_log()["rounds"].sum()),
                            kernel_ms_sum=sum(v[0] for v in prof.values()) / args.steps)
     clocks = clk.stop()
     barrier()
@@ -232,6 +264,8 @@ def bench_ours(args, rank, world):
     apply = {}
     pk = peaks()
     for prec in args.forms.split(","):
+        if prec == "fp32_learned":
+            continue      # same factor storage and apply kernels as fp32
         tree = hssnd.nd_order(meshdesc, dA, leaf_max=64)
         F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec)
         N = A.n
@@ -290,7 +324,11 @@ def bench_ours(args, rank, world):
         dA2.nb, dA2.bs, dA2.row_ptr, dA2.col_idx, dA2.val = A.nb, A.bs, d_rp, d_ci, d_va
         dA2.c = hssnd.hss_bsr(A.nb, A.bs, d_rp.data_ptr(), d_ci.data_ptr(), d_va.data_ptr())
         tree = hssnd.nd_order(meshdesc, dA2, leaf_max=64)
-        F = hssnd.hss_factor(dA2, tree, tol=TOL, precision=head)
+        if head == "fp32_learned":
+            r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h))[1]
+            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision="fp32", r_init=r0)
+        else:
+            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision=head)
         x, st = hssnd.fgmres_solve(dA2, F, d_b, rtol=RTOL, restart=RESTART)
         xh.copy_(x, non_blocking=True)
         e1.record(stream)
@@ -329,9 +367,10 @@ def bench_ours(args, rank, world):
                       sorted(pf.items(), key=lambda kv: -kv[1][0])} for form, pf in prof_all.items()}
     res = dict(metric=METRIC, value=value, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup,
                ms_per_step=value, higher_is_better=False, scaling="weak", vs_baseline=None,
-               dtype="f32 factor / f64 Krylov" if head == "fp32" else "f64", data="synthetic",
+               dtype="f32 factor / f64 Krylov" if head.startswith("fp32") else "f64", data="synthetic",
                config=dict(workload=WORKLOAD, dofs=A.n, p=P_DEG, mesh=f"{N_ELEM}x{N_ELEM}", id_tol=TOL,
                            rtol=RTOL, restart=RESTART, leaf_max=64, headline_form=head,
+                           learned_widths=learned_info if model is not None else None,
                            l2="flushed by a 256 MB write before every timed step",
                            parallelism=f"replicas x{world} (independent instances)"),
                forms={k: {kk: vv for kk, vv in v.items() if kk != "ms_all"} for k, v in forms.items()},
