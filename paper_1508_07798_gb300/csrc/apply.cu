@@ -143,7 +143,7 @@ template <class T, int RB> static int record_sweep(const hss_factor_t *f, cudaSt
             const int nt = fwd ? st.nfwd : st.nbwd;
             if (nt == 0) continue;
             const ApplyItem *itm = fwd ? st.d_fwd : st.d_bwd;
-            double *part = f->d_apart.as<double>() + (fwd ? st.part_fwd : st.part_bwd) * 32 * 4;
+            double *part = f->d_apart.as<double>() + (fwd ? st.part_fwd : st.part_bwd) * 32 * APPLY_RB;
             int *tk = f->d_tickets.as<int>() + (fwd ? st.tk_fwd : st.tk_bwd);
             if (fwd)
                 k_apply<T, RB, true><<<cdiv(nt, AP_WPB), AP_NT, 0, s>>>(itm, nt, st.d_fronts, arena,
@@ -169,7 +169,7 @@ template <class T> static int build_graph(hss_factor_t *f, int slot) {
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         int nk = 0;
-        rc = slot == 0 ? record_sweep<T, 1>(f, cs, nk) : record_sweep<T, 4>(f, cs, nk);
+        rc = slot == 0 ? record_sweep<T, 1>(f, cs, nk) : record_sweep<T, APPLY_RB>(f, cs, nk);
         e = cudaStreamEndCapture(cs, &g);
         f->graph_kernels[slot] = nk;
     }
@@ -185,7 +185,7 @@ template <class T> static int build_graph(hss_factor_t *f, int slot) {
 int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s) {
     hss_factor_t *mf = const_cast<hss_factor_t *>(f);
     int rc;
-    if ((rc = mf->tvec.alloc(sizeof(double) * (size_t)f->ndof * std::min(nrhs, 4)))) return rc;
+    if ((rc = mf->tvec.alloc(sizeof(double) * (size_t)f->ndof * std::min(nrhs, APPLY_RB)))) return rc;
     if ((rc = mf->d_aparams.alloc(sizeof(ApplyParams)))) return rc;
     const int slot = nrhs == 1 ? 0 : 1;
     if (!f->gexec[slot]) {
@@ -193,9 +193,9 @@ int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, dou
         if (rc) return rc;
     }
     HSS_PROF("apply", s, f->apply_bytes(nrhs));
-    for (int k = 0; k < nrhs; k += 4) {   // one sweep per block of up to 4 right-hand sides
+    for (int k = 0; k < nrhs; k += APPLY_RB) {   // one sweep per block of up to APPLY_RB right-hand sides
         ApplyParams pv{x + ldx * k, ldx, y + ldy * k, ldy, mf->tvec.as<double>(), (long)f->ndof,
-                       std::min(4, nrhs - k)};
+                       std::min(APPLY_RB, nrhs - k)};
         prof_add_launches(f->graph_kernels[slot]);
         k_apply_set<<<1, 32, 0, s>>>(mf->d_aparams.as<ApplyParams>(), pv);
         HSS_CHECK_LAUNCH("k_apply_set");

@@ -783,7 +783,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             return rc;
     }
     {
-        if ((rc = F->d_apart.alloc(sizeof(double) * 32 * 4 * std::max(part_total, 1L))) ||
+        if ((rc = F->d_apart.alloc(sizeof(double) * 32 * APPLY_RB * std::max(part_total, 1L))) ||
             (rc = F->d_tickets.alloc(sizeof(int) * std::max(tk_total, 1))))
             return rc;
         HSS_CUDA(cudaMemsetAsync(F->d_tickets.p, 0, sizeof(int) * std::max(tk_total, 1), s));

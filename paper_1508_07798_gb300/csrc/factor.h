@@ -46,6 +46,8 @@ struct ApplyParams {
     int nrhs;
 };
 
+constexpr int APPLY_RB = 8;   // right-hand sides per sweep of the multi-RHS apply (factor read once per 8)
+
 struct FrontLog {   // per-front record (rank logging, Sec. 5 empirical cost)
     int box, level, ni, nb, r, rounds, kmax, nnodes;
 };
@@ -72,7 +74,7 @@ struct hss_factor_t {
     double factor_bytes = 0, front_flops = 0, exec_flops = 0;
     int max_rank = 0, max_r = 0, rounds = 0;
     int capped_fronts = 0;   // fronts that kept S because the sample width reached rmax
-    // captured apply sweeps (slot 0: one right-hand side, slot 1: blocks of 4)
+    // captured apply sweeps (slot 0: one right-hand side, slot 1: blocks of APPLY_RB)
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_kernels[2] = {0, 0};
     hssnd::DevBuf d_aparams;

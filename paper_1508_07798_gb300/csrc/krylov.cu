@@ -36,6 +36,38 @@ __global__ void k_spmv(int nb, int bs, const int *__restrict__ row_ptr, const in
     y[row + ldy * rr] = acc;
 }
 
+// y = A x for several right-hand sides: one thread per scalar row, the row's
+// blocks read once for up to SPMV_RB right-hand sides (same summation order
+// per right-hand side as k_spmv).
+constexpr int SPMV_RB = 8;
+__global__ void k_spmv_multi(int nb, int bs, const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+                             const double *__restrict__ val, const double *__restrict__ x, long ldx,
+                             double *__restrict__ y, long ldy, int nrhs) {
+    long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long N = (long)nb * bs;
+    if (row >= N) return;
+    int e = (int)(row / bs), r = (int)(row % bs);
+    for (int r0 = 0; r0 < nrhs; r0 += SPMV_RB) {
+        const int nr = min(SPMV_RB, nrhs - r0);
+        double acc[SPMV_RB];
+#pragma unroll
+        for (int k = 0; k < SPMV_RB; ++k) acc[k] = 0.0;
+        for (int t = row_ptr[e]; t < row_ptr[e + 1]; ++t) {
+            const double *blk = val + ((long)t * bs + r) * bs;
+            const double *xs = x + (long)col_idx[t] * bs + ldx * r0;
+            for (int c = 0; c < bs; ++c) {
+                const double a = blk[c];
+#pragma unroll
+                for (int k = 0; k < SPMV_RB; ++k)
+                    if (k < nr) acc[k] = fma(a, xs[c + ldx * k], acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < SPMV_RB; ++k)
+            if (k < nr) y[row + ldy * (r0 + k)] = acc[k];
+    }
+}
+
 // partial[b * KRY_MAXM + q] = sum over this CTA's rows of V(:,q) . w, q < nq
 __global__ void k_dots(const double *__restrict__ V, long ldv, int nq, const double *__restrict__ w, long N,
                        double *__restrict__ partial) {
@@ -176,7 +208,14 @@ int spmv(const hss_bsr *A, int nrhs, const double *x, long ldx, double *y, long 
     long N = (long)A->nb * A->bs;
     long tot = N * nrhs;
     if (tot == 0) return HSS_OK;
-    { HSS_PROF("spmv", s, spmv_bytes(A, nrhs)); k_spmv<<<cdiv(tot, KRY_NT), KRY_NT, 0, s>>>(A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy, nrhs); }
+    if (nrhs == 1) {
+        HSS_PROF("spmv", s, spmv_bytes(A, nrhs));
+        k_spmv<<<cdiv(tot, KRY_NT), KRY_NT, 0, s>>>(A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy, nrhs);
+    } else {
+        HSS_PROF("spmv", s, spmv_bytes(A, nrhs));
+        k_spmv_multi<<<cdiv(N, KRY_NT), KRY_NT, 0, s>>>(A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy,
+                                                       nrhs);
+    }
     HSS_CHECK_LAUNCH("k_spmv");
     return HSS_OK;
 }
