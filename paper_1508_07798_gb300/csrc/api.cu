@@ -2,6 +2,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 
@@ -32,24 +33,118 @@ int DevBuf::alloc(size_t nbytes) {
     return HSS_OK;
 }
 
+// ---- scratch cache: device chunks and pinned buffers kept between calls
+namespace {
+struct ScratchCache {
+    std::mutex mu;
+    std::vector<std::pair<int, DevBuf>> dev;              // (device, chunk)
+    std::vector<std::pair<void *, size_t>> pin;
+    size_t dev_bytes = 0, pin_bytes = 0;
+};
+ScratchCache &cache() {
+    static ScratchCache *c = new ScratchCache();   // never destroyed: no CUDA calls at process exit
+    return *c;
+}
+constexpr size_t CACHE_DEV_MAX = (size_t)8 << 30;
+constexpr size_t CACHE_PIN_MAX = (size_t)512 << 20;
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+}  // namespace
+
+int scratch_cache_take_device(size_t min_bytes, size_t want_bytes, DevBuf &out) {
+    const int d = current_device();
+    {
+        std::lock_guard<std::mutex> lk(cache().mu);
+        auto &v = cache().dev;
+        int best = -1;
+        for (int k = 0; k < (int)v.size(); ++k)
+            if (v[k].first == d && v[k].second.bytes >= min_bytes &&
+                (best < 0 || v[k].second.bytes < v[best].second.bytes))
+                best = k;
+        if (best >= 0) {
+            out = std::move(v[best].second);
+            cache().dev_bytes -= out.bytes;
+            v.erase(v.begin() + best);
+            return HSS_OK;
+        }
+    }
+    return out.alloc(want_bytes);
+}
+
+void scratch_cache_give_device(DevBuf &&b) {
+    if (!b.p) return;
+    std::lock_guard<std::mutex> lk(cache().mu);
+    if (cache().dev_bytes + b.bytes > CACHE_DEV_MAX) {
+        b.release();
+        return;
+    }
+    cache().dev_bytes += b.bytes;
+    cache().dev.emplace_back(current_device(), std::move(b));
+}
+
+void *scratch_cache_take_pinned(size_t min_bytes, size_t want_bytes, size_t &got) {
+    {
+        std::lock_guard<std::mutex> lk(cache().mu);
+        auto &v = cache().pin;
+        int best = -1;
+        for (int k = 0; k < (int)v.size(); ++k)
+            if (v[k].second >= min_bytes && (best < 0 || v[k].second < v[best].second)) best = k;
+        if (best >= 0) {
+            void *p = v[best].first;
+            got = v[best].second;
+            cache().pin_bytes -= got;
+            v.erase(v.begin() + best);
+            return p;
+        }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, want_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        got = 0;
+        return nullptr;
+    }
+    got = want_bytes;
+    return p;
+}
+
+void scratch_cache_give_pinned(void *p, size_t bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(cache().mu);
+    if (cache().pin_bytes + bytes > CACHE_PIN_MAX) {
+        cudaFreeHost(p);
+        return;
+    }
+    cache().pin_bytes += bytes;
+    cache().pin.emplace_back(p, bytes);
+}
+
 Work::~Work() {
     cudaStreamSynchronize(s);
+    for (auto &c : chunks) scratch_cache_give_device(std::move(c));
     chunks.clear();
-    if (hpin) cudaFreeHost(hpin);
-    for (void *p : old_pins) cudaFreeHost(p);
+    if (hpin) scratch_cache_give_pinned(hpin, hcap);
+    for (size_t k = 0; k < old_pins.size(); ++k) scratch_cache_give_pinned(old_pins[k], old_sizes[k]);
 }
 
 int Work::dalloc_bytes(size_t bytes, void **out) {
     bytes = (bytes + 255) & ~(size_t)255;
-    if (chunks.empty() || cur + bytes > chunks.back().bytes) {
-        size_t want = std::max(bytes, std::max((size_t)(16u << 20), chunks.empty() ? 0 : 2 * chunks.back().bytes));
-        DevBuf b;
-        int rc = b.alloc(want);
-        if (rc) return rc;
-        chunks.push_back(std::move(b));
+    while (ci < chunks.size() && cur + bytes > chunks[ci].bytes) {
+        ++ci;
         cur = 0;
     }
-    *out = static_cast<char *>(chunks.back().p) + cur;
+    if (ci >= chunks.size()) {
+        size_t want = std::max(bytes, std::max((size_t)(16u << 20), chunks.empty() ? 0 : 2 * chunks.back().bytes));
+        DevBuf b;
+        int rc = scratch_cache_take_device(bytes, want, b);
+        if (rc) return rc;
+        chunks.push_back(std::move(b));
+        ci = chunks.size() - 1;
+        cur = 0;
+    }
+    *out = static_cast<char *>(chunks[ci].p) + cur;
     cur += bytes;
     return HSS_OK;
 }
@@ -59,13 +154,16 @@ int Work::stage_bytes(const void *src, size_t bytes, void **dev) {
     if (rc || bytes == 0) return rc;
     size_t need = (bytes + 255) & ~(size_t)255;
     if (hused + need > hcap) {
-        if (hpin) old_pins.push_back(hpin);   // copies in flight may still read it
-        hcap = std::max(need, std::max((size_t)(1u << 20), 2 * hcap));
+        if (hpin) old_pins.push_back(hpin), old_sizes.push_back(hcap);   // copies in flight may still read it
+        size_t want = std::max(need, std::max((size_t)(1u << 20), 2 * hcap));
+        size_t got = 0;
+        hpin = scratch_cache_take_pinned(need, want, got);
         hused = 0;
-        if (cudaMallocHost(&hpin, hcap) != cudaSuccess) {
-            hpin = nullptr;
+        hcap = got;
+        if (!hpin) {
             hcap = 0;
-            return cuda_fail(cudaGetLastError(), "cudaMallocHost");
+            set_error("cudaMallocHost of the staging buffer failed");
+            return HSS_ENOMEM;
         }
     }
     void *h = static_cast<char *>(hpin) + hused;
@@ -77,17 +175,12 @@ int Work::stage_bytes(const void *src, size_t bytes, void **dev) {
 }
 
 void Work::reset() {
-    if (chunks.size() > 1) {
-        size_t total = 0;
-        for (auto &c : chunks) total += c.bytes;
-        chunks.clear();
-        DevBuf b;
-        if (b.alloc(total) == HSS_OK) chunks.push_back(std::move(b));
-    }
+    ci = 0;
     cur = 0;
     hused = 0;
-    for (void *p : old_pins) cudaFreeHost(p);
+    for (size_t k = 0; k < old_pins.size(); ++k) scratch_cache_give_pinned(old_pins[k], old_sizes[k]);
     old_pins.clear();
+    old_sizes.clear();
 }
 
 }  // namespace hssnd

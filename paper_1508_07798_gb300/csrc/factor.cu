@@ -535,12 +535,10 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
 }
 
 template <class T>
-int build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, DevBuf &&d_fronts, bool top, long &part_total,
-                      int &tk_total, cudaStream_t s) {
+int build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, bool top, long &part_total, int &tk_total) {
     as.top = top;
     as.nfronts = (int)fr.size();
-    as.fronts_buf = std::move(d_fronts);
-    as.d_fronts = as.fronts_buf.as<FrontDev>();
+    as.h_fronts = fr;
     std::vector<ApplyItem> items[2];
     int tiles[2] = {0, 0};
     as.fwd_bytes = as.bwd_bytes = as.fwd_vec = as.bwd_vec = 0;
@@ -571,12 +569,10 @@ int build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, DevBuf &&
     tk_total += tiles[0];
     as.tk_bwd = tk_total;
     tk_total += tiles[1];
-    int rc;
-    if ((rc = upload(as.fwd_buf, items[0], s)) || (rc = upload(as.bwd_buf, items[1], s))) return rc;
-    as.d_fwd = as.fwd_buf.as<ApplyItem>();
-    as.d_bwd = as.bwd_buf.as<ApplyItem>();
-    as.nfwd = (int)items[0].size();
-    as.nbwd = (int)items[1].size();
+    as.h_fwd = std::move(items[0]);
+    as.h_bwd = std::move(items[1]);
+    as.nfwd = (int)as.h_fwd.size();
+    as.nbwd = (int)as.h_bwd.size();
     return HSS_OK;
 }
 
@@ -610,10 +606,12 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     HSS_CUDA(cudaMemsetAsync(F->arena.p, 0, sizeof(T) * total, s));
     T *arena = F->arena_ptr<T>();
     const int ilen = t->ioff[nbox];
-    DevBuf d_piv, d_scratch, d_slot;
+    Work WL(s);   // scratch for the whole call (never reset)
+    ScratchPtr d_piv, d_scratch, d_slot, d_tcerr;
     if ((rc = upload(F->d_topset, topset, s)) || (rc = F->d_iperm.alloc(sizeof(int) * (ilen + ntop + 1))) ||
-        (rc = d_piv.alloc(sizeof(int) * (ilen + ntop + 1))) || (rc = d_scratch.alloc(sizeof(int) * (ilen + ntop + 1))) ||
-        (rc = d_slot.alloc(sizeof(int) * t->nelem)))
+        (rc = WL.dalloc_bytes(sizeof(int) * (ilen + ntop + 1), &d_piv.p)) ||
+        (rc = WL.dalloc_bytes(sizeof(int) * (ilen + ntop + 1), &d_scratch.p)) ||
+        (rc = WL.dalloc_bytes(sizeof(int) * t->nelem, &d_slot.p)) || (rc = WL.dalloc_bytes(sizeof(int), &d_tcerr.p)))
         return rc;
     HSS_CUDA(cudaMemsetAsync(d_slot.p, 0xff, sizeof(int) * t->nelem, s));
     // optional copies of S and H
@@ -631,8 +629,6 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     }
     T *keep = F->keep.as<T>();
     Work W(s);
-    DevBuf d_tcerr;
-    if ((rc = d_tcerr.alloc(sizeof(int)))) return rc;
     HSS_CUDA(cudaMemsetAsync(d_tcerr.p, 0, sizeof(int), s));
     Engine eng;
     eng.tc = std::is_same<T, float>::value ? o.tensor_cores : 0;
@@ -700,9 +696,11 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             F->factor_bytes += sizeof(T) * (ni * (ni + nb) + ni * nb);
         }
         W.reset();   // the stream is idle: the previous stage ended with a readback
-        DevBuf d_fr;
+        ScratchPtr d_fr;
         int *d_status;
-        if ((rc = upload(d_fr, fr, s)) || (rc = W.dalloc(fr.size(), &d_status))) return rc;
+        FrontDev *d_frp;
+        if ((rc = W.up(fr, &d_frp)) || (rc = W.dalloc(fr.size(), &d_status))) return rc;
+        d_fr.p = d_frp;
         HSS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int) * fr.size(), s));
         if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
             return rc;
@@ -730,8 +728,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             }
         if ((rc = check_tc())) return rc;
         F->apply.emplace_back();
-        if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), false, part_total, tk_total, s)))
-            return rc;
+        if ((rc = build_apply_stage<T>(F->apply.back(), fr, false, part_total, tk_total))) return rc;
     }
     // ---- top blocks A^(0): cross couplings from A, then full Gauss-Jordan inversion
     {
@@ -755,9 +752,11 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             for (int q = 0; q < t->nb[t->inst_top[i]] / t->bs; ++q) sides[i][q] = 0;
         }
         W.reset();
-        DevBuf d_fr;
+        ScratchPtr d_fr;
         int *d_status;
-        if ((rc = upload(d_fr, fr, s)) || (rc = W.dalloc(ninst, &d_status))) return rc;
+        FrontDev *d_frp;
+        if ((rc = W.up(fr, &d_frp)) || (rc = W.dalloc(ninst, &d_status))) return rc;
+        d_fr.p = d_frp;
         HSS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int) * ninst, s));
         if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
             return rc;
@@ -779,10 +778,33 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             F->factor_bytes += sizeof(T) * (double)ntop_i[i] * ntop_i[i];
         }
         F->apply.emplace_back();
-        if ((rc = build_apply_stage<T>(F->apply.back(), fr, std::move(d_fr), true, part_total, tk_total, s)))
-            return rc;
+        if ((rc = build_apply_stage<T>(F->apply.back(), fr, true, part_total, tk_total))) return rc;
     }
     {
+        // every stage's fronts and work items in one device allocation
+        size_t bytes = 0;
+        auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        for (const auto &st : F->apply)
+            bytes += al(sizeof(FrontDev) * st.h_fronts.size()) + al(sizeof(ApplyItem) * st.h_fwd.size()) +
+                     al(sizeof(ApplyItem) * st.h_bwd.size());
+        std::vector<char> pack(std::max(bytes, (size_t)1));
+        if ((rc = F->apply_buf.alloc(pack.size()))) return rc;
+        size_t o = 0;
+        char *base = F->apply_buf.as<char>();
+        auto put = [&](const void *src, size_t b) -> char * {
+            std::memcpy(pack.data() + o, src, b);
+            char *d = base + o;
+            o += al(b);
+            return d;
+        };
+        for (auto &st : F->apply) {
+            st.d_fronts = reinterpret_cast<FrontDev *>(put(st.h_fronts.data(), sizeof(FrontDev) * st.h_fronts.size()));
+            st.d_fwd = reinterpret_cast<ApplyItem *>(put(st.h_fwd.data(), sizeof(ApplyItem) * st.h_fwd.size()));
+            st.d_bwd = reinterpret_cast<ApplyItem *>(put(st.h_bwd.data(), sizeof(ApplyItem) * st.h_bwd.size()));
+            std::vector<ApplyItem>().swap(st.h_fwd);
+            std::vector<ApplyItem>().swap(st.h_bwd);
+        }
+        HSS_CUDA(cudaMemcpyAsync(base, pack.data(), pack.size(), cudaMemcpyHostToDevice, s));
         if ((rc = F->d_apart.alloc(sizeof(double) * 32 * APPLY_RB * std::max(part_total, 1L))) ||
             (rc = F->d_tickets.alloc(sizeof(int) * std::max(tk_total, 1))))
             return rc;

@@ -24,7 +24,8 @@ struct ApplyItem {
 struct ApplyStage {
     bool top = false;
     int nfronts = 0;
-    DevBuf fronts_buf, fwd_buf, bwd_buf;
+    std::vector<FrontDev> h_fronts;       // host copies, packed into the factor's apply buffer
+    std::vector<ApplyItem> h_fwd, h_bwd;
     FrontDev *d_fronts = nullptr;
     ApplyItem *d_fwd = nullptr, *d_bwd = nullptr;
     int nfwd = 0, nbwd = 0;               // work items (warps) of the two sweeps
@@ -80,6 +81,7 @@ struct hss_factor_t {
     hssnd::DevBuf d_aparams;
     hssnd::DevBuf d_apart;       // partial sums of split apply tiles (items x 32 x 4)
     hssnd::DevBuf d_tickets;     // one ticket counter per split tile
+    hssnd::DevBuf apply_buf;     // fronts and work items of every apply stage, one allocation
     // batched factor (hss_factor_batched): device copy of the block-diagonal
     // union of the instances' matrices, used by the batched solver
     int batched = 0;

@@ -67,15 +67,21 @@ template <class T> int upload(DevBuf &b, const std::vector<T> &v, cudaStream_t s
 }
 
 // Scratch of one library call: a device bump allocator and a pinned host
-// staging buffer for uploads.  Nothing is freed until reset() (stream idle)
-// or destruction, so kernels may use the memory until the next sync point.
+// staging buffer for uploads.  Nothing is given back until reset() (stream
+// idle: the bump pointer restarts in the first chunk) or destruction (after
+// a stream synchronize), so kernels may use the memory until the next sync
+// point.  Chunks and pinned buffers come from, and go back to, a
+// process-wide cache (scratch_cache_*), so steady-state calls allocate
+// nothing from CUDA.
 struct Work {
     cudaStream_t s = nullptr;
     std::vector<DevBuf> chunks;
-    size_t cur = 0;
+    size_t ci = 0;     // chunk in use
+    size_t cur = 0;    // bump offset inside it
     void *hpin = nullptr;
     size_t hcap = 0, hused = 0;
     std::vector<void *> old_pins;
+    std::vector<size_t> old_sizes;
     explicit Work(cudaStream_t st) : s(st) {}
     Work(const Work &) = delete;
     Work &operator=(const Work &) = delete;
@@ -96,6 +102,18 @@ struct Work {
     }
     void reset();   // the stream must be idle
 };
+
+// A pointer into call scratch with the same accessor as DevBuf.
+struct ScratchPtr {
+    void *p = nullptr;
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Process-wide cache of scratch memory (bounded; thread-safe).
+int scratch_cache_take_device(size_t min_bytes, size_t want_bytes, DevBuf &out);
+void scratch_cache_give_device(DevBuf &&b);
+void *scratch_cache_take_pinned(size_t min_bytes, size_t want_bytes, size_t &got);
+void scratch_cache_give_pinned(void *p, size_t bytes);
 
 // ---------------------------------------------------------------- tree
 struct HssNode {          // one node of the HSS tree of a front's S (host view)

@@ -220,18 +220,21 @@ int spmv(const hss_bsr *A, int nrhs, const double *x, long ldx, double *y, long 
     return HSS_OK;
 }
 
+// Krylov workspace of one solve, carved from the call scratch (cached between calls).
 struct Krylov {
-    DevBuf V, Z, w, r, part, H, cs, sn, g, y, scal;
+    ScratchPtr V, Z, w, r, part, H, cs, sn, g, y, scal;
     int m = 0;
     long N = 0;
-    int alloc(long n, int mm) {
+    int alloc(Work &W, long n, int mm) {
         int rc;
-        if ((rc = V.alloc(sizeof(double) * n * (mm + 1))) || (rc = Z.alloc(sizeof(double) * n * mm)) ||
-            (rc = w.alloc(sizeof(double) * n)) || (rc = r.alloc(sizeof(double) * n)) ||
-            (rc = part.alloc(sizeof(double) * DOT_BLOCKS * KRY_MAXM)) ||
-            (rc = H.alloc(sizeof(double) * (mm + 1) * mm)) || (rc = cs.alloc(sizeof(double) * mm)) ||
-            (rc = sn.alloc(sizeof(double) * mm)) || (rc = g.alloc(sizeof(double) * (mm + 1))) ||
-            (rc = y.alloc(sizeof(double) * mm)) || (rc = scal.alloc(sizeof(double) * 8)))
+        if ((rc = W.dalloc_bytes(sizeof(double) * n * (mm + 1), &V.p)) ||
+            (rc = W.dalloc_bytes(sizeof(double) * n * mm, &Z.p)) || (rc = W.dalloc_bytes(sizeof(double) * n, &w.p)) ||
+            (rc = W.dalloc_bytes(sizeof(double) * n, &r.p)) ||
+            (rc = W.dalloc_bytes(sizeof(double) * DOT_BLOCKS * KRY_MAXM, &part.p)) ||
+            (rc = W.dalloc_bytes(sizeof(double) * (mm + 1) * mm, &H.p)) ||
+            (rc = W.dalloc_bytes(sizeof(double) * mm, &cs.p)) || (rc = W.dalloc_bytes(sizeof(double) * mm, &sn.p)) ||
+            (rc = W.dalloc_bytes(sizeof(double) * (mm + 1), &g.p)) || (rc = W.dalloc_bytes(sizeof(double) * mm, &y.p)) ||
+            (rc = W.dalloc_bytes(sizeof(double) * 8, &scal.p)))
             return rc;
         m = mm;
         N = n;
@@ -351,9 +354,10 @@ extern "C" int fgmres_solve(const hss_bsr *A, const hss_factor_t *f, int nrhs, c
         return HSS_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    Work W(s);
     Krylov K;
     int rc;
-    if ((rc = K.alloc(N, o.restart))) return rc;
+    if ((rc = K.alloc(W, N, o.restart))) return rc;
     g_hist.assign(nrhs, {});
     fgmres_stats st{0, 0, 0.0, 1};
     for (int k = 0; k < nrhs; ++k) {

@@ -389,12 +389,15 @@ extern "C" int nd_order(const hss_mesh *mesh, const hss_bsr *A, const hss_nd_opt
         hb[b].pos1e = t->pos1[b] / bs;
     }
 
-    DevBuf d_box, d_anc, d_dfs, d_flag, d_err, d_cnt, d_off;
+    // call scratch (returned to the scratch cache when W goes out of scope)
+    Work W(s);
+    ScratchPtr d_box, d_anc, d_dfs, d_flag, d_err, d_cnt, d_off;
     int rc;
-    if ((rc = upload(d_box, hb, s)) || (rc = d_anc.alloc(sizeof(int) * nelem * (maxlev + 1))) ||
-        (rc = d_dfs.alloc(sizeof(int) * nelem)) || (rc = d_flag.alloc(sizeof(unsigned) * nelem)) ||
-        (rc = d_err.alloc(sizeof(int))) || (rc = d_cnt.alloc(sizeof(int) * 2 * nbox)) ||
-        (rc = d_off.alloc(sizeof(int) * 4 * nbox))) {
+    if ((rc = W.stage_bytes(hb.data(), sizeof(NdBoxDev) * hb.size(), &d_box.p)) ||
+        (rc = W.dalloc_bytes(sizeof(int) * nelem * (maxlev + 1), &d_anc.p)) ||
+        (rc = W.dalloc_bytes(sizeof(int) * nelem, &d_dfs.p)) || (rc = W.dalloc_bytes(sizeof(unsigned) * nelem, &d_flag.p)) ||
+        (rc = W.dalloc_bytes(sizeof(int), &d_err.p)) || (rc = W.dalloc_bytes(sizeof(int) * 2 * nbox, &d_cnt.p)) ||
+        (rc = W.dalloc_bytes(sizeof(int) * 4 * nbox, &d_off.p))) {
         delete t;
         return rc;
     }
