@@ -70,6 +70,17 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_TFLOPS = 1.25
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank values over all ranks (the job ends
+    when its slowest replica ends).  Works with any torch.distributed backend
+    whose tensors live on `device`."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(values), device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def profiled_traffic(kernel):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
     when there is none or the kernel's source changed since the capture."""
@@ -340,10 +351,7 @@ def bench_ours(args, rank, world):
     # ---- max over ranks
     value = forms[head]["ms"]
     if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([value, e2e["value"]], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        value, e2e["value"] = float(tt[0]), float(tt[1])
+        value, e2e["value"] = max_over_ranks([value, e2e["value"]], dev)
 
     # ---- roofline of the dominant kernel of the headline form
     prof = prof_all[head]
@@ -518,6 +526,9 @@ def bench_batched(args, rank, world):
         roof = dict(kernel=dom, bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
                     traffic=None, launches=cnt, share=ms / sum(v[0] for v in prof.values()), peak_source=pk["src"])
     value = statistics.mean(times)
+    e2e_v = statistics.mean(ets)
+    if world > 1:
+        value, e2e_v = max_over_ranks([value, e2e_v], dev)
     return dict(metric=METRIC, value=value, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=value, higher_is_better=False, scaling="weak", vs_baseline=None,
                 dtype="f32 factor / f64 Krylov", data="synthetic",
@@ -527,7 +538,7 @@ def bench_batched(args, rank, world):
                             parallelism=f"replicas x{world} (independent batches)"),
                 converged=bool(conv and worst <= RTOL * 1.0001), worst_true_relres=worst,
                 max_iters=max(iters), sequential_ms=sequential_ms,
-                roofline=roof, e2e=dict(value=statistics.mean(ets), unit="ms", h2d_bytes_per_step=int(h2d),
+                roofline=roof, e2e=dict(value=e2e_v, unit="ms", h2d_bytes_per_step=int(h2d),
                                         d2h_bytes_per_step=int(d2h)),
                 clocks=clocks, gpu_launches=int(launches), kernels_instrumented_step=kernels)
 
