@@ -177,33 +177,40 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
     // ---- column-pivoted QR of A = L^t with the relative rank cut; trailing
     // column norms are recomputed (not downdated) by the warp that updates
     // the column
+    // The pivot search is fused into the column updates: each warp keeps the
+    // largest key (ties: lowest column) among the columns it just updated, and
+    // the next step reduces the warps' candidates after one barrier.
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int c = w; c < m; c += ID_NT / 32) {
-        T sq = 0;
-        for (int i = lane; i < r; i += 32) sq += A[i + (long)lda * c] * A[i + (long)lda * c];
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        if (lane == 0) nrm2[c] = sq;
+    __shared__ AM<T> cand[ID_NT / 32];
+    {
+        AM<T> wbest{-1LL, INT_MAX};
+        for (int c = w; c < m; c += ID_NT / 32) {
+            T sq = 0;
+            for (int i = lane; i < r; i += 32) sq += A[i + (long)lda * c] * A[i + (long)lda * c];
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (lane == 0) {
+                nrm2[c] = sq;
+                const long long kc = nn_key(sq);
+                if (kc > wbest.v || (kc == wbest.v && c < wbest.i)) wbest = AM<T>{kc, c};
+            }
+        }
+        if (lane == 0) cand[w] = wbest;
     }
     int k = 0;
     T first = 0;
     const int kmx = min(r, m);
     for (int j = 0; j < kmx; ++j) {
-        AM<T> loc{-1LL, INT_MAX};
-        __syncthreads();
-        for (int c = j + threadIdx.x; c < m; c += ID_NT) {
-            const long long kc = nn_key(nrm2[c]);
-            if (kc > loc.v || (kc == loc.v && c < loc.i)) {
-                loc.v = kc;
-                loc.i = c;
-            }
+        __syncthreads();   // candidates, nrm2, order and the updated columns are visible
+        AM<T> best = cand[0];
+        for (int q = 1; q < ID_NT / 32; ++q) {
+            const AM<T> o = cand[q];
+            if (o.v > best.v || (o.v == best.v && o.i < best.i)) best = o;
         }
-        AM<T> best = blk_argmax(loc, sham);
         const T nn2 = key_val(best.v, T(0));
         const T nrm = sqrt(nn2);
         if (j == 0) first = nrm;
-        if (first == T(0) || nrm <= tol * first) break;
+        if (best.v < 0 || first == T(0) || nrm <= tol * first) break;
         const int p = best.i;
-        // every thread has read nrm2 and order before the barrier inside blk_argmax
         if (threadIdx.x == 0 && p != j) {
             int t = order[j];
             order[j] = order[p];
@@ -216,12 +223,13 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
                 A[i + (long)lda * j] = A[i + (long)lda * p];
                 A[i + (long)lda * p] = t;
             }
-        __syncthreads();
+        __syncthreads();   // every thread has read cand; column j holds the pivot column
         const T x0 = A[j + (long)lda * j];
         const T alpha = (x0 != T(0)) ? -copysign(nrm, x0) : -nrm;
         const T vn = (x0 - alpha) * (x0 - alpha) + (nn2 - x0 * x0);
         for (int i = j + threadIdx.x; i < r; i += ID_NT) v[i] = (i == j) ? x0 - alpha : A[i + (long)lda * j];
         __syncthreads();
+        AM<T> wbest{-1LL, INT_MAX};
         for (int c = j + 1 + w; c < m; c += ID_NT / 32) {
             T d = 0;
             for (int i = j + lane; i < r; i += 32) d += v[i] * A[i + (long)lda * c];
@@ -234,8 +242,13 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
                 if (i > j) sq += a * a;
             }
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if (lane == 0) nrm2[c] = sq;
+            if (lane == 0) {
+                nrm2[c] = sq;
+                const long long kc = nn_key(sq);
+                if (kc > wbest.v || (kc == wbest.v && c < wbest.i)) wbest = AM<T>{kc, c};
+            }
         }
+        if (lane == 0) cand[w] = wbest;
         for (int i = j + threadIdx.x; i < r; i += ID_NT) A[i + (long)lda * j] = (i == j) ? alpha : T(0);
         k = j + 1;
     }
