@@ -122,18 +122,57 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         int off, cnt, reg, kb, rows;
         size_t smem;
     };
+    // Large fronts (n >= PANEL_BLOCK_MIN_N) run in blocks of PANEL_BLOCK
+    // panels: a panel's row moves and update reach only the columns of its
+    // block; at the end of a block the other columns take the block's row
+    // moves and one update of the block's width (for Gauss-Jordan,
+    // C_out <- F(:, B) Aold(B, out) + C_out with the block's pivot rows
+    // zeroed, the panel formula with B for the panel).  This reads the
+    // trailing matrix once per block instead of once per panel, and the
+    // K = 128 product suits the tensor cores; the cost is the explicit
+    // inverse of the block's pivot rows in the update, whose rounding grows
+    // with that block's condition, so smaller fronts keep per-panel updates.
+    std::vector<long> aoffB(nf);
+    long aoldB_total = 0;
+    for (int f = 0; f < nf; ++f) {
+        aoffB[f] = aoldB_total;
+        aoldB_total += (long)PANEL_BLOCK * kb[f] * fr[f].n;
+    }
     std::vector<PanelJob> jobs;
+    std::vector<std::vector<int>> jobs_of(nf);
+    std::vector<BlockJob> bjobs;
     std::vector<GemmDesc<T>> descs;
-    std::vector<GemmTile> tiles, ttiles;   // SIMT and tensor-core tiles
+    std::vector<long> desc_b;        // offset of each descriptor's B operand in Aold (block: in AoldB)
+    std::vector<char> desc_blk;
+    std::vector<GemmTile> tiles, ttiles, btiles, bttiles;   // in-block / block-end, SIMT / tensor cores
     std::vector<PanelTile> ptiles;
+    std::vector<BlockTile> bptiles;
     std::vector<std::vector<Group>> groups(maxsteps);
     std::vector<int> tile_off(maxsteps + 1), ttile_off(maxsteps + 1), ptile_off(maxsteps + 1);
+    std::vector<int> btile_off(maxsteps + 1), bttile_off(maxsteps + 1), bptile_off(maxsteps + 1);
     long xtotal = 0, mtotal = 0;
     std::vector<double> step_flops(maxsteps, 0.0), tstep_flops(maxsteps, 0.0);
+    std::vector<double> bstep_flops(maxsteps, 0.0), btstep_flops(maxsteps, 0.0);
+    auto add_desc = [&](const GemmDesc<T> &d, long boff, bool blk, std::vector<GemmTile> &simt,
+                        std::vector<GemmTile> &tc, double &fl, double &tfl) {
+        descs.push_back(d);
+        desc_b.push_back(boff);
+        desc_blk.push_back(blk);
+        if (use_tc(eng, d)) {
+            tiles_for(eng, descs.back(), (int)descs.size() - 1, tc);
+            tfl += gemm_flops(d);
+        } else {
+            gemm_tiles_for(descs.back(), (int)descs.size() - 1, simt);
+            fl += gemm_flops(d);
+        }
+    };
     for (int st = 0; st < maxsteps; ++st) {
         tile_off[st] = (int)tiles.size();
         ttile_off[st] = (int)ttiles.size();
         ptile_off[st] = (int)ptiles.size();
+        btile_off[st] = (int)btiles.size();
+        bttile_off[st] = (int)bttiles.size();
+        bptile_off[st] = (int)bptiles.size();
         std::vector<int> act;
         for (int f = 0; f < nf; ++f)
             if (st < nsteps[f]) act.push_back(f);
@@ -144,8 +183,14 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             return Rf[a] < Rf[b];
         });
         for (int f : act) {
+            const int n = fr[f].n;
             int k0 = st * kb[f];
             int kbs = std::min(kb[f], fr[f].ni - k0);
+            // fronts below PANEL_BLOCK_MIN_N: one block spanning every column
+            // (the plain per-panel update)
+            const bool blocked = n >= PANEL_BLOCK_MIN_N;
+            const int K0 = blocked ? (st / PANEL_BLOCK) * PANEL_BLOCK * kb[f] : 0;
+            const int bw = blocked ? std::min(PANEL_BLOCK * kb[f], fr[f].ni - K0) : n;
             size_t hT = (size_t)(fr[f].ni - k0);
             int use_smem = 0;
             size_t need = 0;
@@ -165,21 +210,23 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             gs.back().smem = std::max(gs.back().smem, need);
             int jid = (int)jobs.size();
             jobs.push_back({f, k0, kbs, use_smem, aoff[f], xtotal, mtotal});
+            jobs_of[f].push_back(jid);
             xtotal += (long)kbs * kbs;
             mtotal += 1 + 4 * PANEL_KB_MAX;
-            for (int c0 = 0; c0 < fr[f].n; c0 += 32)
-                if (!(c0 >= k0 && c0 + 32 <= k0 + kbs)) ptiles.push_back({jid, 0, c0});
-            int nout = fr[f].n - (fr[f].ni - k0);
-            for (int r0 = 0; r0 < nout; r0 += 64) ptiles.push_back({jid, 1, r0});
+            // in-block columns [K0, K0 + bw) outside the panel
+            for (int c0 = K0; c0 < K0 + bw; c0 += 32)
+                if (!(c0 >= k0 && c0 + 32 <= k0 + kbs)) ptiles.push_back({jid, 0, c0, K0, K0 + bw});
+            int nout = n - (fr[f].ni - k0);
+            for (int r0 = 0; r0 < nout; r0 += 64) ptiles.push_back({jid, 1, r0, 0, 0});
             GemmDesc<T> d{};
-            d.A = arena + fr[f].foff + (long)fr[f].n * k0;
-            d.lda = fr[f].n;
-            d.B = nullptr;  // Aold of this job, set once the workspace exists
-            d.C = arena + fr[f].foff;
-            d.ldc = fr[f].n;
+            d.A = arena + fr[f].foff + (long)n * k0;
+            d.lda = n;
+            d.B = nullptr;  // Aold of this job (columns from K0), set once the workspace exists
+            d.C = arena + fr[f].foff + (long)n * K0;
+            d.ldc = n;
             d.ldb = kbs;
-            d.m = fr[f].n;
-            d.n = fr[f].n;
+            d.m = n;
+            d.n = bw;
             d.k = kbs;
             d.transA = 0;
             d.transB = 0;
@@ -187,33 +234,67 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             d.beta = T(1);
             d.zr_lo = k0;
             d.zr_hi = k0 + kbs;
-            d.skip_lo = k0;
-            d.skip_hi = k0 + kbs;
-            descs.push_back(d);
-            if (use_tc(eng, d)) {
-                tiles_for(eng, descs.back(), (int)descs.size() - 1, ttiles);
-                tstep_flops[st] += gemm_flops(d);
-            } else {
-                gemm_tiles_for(descs.back(), (int)descs.size() - 1, tiles);
-                step_flops[st] += gemm_flops(d);
+            d.skip_lo = k0 - K0;
+            d.skip_hi = k0 - K0 + kbs;
+            if (bw > kbs) add_desc(d, aoff[f] + (long)kbs * K0, false, tiles, ttiles, step_flops[st], tstep_flops[st]);
+            // end of the block: the other columns
+            const bool block_end = blocked && ((st % PANEL_BLOCK == PANEL_BLOCK - 1) || st == nsteps[f] - 1);
+            if (block_end && n > bw) {
+                BlockJob bj{};
+                bj.front = f;
+                bj.k0 = K0;
+                bj.width = bw;
+                bj.np = st % PANEL_BLOCK + 1;
+                for (int q = 0; q < bj.np; ++q) bj.job[q] = jobs_of[f][st - bj.np + 1 + q];
+                bj.aoff = aoffB[f];
+                const int bjid = (int)bjobs.size();
+                bjobs.push_back(bj);
+                for (int c0 = 0; c0 < n; c0 += 32)
+                    if (!(c0 >= K0 && c0 + 32 <= K0 + bw)) bptiles.push_back({bjid, c0});
+                GemmDesc<T> e{};
+                e.A = arena + fr[f].foff + (long)n * K0;
+                e.lda = n;
+                e.B = nullptr;   // AoldB, set once the workspace exists
+                e.ldb = bw;
+                e.C = arena + fr[f].foff;
+                e.ldc = n;
+                e.m = n;
+                e.n = n;
+                e.k = bw;
+                e.transA = 0;
+                e.transB = 0;
+                e.alpha = T(1);
+                e.beta = T(1);
+                e.zr_lo = K0;
+                e.zr_hi = K0 + bw;
+                e.skip_lo = K0;
+                e.skip_hi = K0 + bw;
+                add_desc(e, aoffB[f], true, btiles, bttiles, bstep_flops[st], btstep_flops[st]);
             }
         }
     }
     tile_off[maxsteps] = (int)tiles.size();
     ttile_off[maxsteps] = (int)ttiles.size();
     ptile_off[maxsteps] = (int)ptiles.size();
-    T *d_aold, *d_x;
+    btile_off[maxsteps] = (int)btiles.size();
+    bttile_off[maxsteps] = (int)bttiles.size();
+    bptile_off[maxsteps] = (int)bptiles.size();
+    T *d_aold, *d_aoldB, *d_x;
     int *d_mv;
     PanelJob *d_jobs;
+    BlockJob *d_bjobs;
     GemmDesc<T> *d_descs;
-    GemmTile *d_tiles, *d_ttiles;
+    GemmTile *d_tiles, *d_ttiles, *d_btiles, *d_bttiles;
     PanelTile *d_ptiles;
+    BlockTile *d_bptiles;
     int rc;
-    if ((rc = W.dalloc(aold_total, &d_aold)) || (rc = W.dalloc(xtotal, &d_x)) || (rc = W.dalloc(mtotal, &d_mv)))
+    if ((rc = W.dalloc(aold_total, &d_aold)) || (rc = W.dalloc(std::max(aoldB_total, 1L), &d_aoldB)) ||
+        (rc = W.dalloc(xtotal, &d_x)) || (rc = W.dalloc(mtotal, &d_mv)))
         return rc;
-    for (size_t i = 0; i < descs.size(); ++i) descs[i].B = d_aold + jobs[i].aoff;
-    if ((rc = W.up(jobs, &d_jobs)) || (rc = W.up(descs, &d_descs)) || (rc = W.up(tiles, &d_tiles)) ||
-        (rc = W.up(ttiles, &d_ttiles)) || (rc = W.up(ptiles, &d_ptiles)))
+    for (size_t i = 0; i < descs.size(); ++i) descs[i].B = (desc_blk[i] ? d_aoldB : d_aold) + desc_b[i];
+    if ((rc = W.up(jobs, &d_jobs)) || (rc = W.up(bjobs, &d_bjobs)) || (rc = W.up(descs, &d_descs)) ||
+        (rc = W.up(tiles, &d_tiles)) || (rc = W.up(ttiles, &d_ttiles)) || (rc = W.up(btiles, &d_btiles)) ||
+        (rc = W.up(bttiles, &d_bttiles)) || (rc = W.up(ptiles, &d_ptiles)) || (rc = W.up(bptiles, &d_bptiles)))
         return rc;
     for (int st = 0; st < maxsteps; ++st) {
         for (const Group &g : groups[st]) {
@@ -233,6 +314,15 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             return rc;
         if ((rc = run_gemm<T>(eng, true, d_descs, d_ttiles + ttile_off[st], ttile_off[st + 1] - ttile_off[st], s,
                               tstep_flops[st])))
+            return rc;
+        if ((rc = launch_gj_block_post<T>(d_bptiles + bptile_off[st], bptile_off[st + 1] - bptile_off[st], d_bjobs,
+                                          d_jobs, d_fr, arena, d_aoldB, d_mv, s)))
+            return rc;
+        if ((rc = gemm_batched<T>(d_descs, d_btiles + btile_off[st], btile_off[st + 1] - btile_off[st], s,
+                                  bstep_flops[st])))
+            return rc;
+        if ((rc = run_gemm<T>(eng, true, d_descs, d_bttiles + bttile_off[st], bttile_off[st + 1] - bttile_off[st], s,
+                              btstep_flops[st])))
             return rc;
     }
     return HSS_OK;

@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(256) k_gj_post(const PanelTile *__restrict__ t
         T *Ao = aold_ws + J.aoff;
         for (int cc = wid; cc < 32; cc += 8) {
             const int c = tl.start + cc;
-            if (c >= n || (c >= k0 && c < k0 + kb)) continue;
+            if (c >= n || c < tl.c_lo || c >= tl.c_hi || (c >= k0 && c < k0 + kb)) continue;
             T *col = M + ld * c + k0;
             if (nm > 0) {
                 T v0 = lane < nm ? col[mv[1 + 2 * PANEL_KB_MAX + lane]] : T(0);
@@ -494,6 +494,44 @@ __global__ void __launch_bounds__(256) k_gj_post(const PanelTile *__restrict__ t
         }
 }
 
+// End of a block of panels, for the columns outside the block (32 per tile):
+// replay the row moves of the block's panels in order, then copy the block's
+// pivot rows [k0, k0 + width) into Aold, the B operand of the block's update.
+template <class T>
+__global__ void __launch_bounds__(256) k_gj_block_post(const BlockTile *__restrict__ tiles,
+                                                   const BlockJob *__restrict__ bjobs,
+                                                   const PanelJob *__restrict__ jobs,
+                                                   const FrontDev *__restrict__ fr, T *__restrict__ arena,
+                                                   T *__restrict__ aold_ws, const int *__restrict__ mws) {
+    const BlockTile tl = tiles[blockIdx.x];
+    const BlockJob B = bjobs[tl.bjob];
+    const FrontDev F = fr[B.front];
+    T *M = arena + F.foff;
+    const long ld = F.n;
+    const int n = F.n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T *Ao = aold_ws + B.aoff;
+    for (int cc = wid; cc < 32; cc += 8) {
+        const int c = tl.start + cc;
+        if (c >= n || (c >= B.k0 && c < B.k0 + B.width)) continue;
+        for (int q = 0; q < B.np; ++q) {
+            const PanelJob J = jobs[B.job[q]];
+            const int *mv = mws + J.moff;
+            const int nm = mv[0];
+            if (nm == 0) continue;
+            T *col = M + ld * c + J.k0;
+            T v0 = lane < nm ? col[mv[1 + 2 * PANEL_KB_MAX + lane]] : T(0);
+            T v1 = lane + 32 < nm ? col[mv[1 + 2 * PANEL_KB_MAX + lane + 32]] : T(0);
+            __syncwarp();
+            if (lane < nm) col[mv[1 + lane]] = v0;
+            if (lane + 32 < nm) col[mv[1 + lane + 32]] = v1;
+            __syncwarp();
+        }
+        const T *colk = M + ld * c + B.k0;
+        for (int i = lane; i < B.width; i += 32) Ao[i + (long)B.width * c] = colk[i];
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 template <class T>
 int launch_scatter_A(const hss_bsr *A, const StageElem *se, int nse, int *elem_slot, const FrontDev *fr, T *arena,
@@ -505,6 +543,16 @@ int launch_scatter_A(const hss_bsr *A, const StageElem *se, int nse, int *elem_s
                                                              elem_slot, fr, arena); }
     { HSS_PROF("set_slots", s); k_set_slots<<<cdiv(nse, 256), 256, 0, s>>>(se, nse, elem_slot, 0); }
     HSS_CHECK_LAUNCH("k_scatter_A");
+    return HSS_OK;
+}
+
+template <class T>
+int launch_gj_block_post(const BlockTile *tiles, int ntiles, const BlockJob *bjobs, const PanelJob *jobs,
+                         const FrontDev *fr, T *arena, T *aold, const int *mws, cudaStream_t s) {
+    if (ntiles == 0) return HSS_OK;
+    HSS_PROF(sizeof(T) == 8 ? "gj_post_f64" : "gj_post_f32", s);
+    k_gj_block_post<T><<<ntiles, 256, 0, s>>>(tiles, bjobs, jobs, fr, arena, aold, mws);
+    HSS_CHECK_LAUNCH("k_gj_block_post");
     return HSS_OK;
 }
 
@@ -589,6 +637,10 @@ template int launch_gj_panel_reg<double>(const PanelJob *, int, int, int, const 
                                          int *, int *, int *, const int *, int *, int *, cudaStream_t);
 template int launch_gj_panel_reg<float>(const PanelJob *, int, int, int, const FrontDev *, float *, float *, int *,
                                         int *, int *, const int *, int *, int *, cudaStream_t);
+template int launch_gj_block_post<double>(const BlockTile *, int, const BlockJob *, const PanelJob *,
+                                          const FrontDev *, double *, double *, const int *, cudaStream_t);
+template int launch_gj_block_post<float>(const BlockTile *, int, const BlockJob *, const PanelJob *,
+                                         const FrontDev *, float *, float *, const int *, cudaStream_t);
 template int launch_gj_post<double>(const PanelTile *, int, const PanelJob *, const FrontDev *, double *, double *,
                                     const double *, const int *, cudaStream_t);
 template int launch_gj_post<float>(const PanelTile *, int, const PanelJob *, const FrontDev *, float *, float *,

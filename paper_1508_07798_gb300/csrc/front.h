@@ -42,6 +42,24 @@ struct PanelTile {
     int job;
     int type;         // 0: 32 columns outside the panel; 1: 64 rows outside [k0, ni)
     int start;
+    int c_lo, c_hi;   // type 0: only columns in [c_lo, c_hi) (the panel's block)
+};
+
+// The end of a block of up to PANEL_BLOCK panels of one front: the columns
+// outside the block receive the block's row moves and one update of width
+// `width` (see k_gj_block_post).
+constexpr int PANEL_BLOCK = 4;
+constexpr int PANEL_BLOCK_MIN_N = 2048;   // fronts at least this large run in blocks
+struct BlockJob {
+    int front;        // stage-local front index
+    int k0, width;    // block columns [k0, k0 + width)
+    int np;           // panels in the block
+    int job[PANEL_BLOCK];   // their panel jobs (move lists)
+    long aoff;        // offset of this block's Aold (width x n) in the workspace
+};
+struct BlockTile {
+    int bjob;
+    int start;        // first of 32 columns
 };
 
 template <class T>
@@ -54,6 +72,9 @@ template <class T>
 int launch_gj_panel_reg(const PanelJob *jobs, int njobs, int kb, int rows, const FrontDev *fr, T *arena, T *xws,
                         int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s);
 bool panel_reg_fits(int kb, int rows, int tsize);
+template <class T>
+int launch_gj_block_post(const BlockTile *tiles, int ntiles, const BlockJob *bjobs, const PanelJob *jobs,
+                         const FrontDev *fr, T *arena, T *aold, const int *mws, cudaStream_t s);
 template <class T>
 int launch_gj_post(const PanelTile *tiles, int ntiles, const PanelJob *jobs, const FrontDev *fr, T *arena, T *aold,
                    const T *xws, const int *mws, cudaStream_t s);
