@@ -81,6 +81,25 @@ def max_over_ranks(values, device):
     return [float(v) for v in t.cpu()]
 
 
+def roofline_of(kernel, ms, cnt, work, total_ms, pk):
+    """Roofline entry of one kernel class: FLOP-counted classes (GEMMs and the
+    Gauss-Jordan panels) against the FP32/FP64 arithmetic peak, byte-counted
+    classes (apply, SpMV) against the measured HBM bandwidth."""
+    per_launch_s = ms / cnt * 1e-3
+    if kernel.startswith("gemm") or kernel.startswith("gj_panel"):
+        f32 = kernel.endswith("f32")
+        peak = FP32_SIMT_TFLOPS if f32 else FP64_TFLOPS
+        ach = work / cnt / per_launch_s / 1e12
+        return dict(kernel=kernel, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    traffic=profiled_traffic(kernel), launches=cnt, avg_launch_us=ms / cnt * 1e3,
+                    share=ms / total_ms,
+                    peak_source="derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz" if f32
+                    else "nominal GB300 FP64 1.25 TFLOP/s")
+    ach = work / cnt / per_launch_s / 1e9
+    return dict(kernel=kernel, bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
+                traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms, peak_source=pk["src"])
+
+
 def profiled_traffic(kernel):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
     when there is none or the kernel's source changed since the capture."""
@@ -357,20 +376,11 @@ def bench_ours(args, rank, world):
     prof = prof_all[head]
     tracked = {k: v for k, v in prof.items() if v[2] > 0}
     dom = max(tracked, key=lambda k: tracked[k][0]) if tracked else max(prof, key=lambda k: prof[k][0])
-    ms, cnt, work = prof[dom]
     total_ms = sum(v[0] for v in prof.values())
-    if dom.startswith("gemm"):
-        peak = FP32_SIMT_TFLOPS if dom.endswith("f32") else FP64_TFLOPS
-        ach = work / cnt / (ms / cnt * 1e-3) / 1e12
-        roof = dict(kernel=dom, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                    traffic=profiled_traffic(dom), launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
-                    peak_source="derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz" if dom.endswith("f32")
-                    else "nominal GB300 FP64 1.25 TFLOP/s")
-    else:
-        ach = work / cnt / (ms / cnt * 1e-3) / 1e9
-        roof = dict(kernel=dom, bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
-                    traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
-                    peak_source=pk["src"])
+    roof = roofline_of(dom, *prof[dom], total_ms, pk)
+    # the next tracked classes by time, for context
+    roof["others"] = [roofline_of(k, *prof[k], total_ms, pk) for k in
+                      sorted(tracked, key=lambda k: -tracked[k][0]) if k != dom][:3]
     kernels = {form: {k: dict(ms=round(v[0] / args.steps, 4), launches=v[1] // args.steps) for k, v in
                       sorted(pf.items(), key=lambda kv: -kv[1][0])} for form, pf in prof_all.items()}
     res = dict(metric=METRIC, value=value, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -513,18 +523,8 @@ def bench_batched(args, rank, world):
     kernels = {k: dict(ms=round(v[0], 3), launches=v[1]) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
     tracked = {k: v for k, v in prof.items() if v[2] > 0}
     dom = max(tracked, key=lambda k: tracked[k][0])
-    ms, cnt, work = prof[dom]
     pk = peaks()
-    if dom.startswith("gemm"):
-        ach = work / (ms * 1e-3) / 1e12
-        roof = dict(kernel=dom, bound="alu", achieved=ach, peak=FP32_SIMT_TFLOPS, unit="TFLOP/s",
-                    frac=ach / FP32_SIMT_TFLOPS, traffic=None, launches=cnt,
-                    share=ms / sum(v[0] for v in prof.values()),
-                    peak_source="derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz")
-    else:
-        ach = work / (ms * 1e-3) / 1e9
-        roof = dict(kernel=dom, bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
-                    traffic=None, launches=cnt, share=ms / sum(v[0] for v in prof.values()), peak_source=pk["src"])
+    roof = roofline_of(dom, *prof[dom], sum(v[0] for v in prof.values()), pk)
     value = statistics.mean(times)
     e2e_v = statistics.mean(ets)
     if world > 1:

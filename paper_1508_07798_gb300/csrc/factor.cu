@@ -121,6 +121,7 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
     struct Group {
         int off, cnt, reg, kb, rows;
         size_t smem;
+        double flops;   // algorithmic work of the group's panels: 2 hT kb^2 each
     };
     // Large fronts (n >= PANEL_BLOCK_MIN_N) run in blocks of PANEL_BLOCK
     // panels: a panel's row moves and update reach only the columns of its
@@ -205,8 +206,9 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             auto &gs = groups[st];
             if (gs.empty() || gs.back().reg != isreg[f] || (isreg[f] && (gs.back().kb != kb[f] ||
                                                                          cdiv(gs.back().rows, PANEL_NT) != Rf[f])))
-                gs.push_back({(int)jobs.size(), 0, isreg[f], kb[f], Rf[f] * PANEL_NT, 0});
+                gs.push_back({(int)jobs.size(), 0, isreg[f], kb[f], Rf[f] * PANEL_NT, 0, 0.0});
             gs.back().cnt++;
+            gs.back().flops += 2.0 * (double)hT * kbs * kbs;
             gs.back().smem = std::max(gs.back().smem, need);
             int jid = (int)jobs.size();
             jobs.push_back({f, k0, kbs, use_smem, aoff[f], xtotal, mtotal});
@@ -300,10 +302,10 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         for (const Group &g : groups[st]) {
             if (g.reg)
                 rc = launch_gj_panel_reg<T>(d_jobs + g.off, g.cnt, g.kb, g.rows, d_fr, arena, d_x, d_mv, piv, rperm,
-                                            ilist, iperm, status, s);
+                                            ilist, iperm, status, s, g.flops);
             else
                 rc = launch_gj_panel<T>(d_jobs + g.off, g.cnt, g.smem, d_fr, arena, d_x, d_mv, piv, rperm, ilist,
-                                        iperm, status, s);
+                                        iperm, status, s, g.flops);
             if (rc) return rc;
         }
         if ((rc = launch_gj_post<T>(d_ptiles + ptile_off[st], ptile_off[st + 1] - ptile_off[st], d_jobs, d_fr, arena,

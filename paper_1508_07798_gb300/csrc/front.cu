@@ -583,9 +583,10 @@ static cudaError_t launch_reg(const PanelJob *jobs, int njobs, size_t smem, cons
 // instantiation covers (kb, rows).
 template <class T>
 int launch_gj_panel_reg(const PanelJob *jobs, int njobs, int kb, int rows, const FrontDev *fr, T *arena, T *xws,
-                        int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s) {
+                        int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s,
+                        double flops) {
     if (njobs == 0) return HSS_OK;
-    HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s);
+    HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s, flops);
     const int R = cdiv(rows, PANEL_NT);
     const size_t smem = sizeof(int) * 3 * (size_t)rows;
     cudaError_t e = cudaErrorInvalidValue;
@@ -611,7 +612,7 @@ bool panel_reg_fits(int kb, int rows, int tsize) {
 
 template <class T>
 int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws, int *mws,
-                    int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s) {
+                    int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s, double flops) {
     if (njobs == 0) return HSS_OK;
     static bool configured[2] = {false, false};
     int ti = sizeof(T) == 8 ? 0 : 1;
@@ -619,7 +620,7 @@ int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev
         cudaFuncSetAttribute(k_gj_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX);
         configured[ti] = true;
     }
-    HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s);
+    HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s, flops);
     k_gj_panel<T><<<njobs, PANEL_NT, smem, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
     HSS_CHECK_LAUNCH("k_gj_panel");
     return HSS_OK;
@@ -630,13 +631,13 @@ template int launch_scatter_A<double>(const hss_bsr *, const StageElem *, int, i
 template int launch_scatter_A<float>(const hss_bsr *, const StageElem *, int, int *, const FrontDev *, float *,
                                      cudaStream_t);
 template int launch_gj_panel<double>(const PanelJob *, int, size_t, const FrontDev *, double *, double *, int *,
-                                     int *, int *, const int *, int *, int *, cudaStream_t);
+                                     int *, int *, const int *, int *, int *, cudaStream_t, double);
 template int launch_gj_panel<float>(const PanelJob *, int, size_t, const FrontDev *, float *, float *, int *, int *,
-                                    int *, const int *, int *, int *, cudaStream_t);
+                                    int *, const int *, int *, int *, cudaStream_t, double);
 template int launch_gj_panel_reg<double>(const PanelJob *, int, int, int, const FrontDev *, double *, double *,
-                                         int *, int *, int *, const int *, int *, int *, cudaStream_t);
+                                         int *, int *, int *, const int *, int *, int *, cudaStream_t, double);
 template int launch_gj_panel_reg<float>(const PanelJob *, int, int, int, const FrontDev *, float *, float *, int *,
-                                        int *, int *, const int *, int *, int *, cudaStream_t);
+                                        int *, int *, const int *, int *, int *, cudaStream_t, double);
 template int launch_gj_block_post<double>(const BlockTile *, int, const BlockJob *, const PanelJob *,
                                           const FrontDev *, double *, double *, const int *, cudaStream_t);
 template int launch_gj_block_post<float>(const BlockTile *, int, const BlockJob *, const PanelJob *,

@@ -67,10 +67,12 @@ int launch_scatter_A(const hss_bsr *A, const StageElem *se, int nse, int *elem_s
                      cudaStream_t s);
 template <class T>
 int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws, int *mws,
-                    int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s);
+                    int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s,
+                    double flops = 0.0);
 template <class T>
 int launch_gj_panel_reg(const PanelJob *jobs, int njobs, int kb, int rows, const FrontDev *fr, T *arena, T *xws,
-                        int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s);
+                        int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s,
+                        double flops = 0.0);
 bool panel_reg_fits(int kb, int rows, int tsize);
 template <class T>
 int launch_gj_block_post(const BlockTile *tiles, int ntiles, const BlockJob *bjobs, const PanelJob *jobs,
