@@ -177,11 +177,18 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         std::vector<int> act;
         for (int f = 0; f < nf; ++f)
             if (st < nsteps[f]) act.push_back(f);
-        // register panels grouped by (kb, R), then the memory panels
+        // register panels grouped by (kb, rows of this step's variant), then the
+        // memory panels; the variant follows the rows left at this step
+        auto step_rows = [&](int f) {
+            const int hTs = fr[f].ni - st * kb[f];
+            if (hTs <= PANEL_SMALL_NT) return PANEL_SMALL_NT;
+            if (hTs <= 2 * PANEL_SMALL_NT) return 2 * PANEL_SMALL_NT;
+            return cdiv(hTs, PANEL_NT) * PANEL_NT;
+        };
         std::stable_sort(act.begin(), act.end(), [&](int a, int b) {
             if (isreg[a] != isreg[b]) return isreg[a] > isreg[b];
             if (kb[a] != kb[b]) return kb[a] < kb[b];
-            return Rf[a] < Rf[b];
+            return step_rows(a) < step_rows(b);
         });
         for (int f : act) {
             const int n = fr[f].n;
@@ -204,9 +211,9 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
                 if (!use_smem) need = hT * sizeof(int);
             }
             auto &gs = groups[st];
-            if (gs.empty() || gs.back().reg != isreg[f] || (isreg[f] && (gs.back().kb != kb[f] ||
-                                                                         cdiv(gs.back().rows, PANEL_NT) != Rf[f])))
-                gs.push_back({(int)jobs.size(), 0, isreg[f], kb[f], Rf[f] * PANEL_NT, 0, 0.0});
+            if (gs.empty() || gs.back().reg != isreg[f] ||
+                (isreg[f] && (gs.back().kb != kb[f] || gs.back().rows != step_rows(f))))
+                gs.push_back({(int)jobs.size(), 0, isreg[f], kb[f], isreg[f] ? step_rows(f) : Rf[f] * PANEL_NT, 0, 0.0});
             gs.back().cnt++;
             gs.back().flops += 2.0 * (double)hT * kbs * kbs;
             gs.back().smem = std::max(gs.back().smem, need);

@@ -289,15 +289,15 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
 // (row -> position) and posinv[] (position -> row) replay the interchanges of
 // partial pivoting exactly (the search runs over rows not yet pivoted, ties to
 // the lowest position), and every row is written once, to its final position.
-template <class T, int KB, int R>
-__global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__restrict__ jobs,
+template <class T, int KB, int R, int NT>
+__global__ void __launch_bounds__(NT) k_gj_panel_reg(const PanelJob *__restrict__ jobs,
                                                         const FrontDev *__restrict__ fr, T *__restrict__ arena,
                                                         T *__restrict__ xws, int *__restrict__ mws,
                                                         int *__restrict__ piv, int *__restrict__ rperm,
                                                         const int *__restrict__ ilist, int *__restrict__ iperm,
                                                         int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ ArgMax<T> red[PANEL_NT / 32];
+    __shared__ ArgMax<T> red[NT / 32];
     __shared__ T rowj[KB];
     __shared__ int nmv;
     const PanelJob J = jobs[blockIdx.x];
@@ -314,12 +314,12 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__res
     bool done[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-        const int i = threadIdx.x + PANEL_NT * q;
+        const int i = threadIdx.x + NT * q;
         done[q] = false;
 #pragma unroll
         for (int c = 0; c < KB; ++c) reg[q][c] = (i < hT && c < kb) ? M[(k0 + i) + ld * (k0 + c)] : T(0);
     }
-    for (int i = threadIdx.x; i < hT; i += PANEL_NT) {
+    for (int i = threadIdx.x; i < hT; i += NT) {
         pos[i] = i;
         posinv[i] = i;
         rp[i] = k0 == 0 ? i : rglob[k0 + i];
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__res
     ArgMax<T> loc{-1LL, 0x7fffffff};
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-        const int i = threadIdx.x + PANEL_NT * q;
+        const int i = threadIdx.x + NT * q;
         if (i < hT) {
             const long long v = mag_key(reg[q][0]);
             if (v > loc.v || (v == loc.v && i < loc.i)) {
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__res
         const int y = posinv[j];   // row at position j: trades places with the pivot
 #pragma unroll
         for (int q = 0; q < R; ++q)
-            if (threadIdx.x + PANEL_NT * q == x) {
+            if (threadIdx.x + NT * q == x) {
 #pragma unroll
                 for (int c = 0; c < KB; ++c) rowj[c] = reg[q][c];
                 done[q] = true;
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__res
         loc = ArgMax<T>{-1LL, 0x7fffffff};
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            const int i = threadIdx.x + PANEL_NT * q;
+            const int i = threadIdx.x + NT * q;
             if (i >= hT) continue;
             T head;
             if (i == x) {
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__res
     int *mv = mws + J.moff;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-        const int i = threadIdx.x + PANEL_NT * q;
+        const int i = threadIdx.x + NT * q;
         if (i >= hT) continue;
         const int r = pos[i];
 #pragma unroll
@@ -428,11 +428,11 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel_reg(const PanelJob *__res
             mv[1 + 2 * PANEL_KB_MAX + m] = i;
         }
     }
-    for (int i = threadIdx.x; i < hT; i += PANEL_NT) rglob[k0 + i] = rp[i];
+    for (int i = threadIdx.x; i < hT; i += NT) rglob[k0 + i] = rp[i];
     __syncthreads();
     if (threadIdx.x == 0) mv[0] = nmv;
     if (k0 + kb == ni)
-        for (int j = threadIdx.x; j < ni; j += PANEL_NT) {
+        for (int j = threadIdx.x; j < ni; j += NT) {
             int r = j < k0 ? rglob[j] : rp[j - k0];
             iperm[F.iperm_off + j] = ilist[F.iset_off + r];
         }
@@ -566,33 +566,56 @@ int launch_gj_post(const PanelTile *tiles, int ntiles, const PanelJob *jobs, con
     return HSS_OK;
 }
 
-template <class T, int KB, int R>
+template <class T, int KB, int R, int NT>
 static cudaError_t launch_reg(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws,
                               int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status,
                               cudaStream_t s) {
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_gj_panel_reg<T, KB, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX);
+        cudaFuncSetAttribute(k_gj_panel_reg<T, KB, R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PANEL_SMEM_MAX);
         configured = true;
     }
-    k_gj_panel_reg<T, KB, R><<<njobs, PANEL_NT, smem, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
+    k_gj_panel_reg<T, KB, R, NT><<<njobs, NT, smem, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
     return cudaGetLastError();
 }
 
-// Register panel for kb <= KB and rows <= R * PANEL_NT: returns false when no
-// instantiation covers (kb, rows).
+// Register panel for kb <= KB and rows <= R * NT: panels of at most 128 or 256
+// rows run on that many threads (one row each: fewer warps at the per-pivot
+// barriers), larger panels on PANEL_NT threads.
 template <class T>
 int launch_gj_panel_reg(const PanelJob *jobs, int njobs, int kb, int rows, const FrontDev *fr, T *arena, T *xws,
                         int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s,
                         double flops) {
     if (njobs == 0) return HSS_OK;
     HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s, flops);
-    const int R = cdiv(rows, PANEL_NT);
     const size_t smem = sizeof(int) * 3 * (size_t)rows;
     cudaError_t e = cudaErrorInvalidValue;
+    if (rows <= 2 * PANEL_SMALL_NT) {   // one row per thread on 128 or 256 threads
+#define ONE(NT_)                                                                                                   \
+    {                                                                                                              \
+        if (kb <= 8)                                                                                               \
+            e = launch_reg<T, 8, 1, NT_>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm, status, \
+                                         s);                                                                       \
+        else if (kb <= 16)                                                                                         \
+            e = launch_reg<T, 16, 1, NT_>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm,       \
+                                          status, s);                                                              \
+        else                                                                                                       \
+            e = launch_reg<T, 32, 1, NT_>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm,       \
+                                          status, s);                                                              \
+    }
+        if (rows <= PANEL_SMALL_NT)
+            ONE(PANEL_SMALL_NT)
+        else
+            ONE(2 * PANEL_SMALL_NT)
+#undef ONE
+        if (e != cudaSuccess) return cuda_fail(e, "k_gj_panel_reg");
+        return HSS_OK;
+    }
+    const int R = cdiv(rows, PANEL_NT);
 #define REG(KB_, R_)                                                                                              \
-    else if (kb <= KB_ && R <= R_) e = launch_reg<T, KB_, R_>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, \
-                                                              ilist, iperm, status, s);
+    else if (kb <= KB_ && R <= R_) e = launch_reg<T, KB_, R_, PANEL_NT>(jobs, njobs, smem, fr, arena, xws, mws, piv, \
+                                                                        rperm, ilist, iperm, status, s);
     if (false) {
     }
     REG(8, 1) REG(16, 1) REG(32, 1) REG(8, 2) REG(16, 2) REG(32, 2) REG(8, 3) REG(16, 3)

@@ -5,6 +5,7 @@
 namespace hssnd {
 
 constexpr int PANEL_NT = 512;
+constexpr int PANEL_SMALL_NT = 128;   // register panels of at most this many rows
 constexpr int PANEL_KB_MAX = 32;
 constexpr int PANEL_SMEM_MAX = 200 * 1024;
 
