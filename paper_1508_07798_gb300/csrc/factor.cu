@@ -727,6 +727,14 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         if ((rc = F->keep.alloc(sizeof(T) * std::max(ks, 1L)))) return rc;
     }
     T *keep = F->keep.as<T>();
+    // zero-pivot flags of every front of every stage and of the top blocks,
+    // read once at the end of the call
+    size_t nstat = (size_t)ninst;
+    for (const auto &st : t->stages) nstat += st.size();
+    ScratchPtr d_status_all;
+    if ((rc = WL.dalloc_bytes(sizeof(int) * std::max(nstat, (size_t)1), &d_status_all.p))) return rc;
+    HSS_CUDA(cudaMemsetAsync(d_status_all.p, 0, sizeof(int) * std::max(nstat, (size_t)1), s));
+    std::vector<int> status_box;   // box id per flag (-1 - i: top block of instance i)
     Work W(s);
     HSS_CUDA(cudaMemsetAsync(d_tcerr.p, 0, sizeof(int), s));
     Engine eng;
@@ -794,13 +802,13 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             F->front_flops += 2.0 / 3.0 * ni * ni * ni + 2.0 * ni * ni * nb + 2.0 * nb * nb * ni;
             F->factor_bytes += sizeof(T) * (ni * (ni + nb) + ni * nb);
         }
-        W.reset();   // the stream is idle: the previous stage ended with a readback
+        W.reset_device();
         ScratchPtr d_fr;
-        int *d_status;
+        int *d_status = d_status_all.as<int>() + status_box.size();
+        for (int b : boxes) status_box.push_back(b);
         FrontDev *d_frp;
-        if ((rc = W.up(fr, &d_frp)) || (rc = W.dalloc(fr.size(), &d_status))) return rc;
+        if ((rc = W.up(fr, &d_frp))) return rc;
         d_fr.p = d_frp;
-        HSS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int) * fr.size(), s));
         if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
             return rc;
         if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
@@ -817,15 +825,6 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         if ((rc = compress_stage<T>(t, o, fr, boxes, poff, pn, keeph, arena, keep, d_status, (int)fr.size(), F->log,
                                     F, eng, W, s)))
             return rc;
-        std::vector<int> hst(fr.size());
-        HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status, sizeof(int) * fr.size(), cudaMemcpyDeviceToHost, s));
-        HSS_CUDA(cudaStreamSynchronize(s));
-        for (size_t f = 0; f < fr.size(); ++f)
-            if (hst[f]) {
-                set_error("hss_factor: zero pivot in the front of box " + std::to_string(boxes[f]));
-                return HSS_ESINGULAR;
-            }
-        if ((rc = check_tc())) return rc;
         F->apply.emplace_back();
         if ((rc = build_apply_stage<T>(F->apply.back(), fr, false, part_total, tk_total))) return rc;
     }
@@ -850,28 +849,33 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             sides[i].assign(ntop_i[i] / t->bs, 1);
             for (int q = 0; q < t->nb[t->inst_top[i]] / t->bs; ++q) sides[i][q] = 0;
         }
-        W.reset();
+        W.reset_device();
         ScratchPtr d_fr;
-        int *d_status;
+        int *d_status = d_status_all.as<int>() + status_box.size();
+        for (int i = 0; i < ninst; ++i) status_box.push_back(-1 - i);
         FrontDev *d_frp;
-        if ((rc = W.up(fr, &d_frp)) || (rc = W.dalloc(ninst, &d_status))) return rc;
+        if ((rc = W.up(fr, &d_frp))) return rc;
         d_fr.p = d_frp;
-        HSS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int) * ninst, s));
         if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
             return rc;
         if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
                                      F->d_topset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, eng, W, s)))
             return rc;
-        std::vector<int> hst(ninst);
-        HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status, sizeof(int) * ninst, cudaMemcpyDeviceToHost, s));
+        std::vector<int> hst(status_box.size());
+        HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status_all.p, sizeof(int) * hst.size(), cudaMemcpyDeviceToHost, s));
         HSS_CUDA(cudaStreamSynchronize(s));
-        for (int i = 0; i < ninst; ++i)
-            if (hst[i]) {
-                set_error(ninst == 1 ? std::string("hss_factor: zero pivot in the top block")
-                                     : "hss_factor: zero pivot in the top block of instance " + std::to_string(i));
+        for (size_t q = 0; q < hst.size(); ++q)
+            if (hst[q]) {
+                const int b = status_box[q];
+                if (b >= 0)
+                    set_error("hss_factor: zero pivot in the front of box " + std::to_string(b));
+                else
+                    set_error(ninst == 1 ? std::string("hss_factor: zero pivot in the top block")
+                                         : "hss_factor: zero pivot in the top block of instance " +
+                                               std::to_string(-1 - b));
                 return HSS_ESINGULAR;
             }
-        if ((rc = check_tc())) return rc;
+        if (eng.tc && (rc = check_tc())) return rc;
         for (int i = 0; i < ninst; ++i) {
             F->front_flops += 2.0 / 3.0 * (double)ntop_i[i] * ntop_i[i] * ntop_i[i];
             F->factor_bytes += sizeof(T) * (double)ntop_i[i] * ntop_i[i];

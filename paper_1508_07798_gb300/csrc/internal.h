@@ -101,6 +101,13 @@ struct Work {
         return rc;
     }
     void reset();   // the stream must be idle
+    // restart the device bump pointer only: later uploads and kernels on the
+    // same stream are ordered after the work that used the memory, and the
+    // pinned staging keeps growing (its pending copies are not overwritten)
+    void reset_device() {
+        ci = 0;
+        cur = 0;
+    }
 };
 
 // A pointer into call scratch with the same accessor as DevBuf.
