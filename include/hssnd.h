@@ -239,9 +239,11 @@ int hss_spmv(const hss_bsr *A, int nrhs, const double *x, int ldx, double *y, in
  * (column-major; x holds x0 on entry and the iterate on exit).  FP64 Arnoldi
  * with classical Gram-Schmidt applied twice, Givens rotations on the device;
  * stops when the true FP64 residual, recomputed at every restart, is
- * <= rtol ||b||.  Synchronizes once per Arnoldi step and fills *stats (HOST,
- * may be NULL).  Returns HSS_ENOCONV when some right-hand side did not reach
- * rtol within maxit steps. */
+ * <= rtol ||b||.  With several right-hand sides their Krylov processes
+ * advance in lock step (one multi-vector apply and SpMV per Arnoldi step;
+ * a process that has stopped is masked).  Synchronizes once per Arnoldi step
+ * and fills *stats (HOST, may be NULL).  Returns HSS_ENOCONV when some
+ * right-hand side did not reach rtol within maxit steps. */
 int fgmres_solve(const hss_bsr *A, const hss_factor_t *f, int nrhs, const double *b, int ldb,
                  double *x, int ldx, const fgmres_opts *opts, fgmres_stats *stats, void *stream);
 

@@ -221,24 +221,23 @@ __global__ void k_bupdate_x(const double *__restrict__ Z, long ldz, long zstride
 
 using namespace hssnd;
 
-extern "C" int fgmres_solve_batched(const hss_factor_t *f, int nrhs, const double *b, int ldb, double *x, int ldx,
-                                    const fgmres_opts *opts, fgmres_stats *stats, void *stream) {
-    fgmres_opts o;
-    fgmres_opts_default(&o);
-    if (opts) o = *opts;
-    const long N = f ? f->ndof : 0;
-    if (!f || !f->batched || !b || !x || nrhs < 0 || ldb < N || ldx < N || o.restart < 1 ||
-        o.restart > BK_MAXM - 1 || o.maxit < 0) {
-        set_error("fgmres_solve_batched: invalid argument (needs a factor from hss_factor_batched; restart in [1, 31])");
-        return HSS_EINVAL;
-    }
-    const hss_tree *t = f->tree;
-    const int ninst = t->ninst, m = o.restart;
+namespace hssnd {
+
+// The lock-step solver: one Krylov process per (instance, right-hand side),
+// instance i owning rows [inst_dof[i], inst_dof[i + 1]) of the block vectors.
+// A is the (block-diagonal) matrix of all instances, f its preconditioner
+// (NULL: none), stats one entry per instance, hist (optional) one residual
+// history per process.
+int fgmres_lockstep(const hss_bsr *A, const hss_factor_t *f, const std::vector<int> &inst_dof, int nrhs,
+                    const double *b, int ldb, double *x, int ldx, const fgmres_opts &o, fgmres_stats *stats,
+                    std::vector<std::vector<double>> *hist, cudaStream_t s) {
+    const int ninst = (int)inst_dof.size() - 1, m = o.restart;
+    const long N = inst_dof.back();
     const int P = ninst * nrhs;
     if (stats)
         for (int i = 0; i < ninst; ++i) stats[i] = fgmres_stats{0, 0, 0.0, 1};
+    if (hist) hist->assign(P, {});
     if (P == 0 || N == 0) return HSS_OK;
-    cudaStream_t s = (cudaStream_t)stream;
 
     // processes (column-major over instances) and their row chunks
     std::vector<BProc> pr(P);
@@ -246,7 +245,7 @@ extern "C" int fgmres_solve_batched(const hss_factor_t *f, int nrhs, const doubl
     for (int c = 0; c < nrhs; ++c)
         for (int i = 0; i < ninst; ++i) {
             const int p = c * ninst + i;
-            const int r0 = t->inst_dof[i], len = t->inst_dof[i + 1] - r0;
+            const int r0 = inst_dof[i], len = inst_dof[i + 1] - r0;
             pr[p] = BProc{c, r0, len, (int)ch.size(), 0};
             for (int q = 0; q < len; q += BK_CHUNK) ch.push_back(BChunk{p, c, r0 + q, std::min(BK_CHUNK, len - q)});
             pr[p].c1 = (int)ch.size();
@@ -319,7 +318,7 @@ extern "C" int fgmres_solve_batched(const hss_factor_t *f, int nrhs, const doubl
         for (int p = 0; p < P; ++p) nact += (act_h[p] = !done[p]);
         if (nact == 0) break;
         // r = b - A x, beta = ||r||
-        if ((rc = push_act()) || (rc = spmv(&f->bA, nrhs, x, ldx, dr, N, s))) return rc;
+        if ((rc = push_act()) || (rc = spmv(A, nrhs, x, ldx, dr, N, s))) return rc;
         { HSS_PROF("bresid", s); k_bresid<<<nch, BK_NT, 0, s>>>(b, ldb, dr, N, dch, dact); }
         if ((rc = dots(dr, N, 0, 1, dr, N, dsc + 2, 8, 0))) return rc;
         { HSS_PROF("bsqrt", s); k_bsqrt<<<pb, 128, 0, s>>>(dsc + 2, 8, dsc + 3, 8, P, dact); }
@@ -341,7 +340,12 @@ extern "C" int fgmres_solve_batched(const hss_factor_t *f, int nrhs, const doubl
         for (int j = 0; j < m; ++j) {
             const double *Vj = dV + NB * j;
             double *Zj = dZ + NB * j;
-            if ((rc = apply_factor(f, nrhs, Vj, N, Zj, N, s)) || (rc = spmv(&f->bA, nrhs, Zj, N, dw, N, s))) return rc;
+            if (f) {
+                if ((rc = apply_factor(f, nrhs, Vj, N, Zj, N, s))) return rc;
+            } else {
+                HSS_CUDA(cudaMemcpyAsync(Zj, Vj, sizeof(double) * NB, cudaMemcpyDeviceToDevice, s));
+            }
+            if ((rc = spmv(A, nrhs, Zj, N, dw, N, s))) return rc;
             double *hcol = dH + (long)(m + 1) * j;
             // classical Gram-Schmidt, twice; the second pass's coefficients are added to the column
             if ((rc = dots(dV, N, NB, j + 1, dw, N, hcol, hst, 0))) return rc;
@@ -363,6 +367,7 @@ extern "C" int fgmres_solve_batched(const hss_factor_t *f, int nrhs, const doubl
                 ++iters[p];
                 jend_h[p] = j + 1;
                 const double e = eh[p] / bnorm[p];
+                if (hist) (*hist)[p].push_back(e);
                 if (e <= o.rtol || iters[p] >= o.maxit || !(e == e)) {
                     act_h[p] = 0;
                     changed = true;
@@ -390,4 +395,21 @@ extern "C" int fgmres_solve_batched(const hss_factor_t *f, int nrhs, const doubl
         all = all && conv[p];
     }
     return all ? HSS_OK : HSS_ENOCONV;
+}
+
+}  // namespace hssnd
+
+extern "C" int fgmres_solve_batched(const hss_factor_t *f, int nrhs, const double *b, int ldb, double *x, int ldx,
+                                    const fgmres_opts *opts, fgmres_stats *stats, void *stream) {
+    fgmres_opts o;
+    fgmres_opts_default(&o);
+    if (opts) o = *opts;
+    const long N = f ? f->ndof : 0;
+    if (!f || !f->batched || !b || !x || nrhs < 0 || ldb < N || ldx < N || o.restart < 1 ||
+        o.restart > BK_MAXM - 1 || o.maxit < 0) {
+        set_error("fgmres_solve_batched: invalid argument (needs a factor from hss_factor_batched; restart in [1, 31])");
+        return HSS_EINVAL;
+    }
+    return fgmres_lockstep(&f->bA, f, f->tree->inst_dof, nrhs, b, ldb, x, ldx, o, stats, nullptr,
+                           (cudaStream_t)stream);
 }

@@ -55,6 +55,9 @@ struct FrontLog {   // per-front record (rank logging, Sec. 5 empirical cost)
 
 int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);
 int spmv(const hss_bsr *A, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);
+int fgmres_lockstep(const hss_bsr *A, const hss_factor_t *f, const std::vector<int> &inst_dof, int nrhs,
+                    const double *b, int ldb, double *x, int ldx, const fgmres_opts &o, fgmres_stats *stats,
+                    std::vector<std::vector<double>> *hist, cudaStream_t s);
 
 }  // namespace hssnd
 

@@ -354,6 +354,15 @@ extern "C" int fgmres_solve(const hss_bsr *A, const hss_factor_t *f, int nrhs, c
         return HSS_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    if (nrhs > 1) {
+        // several right-hand sides: independent Krylov processes in lock step,
+        // one multi-vector apply and SpMV per Arnoldi step
+        fgmres_stats st{0, 0, 0.0, 1};
+        int rc = fgmres_lockstep(A, f, std::vector<int>{0, (int)N}, nrhs, b, ldb, x, ldx, o, &st, &g_hist, s);
+        if (rc != HSS_OK && rc != HSS_ENOCONV) return rc;
+        if (stats) *stats = st;
+        return st.converged ? HSS_OK : HSS_ENOCONV;
+    }
     Work W(s);
     Krylov K;
     int rc;
