@@ -229,23 +229,67 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
         const T vn = (x0 - alpha) * (x0 - alpha) + (nn2 - x0 * x0);
         for (int i = j + threadIdx.x; i < r; i += ID_NT) v[i] = (i == j) ? x0 - alpha : A[i + (long)lda * j];
         __syncthreads();
+        // FP32: two columns per warp iteration (c and c + ID_NT / 32): their
+        // reductions are independent, so their shuffle chains overlap (FP64
+        // keeps one column per iteration: the pair spills registers)
         AM<T> wbest{-1LL, INT_MAX};
-        for (int c = j + 1 + w; c < m; c += ID_NT / 32) {
-            T d = 0;
-            for (int i = j + lane; i < r; i += 32) d += v[i] * A[i + (long)lda * c];
-            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            const T coef = vn > T(0) ? T(2) * d / vn : T(0);
-            T sq = 0;
-            for (int i = j + lane; i < r; i += 32) {
-                T a = A[i + (long)lda * c] - coef * v[i];
-                A[i + (long)lda * c] = a;
-                if (i > j) sq += a * a;
+        constexpr int NW = ID_NT / 32;
+        auto track = [&](int c, T sq) {
+            nrm2[c] = sq;
+            const long long kc = nn_key(sq);
+            if (kc > wbest.v || (kc == wbest.v && c < wbest.i)) wbest = AM<T>{kc, c};
+        };
+        if constexpr (sizeof(T) == 4) {
+            for (int c = j + 1 + w; c < m; c += 2 * NW) {
+                const int c2 = c + NW;
+                const bool two = c2 < m;
+                T *A1 = A + (long)lda * c;
+                T *A2 = A + (long)lda * (two ? c2 : c);
+                T d1 = 0, d2 = 0;
+                for (int i = j + lane; i < r; i += 32) {
+                    d1 += v[i] * A1[i];
+                    d2 += v[i] * A2[i];
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+                    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+                }
+                const T coef1 = vn > T(0) ? T(2) * d1 / vn : T(0);
+                const T coef2 = vn > T(0) ? T(2) * d2 / vn : T(0);
+                T sq1 = 0, sq2 = 0;
+                for (int i = j + lane; i < r; i += 32) {
+                    const T a1 = A1[i] - coef1 * v[i];
+                    A1[i] = a1;
+                    if (i > j) sq1 += a1 * a1;
+                    if (two) {
+                        const T a2 = A2[i] - coef2 * v[i];
+                        A2[i] = a2;
+                        if (i > j) sq2 += a2 * a2;
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    sq1 += __shfl_xor_sync(0xffffffffu, sq1, o);
+                    sq2 += __shfl_xor_sync(0xffffffffu, sq2, o);
+                }
+                if (lane == 0) {
+                    track(c, sq1);
+                    if (two) track(c2, sq2);
+                }
             }
-            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if (lane == 0) {
-                nrm2[c] = sq;
-                const long long kc = nn_key(sq);
-                if (kc > wbest.v || (kc == wbest.v && c < wbest.i)) wbest = AM<T>{kc, c};
+        } else {
+            for (int c = j + 1 + w; c < m; c += NW) {
+                T d = 0;
+                for (int i = j + lane; i < r; i += 32) d += v[i] * A[i + (long)lda * c];
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                const T coef = vn > T(0) ? T(2) * d / vn : T(0);
+                T sq = 0;
+                for (int i = j + lane; i < r; i += 32) {
+                    T a = A[i + (long)lda * c] - coef * v[i];
+                    A[i + (long)lda * c] = a;
+                    if (i > j) sq += a * a;
+                }
+                for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                if (lane == 0) track(c, sq);
             }
         }
         if (lane == 0) cand[w] = wbest;
