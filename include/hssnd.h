@@ -94,7 +94,14 @@ typedef struct hss_factor_opts {
     const int *r_init;      /* HOST array of one initial sample width per box (NULL, the default: r0 for
                                every front), e.g. from hss_rank_model_predict; the adaptive growth by dr
                                still applies whenever a rank exceeds r - oversample */
+    int cap_policy;         /* a front whose rank still exceeds r - oversample when r + dr > rmax stops the
+                               growth: HSS_CAP_KEEP (default) keeps S itself (Theorem 1's bound needs k + p
+                               samples); HSS_CAP_ACCEPT keeps the approximant built from the r samples it
+                               has (ranks up to r, no error bound) -- with r0 = rmax = l this is the fixed
+                               anticipated rank l of the experiments of Sec. 5 */
 } hss_factor_opts;
+
+enum { HSS_CAP_KEEP = 0, HSS_CAP_ACCEPT = 1 };
 
 typedef struct fgmres_opts {
     int restart;            /* default 30 */

@@ -54,9 +54,13 @@ def box_schur(A_csr, nd, b):
 
 
 def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=10, rmax=None,
-           keep_h=False):
+           keep_h=False, cap="keep"):
     """Returns a dict with the per-box factors, the top block LU and logs.
-    rmax caps the HSS sample width; keep_h stores each approximant H."""
+    rmax caps the HSS sample width; cap is the policy for a front whose ranks
+    outgrow the cap ("keep": H = S; "accept": the approximant from the samples
+    it has, see hss.py); keep_h stores each approximant H."""
+    if cap not in ("keep", "accept"):
+        raise ValueError("cap policy: 'keep' or 'accept'")
     A = A_csr.tocsr()
     boxes = {}
     H = {}
@@ -88,7 +92,8 @@ def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=
         rec = dict(box=b, level=int(nd["level"][b]), ni=ni, nb=B.size)
         if compress and B.size > 0:
             nodes = hss_tree_for_front(nd, b)
-            Hs, rep = hss_compress(S, nodes, tol, seed, b, r0=r0, dr=dr, oversample=oversample, rmax=rmax)
+            Hs, rep = hss_compress(S, nodes, tol, seed, b, r0=r0, dr=dr, oversample=oversample, rmax=rmax,
+                                   cap=cap)
             rec.update(r=rep["r"], rounds=rep["rounds"], capped=rep.get("capped", False),
                        kmax=max(list(rep["krow"].values()) + list(rep["kcol"].values()) + [0]),
                        nnodes=len(nodes), rep=rep)

@@ -29,7 +29,11 @@ Readings where the paper is silent:
   * the ID tolerance is relative per ID (see idecomp.py);
   * when the cap rmax stops the growth while some rank still exceeds r - 10,
     Theorem 1's error bound (which needs k + p samples) does not apply, and
-    the front keeps S itself (H = S, rep["capped"] = True).
+    the front keeps S itself (H = S, rep["capped"] = True) under the default
+    cap policy "keep"; under the policy "accept" it keeps the approximant
+    built from the r samples it has (ranks up to r, no error bound), which is
+    the fixed anticipated rank l of the paper's experiments (Sec. 5: l chosen
+    beforehand, the preconditioner judged by the GMRES iterations).
 The approximant is returned expanded to a dense matrix H (the parent front is
 built from H, eq. (32)), together with the representation and its ranks.
 """
@@ -79,11 +83,14 @@ def hss_tree_for_front(nd, box):
     return nodes
 
 
-def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rmax=None):
+def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rmax=None, cap="keep"):
     """Randomized HSS approximant of S.  Returns (H, rep) with H dense.
 
     rmax (optional) caps the sample width: growth stops once r + dr > rmax,
-    and a front whose ranks still need more samples then returns H = S."""
+    and a front whose ranks still need more samples then returns H = S
+    (cap="keep") or the approximant from the r samples (cap="accept")."""
+    if cap not in ("keep", "accept"):
+        raise ValueError("cap policy: 'keep' or 'accept'")
     S = np.asarray(S, dtype=np.float64)
     n = S.shape[0]
     root = len(nodes) - 1
@@ -129,7 +136,7 @@ def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rma
             r += dr
             continue
         break
-    if short_of_samples:
+    if short_of_samples and cap == "keep":
         return S.copy(), dict(r=r, rounds=rounds, nodes=nodes, capped=True,
                               krow={t: st[t]["U"].shape[1] for t in order},
                               kcol={t: st[t]["V"].shape[1] for t in order},
@@ -157,7 +164,7 @@ def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rma
             Rb = slice(nodes[b]["lo"], nodes[b]["hi"])
             H[Ra, Rb] = Ut[a] @ S[np.ix_(st[a]["J"], st[b]["K"])] @ Vt[b].T
             H[Rb, Ra] = Ut[b] @ S[np.ix_(st[b]["J"], st[a]["K"])] @ Vt[a].T
-    rep = dict(r=r, rounds=rounds, nodes=nodes, capped=False,
+    rep = dict(r=r, rounds=rounds, nodes=nodes, capped=bool(short_of_samples), truncated=bool(short_of_samples),
                krow={t: st[t]["U"].shape[1] for t in order},
                kcol={t: st[t]["V"].shape[1] for t in order},
                J={t: st[t]["J"] for t in order}, K={t: st[t]["K"] for t in order},

@@ -207,6 +207,8 @@ void hss_factor_opts_default(hss_factor_opts *o) {
     o->seed = 0;
     o->keep_schur = 0;
     o->tensor_cores = 0;
+    o->r_init = nullptr;
+    o->cap_policy = HSS_CAP_KEEP;
 }
 
 void fgmres_opts_default(fgmres_opts *o) {

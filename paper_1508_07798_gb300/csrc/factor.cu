@@ -552,7 +552,9 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         // ---- decide: fronts whose rank reached r - oversample sample again, wider
         // A front whose rank still needs more samples when the cap rmax stops
         // the growth has no oversampling margin left: Theorem 1's error bound
-        // (l = k + p samples) does not hold, so it keeps S itself (H = S).
+        // (l = k + p samples) does not hold, so it keeps S itself (H = S), or,
+        // under HSS_CAP_ACCEPT, the approximant from the r samples it has (the
+        // IDs already allow ranks up to r).
         std::vector<RoundFront> next;
         std::vector<char> done(nc, 0), dense(nc, 0);
         for (int c = 0; c < nc; ++c) {
@@ -565,7 +567,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
                 next.push_back({f, r + o.dr});
             } else {
                 done[c] = 1;
-                dense[c] = short_of_samples;
+                dense[c] = short_of_samples && o.cap_policy == HSS_CAP_KEEP;
                 capped[f] = short_of_samples;
             }
         }
@@ -932,7 +934,8 @@ __global__ void k_shift_index(const int *__restrict__ src, int n, int add, int *
 
 static int check_factor_opts(const hss_factor_opts &o, const char *who) {
     if (!(o.tol >= 0) || o.r0 < 1 || o.dr < 1 || o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 ||
-        (o.precision != HSS_FP64 && o.precision != HSS_FP32)) {
+        (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
+        (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT)) {
         set_error(std::string(who) + ": options out of range (rmax <= 128)");
         return HSS_EINVAL;
     }
@@ -1036,7 +1039,8 @@ extern "C" int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_fact
     hss_factor_opts_default(&o);
     if (opts) o = *opts;
     if (A->nb != tree->nelem || A->bs != tree->bs || !A->val || !(o.tol >= 0) || o.r0 < 1 || o.dr < 1 ||
-        o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 || (o.precision != HSS_FP64 && o.precision != HSS_FP32)) {
+        o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 || (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
+        (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT)) {
         set_error("hss_factor: invalid argument (matrix/tree mismatch or options out of range; rmax <= 128)");
         return HSS_EINVAL;
     }

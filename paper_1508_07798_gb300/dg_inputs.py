@@ -10,9 +10,11 @@ Discretisation (paper Sec. 5 uses interior-penalty DG on the unit square; the
 operators below are the ones of Sec. 5, on uniform quadrilateral/hexahedral
 grids with an orthonormal tensor-Legendre basis per element):
 
-    -div(a grad u) - kappa^2 c(x) u = f  in (0,1)^d,   u = 0 on the boundary,
+    -div(a K grad u) - kappa^2 c(x) u + r u = f  in (0,1)^d,   u = 0 on the boundary,
 
-symmetric interior penalty with penalty sigma_e = 10 p^2 / h * max(a-, a+),
+K = diag(s_x, s_y[, s_z]) a constant axis-aligned diffusion tensor (identity
+unless given; the anisotropic reaction-diffusion problem, eq. (60)), symmetric
+interior penalty with penalty sigma_e = 10 p^2 / h * max(a-, a+) * (n.K.n),
 (p+2)-point Gauss rules, element-wise constant a and c.  Element e has the
 lexicographic index e = ix + nx*(iy + ny*iz); its local dof l = a + (p+1)*b
 (+ (p+1)^2 * c in 3D) belongs to the basis function L_a(xi) L_b(eta) [L_c(zeta)];
@@ -31,7 +33,8 @@ import numpy as np
 
 __all__ = [
     "Mesh", "BSR", "assemble_sipg", "poisson_2d", "helmholtz_2d", "diffusion_3d",
-    "helmholtz_kappa", "bsr_to_csr", "bsr_to_dense", "random_rhs", "point_source_rhs",
+    "reaction_diffusion_2d", "density_helmholtz_2d", "enclosure_density", "helmholtz_kappa",
+    "bsr_to_csr", "bsr_to_dense", "random_rhs", "point_source_rhs",
     "splitmix64",
 ]
 
@@ -125,11 +128,15 @@ def _kron_axes(mats):
 
 
 def assemble_sipg(mesh: Mesh, a_elem=None, c_elem=None, kappa: float = 0.0,
-                  penalty: float = 10.0) -> BSR:
-    """Assemble the SIPG matrix of -div(a grad u) - kappa^2 c u on (0,1)^d.
+                  penalty: float = 10.0, diff_axes=None, reaction: float = 0.0) -> BSR:
+    """Assemble the SIPG matrix of -div(a K grad u) - kappa^2 c u + reaction u on (0,1)^d.
 
-    a_elem, c_elem: per-element constants (default 1).  Dirichlet u=0 on all
-    boundary faces, imposed weakly by one-sided fluxes.
+    a_elem, c_elem: per-element constants (default 1).  diff_axes: the
+    diagonal of K, one factor per axis (default all 1).  K scales the axis-k
+    stiffness and every term of the faces normal to axis k (flux, symmetry
+    and penalty, since n.K.n = K_kk there), so the matrix is linear in K when
+    kappa = reaction = 0.  Dirichlet u=0 on all boundary faces, imposed weakly
+    by one-sided fluxes.
     """
     d, p = mesh.dim, mesh.p
     n = tuple(int(v) for v in mesh.n[:d])
@@ -141,17 +148,21 @@ def assemble_sipg(mesh: Mesh, a_elem=None, c_elem=None, kappa: float = 0.0,
     M1, K1 = lg["M1"], lg["K1"]
     a_elem = np.ones(ne) if a_elem is None else np.asarray(a_elem, dtype=np.float64)
     c_elem = np.ones(ne) if c_elem is None else np.asarray(c_elem, dtype=np.float64)
+    kdiag = np.ones(d) if diff_axes is None else np.asarray(diff_axes, dtype=np.float64)
+    if kdiag.shape != (d,) or (kdiag < 0).any():
+        raise ValueError("diff_axes: one non-negative factor per axis")
     vol = float(np.prod(h))
 
     # volume: stiffness per axis and mass
     stiff = np.zeros((bs, bs))
     for k in range(d):
         mats = [K1 if j == k else M1 for j in range(d)]
-        scale = vol * (2.0 / h[k]) ** 2 / 2.0 ** d
+        scale = kdiag[k] * vol * (2.0 / h[k]) ** 2 / 2.0 ** d
         stiff += scale * _kron_axes(mats)
     mass = (vol / 2.0 ** d) * _kron_axes([M1] * d)
 
-    diag = a_elem[:, None, None] * stiff[None] - (kappa ** 2) * c_elem[:, None, None] * mass[None]
+    diag = (a_elem[:, None, None] * stiff[None] - (kappa ** 2) * c_elem[:, None, None] * mass[None]
+            + reaction * mass[None])
 
     idx = np.arange(ne).reshape(tuple(reversed(n)))  # idx[iz][iy][ix]
 
@@ -164,7 +175,7 @@ def assemble_sipg(mesh: Mesh, a_elem=None, c_elem=None, kappa: float = 0.0,
     orow, ocol, oblk = [], [], []
     idx3 = idx.reshape((1,) * (3 - d) + idx.shape)
     for k in range(d):
-        fscale = vol / h[k] / 2.0 ** (d - 1)   # face measure / reference face measure
+        fscale = kdiag[k] * vol / h[k] / 2.0 ** (d - 1)   # K_kk * face measure / reference face measure
         g = 2.0 / h[k]
         ax = 2 - k                              # axis k inside idx3 (z, y, x order)
 
@@ -223,7 +234,8 @@ def assemble_sipg(mesh: Mesh, a_elem=None, c_elem=None, kappa: float = 0.0,
     row_ptr = np.cumsum(row_ptr).astype(np.int32)
     return BSR(nb=ne, bs=bs, row_ptr=row_ptr, col_idx=ecol.astype(np.int32),
                val=np.ascontiguousarray(eblk, dtype=np.float64),
-               meta=dict(dim=d, n=n, p=p, kappa=kappa))
+               meta=dict(dim=d, n=n, p=p, kappa=kappa, diff_axes=tuple(float(v) for v in kdiag),
+                         reaction=reaction))
 
 
 # --------------------------------------------------------------------------
@@ -287,6 +299,45 @@ def diffusion_3d(n: int, p: int, seed: int) -> tuple:
     a = gaussian_log_field(mesh, seed)
     A = assemble_sipg(mesh, a_elem=a)
     A.meta.update(contrast=float(a.max() / a.min()))
+    return mesh, A
+
+
+def reaction_diffusion_2d(n: int, p: int, a0: float, c0: float) -> tuple:
+    """Constant-coefficient anisotropic reaction-diffusion, eq. (60) divided by
+    a_11: -u_xx - a0 u_yy + c0 u = f0 (a0 = a_22/a_11, c0 = c/a_11), with
+    a0 << 1 making the x direction the strongly coupled one (Sec. 5)."""
+    mesh = Mesh(2, (n, n, 1), p)
+    A = assemble_sipg(mesh, diff_axes=(1.0, a0), reaction=c0)
+    A.meta.update(a0=a0, c0=c0)
+    return mesh, A
+
+
+def enclosure_density(mesh: Mesh, rho_d: float, rho_0: float = 1.0, box=(0.25, 0.75, 0.25, 0.75),
+                      wall: float = 1.0 / 16) -> np.ndarray:
+    """Element-wise density of the high-contrast Helmholtz problem (Sec. 5): a
+    rectangular enclosure D -- the walls, of thickness `wall`, of the
+    rectangle [x0, x1] x [y0, y1] given by `box` -- has density rho_d, the
+    rest of the unit square rho_0.  An element belongs to D when its centre
+    does (at least one element across each wall)."""
+    x0, x1, y0, y1 = box
+    cen = _elem_centres(mesh)
+    x, y = cen[:, 0], cen[:, 1]
+    hx, hy = 1.0 / mesh.n[0], 1.0 / mesh.n[1]
+    tx, ty = max(wall, hx), max(wall, hy)
+    inside_outer = (x > x0) & (x < x1) & (y > y0) & (y < y1)
+    inside_inner = (x > x0 + tx) & (x < x1 - tx) & (y > y0 + ty) & (y < y1 - ty)
+    return np.where(inside_outer & ~inside_inner, rho_d, rho_0)
+
+
+def density_helmholtz_2d(n: int, p: int, rho_ratio: float = 1e3, kappa: float | None = None) -> tuple:
+    """-div(rho^-1 grad u) - kappa^2 u = f with the piecewise-constant density
+    of `enclosure_density` (rho_0 = 1, rho_d = rho_ratio); kappa defaults to
+    the same 10 dofs per wavelength as `helmholtz_2d` (with respect to rho_0)."""
+    mesh = Mesh(2, (n, n, 1), p)
+    kap = helmholtz_kappa(n, p) if kappa is None else kappa
+    rho = enclosure_density(mesh, rho_ratio)
+    A = assemble_sipg(mesh, a_elem=1.0 / rho, kappa=kap)
+    A.meta.update(rho_ratio=rho_ratio, wall_elems=int((rho != 1.0).sum()))
     return mesh, A
 
 

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libhssnd.so")
 HSS_OK, HSS_EINVAL, HSS_ENOMEM, HSS_ESINGULAR, HSS_ENOCONV, HSS_ETIMEOUT, HSS_ECUDA = range(7)
 SCHEMES = {"box": 0, "hslab": 1, "vslab": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1}
+CAP_POLICIES = {"keep": 0, "accept": 1}
 
 EXPORTED = [
     "hss_nd_opts_default", "hss_factor_opts_default", "fgmres_opts_default",
@@ -56,7 +57,8 @@ class hss_nd_opts(C.Structure):
 class hss_factor_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("compress", C.c_int), ("r0", C.c_int), ("dr", C.c_int),
                 ("rmax", C.c_int), ("oversample", C.c_int), ("precision", C.c_int),
-                ("seed", C.c_uint64), ("keep_schur", C.c_int), ("tensor_cores", C.c_int), ("r_init", C.c_void_p)]
+                ("seed", C.c_uint64), ("keep_schur", C.c_int), ("tensor_cores", C.c_int), ("r_init", C.c_void_p),
+                ("cap_policy", C.c_int)]
 
 
 class fgmres_opts(C.Structure):
@@ -268,6 +270,8 @@ def factor_opts(**kw) -> hss_factor_opts:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "cap_policy" and isinstance(v, str):
+            v = CAP_POLICIES[v]
         setattr(o, k, v)
     return o
 

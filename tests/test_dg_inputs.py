@@ -85,3 +85,94 @@ def test_diffusion_3d_contrast():
     assert A.meta["contrast"] > 10.0
     D = dg.bsr_to_dense(A)
     np.linalg.cholesky(0.5 * (D + D.T))
+
+
+# --- anisotropic reaction-diffusion (eq. (60)) and the high-contrast density Helmholtz problem
+
+def test_axis_factors_enter_linearly_and_default_is_poisson():
+    """Every stiffness, flux, symmetry and penalty term of the faces normal to
+    axis k carries K_kk, so A(K) is linear in the axis factors."""
+    mesh = dg.Mesh(2, (5, 4, 1), 2)
+    Ax = dg.bsr_to_dense(dg.assemble_sipg(mesh, diff_axes=(1.0, 0.0)))
+    Ay = dg.bsr_to_dense(dg.assemble_sipg(mesh, diff_axes=(0.0, 1.0)))
+    A1 = dg.bsr_to_dense(dg.assemble_sipg(mesh))
+    Am = dg.bsr_to_dense(dg.assemble_sipg(mesh, diff_axes=(2.5, 0.01)))
+    sc = np.abs(A1).max()
+    assert np.abs(Ax + Ay - A1).max() <= 1e-13 * sc
+    assert np.abs(2.5 * Ax + 0.01 * Ay - Am).max() <= 1e-13 * sc
+    assert np.abs(Ax - Ax.T).max() <= 1e-13 * sc and np.abs(Am - Am.T).max() <= 1e-13 * sc
+    with pytest.raises(ValueError):
+        dg.assemble_sipg(mesh, diff_axes=(1.0,))
+
+
+def test_reaction_adds_the_mass_matrix():
+    """The orthonormal Legendre basis makes each element's mass matrix
+    (|K| / 2^d) I, so +c0 u adds c0 h^2 / 4 to the diagonal in 2D."""
+    n = 6
+    _, A0 = dg.reaction_diffusion_2d(n, 2, a0=0.1, c0=0.0)
+    _, A1 = dg.reaction_diffusion_2d(n, 2, a0=0.1, c0=7.0)
+    D = dg.bsr_to_dense(A1) - dg.bsr_to_dense(A0)
+    assert np.abs(D - 7.0 / n ** 2 / 4 * np.eye(D.shape[0])).max() <= 1e-12 * np.abs(dg.bsr_to_dense(A0)).max()
+
+
+def _quad(mesh):
+    p, d = mesh.p, 2
+    lg = dg._legendre_1d(p)
+    q = lg["xg"].size
+    hs = np.array([1.0 / mesh.n[0], 1.0 / mesh.n[1]])
+    qidx = np.stack(np.meshgrid(*([np.arange(q)] * d), indexing="ij"), axis=-1).reshape(-1, d)[:, ::-1]
+    lidx = np.stack(np.meshgrid(*([np.arange(p + 1)] * d), indexing="ij"), axis=-1).reshape(-1, d)[:, ::-1]
+    pts = dg._elem_centres(mesh)[:, None, :] + 0.5 * hs * lg["xg"][qidx][None]
+    w = np.prod(lg["wg"][qidx], axis=1) * np.prod(hs) / 2 ** d
+    phi = np.ones((lidx.shape[0], qidx.shape[0]))
+    for k in range(d):
+        phi *= lg["V"][lidx[:, k]][:, qidx[:, k]]
+    return pts, w, phi
+
+
+@pytest.mark.parametrize("a0,c0", [(1.0, 0.0), (0.05, 0.0), (0.05, 3.0), (1e-3, 1e3)])
+def test_anisotropic_discrete_solution_is_exact_for_a_polynomial(a0, c0):
+    """u = x(1-x) y(1-y) lies in the p = 2 space and vanishes on the boundary;
+    SIPG is consistent, so the discrete solution of -u_xx - a0 u_yy + c0 u = f
+    is u itself (its L2 projection, up to the solve's rounding)."""
+    mesh, A = dg.reaction_diffusion_2d(6, 2, a0=a0, c0=c0)
+    pts, w, phi = _quad(mesh)
+    x, y = pts[..., 0], pts[..., 1]
+    u = x * (1 - x) * y * (1 - y)
+    f = 2 * y * (1 - y) + a0 * 2 * x * (1 - x) + c0 * u
+    b = ((f * w) @ phi.T).ravel()
+    # orthonormal basis: the projection coefficients are (u, phi) / (|K| / 4)
+    uproj = ((u * w) @ phi.T).ravel() / (1.0 / mesh.nelem / 4.0)
+    xs = np.linalg.solve(dg.bsr_to_dense(A), b)
+    assert np.abs(xs - uproj).max() <= 1e-9 * np.abs(uproj).max()
+
+
+def test_enclosure_density_and_operator():
+    mesh, A = dg.density_helmholtz_2d(32, 1, rho_ratio=1e3)
+    rho = dg.enclosure_density(mesh, 1e3)
+    assert set(np.unique(rho)) == {1.0, 1e3}
+    g = rho.reshape(32, 32)                       # g[iy, ix]
+    # a closed rectangular frame: rows 8..23 and columns 8..23, two elements thick
+    frame = np.zeros((32, 32), bool)
+    frame[8:24, 8:24] = True
+    frame[10:22, 10:22] = False
+    assert np.array_equal(g == 1e3, frame)
+    assert A.meta["wall_elems"] == frame.sum()
+    D = dg.bsr_to_dense(A)
+    assert np.abs(D - D.T).max() <= 1e-12 * np.abs(D).max()
+    # rho_ratio = 1: the plain constant-coefficient Helmholtz operator
+    _, A1 = dg.density_helmholtz_2d(32, 1, rho_ratio=1.0)
+    ref = dg.assemble_sipg(mesh, kappa=dg.helmholtz_kappa(32, 1))
+    assert np.array_equal(A1.val, ref.val) and np.array_equal(A1.col_idx, ref.col_idx)
+    # the walls (a = 1e-3) change the blocks of the wall elements and their neighbours only
+    dif = np.abs(A.val - ref.val).max(axis=(1, 2)) > 0
+    rows = np.repeat(np.arange(A.nb), np.diff(A.row_ptr))
+    touched = np.zeros(A.nb, bool)
+    touched[rows[dif]] = True
+    touched[A.col_idx[dif]] = True
+    near = frame.copy()
+    near[1:] |= frame[:-1]
+    near[:-1] |= frame[1:]
+    near[:, 1:] |= frame[:, :-1]
+    near[:, :-1] |= frame[:, 1:]
+    assert np.array_equal(touched, near.ravel())

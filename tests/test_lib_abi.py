@@ -54,3 +54,46 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib2.nd_order(None, None, None, None, ctypes.byref(out)) == hssnd.HSS_EINVAL
     assert b"null" in lib2.hss_last_error()
     assert lib2.hss_apply(None, 1, None, 1, None, 1, None) == hssnd.HSS_EINVAL
+
+
+STRUCTS = ["hss_bsr", "hss_mesh", "hss_nd_opts", "hss_factor_opts", "fgmres_opts", "fgmres_stats",
+           "hss_tree_desc", "hss_factor_info"]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes mirror has the header struct's size and field offsets (a C
+    program compiled against include/hssnd.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_1508_07798_gb300 import hssnd
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hssnd.h"', 'int main(void) {']
+    for s in STRUCTS:
+        lines.append(f'  printf("{s} size %zu\\n", sizeof({s}));')
+        for f, _ in getattr(hssnd, s)._fields_:
+            lines.append(f'  printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.splitlines())
+    for s in STRUCTS:
+        cls = getattr(hssnd, s)
+        assert int(got[f"{s} size"]) == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert int(got[f"{s} {f}"]) == getattr(cls, f).offset, (s, f)
+
+
+def test_factor_defaults_overwrite_every_field(lib):
+    """hss_factor_opts_default sets every field, so a C caller's uninitialised
+    struct gets r_init = NULL and the default cap policy."""
+    from paper_1508_07798_gb300 import hssnd
+    o = hssnd.hss_factor_opts()
+    ctypes.memset(ctypes.byref(o), 0xA5, ctypes.sizeof(o))
+    hssnd._lib.hss_factor_opts_default(ctypes.byref(o))
+    assert o.r_init is None and o.cap_policy == 0 and o.keep_schur == 0 and o.seed == 0 and o.rmax == 96
+    assert hssnd.factor_opts(cap_policy="accept").cap_policy == 1

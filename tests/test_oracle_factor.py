@@ -139,3 +139,67 @@ def test_gmres_restart_and_nonconvergence():
     assert np.linalg.norm(b - Acsr @ x) <= 1e-8 * np.linalg.norm(b)
     x2, info2 = oracle.fgmres(lambda v: Acsr @ v, None, b, restart=5, rtol=1e-12, maxit=3)
     assert not info2["converged"] and info2["iters"] == 3
+
+
+# --- sample-width cap policies (Theorem 1 needs k + p samples; Sec. 5 fixes the width l)
+
+def _capped_runs(r=16):
+    mesh, A, nd, Acsr = _setup(2, (16, 16), 1, kind="helm")
+    kw = dict(tol=1e-12, seed=5, r0=r, rmax=r, keep_h=True)
+    return nd, oracle.factor(Acsr, nd, cap="keep", **kw), oracle.factor(Acsr, nd, cap="accept", **kw)
+
+
+def test_cap_policies_differ_only_on_capped_fronts():
+    nd, fk, fa = _capped_runs()
+    capped = {r["box"] for r in fk["log"] if r.get("capped")}
+    assert capped and capped == {r["box"] for r in fa["log"] if r.get("capped")}
+    for b in fk["boxes"]:
+        Hk, Ha, S = fk["boxes"][b]["H"], fa["boxes"][b]["H"], fk["boxes"][b]["S"]
+        if b in capped:
+            assert np.array_equal(Hk, S) and not np.array_equal(Ha, S)
+        else:
+            assert np.array_equal(Hk, Ha)
+    with pytest.raises(ValueError):
+        oracle.factor(dg.bsr_to_csr(dg.poisson_2d(16, 1)[1]), nd, cap="drop")
+
+
+def test_accepted_approximant_is_hss_with_ranks_at_most_r():
+    """Under the accept policy a capped front's H keeps the nested-basis
+    structure: for every HSS node a, the off-diagonal block row H(R_a, ~R_a)
+    lies in the span of U^tall_a, so its rank is at most the sample width."""
+    nd, fk, fa = _capped_runs(r=8)
+    checked = 0
+    for rec in fa["log"]:
+        if not rec.get("capped"):
+            continue
+        H, S = fa["boxes"][rec["box"]]["H"], fa["boxes"][rec["box"]]["S"]
+        nodes = rec["rep"]["nodes"]
+        for t, nd_ in enumerate(nodes[:-1]):
+            R = np.arange(nd_["lo"], nd_["hi"])
+            C_ = np.setdiff1d(np.arange(H.shape[0]), R)
+            sv = np.linalg.svd(H[np.ix_(R, C_)], compute_uv=False)
+            assert (sv > 1e-11 * sv[0]).sum() <= rec["r"], (rec["box"], t)
+            full = np.linalg.svd(S[np.ix_(R, C_)], compute_uv=False)
+            checked += (full > 1e-11 * full[0]).sum() > rec["r"]
+    assert checked > 0          # somewhere S itself needed more than r
+
+
+def test_partition_scheme_matters_for_anisotropic_diffusion():
+    """Sec. 5, eq. (60) with a0 = 1e-3 and a fixed sample width l = 16: when
+    diffusion dominates, vertical slabs (cuts across the strong x coupling)
+    fail while horizontal slabs converge; in the reaction-dominated regime the
+    scheme matters much less and both converge."""
+    its = {}
+    for c0 in (1e-3, 1e6):
+        mesh, A = dg.reaction_diffusion_2d(32, 1, a0=1e-3, c0=c0)
+        Acsr = dg.bsr_to_csr(A)
+        b = dg.random_rhs(A.n, 1, 0)[:, 0]
+        for sc in ("hslab", "vslab"):
+            nd = oracle.nd_order(2, mesh.n, 1, A.row_ptr, A.col_idx, scheme=sc)
+            fac = oracle.factor(Acsr, nd, tol=1e-12, seed=0, r0=16, rmax=16, cap="accept")
+            _, info = oracle.fgmres(lambda v: Acsr @ v, lambda v: oracle.apply(fac, v), b, rtol=1e-8,
+                                    restart=30, maxit=120)
+            its[c0, sc] = info["iters"] if info["converged"] else None
+    assert its[1e-3, "hslab"] is not None and its[1e-3, "vslab"] is None, its
+    assert its[1e6, "hslab"] is not None and its[1e6, "vslab"] is not None, its
+    assert its[1e6, "vslab"] <= 30 and its[1e6, "hslab"] <= its[1e-3, "hslab"], its
