@@ -18,13 +18,15 @@ FP64, with no blocking, fusion or reordering beyond what the paper states:
   fgmres.py    restarted flexible GMRES with right preconditioning
   mlp.py       rank-prediction MLP of the learned-rank form (not in the paper):
                forward, loss gradient, Adam, standardisation
+  ilu.py       block ILU(0), the comparison preconditioner of Sec. 5
 
 Pins (tests/test_oracle_*.py): exact LDM^t with compression off equals a dense
 LU solve; GMRES converges in one iteration then; ID error within the strong
 rank-revealing bound of the SVD and |P| <= 2; HSS recovery of matrices that are
 HSS by construction; Schur complement equals the inverse of the trailing block
 of the front inverse; brute-force interior/boundary sets on tiny meshes;
-unpreconditioned GMRES history equals SciPy's.
+unpreconditioned GMRES history equals SciPy's; ILU(0)'s product equals A on
+A's pattern, is exact on a block-tridiagonal chain and equals scalar ILU(0).
 """
 from .nd import nd_order                      # noqa: F401
 from .idecomp import interp_decomp            # noqa: F401
@@ -34,3 +36,4 @@ from .apply import apply                      # noqa: F401
 from .fgmres import fgmres                    # noqa: F401
 from .rademacher import rademacher            # noqa: F401
 from . import mlp                             # noqa: F401
+from .ilu import ilu0, ilu0_apply             # noqa: F401
