@@ -118,6 +118,7 @@ typedef struct fgmres_stats {
 
 typedef struct hss_tree hss_tree;
 typedef struct hss_factor_t hss_factor_t;
+typedef struct hss_ilu_t hss_ilu_t;
 
 /* Default option values (host structs). */
 void hss_nd_opts_default(hss_nd_opts *o);
@@ -348,6 +349,31 @@ int hss_rank_model_predict(hss_rank_model *m, int n, const float *feat, int over
  * rounds; fronts with a single-node HSS tree (not compressed) report r = 0.
  * Returns the number of records (all fronts with |B| > 0), -1 for a null handle. */
 int hss_factor_export_log(const hss_factor_t *f, int cap, int *box, int *kmax, int *r, int *rounds);
+
+/* ---- ILU(0): the comparison preconditioner of Sec. 5 ("a standard ILU
+ * preconditioner"; the variant is not named there).  Block ILU(0) on the BSR
+ * pattern of A in the natural element order: L block unit lower triangular on
+ * A's strictly lower pattern, U block upper triangular on A's upper pattern,
+ * (L U)_ij = A_ij at every stored block, fill elsewhere dropped.  Since every
+ * stored block is dense this equals scalar ILU(0) on A's scalar pattern.
+ *
+ * ilu0_factor: FP64, level-scheduled (a block row's level is one more than the
+ * highest level of the rows it depends on; one launch per level, one CTA per
+ * row).  Reads A's structure to the host once (synchronizes `stream`); does
+ * not modify A.  bs <= 64; every block row must store its diagonal block.
+ * Errors: HSS_EINVAL, HSS_ESINGULAR (a diagonal block of U is singular; the
+ * block row goes to hss_last_error), HSS_ENOMEM, HSS_ECUDA.  *out receives a
+ * new handle, owned by the caller until ilu0_destroy. */
+int ilu0_factor(const hss_bsr *A, void *stream, hss_ilu_t **out);
+/* y = U^-1 L^-1 x for nrhs columns (DEVICE, column-major, block-row order).
+ * y may alias x.  Forward and backward level sweeps, captured once per handle
+ * in a CUDA graph (one for nrhs = 1, one for blocks of 8).  Asynchronous. */
+int ilu0_apply(const hss_ilu_t *M, int nrhs, const double *x, int ldx, double *y, int ldy, void *stream);
+/* fgmres_solve with ILU(0) as the right preconditioner (same options,
+ * statistics, errors and synchronization as fgmres_solve). */
+int fgmres_solve_ilu0(const hss_bsr *A, const hss_ilu_t *M, int nrhs, const double *b, int ldb, double *x,
+                      int ldx, const fgmres_opts *opts, fgmres_stats *stats, void *stream);
+void ilu0_destroy(hss_ilu_t *M);
 
 /* Convergence history of the last fgmres_solve on this thread: Arnoldi residual
  * estimates |g_{j+1}|/||b|| of right-hand side `rhs` (HOST, up to cap values);

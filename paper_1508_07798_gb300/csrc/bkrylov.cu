@@ -225,10 +225,10 @@ namespace hssnd {
 
 // The lock-step solver: one Krylov process per (instance, right-hand side),
 // instance i owning rows [inst_dof[i], inst_dof[i + 1]) of the block vectors.
-// A is the (block-diagonal) matrix of all instances, f its preconditioner
-// (NULL: none), stats one entry per instance, hist (optional) one residual
+// A is the (block-diagonal) matrix of all instances, pc its preconditioner
+// (HSS, ILU(0) or none), stats one entry per instance, hist (optional) one residual
 // history per process.
-int fgmres_lockstep(const hss_bsr *A, const hss_factor_t *f, const std::vector<int> &inst_dof, int nrhs,
+int fgmres_lockstep(const hss_bsr *A, const Precond &pc, const std::vector<int> &inst_dof, int nrhs,
                     const double *b, int ldb, double *x, int ldx, const fgmres_opts &o, fgmres_stats *stats,
                     std::vector<std::vector<double>> *hist, cudaStream_t s) {
     const int ninst = (int)inst_dof.size() - 1, m = o.restart;
@@ -340,8 +340,8 @@ int fgmres_lockstep(const hss_bsr *A, const hss_factor_t *f, const std::vector<i
         for (int j = 0; j < m; ++j) {
             const double *Vj = dV + NB * j;
             double *Zj = dZ + NB * j;
-            if (f) {
-                if ((rc = apply_factor(f, nrhs, Vj, N, Zj, N, s))) return rc;
+            if (!pc.none()) {
+                if ((rc = precond_apply(pc, nrhs, Vj, N, Zj, N, s))) return rc;
             } else {
                 HSS_CUDA(cudaMemcpyAsync(Zj, Vj, sizeof(double) * NB, cudaMemcpyDeviceToDevice, s));
             }
@@ -410,6 +410,6 @@ extern "C" int fgmres_solve_batched(const hss_factor_t *f, int nrhs, const doubl
         set_error("fgmres_solve_batched: invalid argument (needs a factor from hss_factor_batched; restart in [1, 31])");
         return HSS_EINVAL;
     }
-    return fgmres_lockstep(&f->bA, f, f->tree->inst_dof, nrhs, b, ldb, x, ldx, o, stats, nullptr,
+    return fgmres_lockstep(&f->bA, Precond{f, nullptr}, f->tree->inst_dof, nrhs, b, ldb, x, ldx, o, stats, nullptr,
                            (cudaStream_t)stream);
 }

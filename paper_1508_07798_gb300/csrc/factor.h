@@ -54,8 +54,23 @@ struct FrontLog {   // per-front record (rank logging, Sec. 5 empirical cost)
 };
 
 int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);
+int ilu_apply(const hss_ilu_t *M, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);
+long ilu_ndof(const hss_ilu_t *M);
 int spmv(const hss_bsr *A, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);
-int fgmres_lockstep(const hss_bsr *A, const hss_factor_t *f, const std::vector<int> &inst_dof, int nrhs,
+
+// Right preconditioner of the Krylov solvers: the HSS factorization, block
+// ILU(0), or none (both null).
+struct Precond {
+    const hss_factor_t *hss = nullptr;
+    const hss_ilu_t *ilu = nullptr;
+    bool none() const { return !hss && !ilu; }
+};
+inline int precond_apply(const Precond &P, int nrhs, const double *x, long ldx, double *y, long ldy,
+                         cudaStream_t s) {
+    return P.hss ? apply_factor(P.hss, nrhs, x, ldx, y, ldy, s) : ilu_apply(P.ilu, nrhs, x, ldx, y, ldy, s);
+}
+
+int fgmres_lockstep(const hss_bsr *A, const Precond &pc, const std::vector<int> &inst_dof, int nrhs,
                     const double *b, int ldb, double *x, int ldx, const fgmres_opts &o, fgmres_stats *stats,
                     std::vector<std::vector<double>> *hist, cudaStream_t s);
 

@@ -252,7 +252,7 @@ static int dot1(const double *v, const double *w, long N, double *part, double *
     return HSS_OK;
 }
 
-static int fgmres_one(const hss_bsr *A, const hss_factor_t *f, const double *b, double *x, const fgmres_opts &o,
+static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, double *x, const fgmres_opts &o,
                       Krylov &K, int &iters, double &relres, bool &conv, std::vector<double> &hist, cudaStream_t s) {
     const long N = K.N;
     const int m = K.m;
@@ -296,8 +296,8 @@ static int fgmres_one(const hss_bsr *A, const hss_factor_t *f, const double *b, 
         int jend = 0;
         for (int j = 0; j < m; ++j) {
             double *vj = V + N * j, *zj = Z + N * j;
-            if (f) {
-                if ((rc = apply_factor(f, 1, vj, N, zj, N, s))) return rc;
+            if (!pc.none()) {
+                if ((rc = precond_apply(pc, 1, vj, N, zj, N, s))) return rc;
             } else {
                 HSS_CUDA(cudaMemcpyAsync(zj, vj, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
             }
@@ -342,23 +342,16 @@ extern "C" int hss_spmv(const hss_bsr *A, int nrhs, const double *x, int ldx, do
     return spmv(A, nrhs, x, ldx, y, ldy, (cudaStream_t)stream);
 }
 
-extern "C" int fgmres_solve(const hss_bsr *A, const hss_factor_t *f, int nrhs, const double *b, int ldb, double *x,
-                            int ldx, const fgmres_opts *opts, fgmres_stats *stats, void *stream) {
-    fgmres_opts o;
-    fgmres_opts_default(&o);
-    if (opts) o = *opts;
-    long N = A ? (long)A->nb * A->bs : 0;
-    if (!A || !b || !x || nrhs < 0 || ldb < N || ldx < N || o.restart < 1 || o.restart > KRY_MAXM - 1 || o.maxit < 0 ||
-        (f && f->ndof != N)) {
-        set_error("fgmres_solve: invalid argument (restart must be in [1, 31])");
-        return HSS_EINVAL;
-    }
-    cudaStream_t s = (cudaStream_t)stream;
+// fgmres_solve for any right preconditioner: one Krylov space at a time for a
+// single right-hand side, lock-step processes for several.
+static int fgmres_driver(const hss_bsr *A, const Precond &pc, int nrhs, const double *b, int ldb, double *x, int ldx,
+                         const fgmres_opts &o, fgmres_stats *stats, cudaStream_t s) {
+    const long N = (long)A->nb * A->bs;
     if (nrhs > 1) {
         // several right-hand sides: independent Krylov processes in lock step,
         // one multi-vector apply and SpMV per Arnoldi step
         fgmres_stats st{0, 0, 0.0, 1};
-        int rc = fgmres_lockstep(A, f, std::vector<int>{0, (int)N}, nrhs, b, ldb, x, ldx, o, &st, &g_hist, s);
+        int rc = fgmres_lockstep(A, pc, std::vector<int>{0, (int)N}, nrhs, b, ldb, x, ldx, o, &st, &g_hist, s);
         if (rc != HSS_OK && rc != HSS_ENOCONV) return rc;
         if (stats) *stats = st;
         return st.converged ? HSS_OK : HSS_ENOCONV;
@@ -373,7 +366,7 @@ extern "C" int fgmres_solve(const hss_bsr *A, const hss_factor_t *f, int nrhs, c
         int it = 0;
         double rel = 0;
         bool conv = false;
-        if ((rc = fgmres_one(A, f, b + (long)ldb * k, x + (long)ldx * k, o, K, it, rel, conv, g_hist[k], s)))
+        if ((rc = fgmres_one(A, pc, b + (long)ldb * k, x + (long)ldx * k, o, K, it, rel, conv, g_hist[k], s)))
             return rc;
         st.iters += it;
         st.max_iters = std::max(st.max_iters, it);
@@ -382,6 +375,37 @@ extern "C" int fgmres_solve(const hss_bsr *A, const hss_factor_t *f, int nrhs, c
     }
     if (stats) *stats = st;
     return st.converged ? HSS_OK : HSS_ENOCONV;
+}
+
+static bool fgmres_args_ok(const hss_bsr *A, int nrhs, const double *b, int ldb, const double *x, int ldx,
+                           const fgmres_opts &o, long M_ndof) {
+    const long N = A ? (long)A->nb * A->bs : 0;
+    return A && b && x && nrhs >= 0 && ldb >= N && ldx >= N && o.restart >= 1 && o.restart <= KRY_MAXM - 1 &&
+           o.maxit >= 0 && (M_ndof < 0 || M_ndof == N);
+}
+
+extern "C" int fgmres_solve(const hss_bsr *A, const hss_factor_t *f, int nrhs, const double *b, int ldb, double *x,
+                            int ldx, const fgmres_opts *opts, fgmres_stats *stats, void *stream) {
+    fgmres_opts o;
+    fgmres_opts_default(&o);
+    if (opts) o = *opts;
+    if (!fgmres_args_ok(A, nrhs, b, ldb, x, ldx, o, f ? (long)f->ndof : -1)) {
+        set_error("fgmres_solve: invalid argument (restart must be in [1, 31])");
+        return HSS_EINVAL;
+    }
+    return fgmres_driver(A, Precond{f, nullptr}, nrhs, b, ldb, x, ldx, o, stats, (cudaStream_t)stream);
+}
+
+extern "C" int fgmres_solve_ilu0(const hss_bsr *A, const hss_ilu_t *M, int nrhs, const double *b, int ldb,
+                                 double *x, int ldx, const fgmres_opts *opts, fgmres_stats *stats, void *stream) {
+    fgmres_opts o;
+    fgmres_opts_default(&o);
+    if (opts) o = *opts;
+    if (!M || !fgmres_args_ok(A, nrhs, b, ldb, x, ldx, o, ilu_ndof(M))) {
+        set_error("fgmres_solve_ilu0: invalid argument (null preconditioner, size mismatch, or restart outside [1, 31])");
+        return HSS_EINVAL;
+    }
+    return fgmres_driver(A, Precond{nullptr, M}, nrhs, b, ldb, x, ldx, o, stats, (cudaStream_t)stream);
 }
 
 extern "C" int fgmres_history(int rhs, double *hist, int cap) {

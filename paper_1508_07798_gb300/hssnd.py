@@ -31,7 +31,8 @@ EXPORTED = [
     "hss_gemm_f32_static", "nd_order_batched", "hss_factor_batched", "fgmres_solve_batched",
     "hss_rank_features", "hss_rank_model_create", "hss_rank_model_destroy", "hss_rank_model_get",
     "hss_rank_model_set", "hss_rank_model_fit_norm", "hss_rank_model_loss_grad", "hss_rank_model_train",
-    "hss_rank_model_predict", "hss_factor_export_log",
+    "hss_rank_model_predict", "hss_factor_export_log", "ilu0_factor", "ilu0_apply", "fgmres_solve_ilu0",
+    "ilu0_destroy",
 ]
 
 
@@ -127,6 +128,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                            C.POINTER(C.c_float), P]),
         "hss_rank_model_predict": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int, P, P, P]),
         "hss_factor_export_log": (C.c_int, [P, C.c_int, ip, ip, ip, ip]),
+        "ilu0_factor": (C.c_int, [C.POINTER(hss_bsr), P, C.POINTER(P)]),
+        "ilu0_apply": (C.c_int, [P, C.c_int, P, C.c_int, P, C.c_int, P]),
+        "fgmres_solve_ilu0": (C.c_int, [C.POINTER(hss_bsr), P, C.c_int, P, C.c_int, P, C.c_int,
+                                        C.POINTER(fgmres_opts), C.POINTER(fgmres_stats), P]),
+        "ilu0_destroy": (None, [P]),
         "hss_profile_enable": (C.c_int, [C.c_int]),
         "hss_profile_reset": (C.c_int, []),
         "hss_profile_read": (C.c_int, [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
@@ -319,15 +325,49 @@ class SolveStats:
     converged: bool
 
 
-def fgmres_solve(A: DeviceBSR, F: Factor | None, b: torch.Tensor, x0: torch.Tensor | None = None,
+class ILU0:
+    """Block ILU(0) of a device BSR matrix (the comparison preconditioner)."""
+
+    def __init__(self, handle, A):
+        self.h = C.c_void_p(handle)
+        self.A = A                # keeps the matrix alive
+        self.ndof = A.n
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ilu0_destroy(self.h)
+            self.h = None
+
+
+def ilu0_factor(A: DeviceBSR, stream=None) -> ILU0:
+    out = C.c_void_p()
+    _check(_lib.ilu0_factor(C.byref(A.c), _stream(stream), C.byref(out)))
+    return ILU0(out.value, A)
+
+
+def ilu0_apply(M: ILU0, x: torch.Tensor, stream=None) -> torch.Tensor:
+    N = M.ndof
+    xs, k = _colmajor(x, N)
+    ys = torch.empty_like(xs)
+    _check(_lib.ilu0_apply(M.h, k, _ptr(xs), N, _ptr(ys), N, _stream(stream)))
+    y = ys.t()
+    return y.reshape(N) if x.dim() == 1 else y
+
+
+def fgmres_solve(A: DeviceBSR, F, b: torch.Tensor, x0: torch.Tensor | None = None,
                  restart=30, rtol=1e-8, maxit=1000, stream=None):
+    """F: a Factor (the HSS preconditioner), an ILU0, or None (no preconditioner)."""
     N = A.n
     bs_, k = _colmajor(b, N)
     xs = torch.zeros_like(bs_) if x0 is None else _colmajor(x0, N)[0]
     o = fgmres_opts(restart, rtol, maxit)
     st = fgmres_stats()
-    _check(_lib.fgmres_solve(C.byref(A.c), F.h if F is not None else None, k, _ptr(bs_), N, _ptr(xs), N,
-                             C.byref(o), C.byref(st), _stream(stream)), allow=(HSS_ENOCONV,))
+    if isinstance(F, ILU0):
+        _check(_lib.fgmres_solve_ilu0(C.byref(A.c), F.h, k, _ptr(bs_), N, _ptr(xs), N, C.byref(o), C.byref(st),
+                                      _stream(stream)), allow=(HSS_ENOCONV,))
+    else:
+        _check(_lib.fgmres_solve(C.byref(A.c), F.h if F is not None else None, k, _ptr(bs_), N, _ptr(xs), N,
+                                 C.byref(o), C.byref(st), _stream(stream)), allow=(HSS_ENOCONV,))
     x = xs.t()
     return (x.reshape(N) if b.dim() == 1 else x), SolveStats(st.iters, st.max_iters, st.relres, bool(st.converged))
 
