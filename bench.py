@@ -224,9 +224,9 @@ def bench_ours(args, rank, world):
         tree = hssnd.nd_order(meshdesc, dA, leaf_max=64)
         if prec == "fp32_learned":
             r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h))[1]
-            F = hssnd.hss_factor(dA, tree, tol=TOL, precision="fp32", r_init=r0)
+            F = hssnd.hss_factor(dA, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1)
         else:
-            F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec)
+            F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec, autotune=1)
         x, st = hssnd.fgmres_solve(dA, F, b, rtol=RTOL, restart=RESTART)
         return tree, F, x, st
 
@@ -297,7 +297,7 @@ def bench_ours(args, rank, world):
         if prec == "fp32_learned":
             continue      # same factor storage and apply kernels as fp32
         tree = hssnd.nd_order(meshdesc, dA, leaf_max=64)
-        F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec)
+        F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec, autotune=1)
         N = A.n
         xv = torch.randn(N, dtype=torch.float64, device=dev)
         yv = torch.empty_like(xv)
@@ -324,6 +324,8 @@ def bench_ours(args, rank, world):
                            gbs=per_apply_bytes / (statistics.median(ts) * 1e-3) / 1e9,
                            kernel_gbs=byt / (kms * 1e-3) / 1e9 if kms > 0 else None)
         apply[prec]["frac"] = apply[prec]["gbs"] / pk["hbm"]
+        fw, bw = F.apply_plan()
+        apply[prec]["work_split"] = dict(fwd=fw.tolist(), bwd=bw.tolist())
 
     # ---- e2e through the C ABI with host buffers: H2D of A and b, solve, D2H of x
     e2e = None
@@ -356,9 +358,9 @@ def bench_ours(args, rank, world):
         tree = hssnd.nd_order(meshdesc, dA2, leaf_max=64)
         if head == "fp32_learned":
             r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h))[1]
-            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision="fp32", r_init=r0)
+            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1)
         else:
-            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision=head)
+            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision=head, autotune=1)
         x, st = hssnd.fgmres_solve(dA2, F, d_b, rtol=RTOL, restart=RESTART)
         xh.copy_(x, non_blocking=True)
         e1.record(stream)
@@ -390,6 +392,8 @@ def bench_ours(args, rank, world):
                            rtol=RTOL, restart=RESTART, leaf_max=64, headline_form=head,
                            learned_widths=learned_info if model is not None else None,
                            l2="flushed by a 256 MB write before every timed step",
+                           apply_autotune="per-level work split timed on the first factorization of the "
+                                          "structure (a warm-up step), cached for the process",
                            parallelism=f"replicas x{world} (independent instances)"),
                forms={k: {kk: vv for kk, vv in v.items() if kk != "ms_all"} for k, v in forms.items()},
                apply=apply, roofline=roof, e2e=e2e, clocks=clocks, gpu_launches=int(launches_total // max(1, len(forms))),
@@ -430,7 +434,7 @@ def bench_batched(args, rank, world):
         out = []
         for g in G:
             forest = hssnd.nd_order_batched(g["meshes"], g["dAs"])
-            F = hssnd.hss_factor_batched(g["dAs"], forest, tol=BATCH_TOL, precision="fp32")
+            F = hssnd.hss_factor_batched(g["dAs"], forest, tol=BATCH_TOL, precision="fp32", autotune=1)
             X, st = hssnd.fgmres_solve_batched(F, g["B"], rtol=RTOL, restart=RESTART)
             out.append((forest, F, X, st))
         return out
@@ -485,7 +489,7 @@ def bench_batched(args, rank, world):
         off = np.concatenate([[0], np.cumsum([A.n for A in g["dAs"]])])
         for i, (A, m) in enumerate(zip(g["dAs"], g["meshes"])):
             t = hssnd.nd_order(m, A)
-            F = hssnd.hss_factor(A, t, tol=BATCH_TOL, precision="fp32")
+            F = hssnd.hss_factor(A, t, tol=BATCH_TOL, precision="fp32", autotune=1)
             hssnd.fgmres_solve(A, F, g["B"][off[i]:off[i + 1]], rtol=RTOL, restart=RESTART)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -535,6 +539,7 @@ def bench_batched(args, rank, world):
                 config=dict(workload="batched_256_instances_32rhs", instances=BATCH_COUNT, rhs=BATCH_RHS, dofs=dofs,
                             id_tol=BATCH_TOL, rtol=RTOL, restart=RESTART, groups=groups_out,
                             l2="inputs larger than L2 (A and the Krylov blocks take tens of GB)",
+                            apply_autotune="per-level work split timed in the warm-up, cached for the process",
                             parallelism=f"replicas x{world} (independent batches)"),
                 converged=bool(conv and worst <= RTOL * 1.0001), worst_true_relres=worst,
                 max_iters=max(iters), sequential_ms=sequential_ms,

@@ -99,6 +99,11 @@ typedef struct hss_factor_opts {
                                samples); HSS_CAP_ACCEPT keeps the approximant built from the r samples it
                                has (ranks up to r, no error bound) -- with r0 = rmax = l this is the fixed
                                anticipated rank l of the experiments of Sec. 5 */
+    int autotune;           /* 1: choose each level's apply work split (columns per work item of the
+                               forward and backward sweeps, from 32, 64, 128, 256) by timing the candidates
+                               on the factor's stream; choices are cached for the process, keyed by the
+                               level's front shapes, so a structure is timed once.  0 (default): 64.  The
+                               split changes only the summation order of the apply. */
 } hss_factor_opts;
 
 enum { HSS_CAP_KEEP = 0, HSS_CAP_ACCEPT = 1 };
@@ -374,6 +379,12 @@ int ilu0_apply(const hss_ilu_t *M, int nrhs, const double *x, int ldx, double *y
 int fgmres_solve_ilu0(const hss_bsr *A, const hss_ilu_t *M, int nrhs, const double *b, int ldb, double *x,
                       int ldx, const fgmres_opts *opts, fgmres_stats *stats, void *stream);
 void ilu0_destroy(hss_ilu_t *M);
+
+/* The apply's work split of a factorization: per stage (deepest level first,
+ * the top block last) the columns per work item of the forward and backward
+ * sweeps (HOST arrays of at least cap entries, either may be NULL).  Returns
+ * the number of stages, or a negative error code. */
+int hss_factor_apply_plan(const hss_factor_t *f, int cap, int *chunk_fwd, int *chunk_bwd);
 
 /* Convergence history of the last fgmres_solve on this thread: Arnoldi residual
  * estimates |g_{j+1}|/||b|| of right-hand side `rhs` (HOST, up to cap values);

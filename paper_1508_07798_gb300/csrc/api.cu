@@ -209,6 +209,7 @@ void hss_factor_opts_default(hss_factor_opts *o) {
     o->tensor_cores = 0;
     o->r_init = nullptr;
     o->cap_policy = HSS_CAP_KEEP;
+    o->autotune = 0;
 }
 
 void fgmres_opts_default(fgmres_opts *o) {

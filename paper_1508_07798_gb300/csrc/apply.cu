@@ -15,6 +15,9 @@
 #include "prof.h"
 
 #include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 namespace hssnd {
 
@@ -160,6 +163,203 @@ template <class T, int RB> static int record_sweep(const hss_factor_t *f, cudaSt
     return HSS_OK;
 }
 
+// Work items of one sweep direction of a stage: 32-row tiles, each split into
+// column chunks of `chunk` (pass 0: forward, n rows x ni columns; pass 1:
+// backward, ni rows x nb columns).
+static void stage_items(const ApplyStage &st, int pass, int chunk, std::vector<ApplyItem> &items, int &tiles) {
+    items.clear();
+    tiles = 0;
+    for (int f = 0; f < (int)st.h_fronts.size(); ++f) {
+        const FrontDev &d = st.h_fronts[f];
+        if (d.ni == 0) continue;
+        const int nrows = pass == 0 ? d.n : d.ni;
+        const int ncols = pass == 0 ? d.ni : d.nb;
+        const int nch = std::max(1, cdiv(ncols, chunk));
+        for (int r0 = 0; r0 < nrows; r0 += 32) {
+            const int first = (int)items.size();
+            const int tile = nch > 1 ? tiles++ : -1;
+            for (int ch = 0; ch < nch; ++ch)
+                items.push_back({f, r0, std::min(ncols, ch * chunk), std::min(ncols, (ch + 1) * chunk), tile, first, nch});
+        }
+    }
+}
+
+int pack_apply(hss_factor_t *F, cudaStream_t s) {
+    for (auto &g : F->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    const size_t nst = F->apply.size();
+    std::vector<std::vector<ApplyItem>> items(2 * nst);
+    long part_total = 0;
+    int tk_total = 0;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t bytes = 0;
+    for (size_t q = 0; q < nst; ++q) {
+        ApplyStage &st = F->apply[q];
+        int tiles[2];
+        for (int pass = 0; pass < 2; ++pass) stage_items(st, pass, st.chunk[pass], items[2 * q + pass], tiles[pass]);
+        st.nfwd = (int)items[2 * q].size();
+        st.nbwd = (int)items[2 * q + 1].size();
+        st.part_fwd = part_total;
+        part_total += st.nfwd;
+        st.part_bwd = part_total;
+        part_total += st.nbwd;
+        st.tk_fwd = tk_total;
+        tk_total += tiles[0];
+        st.tk_bwd = tk_total;
+        tk_total += tiles[1];
+        bytes += al(sizeof(FrontDev) * st.h_fronts.size()) + al(sizeof(ApplyItem) * st.nfwd) +
+                 al(sizeof(ApplyItem) * st.nbwd);
+    }
+    // every stage's fronts and work items in one device allocation
+    std::vector<char> pack(std::max(bytes, (size_t)1));
+    int rc;
+    if ((rc = F->apply_buf.alloc(pack.size()))) return rc;
+    size_t o = 0;
+    char *base = F->apply_buf.as<char>();
+    auto put = [&](const void *src, size_t b) -> char * {
+        if (b) std::memcpy(pack.data() + o, src, b);
+        char *d = base + o;
+        o += al(b);
+        return d;
+    };
+    for (size_t q = 0; q < nst; ++q) {
+        ApplyStage &st = F->apply[q];
+        st.d_fronts = reinterpret_cast<FrontDev *>(put(st.h_fronts.data(), sizeof(FrontDev) * st.h_fronts.size()));
+        st.d_fwd = reinterpret_cast<ApplyItem *>(put(items[2 * q].data(), sizeof(ApplyItem) * st.nfwd));
+        st.d_bwd = reinterpret_cast<ApplyItem *>(put(items[2 * q + 1].data(), sizeof(ApplyItem) * st.nbwd));
+    }
+    HSS_CUDA(cudaMemcpyAsync(base, pack.data(), pack.size(), cudaMemcpyHostToDevice, s));
+    if ((rc = F->d_apart.alloc(sizeof(double) * 32 * APPLY_RB * std::max(part_total, 1L))) ||
+        (rc = F->d_tickets.alloc(sizeof(int) * std::max(tk_total, 1))))
+        return rc;
+    HSS_CUDA(cudaMemsetAsync(F->d_tickets.p, 0, sizeof(int) * std::max(tk_total, 1), s));
+    // (a copy from pageable memory has left `pack` by the time cudaMemcpyAsync returns)
+    return HSS_OK;
+}
+
+// One sweep with events around every stage launch (the same launches as the
+// captured graph for one right-hand side); ms[2 * q + pass] = that launch's time.
+template <class T> static int timed_sweep(const hss_factor_t *f, cudaStream_t s, std::vector<cudaEvent_t> &ev,
+                                          std::vector<float> &ms) {
+    const T *arena = f->arena_ptr<T>();
+    const ApplyParams *prm = f->d_aparams.as<ApplyParams>();
+    const size_t nst = f->apply.size();
+    k_apply_copyin<<<2 * 152, 256, 0, s>>>(prm, f->ndof);
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool fwd = pass == 0;
+        for (size_t k = 0; k < nst; ++k) {
+            const size_t q = fwd ? k : nst - 1 - k;
+            const ApplyStage &st = f->apply[q];
+            const int nt = fwd ? st.nfwd : st.nbwd;
+            if (nt == 0) continue;
+            const int *ilist = st.top ? f->d_topset.as<int>() : f->tree->d_iset.as<int>();
+            double *part = f->d_apart.as<double>() + (fwd ? st.part_fwd : st.part_bwd) * 32 * APPLY_RB;
+            int *tk = f->d_tickets.as<int>() + (fwd ? st.tk_fwd : st.tk_bwd);
+            HSS_CUDA(cudaEventRecord(ev[2 * (2 * q + pass)], s));
+            if (fwd)
+                k_apply<T, 1, true><<<cdiv(nt, AP_WPB), AP_NT, 0, s>>>(st.d_fwd, nt, st.d_fronts, arena,
+                                                                       f->d_iperm.as<int>(), ilist,
+                                                                       f->tree->d_bset.as<int>(), prm, part, tk);
+            else
+                k_apply<T, 1, false><<<cdiv(nt, AP_WPB), AP_NT, 0, s>>>(st.d_bwd, nt, st.d_fronts, arena,
+                                                                        f->d_iperm.as<int>(), ilist,
+                                                                        f->tree->d_bset.as<int>(), prm, part, tk);
+            HSS_CUDA(cudaEventRecord(ev[2 * (2 * q + pass) + 1], s));
+        }
+    }
+    HSS_CHECK_LAUNCH("timed apply sweep");
+    HSS_CUDA(cudaStreamSynchronize(s));
+    for (size_t q = 0; q < nst; ++q)
+        for (int pass = 0; pass < 2; ++pass) {
+            const ApplyStage &st = f->apply[q];
+            if ((pass == 0 ? st.nfwd : st.nbwd) == 0) continue;
+            float t = 0;
+            HSS_CUDA(cudaEventElapsedTime(&t, ev[2 * (2 * q + pass)], ev[2 * (2 * q + pass) + 1]));
+            ms[2 * q + pass] = t;
+        }
+    return HSS_OK;
+}
+
+// Process-wide choices of the tuner: (precision, direction, stage shape) -> chunk.
+static std::mutex g_tune_mu;
+static std::unordered_map<uint64_t, int> g_tune;
+
+static uint64_t mix64(uint64_t z) {   // SplitMix64 finaliser
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+static uint64_t stage_key(const ApplyStage &st, int pass, int precision) {
+    uint64_t h = mix64(0x9e3779b97f4a7c15ULL + (uint64_t)(precision * 4 + pass * 2 + (st.top ? 1 : 0)));
+    for (const FrontDev &d : st.h_fronts)
+        h = mix64(h ^ (((uint64_t)d.n << 42) | ((uint64_t)d.ni << 21) | (uint64_t)d.nb));
+    return h;
+}
+
+int tune_apply(hss_factor_t *F, cudaStream_t s) {
+    static const int cand[] = {32, 64, 128, 256};
+    const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
+    const size_t nst = F->apply.size();
+    std::vector<uint64_t> key(2 * nst);
+    bool all_known = true;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (size_t q = 0; q < nst; ++q)
+            for (int pass = 0; pass < 2; ++pass) {
+                key[2 * q + pass] = stage_key(F->apply[q], pass, F->precision);
+                auto it = g_tune.find(key[2 * q + pass]);
+                if (it != g_tune.end()) F->apply[q].chunk[pass] = it->second;
+                else all_known = false;
+            }
+    }
+    if (all_known) return pack_apply(F, s);
+    int rc;
+    DevBuf yb;
+    if ((rc = F->tvec.alloc(sizeof(double) * (size_t)F->ndof * APPLY_RB)) ||
+        (rc = F->d_aparams.alloc(sizeof(ApplyParams))) || (rc = yb.alloc(sizeof(double) * (size_t)F->ndof)))
+        return rc;
+    HSS_CUDA(cudaMemsetAsync(yb.p, 0, sizeof(double) * F->ndof, s));
+    HSS_CUDA(cudaMemsetAsync(F->tvec.p, 0, sizeof(double) * F->ndof, s));
+    ApplyParams pv{yb.as<double>(), (long)F->ndof, yb.as<double>(), (long)F->ndof, F->tvec.as<double>(),
+                   (long)F->ndof, 1};
+    k_apply_set<<<1, 32, 0, s>>>(F->d_aparams.as<ApplyParams>(), pv);
+    HSS_CHECK_LAUNCH("k_apply_set");
+    std::vector<cudaEvent_t> ev(4 * nst, nullptr);
+    for (auto &e : ev) HSS_CUDA(cudaEventCreate(&e));
+    std::vector<float> best(2 * nst, 1e30f), ms(2 * nst, 0.f);
+    std::vector<int> pick(2 * nst, APPLY_CHUNK);
+    for (int c = 0; c < ncand && rc == HSS_OK; ++c) {
+        for (auto &st : F->apply) st.chunk[0] = st.chunk[1] = cand[c];
+        if ((rc = pack_apply(F, s))) break;
+        std::vector<float> mn(2 * nst, 1e30f);
+        for (int rep = 0; rep < 3 && rc == HSS_OK; ++rep) {   // the first sweep warms up; keep the fastest
+            rc = F->precision == HSS_FP32 ? timed_sweep<float>(F, s, ev, ms) : timed_sweep<double>(F, s, ev, ms);
+            if (rep > 0)
+                for (size_t i = 0; i < mn.size(); ++i) mn[i] = std::min(mn[i], ms[i]);
+        }
+        for (size_t i = 0; i < mn.size(); ++i)
+            if (mn[i] < best[i]) {
+                best[i] = mn[i];
+                pick[i] = cand[c];
+            }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (size_t q = 0; q < nst; ++q)
+            for (int pass = 0; pass < 2; ++pass) {
+                F->apply[q].chunk[pass] = pick[2 * q + pass];
+                g_tune[key[2 * q + pass]] = pick[2 * q + pass];
+            }
+    }
+    return pack_apply(F, s);
+}
+
 template <class T> static int build_graph(hss_factor_t *f, int slot) {
     cudaStream_t cs;
     HSS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -207,6 +407,19 @@ int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, dou
 }  // namespace hssnd
 
 using namespace hssnd;
+
+extern "C" int hss_factor_apply_plan(const hss_factor_t *f, int cap, int *chunk_fwd, int *chunk_bwd) {
+    if (!f || cap < 0) {
+        set_error("hss_factor_apply_plan: invalid argument");
+        return -HSS_EINVAL;
+    }
+    const int n = (int)f->apply.size();
+    for (int q = 0; q < std::min(n, cap); ++q) {
+        if (chunk_fwd) chunk_fwd[q] = f->apply[q].chunk[0];
+        if (chunk_bwd) chunk_bwd[q] = f->apply[q].chunk[1];
+    }
+    return n;
+}
 
 extern "C" int hss_apply(const hss_factor_t *f, int nrhs, const double *x, int ldx, double *y, int ldy,
                          void *stream) {

@@ -635,46 +635,20 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
     return HSS_OK;
 }
 
-template <class T>
-int build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, bool top, long &part_total, int &tk_total) {
+// Fronts and byte counts of one apply stage (its work items are built by
+// pack_apply once every stage exists).
+static void build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, bool top) {
     as.top = top;
     as.nfronts = (int)fr.size();
     as.h_fronts = fr;
-    std::vector<ApplyItem> items[2];
-    int tiles[2] = {0, 0};
     as.fwd_bytes = as.bwd_bytes = as.fwd_vec = as.bwd_vec = 0;
     for (int f = 0; f < (int)fr.size(); ++f) {
         if (fr[f].ni == 0) continue;
-        for (int pass = 0; pass < 2; ++pass) {
-            const int nrows = pass == 0 ? fr[f].n : fr[f].ni;
-            const int ncols = pass == 0 ? fr[f].ni : fr[f].nb;
-            const int nch = std::max(1, cdiv(ncols, APPLY_CHUNK));
-            for (int r0 = 0; r0 < nrows; r0 += 32) {
-                const int first = (int)items[pass].size();
-                const int tile = nch > 1 ? tiles[pass]++ : -1;
-                for (int ch = 0; ch < nch; ++ch)
-                    items[pass].push_back({f, r0, std::min(ncols, ch * APPLY_CHUNK),
-                                           std::min(ncols, (ch + 1) * APPLY_CHUNK), tile, first, nch});
-            }
-        }
         as.fwd_bytes += 8.0 * fr[f].n * (double)fr[f].ni;
         as.bwd_bytes += 8.0 * fr[f].ni * (double)fr[f].nb;
         as.fwd_vec += fr[f].ni + fr[f].ni + 2.0 * fr[f].nb;      // x_I read, t written, x_B read+written
         as.bwd_vec += fr[f].nb + fr[f].ni + fr[f].ni;           // x_B read, t read, x_I written
     }
-    as.part_fwd = part_total;
-    part_total += (long)items[0].size();
-    as.part_bwd = part_total;
-    part_total += (long)items[1].size();
-    as.tk_fwd = tk_total;
-    tk_total += tiles[0];
-    as.tk_bwd = tk_total;
-    tk_total += tiles[1];
-    as.h_fwd = std::move(items[0]);
-    as.h_bwd = std::move(items[1]);
-    as.nfwd = (int)as.h_fwd.size();
-    as.nbwd = (int)as.h_bwd.size();
-    return HSS_OK;
 }
 
 template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hss_factor_opts &o, cudaStream_t s,
@@ -751,8 +725,6 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         }
         return HSS_OK;
     };
-    long part_total = 0;
-    int tk_total = 0;
     F->factor_bytes = 0;
     F->front_flops = 0;
     F->exec_flops = 0;
@@ -828,7 +800,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
                                     F, eng, W, s)))
             return rc;
         F->apply.emplace_back();
-        if ((rc = build_apply_stage<T>(F->apply.back(), fr, false, part_total, tk_total))) return rc;
+        build_apply_stage(F->apply.back(), fr, false);
     }
     // ---- top blocks A^(0): cross couplings from A, then full Gauss-Jordan inversion
     {
@@ -883,38 +855,10 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             F->factor_bytes += sizeof(T) * (double)ntop_i[i] * ntop_i[i];
         }
         F->apply.emplace_back();
-        if ((rc = build_apply_stage<T>(F->apply.back(), fr, true, part_total, tk_total))) return rc;
+        build_apply_stage(F->apply.back(), fr, true);
     }
-    {
-        // every stage's fronts and work items in one device allocation
-        size_t bytes = 0;
-        auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-        for (const auto &st : F->apply)
-            bytes += al(sizeof(FrontDev) * st.h_fronts.size()) + al(sizeof(ApplyItem) * st.h_fwd.size()) +
-                     al(sizeof(ApplyItem) * st.h_bwd.size());
-        std::vector<char> pack(std::max(bytes, (size_t)1));
-        if ((rc = F->apply_buf.alloc(pack.size()))) return rc;
-        size_t o = 0;
-        char *base = F->apply_buf.as<char>();
-        auto put = [&](const void *src, size_t b) -> char * {
-            std::memcpy(pack.data() + o, src, b);
-            char *d = base + o;
-            o += al(b);
-            return d;
-        };
-        for (auto &st : F->apply) {
-            st.d_fronts = reinterpret_cast<FrontDev *>(put(st.h_fronts.data(), sizeof(FrontDev) * st.h_fronts.size()));
-            st.d_fwd = reinterpret_cast<ApplyItem *>(put(st.h_fwd.data(), sizeof(ApplyItem) * st.h_fwd.size()));
-            st.d_bwd = reinterpret_cast<ApplyItem *>(put(st.h_bwd.data(), sizeof(ApplyItem) * st.h_bwd.size()));
-            std::vector<ApplyItem>().swap(st.h_fwd);
-            std::vector<ApplyItem>().swap(st.h_bwd);
-        }
-        HSS_CUDA(cudaMemcpyAsync(base, pack.data(), pack.size(), cudaMemcpyHostToDevice, s));
-        if ((rc = F->d_apart.alloc(sizeof(double) * 32 * APPLY_RB * std::max(part_total, 1L))) ||
-            (rc = F->d_tickets.alloc(sizeof(int) * std::max(tk_total, 1))))
-            return rc;
-        HSS_CUDA(cudaMemsetAsync(F->d_tickets.p, 0, sizeof(int) * std::max(tk_total, 1), s));
-    }
+    // the apply's work items: tuned (packed by the tuner) or the default split
+    if ((rc = o.autotune ? tune_apply(F, s) : pack_apply(F, s))) return rc;
     HSS_CUDA(cudaStreamSynchronize(s));
     return HSS_OK;
 }
@@ -935,7 +879,7 @@ __global__ void k_shift_index(const int *__restrict__ src, int n, int add, int *
 static int check_factor_opts(const hss_factor_opts &o, const char *who) {
     if (!(o.tol >= 0) || o.r0 < 1 || o.dr < 1 || o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 ||
         (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
-        (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT)) {
+        (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1)) {
         set_error(std::string(who) + ": options out of range (rmax <= 128)");
         return HSS_EINVAL;
     }
@@ -1040,7 +984,7 @@ extern "C" int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_fact
     if (opts) o = *opts;
     if (A->nb != tree->nelem || A->bs != tree->bs || !A->val || !(o.tol >= 0) || o.r0 < 1 || o.dr < 1 ||
         o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 || (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
-        (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT)) {
+        (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1)) {
         set_error("hss_factor: invalid argument (matrix/tree mismatch or options out of range; rmax <= 128)");
         return HSS_EINVAL;
     }

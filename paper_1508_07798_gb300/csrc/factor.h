@@ -25,7 +25,7 @@ struct ApplyStage {
     bool top = false;
     int nfronts = 0;
     std::vector<FrontDev> h_fronts;       // host copies, packed into the factor's apply buffer
-    std::vector<ApplyItem> h_fwd, h_bwd;
+    int chunk[2] = {APPLY_CHUNK, APPLY_CHUNK};   // columns per work item of the forward / backward sweep
     FrontDev *d_fronts = nullptr;
     ApplyItem *d_fwd = nullptr, *d_bwd = nullptr;
     int nfwd = 0, nbwd = 0;               // work items (warps) of the two sweeps
@@ -54,6 +54,13 @@ struct FrontLog {   // per-front record (rank logging, Sec. 5 empirical cost)
 };
 
 int apply_factor(const hss_factor_t *f, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);
+// Work items of every apply stage from its fronts and column chunks, packed
+// into one device buffer with the partial-sum and ticket arrays (drops any
+// captured graph).
+int pack_apply(hss_factor_t *F, cudaStream_t s);
+// Chooses each stage's forward and backward column chunk by timing the
+// candidates (process-wide cache keyed by the stage's front shapes).
+int tune_apply(hss_factor_t *F, cudaStream_t s);
 int ilu_apply(const hss_ilu_t *M, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);
 long ilu_ndof(const hss_ilu_t *M);
 int spmv(const hss_bsr *A, int nrhs, const double *x, long ldx, double *y, long ldy, cudaStream_t s);

@@ -32,7 +32,7 @@ EXPORTED = [
     "hss_rank_features", "hss_rank_model_create", "hss_rank_model_destroy", "hss_rank_model_get",
     "hss_rank_model_set", "hss_rank_model_fit_norm", "hss_rank_model_loss_grad", "hss_rank_model_train",
     "hss_rank_model_predict", "hss_factor_export_log", "ilu0_factor", "ilu0_apply", "fgmres_solve_ilu0",
-    "ilu0_destroy",
+    "ilu0_destroy", "hss_factor_apply_plan",
 ]
 
 
@@ -59,7 +59,7 @@ class hss_factor_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("compress", C.c_int), ("r0", C.c_int), ("dr", C.c_int),
                 ("rmax", C.c_int), ("oversample", C.c_int), ("precision", C.c_int),
                 ("seed", C.c_uint64), ("keep_schur", C.c_int), ("tensor_cores", C.c_int), ("r_init", C.c_void_p),
-                ("cap_policy", C.c_int)]
+                ("cap_policy", C.c_int), ("autotune", C.c_int)]
 
 
 class fgmres_opts(C.Structure):
@@ -133,6 +133,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fgmres_solve_ilu0": (C.c_int, [C.POINTER(hss_bsr), P, C.c_int, P, C.c_int, P, C.c_int,
                                         C.POINTER(fgmres_opts), C.POINTER(fgmres_stats), P]),
         "ilu0_destroy": (None, [P]),
+        "hss_factor_apply_plan": (C.c_int, [P, C.c_int, ip, ip]),
         "hss_profile_enable": (C.c_int, [C.c_int]),
         "hss_profile_reset": (C.c_int, []),
         "hss_profile_read": (C.c_int, [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double),
@@ -246,6 +247,16 @@ class Factor:
         ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))  # noqa: E731
         _lib.hss_factor_export_log(self.h, n, *[ip(arrs[k]) for k in ("box", "kmax", "r", "rounds")])
         return {k: v[:n] for k, v in arrs.items()}
+
+    def apply_plan(self) -> tuple:
+        """Columns per work item of each apply stage: (forward, backward) arrays."""
+        n = _lib.hss_factor_apply_plan(self.h, 0, None, None)
+        if n < 0:
+            _check(-n)
+        fw, bw = np.zeros(max(n, 1), np.int32), np.zeros(max(n, 1), np.int32)
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))  # noqa: E731
+        _lib.hss_factor_apply_plan(self.h, n, ip(fw), ip(bw))
+        return fw[:n], bw[:n]
 
     def export_front(self, box: int):
         if getattr(self, "_nb", None) is None:

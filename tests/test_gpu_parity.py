@@ -311,3 +311,31 @@ def test_fp32_form_tensor_cores_match_simt():
     xt, st = hs.fgmres_solve(dA, Ftc, bvec, rtol=1e-8)
     xs, ss = hs.fgmres_solve(dA, Fsi, bvec, rtol=1e-8)
     assert st.converged and ss.converged and abs(st.iters - ss.iters) <= 2
+
+
+def test_autotuned_apply_matches_oracle_and_is_cached():
+    """The tuned work split (columns per apply work item, per stage and
+    direction) changes only the summation order: the apply still matches the
+    oracle to 1e-10 and the untuned apply to 1e-13; a second factorization of
+    the same structure reuses the cached choice."""
+    import torch
+    hs = _hss()
+    mesh, A = _setup("helm", (24, 24), 2)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((2, (24, 24), 2), dA)
+    F0 = hs.hss_factor(dA, tree, tol=1e-6, seed=3)
+    F1 = hs.hss_factor(dA, tree, tol=1e-6, seed=3, autotune=1)
+    F2 = hs.hss_factor(dA, tree, tol=1e-6, seed=4, autotune=1)
+    p0, p1, p2 = F0.apply_plan(), F1.apply_plan(), F2.apply_plan()
+    assert (p0[0] == 64).all() and (p0[1] == 64).all()
+    assert set(p1[0].tolist() + p1[1].tolist()) <= {32, 64, 128, 256}
+    assert np.array_equal(p1[0], p2[0]) and np.array_equal(p1[1], p2[1])
+    nd = oracle.nd_order(2, mesh.n, 2, A.row_ptr, A.col_idx)
+    fac = oracle.factor(dg.bsr_to_csr(A), nd, tol=1e-6, seed=3, rmax=96)
+    X = dg.random_rhs(A.n, 3, 5)
+    for k in (1, 3):
+        Xk = torch.as_tensor(np.asfortranarray(X[:, :k]), device="cuda")
+        Y0 = hs.hss_apply(F0, Xk).cpu().numpy().reshape(A.n, k)
+        Y1 = hs.hss_apply(F1, Xk).cpu().numpy().reshape(A.n, k)
+        assert _rel(Y1, oracle.apply(fac, X[:, :k])) <= TOL
+        assert _rel(Y1, Y0) <= 1e-13
