@@ -14,6 +14,7 @@
 // the Schur complement of eq. (32).  P is the pivot row permutation; the
 // apply undoes it by gathering x_I through a permuted index list.
 #include <cfloat>
+#include <type_traits>
 
 #include "internal.h"
 #include "front.h"
@@ -69,22 +70,38 @@ __device__ __forceinline__ long long mag_key(double a) { return __double_as_long
 // Block-wide argmax (largest |v|, ties to the lowest index) with one barrier:
 // every thread reduces the per-warp results itself.  The caller guarantees a
 // barrier between two calls (so nobody still reads sh when it is rewritten).
-template <class T> __device__ ArgMax<T> block_argmax(ArgMax<T> x, ArgMax<T> *sh) {
-    for (int o = 16; o > 0; o >>= 1) {
-        long long v2 = __shfl_down_sync(0xffffffffu, x.v, o);
-        int i2 = __shfl_down_sync(0xffffffffu, x.i, o);
-        if (v2 > x.v || (v2 == x.v && i2 < x.i)) {
-            x.v = v2;
-            x.i = i2;
+// Warp argmax of (key, position): largest key, lowest position on ties; every
+// lane gets the result.
+template <class T> __device__ __forceinline__ ArgMax<T> warp_argmax(ArgMax<T> x) {
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 magnitude keys fit in 31 bits; +1 maps "no candidate" (-1) to 0.
+        // Two warp reductions: the largest key, then the lowest position holding it.
+        const unsigned k = (unsigned)(x.v + 1);
+        const unsigned m = __reduce_max_sync(0xffffffffu, k);
+        const int pos = __reduce_min_sync(0xffffffffu, k == m ? x.i : 0x7fffffff);
+        return ArgMax<T>{(long long)m - 1, pos};
+    } else {
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long v2 = __shfl_xor_sync(0xffffffffu, x.v, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, x.i, o);
+            if (v2 > x.v || (v2 == x.v && i2 < x.i)) {
+                x.v = v2;
+                x.i = i2;
+            }
         }
+        return x;
     }
+}
+
+template <class T> __device__ ArgMax<T> block_argmax(ArgMax<T> x, ArgMax<T> *sh) {
+    x = warp_argmax(x);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) sh[w] = x;
     __syncthreads();
-    ArgMax<T> b = sh[0];
-    for (int k = 1; k < nw; ++k)
-        if (sh[k].v > b.v || (sh[k].v == b.v && sh[k].i < b.i)) b = sh[k];
-    return b;
+    // every warp reduces the per-warp results (at most 32) in parallel
+    ArgMax<T> y{-1LL, 0x7fffffff};
+    if (lane < nw) y = sh[lane];
+    return warp_argmax(y);
 }
 
 // One CTA per front with an active panel [k0, k0+kb) of its I columns.

@@ -14,6 +14,7 @@
 // dense approximant H = D on leaf blocks, U^tall_a S(J_a,K_b) V^tall_b^t across
 // siblings, written straight into the parent front (eq. (32)).
 #include <climits>
+#include <type_traits>
 
 #include "hss.h"
 #include "prof.h"
@@ -33,23 +34,47 @@ __device__ __forceinline__ long long abs_key(double a) { return __double_as_long
 __device__ __forceinline__ float key_val(long long k, float) { return __int_as_float((int)k); }
 __device__ __forceinline__ double key_val(long long k, double) { return __longlong_as_double(k); }
 
+// FP32 keys (non-negative IEEE bit patterns, -1 = none) fit in 31 bits: the
+// warp argmax is two reductions, the largest key + 1, then the lowest index
+// holding it (ties to the lowest index, as in the shuffle form).
+__device__ __forceinline__ AM<float> warp_am_redux(AM<float> x) {
+    const unsigned k = (unsigned)(x.v + 1);
+    const unsigned m = __reduce_max_sync(0xffffffffu, k);
+    const int i = __reduce_min_sync(0xffffffffu, k == m ? x.i : INT_MAX);
+    return AM<float>{(long long)m - 1, i};
+}
+
+// Argmax of the per-warp candidates (ID_NT / 32 of them), computed by every thread.
+template <class T> __device__ __forceinline__ AM<T> reduce_candidates(const AM<T> *c) {
+    if constexpr (std::is_same<T, float>::value) {
+        const int lane = threadIdx.x & 31;
+        return warp_am_redux(lane < ID_NT / 32 ? c[lane] : AM<float>{-1LL, INT_MAX});
+    } else {
+        AM<T> b = c[0];
+        for (int k = 1; k < ID_NT / 32; ++k)
+            if (c[k].v > b.v || (c[k].v == b.v && c[k].i < b.i)) b = c[k];
+        return b;
+    }
+}
+
 template <class T> __device__ AM<T> blk_argmax(AM<T> x, AM<T> *sh) {
-    for (int o = 16; o > 0; o >>= 1) {
-        long long v2 = __shfl_down_sync(0xffffffffu, x.v, o);
-        int i2 = __shfl_down_sync(0xffffffffu, x.i, o);
-        if (v2 > x.v || (v2 == x.v && i2 < x.i)) {
-            x.v = v2;
-            x.i = i2;
+    if constexpr (std::is_same<T, float>::value) {
+        x = warp_am_redux(x);
+    } else {
+        for (int o = 16; o > 0; o >>= 1) {
+            long long v2 = __shfl_down_sync(0xffffffffu, x.v, o);
+            int i2 = __shfl_down_sync(0xffffffffu, x.i, o);
+            if (v2 > x.v || (v2 == x.v && i2 < x.i)) {
+                x.v = v2;
+                x.i = i2;
+            }
         }
     }
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();   // previous readers of sh are done
     if (lane == 0) sh[w] = x;
     __syncthreads();
-    AM<T> b = sh[0];
-    for (int k = 1; k < ID_NT / 32; ++k)
-        if (sh[k].v > b.v || (sh[k].v == b.v && sh[k].i < b.i)) b = sh[k];
-    return b;
+    return reduce_candidates(sh);
 }
 
 template <class T> __device__ T blk_sum(T x, T *sh) {
@@ -201,11 +226,7 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
     const int kmx = min(r, m);
     for (int j = 0; j < kmx; ++j) {
         __syncthreads();   // candidates, nrm2, order and the updated columns are visible
-        AM<T> best = cand[0];
-        for (int q = 1; q < ID_NT / 32; ++q) {
-            const AM<T> o = cand[q];
-            if (o.v > best.v || (o.v == best.v && o.i < best.i)) best = o;
-        }
+        const AM<T> best = reduce_candidates(cand);
         const T nn2 = key_val(best.v, T(0));
         const T nrm = sqrt(nn2);
         if (j == 0) first = nrm;
