@@ -220,13 +220,18 @@ def bench_ours(args, rank, world):
         train_loss = model.train(Xt, tt, epochs=60, batch=256, lr=2e-3, seed=3)
         learned_info = dict(train_samples=int(len(tt)), train_loss=train_loss)
 
-    def step(prec):
+    def step(prec, marks=None):
+        # marks: two CUDA events recorded after the ordering and after the factor
         tree = hssnd.nd_order(meshdesc, dA, leaf_max=64)
+        if marks is not None:
+            marks[0].record(stream)
         if prec == "fp32_learned":
             r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h))[1]
             F = hssnd.hss_factor(dA, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1)
         else:
             F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec, autotune=1)
+        if marks is not None:
+            marks[1].record(stream)
         x, st = hssnd.fgmres_solve(dA, F, b, rtol=RTOL, restart=RESTART)
         return tree, F, x, st
 
@@ -247,23 +252,29 @@ def bench_ours(args, rank, world):
         if prec == args.forms.split(",")[0]:
             clk.start()
 
-        def timed(steps):
+        def timed(steps, phases=None):
             ts, lastv = [], None
             for _ in range(steps):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
+                marks = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
                 torch.cuda.synchronize()
                 e0.record(stream)
-                lastv = step(prec)
+                lastv = step(prec, marks)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1))
+                if phases is not None:
+                    phases["nd_order"].append(e0.elapsed_time(marks[0]))
+                    phases["factor"].append(marks[0].elapsed_time(marks[1]))
+                    phases["fgmres"].append(marks[1].elapsed_time(e1))
             return ts, lastv
 
         # pass 1: the headline time, no instrumentation
         l0 = hssnd.launch_count()
-        times, last = timed(args.steps)
+        phases = {"nd_order": [], "factor": [], "fgmres": []}
+        times, last = timed(args.steps, phases)
         launches_total += hssnd.launch_count() - l0
         # pass 2: the same steps with every kernel launch bracketed by CUDA events
         hssnd.profile_reset()
@@ -276,7 +287,8 @@ def bench_ours(args, rank, world):
         xr = x.cpu().numpy()
         relres = float(np.linalg.norm(b_host - Acsr @ xr) / np.linalg.norm(b_host))
         info = F.info()
-        forms[prec] = dict(ms=statistics.mean(times), ms_min=min(times), ms_all=times,
+        forms[prec] = dict(ms=statistics.mean(times), ms_min=min(times), ms_median=statistics.median(times),
+                           ms_all=times, phases_ms={k: statistics.mean(v) for k, v in phases.items()},
                            ms_instrumented=statistics.mean(ptimes), iters=st.iters,
                            relres=relres, converged=bool(st.converged and relres <= RTOL * 1.0001),
                            factor_bytes=info["factor_bytes"], front_flops=info["front_flops"],
