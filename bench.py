@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--workload", default="helmholtz64", choices=["helmholtz64", "batched256"],
                     help="helmholtz64: the timed workload (default); batched256: 256 independent "
                          "instances x 32 right-hand sides through the batched form (its own JSON line)")
+    ap.add_argument("--probe", type=int, default=4,
+                    help="residual probe vectors per accepted front in the learned-width form (0: off)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no apply loop, no host-buffer run): for profiling")
     return ap.parse_args()
@@ -227,7 +229,7 @@ def bench_ours(args, rank, world):
             marks[0].record(stream)
         if prec == "fp32_learned":
             r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h))[1]
-            F = hssnd.hss_factor(dA, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1)
+            F = hssnd.hss_factor(dA, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1, probe=args.probe)
         else:
             F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec, autotune=1)
         if marks is not None:
@@ -294,6 +296,7 @@ def bench_ours(args, rank, world):
                            factor_bytes=info["factor_bytes"], front_flops=info["front_flops"],
                            executed_flops=info["executed_flops"], max_rank=info["max_rank"], max_r=info["max_r"],
                            sampling_rounds=int(F.export_log()["rounds"].sum()),
+                           probe_regrown=info["probe_regrown"],
                            kernel_ms_sum=sum(v[0] for v in prof.values()) / args.steps)
     clocks = clk.stop()
     barrier()
@@ -370,7 +373,7 @@ def bench_ours(args, rank, world):
         tree = hssnd.nd_order(meshdesc, dA2, leaf_max=64)
         if head == "fp32_learned":
             r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h))[1]
-            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1)
+            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1, probe=args.probe)
         else:
             F = hssnd.hss_factor(dA2, tree, tol=TOL, precision=head, autotune=1)
         x, st = hssnd.fgmres_solve(dA2, F, d_b, rtol=RTOL, restart=RESTART)
@@ -403,6 +406,7 @@ def bench_ours(args, rank, world):
                config=dict(workload=WORKLOAD, dofs=A.n, p=P_DEG, mesh=f"{N_ELEM}x{N_ELEM}", id_tol=TOL,
                            rtol=RTOL, restart=RESTART, leaf_max=64, headline_form=head,
                            learned_widths=learned_info if model is not None else None,
+                           learned_probe_vectors=args.probe,
                            l2="flushed by a 256 MB write before every timed step",
                            apply_autotune="per-level work split timed on the first factorization of the "
                                           "structure (a warm-up step), cached for the process",

@@ -104,6 +104,11 @@ typedef struct hss_factor_opts {
                                on the factor's stream; choices are cached for the process, keyed by the
                                level's front shapes, so a structure is timed once.  0 (default): 64.  The
                                split changes only the summation order of the apply. */
+    int probe;              /* residual probe of every approximant the rank test accepts (the fallback check
+                               of learned widths): with W = `probe` +-1 vectors (0 = off, the default; at
+                               most 8) from stream 2 of the counter generator, a front with
+                               ||(S - H) W||_F > 10 tol depth ||S W||_F (depth = depth of its HSS tree, at
+                               least 1) samples again with r + dr while r + dr <= rmax.  Needs tol > 0. */
 } hss_factor_opts;
 
 enum { HSS_CAP_KEEP = 0, HSS_CAP_ACCEPT = 1 };
@@ -187,6 +192,7 @@ typedef struct hss_factor_info {
     int rounds;
     int nfronts;
     int capped_fronts;
+    int probe_regrown;      /* sampling rounds added because a residual probe failed */
 } hss_factor_info;
 int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info);
 

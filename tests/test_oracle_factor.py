@@ -203,3 +203,40 @@ def test_partition_scheme_matters_for_anisotropic_diffusion():
     assert its[1e-3, "hslab"] is not None and its[1e-3, "vslab"] is None, its
     assert its[1e6, "hslab"] is not None and its[1e6, "vslab"] is not None, its
     assert its[1e6, "vslab"] <= 30 and its[1e6, "hslab"] <= its[1e-3, "hslab"], its
+
+
+# --- residual probe of accepted approximants (fallback check of the learned widths)
+
+def test_probe_leaves_healthy_runs_unchanged():
+    """With oversampling 10 every front passes the probe: the approximants are
+    those of the run without it, and each probe ratio is within its threshold."""
+    mesh, A, nd, Acsr = _setup(2, (16, 16), 2, kind="helm")
+    f0 = oracle.factor(Acsr, nd, tol=1e-6, seed=1, rmax=96, keep_h=True)
+    f1 = oracle.factor(Acsr, nd, tol=1e-6, seed=1, rmax=96, keep_h=True, probe=4)
+    for b in f0["boxes"]:
+        assert np.array_equal(f0["boxes"][b]["H"], f1["boxes"][b]["H"])
+    recs = [r for r in f1["log"] if r.get("nnodes", 1) > 1]
+    assert recs and all(r["probe_regrown"] == 0 for r in recs)
+    for r in recs:
+        assert r["probe_rel"] <= oracle.probe_threshold(1e-6, r["rep"]["nodes"])
+
+
+def test_probe_catches_undersampled_fronts():
+    """Without oversampling (p = 0) the rank test never asks for more samples;
+    the probe does, and the regrown fronts pass it at their final width."""
+    mesh, A, nd, Acsr = _setup(2, (16, 16), 2, kind="helm")
+    kw = dict(tol=1e-6, seed=1, r0=8, rmax=96, oversample=0)
+    f0 = oracle.factor(Acsr, nd, **kw)
+    f1 = oracle.factor(Acsr, nd, probe=4, **kw)
+    recs = [r for r in f1["log"] if r.get("nnodes", 1) > 1]
+    assert sum(r["probe_regrown"] for r in recs) > 0
+    assert all(r["rounds"] == 1 for r in f0["log"] if r.get("nnodes", 1) > 1)
+    for r in recs:
+        if not r["capped"]:
+            assert r["probe_rel"] <= oracle.probe_threshold(1e-6, r["rep"]["nodes"])
+    b = dg.random_rhs(A.n, 1, 0)[:, 0]
+    its = []
+    for fac in (f0, f1):
+        _, info = oracle.fgmres(lambda v: Acsr @ v, lambda v: oracle.apply(fac, v), b, rtol=1e-8, maxit=300)
+        its.append(info["iters"] if info["converged"] else 10 ** 6)
+    assert its[1] < its[0], its
