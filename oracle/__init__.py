@@ -19,6 +19,8 @@ FP64, with no blocking, fusion or reordering beyond what the paper states:
   mlp.py       rank-prediction MLP of the learned-rank form (not in the paper):
                forward, loss gradient, Adam, standardisation
   ilu.py       block ILU(0), the comparison preconditioner of Sec. 5
+  merge.py     structured merge (reading R2): eq. (37) block solve with the
+               second Schur complement compressed (Algorithms 1 and 3)
 
 Pins (tests/test_oracle_*.py): exact LDM^t with compression off equals a dense
 LU solve; GMRES converges in one iteration then; ID error within the strong
@@ -26,7 +28,9 @@ rank-revealing bound of the SVD and |P| <= 2; HSS recovery of matrices that are
 HSS by construction; Schur complement equals the inverse of the trailing block
 of the front inverse; brute-force interior/boundary sets on tiny meshes;
 unpreconditioned GMRES history equals SciPy's; ILU(0)'s product equals A on
-A's pattern, is exact on a block-tridiagonal chain and equals scalar ILU(0).
+A's pattern, is exact on a block-tridiagonal chain and equals scalar ILU(0);
+the structured merge's block solve is the exact inverse of the interior block
+perturbed by H~ - S~ (every parent and the top block).
 """
 from .nd import nd_order                      # noqa: F401
 from .idecomp import interp_decomp            # noqa: F401

@@ -5,6 +5,8 @@ M(B,I)^t = F_ii^-1 F_ib = W, solving L D M^t y = x box by box is:
   forward, in elimination order:  t_sigma = F_ii^-1 x_I ;  x_B -= F_bi t_sigma
   top:                            x_top = A^(0)^-1 x_top           (eq. (36))
   backward, reverse order:        x_I = t_sigma - W x_B
+Under the structured merge (reading R2) F_ii^-1 and A^(0)^-1 are the
+approximate inverses of eq. (37) (Algorithms 1 and 3), stored densely.
 Vectors are in the original dof numbering; x may have several columns.
 """
 import numpy as np
@@ -24,12 +26,15 @@ def apply(fac, x):
         f = fac["boxes"][b]
         if I.size == 0:
             continue
-        tb = sla.lu_solve(f["lu"], w[I])
+        tb = f["Xinv"] @ w[I] if f.get("Xinv") is not None else sla.lu_solve(f["lu"], w[I])
         w[B] -= f["Fbi"] @ tb
         t[b] = tb
     top = fac["top"]
     if top.size:
-        w[top] = sla.lu_solve(fac["top_lu"], w[top])
+        if fac.get("top_inv") is not None:
+            w[top] = fac["top_inv"] @ w[top]
+        else:
+            w[top] = sla.lu_solve(fac["top_lu"], w[top])
     for b in nd["order"][::-1]:
         b = int(b)
         I, B = nd["iset"][b], nd["bset"][b]

@@ -19,6 +19,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 from .hss import hss_tree_for_front, hss_compress
+from .merge import block_inverse, interior_split
 
 
 def csr_from_bsr(nb, bs, row_ptr, col_idx, val):
@@ -54,16 +55,26 @@ def box_schur(A_csr, nd, b):
 
 
 def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=10, rmax=None,
-           keep_h=False, cap="keep", probe=0, r_init=None):
+           keep_h=False, cap="keep", probe=0, r_init=None, merge="dense"):
     """Returns a dict with the per-box factors, the top block LU and logs.
     rmax caps the HSS sample width; cap is the policy for a front whose ranks
     outgrow the cap ("keep": H = S; "accept": the approximant from the samples
     it has, see hss.py); probe > 0 checks each accepted approximant on that
     many +-1 vectors and samples again when the check fails (hss.py);
     r_init (optional) maps a box id to its first sample width (the learned
-    widths), in place of r0; keep_h stores each approximant H."""
+    widths), in place of r0; keep_h stores each approximant H.
+    merge="dense" is reading R1; merge="structured" is reading R2: each
+    parent's interior block and the top block are inverted by the block solve
+    of eq. (37) with the second Schur complement compressed (merge.py).  The
+    apply then uses those approximate inverses (stored densely as "Xinv" and
+    "top_inv")."""
     if cap not in ("keep", "accept"):
         raise ValueError("cap policy: 'keep' or 'accept'")
+    if merge not in ("dense", "structured"):
+        raise ValueError("merge: 'dense' or 'structured'")
+    structured = merge == "structured" and compress
+    ckw = dict(r0=r0, dr=dr, oversample=oversample, rmax=rmax, cap=cap, probe=probe)
+    nbox = int(nd["nbox"])
     A = A_csr.tocsr()
     boxes = {}
     H = {}
@@ -85,14 +96,23 @@ def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=
                 F[np.ix_(fm, fm)] = H.pop(c)
         Fii, Fib = F[:ni, :ni], F[:ni, ni:]
         Fbi, Fbb = F[ni:, :ni], F[ni:, ni:]
-        if ni > 0:
+        rec = dict(box=b, level=int(nd["level"][b]), ni=ni, nb=B.size)
+        Xinv = None
+        if ni > 0 and structured and not nd["is_leaf"][b]:
+            # Algorithm 1: block solve of eq. (37), S~ of the second child compressed
+            n1, dofs2 = interior_split(nd, b)
+            nodes2 = hss_tree_for_front(nd, int(nd["child"][b][1]), dofs2)
+            Xinv, minfo = block_inverse(Fii, n1, nodes2, tol, seed, nbox + b, **ckw)
+            rec["tilde"] = minfo
+            lu = None
+            W = Xinv @ Fib
+        elif ni > 0:
             lu = sla.lu_factor(Fii)
             W = sla.lu_solve(lu, Fib)
         else:
             lu = None
             W = np.zeros((0, B.size))
         S = Fbb - Fbi @ W
-        rec = dict(box=b, level=int(nd["level"][b]), ni=ni, nb=B.size)
         if compress and B.size > 0:
             nodes = hss_tree_for_front(nd, b)
             rb = r0 if r_init is None else max(1, min(int(r_init[b]), rmax if rmax is not None else 1 << 30))
@@ -105,7 +125,7 @@ def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=
         else:
             Hs = S.copy()
         H[b] = Hs
-        boxes[b] = dict(lu=lu, Fbi=Fbi.copy(), W=W, S=S, F=F)
+        boxes[b] = dict(lu=lu, Fbi=Fbi.copy(), W=W, S=S, F=F, Xinv=Xinv)
         if keep_h:
             boxes[b]["H"] = Hs.copy()
         log.append(rec)
@@ -115,5 +135,12 @@ def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=
     A0 = A[top][:, top].toarray()
     A0[np.ix_(nd["fmap"][0], nd["fmap"][0])] = H.pop(0)
     A0[np.ix_(nd["fmap"][1], nd["fmap"][1])] = H.pop(1)
-    top_lu = sla.lu_factor(A0) if top.size else None
-    return dict(boxes=boxes, top=top, top_lu=top_lu, A0=A0, log=log, nd=nd)
+    top_inv, top_info = None, None
+    if structured and top.size:
+        # Algorithm 3: S^1 = H^1 inverted, S~^2 = H^2 - A^(2,1) (H^1)^-1 A^(1,2) compressed
+        top_inv, top_info = block_inverse(A0, B0.size, hss_tree_for_front(nd, 1), tol, seed, 2 * nbox, **ckw)
+        top_lu = None
+    else:
+        top_lu = sla.lu_factor(A0) if top.size else None
+    return dict(boxes=boxes, top=top, top_lu=top_lu, top_inv=top_inv, top_info=top_info, A0=A0, log=log, nd=nd,
+                merge=merge)

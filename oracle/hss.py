@@ -49,13 +49,18 @@ from .idecomp import interp_decomp
 from .rademacher import rademacher
 
 
-def hss_tree_for_front(nd, box):
-    """HSS tree over the index set B^box (in its stored order).
+def hss_tree_for_front(nd, box, dofs=None):
+    """HSS tree over the index set B^box (in its stored order), or over a
+    subset `dofs` of it (kept in that order; the structured merge compresses
+    blocks indexed by B^box n I^parent).
 
     Returns a list of nodes; each node is a dict with 'lo', 'hi' (range inside
-    B^box), 'children' (node indices) and 'depth'.  The last node is the root.
+    the index set), 'children' (node indices) and 'depth'.  The last node is
+    the root.
     """
-    bs_dofs = nd["bset"][box]
+    bs_dofs = nd["bset"][box] if dofs is None else np.asarray(dofs)
+    if bs_dofs.size == 0:
+        return []
     dfs_pos = np.empty(nd["dfs_dof"].size, dtype=np.int64)
     dfs_pos[nd["dfs_dof"]] = np.arange(nd["dfs_dof"].size)
     pos = dfs_pos[bs_dofs]                 # ascending (B^box is DFS ordered)
