@@ -619,7 +619,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
                                            kmax_done, s)))
                 return rc;
         }
-        // ---- residual probe of the approximants accepted this round: a front
+        // ---- residual probe of the approximants accepted in this sampling round: a front
         // with ||(S - H) W|| > 10 tol depth ||S W|| samples again with r + dr
         if (o.probe > 0) {
             std::vector<ProbeItem> pit;

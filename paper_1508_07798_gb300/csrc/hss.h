@@ -13,7 +13,7 @@ template <class T> struct CompFront {
     const T *S;       // Schur complement inside the front (column-major)
     long lds;         // its leading dimension (the front size)
     int nb;           // order of S
-    int r;            // sample width of this round
+    int r;            // sample width of the current sampling round
     int box;          // front id of the test-matrix counter
     long yoff, zoff;  // samples Y = S Omega, Z = S^t Psi (nb x r, ld nb) in the sample buffer
 };
