@@ -625,14 +625,14 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             std::vector<ProbeItem> pit;
             std::vector<ProbeFront> pfr;
             std::vector<int> pc;   // round-front index of each probed front
-            long rows = 0;
+            long rows = 0;   // doubles of row sums: per front, column tiles x rows x 2 PROBE_MAX
             for (int c = 0; c < nc; ++c) {
                 if (!done[c] || dense[c]) continue;
                 const int f = active[c].f, slot = (int)pc.size();
-                const long ra = rows * 2 * PROBE_MAX;
+                const long ra = rows;
                 pc.push_back(c);
                 pfr.push_back({f, ra});
-                rows += fr[f].nb;
+                rows += (long)cdiv(fr[f].nb, PROBE_NT) * fr[f].nb * 2 * PROBE_MAX;
                 for (int r0 = 0; r0 < fr[f].nb; r0 += PROBE_NT)
                     for (int c0 = 0; c0 < fr[f].nb; c0 += PROBE_NT)
                         pit.push_back({slot, f, t->box_local[boxes[f]], r0, c0, ra});
@@ -642,9 +642,8 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
                 ProbeFront *d_pfr;
                 double *d_acc, *d_rowacc;
                 if ((rc = W.up(pit, &d_pit)) || (rc = W.up(pfr, &d_pfr)) || (rc = W.dalloc(2 * pc.size(), &d_acc)) ||
-                    (rc = W.dalloc((size_t)rows * 2 * PROBE_MAX, &d_rowacc)))
+                    (rc = W.dalloc((size_t)rows, &d_rowacc)))
                     return rc;
-                HSS_CUDA(cudaMemsetAsync(d_rowacc, 0, sizeof(double) * rows * 2 * PROBE_MAX, s));
                 if ((rc = launch_hss_probe<T>(d_pit, (int)pit.size(), d_pfr, (int)pfr.size(), d_ef, arena, o.seed,
                                               o.probe, d_rowacc, d_acc, s)))
                     return rc;

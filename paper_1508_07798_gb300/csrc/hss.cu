@@ -589,6 +589,7 @@ __global__ void __launch_bounds__(PROBE_NT) k_hss_probe(const ProbeItem *__restr
                                                         const T *__restrict__ arena, uint64_t seed, int nprobe,
                                                         double *__restrict__ rowacc) {
     __shared__ T w[PROBE_NT * PROBE_MAX];
+    __shared__ long hcol[PROBE_NT];
     const ProbeItem it = items[blockIdx.x];
     const ExpandFront E = ef[it.f];
     const T *S = static_cast<const T *>(E.S);
@@ -598,18 +599,19 @@ __global__ void __launch_bounds__(PROBE_NT) k_hss_probe(const ProbeItem *__restr
         const int jj = e / nprobe, q = e - jj * nprobe;
         w[jj * PROBE_MAX + q] = (T)rademacher(seed, 2, it.box, it.col0 + jj, q);
     }
+    for (int jj = threadIdx.x; jj < jn; jj += PROBE_NT) hcol[jj] = (long)E.pn * E.fmap[it.col0 + jj];
     __syncthreads();
     const int i = it.row0 + (int)threadIdx.x;
     if (i >= E.nb) return;
-    const long hrow = E.fmap[i];
+    const T *Hr = Mp + E.fmap[i];
+    const T *Sr = S + i + E.lds * (long)it.col0;
     T sw[PROBE_MAX], dw[PROBE_MAX];
 #pragma unroll
     for (int q = 0; q < PROBE_MAX; ++q) sw[q] = dw[q] = T(0);
 #pragma unroll 8
     for (int jj = 0; jj < jn; ++jj) {
-        const int j = it.col0 + jj;
-        const T sv = S[i + E.lds * j];
-        const T dv = sv - Mp[hrow + (long)E.pn * E.fmap[j]];
+        const T sv = Sr[E.lds * jj];
+        const T dv = sv - Hr[hcol[jj]];
 #pragma unroll
         for (int q = 0; q < PROBE_MAX; ++q)
             if (q < nprobe) {
@@ -618,12 +620,13 @@ __global__ void __launch_bounds__(PROBE_NT) k_hss_probe(const ProbeItem *__restr
                 dw[q] = fma(dv, wq, dw[q]);
             }
     }
-    double *ra = rowacc + it.rowacc + (long)i * 2 * PROBE_MAX;
+    // this column tile's share of row i: region [column tile][row][2 x PROBE_MAX]
+    double *ra = rowacc + it.rowacc + ((long)(it.col0 / PROBE_NT) * E.nb + i) * 2 * PROBE_MAX;
 #pragma unroll
     for (int q = 0; q < PROBE_MAX; ++q)
         if (q < nprobe) {
-            atomicAdd(ra + q, (double)sw[q]);
-            atomicAdd(ra + PROBE_MAX + q, (double)dw[q]);
+            ra[q] = (double)sw[q];
+            ra[PROBE_MAX + q] = (double)dw[q];
         }
 }
 
@@ -633,15 +636,19 @@ __global__ void __launch_bounds__(PROBE_NT) k_hss_probe_norms(const ProbeFront *
                                                               double *__restrict__ acc) {
     __shared__ double red[2][PROBE_NT / 32];
     const ProbeFront P = pf[blockIdx.x];
-    const int nb = ef[P.f].nb;
+    const int nb = ef[P.f].nb, ntc = (nb + PROBE_NT - 1) / PROBE_NT;
     double num = 0.0, den = 0.0;
-    for (int i = threadIdx.x; i < nb; i += PROBE_NT) {
-        const double *ra = rowacc + P.rowacc + (long)i * 2 * PROBE_MAX;
+    for (int i = threadIdx.x; i < nb; i += PROBE_NT)
         for (int q = 0; q < nprobe; ++q) {
-            den += ra[q] * ra[q];
-            num += ra[PROBE_MAX + q] * ra[PROBE_MAX + q];
+            double sv = 0.0, dv = 0.0;
+            for (int ct = 0; ct < ntc; ++ct) {   // column tiles in order: a fixed summation order
+                const double *ra = rowacc + P.rowacc + ((long)ct * nb + i) * 2 * PROBE_MAX;
+                sv += ra[q];
+                dv += ra[PROBE_MAX + q];
+            }
+            den += sv * sv;
+            num += dv * dv;
         }
-    }
     for (int o = 16; o > 0; o >>= 1) {
         num += __shfl_xor_sync(0xffffffffu, num, o);
         den += __shfl_xor_sync(0xffffffffu, den, o);
