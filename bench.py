@@ -595,9 +595,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # the reference arm is the CPU oracle (no reference implementation exists)
-        for _ in range(min(args.warmup, 1)):
-            pass
+        # the reference arm is the CPU oracle (no reference implementation
+        # exists); it keeps no state between solves, so there is nothing to warm
         ts, its = [], None
         for _ in range(args.steps):
             ms, info = cpu_baseline_run(0)

@@ -1,0 +1,59 @@
+"""Host-side helpers of bench.py (no GPU): roofline arithmetic, the peaks
+file, and the rule that a committed ncu traffic figure is used only while the
+kernel's source is unchanged."""
+import hashlib
+import importlib
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture
+def bench():
+    sys.path.insert(0, ROOT)
+    try:
+        yield importlib.import_module("bench")
+    finally:
+        sys.path.remove(ROOT)
+
+
+def test_roofline_arithmetic(bench):
+    pk = dict(hbm=6000.0, src="measured")
+    # 10 launches, 2 ms in all, 1e9 bytes of algorithmic traffic per launch: 5e12 B/s
+    r = bench.roofline_of("apply", 2.0, 10, 1e10, 8.0, pk)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(5000.0) and r["frac"] == pytest.approx(5000.0 / 6000.0)
+    assert r["share"] == pytest.approx(0.25) and r["avg_launch_us"] == pytest.approx(200.0)
+    # 4 launches, 1 ms in all, 2e9 flops per launch: 8e12 flop/s against the FP32 SIMT peak
+    g = bench.roofline_of("gj_panel_f32", 1.0, 4, 8e9, 4.0, pk)
+    assert g["bound"] == "alu" and g["achieved"] == pytest.approx(8.0)
+    assert g["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12) and g["traffic"] is None
+    d = bench.roofline_of("gemm_f64", 1.0, 1, 1e9, 1.0, pk)
+    assert d["peak"] == 1.25 and d["achieved"] == pytest.approx(1.0)
+
+
+def test_peaks_file_and_fallback(bench, tmp_path, monkeypatch):
+    pk = bench.peaks()
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert pk["src"] == "measured" and pk["hbm"] > 1000
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    fb = bench.peaks()
+    assert fb["src"] == "fallback" and fb["hbm"] == 6800.0 and fb["bf16"] == 1900.0
+
+
+def test_profiled_traffic_only_for_the_profiled_source(bench, tmp_path, monkeypatch):
+    src = tmp_path / "paper_1508_07798_gb300" / "csrc" / "gemm.cu"
+    src.parent.mkdir(parents=True)
+    src.write_text("// kernel source\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    prof = tmp_path / "profiles" / "k_gemm_f32_dram_helmholtz64_p2.md"
+    prof.parent.mkdir()
+    prof.write_text(f"traffic_bytes_per_launch: 1234\nkernel_source_sha256_prefix: {sha[:16]}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("gemm_f32") == 1234
+    assert bench.profiled_traffic("apply") is None
+    src.write_text("// kernel source, changed\n")
+    assert bench.profiled_traffic("gemm_f32") is None
