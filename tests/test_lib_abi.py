@@ -98,3 +98,19 @@ def test_factor_defaults_overwrite_every_field(lib):
     assert o.r_init is None and o.cap_policy == 0 and o.autotune == 0 and o.keep_schur == 0 and o.seed == 0
     assert o.rmax == 96 and o.probe == 0
     assert hssnd.factor_opts(cap_policy="accept").cap_policy == 1
+
+
+def test_new_entry_points_reject_null_arguments_without_gpu(lib):
+    from paper_1508_07798_gb300 import hssnd
+    L = hssnd._lib
+    out = ctypes.c_void_p()
+    assert L.ilu0_factor(None, None, ctypes.byref(out)) == hssnd.HSS_EINVAL
+    assert L.ilu0_factor(None, None, None) == hssnd.HSS_EINVAL
+    assert L.ilu0_apply(None, 1, None, 1, None, 1, None) == hssnd.HSS_EINVAL
+    assert L.fgmres_solve_ilu0(None, None, 1, None, 1, None, 1, None, None, None) == hssnd.HSS_EINVAL
+    assert L.hss_factor_apply_plan(None, 0, None, None) == -hssnd.HSS_EINVAL
+    # a block size outside [1, 64] is refused before any device access
+    bad = hssnd.hss_bsr(4, 65, 1, 1, 1)
+    assert L.ilu0_factor(ctypes.byref(bad), None, ctypes.byref(out)) == hssnd.HSS_EINVAL
+    assert b"block size" in L.hss_last_error()
+    L.ilu0_destroy(None)
