@@ -61,15 +61,30 @@ def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_s=d["bf16_tflops_sustained"], src="measured")
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_s=d["bf16_tflops_sustained"],
+                    sm_mhz=float(d.get("sm_max_mhz", 2070.0)), src="measured")
     except Exception:
-        return dict(hbm=6800.0, bf16=1900.0, bf16_s=1700.0, src="fallback")
+        return dict(hbm=6800.0, bf16=1900.0, bf16_s=1700.0, sm_mhz=2070.0, src="fallback")
 
 
-# FP64 and FP32 SIMT peaks from unit counts and clock: 152 SMs x FMA/clk/SM x 2 x 2.07 GHz.
-# FP32: 128 FMA/clk/SM -> 80.5 TFLOP/s.  FP64: the nominal 1.25 TFLOP/s of GB300.
-FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP32 SIMT peak from unit counts and clock: SMs (read from the device) x 128
+# FP32 FMA/clk/SM x 2 flop x the maximum SM clock (from the peaks file, else
+# GB300's 2,070 MHz).  FP64: the nominal 1.25 TFLOP/s of GB300.
 FP64_TFLOPS = 1.25
+
+
+def with_simt_peak(pk, sms):
+    """pk plus the derived FP32 SIMT peak for a device with `sms` SMs."""
+    out = dict(pk)
+    out["sms"] = int(sms)
+    out["fp32"] = sms * 128 * 2 * pk["sm_mhz"] * 1e6 / 1e12
+    out["fp32_src"] = f"derived: {sms} SMs x 128 FP32 FMA/clk x 2 x {pk['sm_mhz']:.0f} MHz"
+    return out
+
+
+def device_sms(dev):
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
 
 
 def max_over_ranks(values, device):
@@ -86,20 +101,22 @@ def max_over_ranks(values, device):
 def roofline_of(kernel, ms, cnt, work, total_ms, pk):
     """Roofline entry of one kernel class: FLOP-counted classes (GEMMs and the
     Gauss-Jordan panels) against the FP32/FP64 arithmetic peak, byte-counted
-    classes (apply, SpMV) against the measured HBM bandwidth."""
+    classes (apply, SpMV) against the measured HBM bandwidth.  pk: peaks() with
+    the FP32 SIMT peak of the device (with_simt_peak)."""
     per_launch_s = ms / cnt * 1e-3
     if kernel.startswith("gemm") or kernel.startswith("gj_panel"):
         f32 = kernel.endswith("f32")
-        peak = FP32_SIMT_TFLOPS if f32 else FP64_TFLOPS
+        peak = pk["fp32"] if f32 else FP64_TFLOPS
         ach = work / cnt / per_launch_s / 1e12
         return dict(kernel=kernel, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
                     traffic=profiled_traffic(kernel), launches=cnt, avg_launch_us=ms / cnt * 1e3,
                     share=ms / total_ms,
-                    peak_source="derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz" if f32
-                    else "nominal GB300 FP64 1.25 TFLOP/s")
+                    peak_source=pk["fp32_src"] if f32 else "nominal GB300 FP64 1.25 TFLOP/s")
     ach = work / cnt / per_launch_s / 1e9
     return dict(kernel=kernel, bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
-                traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms, peak_source=pk["src"])
+                traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
+                peak_source=f"{pk['src']} (MEASURED_PEAKS.json hbm_gbs)" if pk["src"] == "measured"
+                else pk["src"])
 
 
 def profiled_traffic(kernel):
@@ -307,7 +324,7 @@ def bench_ours(args, rank, world):
 
     # ---- apply GB/s: 20 applies of the last factor of each form, L2 flushed between
     apply = {}
-    pk = peaks()
+    pk = with_simt_peak(peaks(), device_sms(dev))
     for prec in args.forms.split(","):
         if prec == "fp32_learned":
             continue      # same factor storage and apply kernels as fp32
@@ -543,7 +560,7 @@ def bench_batched(args, rank, world):
     kernels = {k: dict(ms=round(v[0], 3), launches=v[1]) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
     tracked = {k: v for k, v in prof.items() if v[2] > 0}
     dom = max(tracked, key=lambda k: tracked[k][0])
-    pk = peaks()
+    pk = with_simt_peak(peaks(), device_sms(dev))
     roof = roofline_of(dom, *prof[dom], sum(v[0] for v in prof.values()), pk)
     value = statistics.mean(times)
     e2e_v = statistics.mean(ets)
@@ -580,12 +597,20 @@ def cpu_baseline_run(seed=0):
 
 
 def cpu_cores():
+    """Host cores this process may run on (the oracle's BLAS and NumPy use
+    them all)."""
     try:
-        from threadpoolctl import threadpool_info
-        n = max((d.get("num_threads", 1) for d in threadpool_info()), default=1)
-        return int(n)
+        return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count()
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return int(max((d.get("num_threads", 1) for d in threadpool_info()), default=1))
+    except Exception:
+        return None
 
 
 def main():
@@ -607,7 +632,8 @@ def main():
                     ms_per_step=v, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
                     data="synthetic", impl="reference",
                     config=dict(workload=WORKLOAD, dofs=N_ELEM * N_ELEM * (P_DEG + 1) ** 2, id_tol=TOL, rtol=RTOL),
-                    cpu_baseline=dict(kind="oracle", cores=cpu_cores(), value=v, unit="ms",
+                    cpu_baseline=dict(kind="oracle", cores=cpu_cores(), blas_threads=blas_threads(), value=v,
+                                      unit="ms",
                                       sample="one full 36,864-dof solve per step (nd + factor + FGMRES), "
                                              "warm-up skipped (no state to warm)", iters=its),
                     e2e=dict(value=v, unit="ms", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -632,7 +658,7 @@ def main():
     res = bench_ours(args, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         ms, info = cpu_baseline_run(0)
-        res["cpu_baseline"] = dict(value=ms, unit="ms", cores=cpu_cores(), kind="oracle",
+        res["cpu_baseline"] = dict(value=ms, unit="ms", cores=cpu_cores(), blas_threads=blas_threads(), kind="oracle",
                                    sample="one full 36,864-dof solve (nd + factor + FGMRES), seed 0",
                                    iters=info["iters"])
     if rank == 0:

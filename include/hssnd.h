@@ -172,8 +172,9 @@ int hss_tree_export(const hss_tree *t, int *level, int *parent, int *child0, int
  * A^(0) = [[H^1, A12], [A21, H^2]] (eq. (36)).  The factor keeps, per front,
  * F_ii^-1, -F_bi F_ii^-1 and F_ii^-1 F_ib in FP64 (or FP32 with
  * precision = HSS_FP32).  Synchronizes `stream` once per tree level (rank
- * decisions).  Errors: HSS_EINVAL, HSS_ENOMEM, HSS_ESINGULAR (box id in
- * hss_last_error), HSS_ECUDA. */
+ * decisions).  Errors: HSS_EINVAL (also when a stored value of A is NaN or
+ * infinite: a device scan of A's values, reported at the end of the call),
+ * HSS_ENOMEM, HSS_ESINGULAR (box id in hss_last_error), HSS_ECUDA. */
 int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_factor_opts *opts,
                void *stream, hss_factor_t **out);
 
@@ -214,7 +215,8 @@ int hss_apply(const hss_factor_t *f, int nrhs, const double *x, int ldx, double 
  * (the GEMM of the FP32 form, exposed for testing and reuse).  engine: 0 SIMT
  * FMA; 1 tcgen05 TF32 with the three-product hi/lo split; 2 tcgen05 single
  * TF32.  No counterpart in the paper (a building block of eq. (32)'s update).
- * Synchronizes `stream`; HSS_ETIMEOUT if a bounded tensor-core wait expired. */
+ * k = 0 gives C = beta C with every engine.  Synchronizes `stream`;
+ * HSS_ETIMEOUT if a bounded tensor-core wait expired. */
 int hss_gemm_f32(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
                  float alpha, float beta, int engine, void *stream);
 
@@ -234,15 +236,19 @@ int hss_gemm_f32(int m, int n, int k, const float *A, int lda, const float *B, i
  * engines 1 and 2) and at most HSS_GEMM_STATIC_MAX_TILES tiles fit, e.g.
  * m = n = 8192 with engine 0, 16384 with engines 1 and 2; a larger m x n
  * returns HSS_EINVAL with the tile count in hss_last_error().
+ * k = 0 gives C = beta C with every engine and uses no tile records (no
+ * tile limit).
  * Nothing in the scratch has to start at zero: each call writes the
  * descriptor, tile list and a cleared timeout flag on `stream` before the
  * GEMM reads them.  There is one array per device: two calls that overlap in
  * time (on different streams or host threads) race on it and give undefined
- * results; callers serialize them.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, which can load the module);
- * a caller that wants that setup out of a timed or restricted region makes
- * one small call first.  The optional event timing of hss_profile_enable
- * creates CUDA events: leave it off where nothing may be allocated.
+ * results; callers serialize them.  The first call on a device, whatever its
+ * engine, does all one-time setup of that device: it looks up the array's
+ * device address (cudaGetSymbolAddress), loads every kernel this call can
+ * launch and sets the tensor-core kernel's shared-memory attribute.  A caller
+ * that wants that setup out of a timed or restricted region makes one small
+ * call first.  The optional event timing of hss_profile_enable creates CUDA
+ * events: leave it off where nothing may be allocated.
  * Synchronizes `stream`; HSS_ETIMEOUT if a bounded tensor-core wait expired,
  * HSS_ECUDA if the address lookup or a launch failed. */
 #define HSS_GEMM_STATIC_MAX_TILES 16384
@@ -407,8 +413,20 @@ int fgmres_history(int rhs, double *hist, int cap);
  * ms, the launch count and the algorithmic work the library attributes to
  * those launches (flops for GEMM classes, bytes for apply/SpMV classes, 0 when
  * not tracked).  Reading synchronizes the pending events.
- * hss_profile_reset clears the classes. */
+ * hss_profile_reset clears the classes.
+ * hss_alloc_count: number of memory requests the library has served since it
+ * was loaded (all threads): every device allocation (cudaMalloc), every
+ * chunk or pinned staging buffer taken from its scratch pool, every piece of
+ * call scratch (device bump allocation or upload staging).  A call that
+ * leaves it unchanged allocated nothing.
+ * hss_tc_timeout_selftest: runs one tile of the tensor-core GEMM kernel on an
+ * internal 128 x 128 x 32 problem with the MMAs left out, so its bounded
+ * mbarrier wait expires after spin_limit polls (1 .. 2^26); returns
+ * HSS_ETIMEOUT when the kernel reported the expiry (the expected result),
+ * with nothing left in flight and the context usable.  Test hook. */
 long hss_launch_count(void);
+long hss_alloc_count(void);
+int hss_tc_timeout_selftest(long spin_limit, void *stream);
 int hss_profile_enable(int on);
 int hss_profile_reset(void);
 int hss_profile_read(int idx, char *name, int cap, double *total_ms, long *launches, double *work);

@@ -1,6 +1,7 @@
 // Error state, option defaults and small shared host utilities of libhssnd.
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -9,6 +10,10 @@
 namespace hssnd {
 
 static thread_local std::string g_last_error;
+
+// Memory requests served by the library (diagnostics: hss_alloc_count).
+static std::atomic<long> g_alloc_requests{0};
+void count_alloc() { g_alloc_requests.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -22,6 +27,7 @@ int DevBuf::alloc(size_t nbytes) {
     if (nbytes <= bytes && p) return HSS_OK;
     release();
     if (nbytes == 0) nbytes = 1;
+    count_alloc();
     cudaError_t e = cudaMalloc(&p, nbytes);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -55,6 +61,7 @@ int current_device() {
 }  // namespace
 
 int scratch_cache_take_device(size_t min_bytes, size_t want_bytes, DevBuf &out) {
+    count_alloc();
     const int d = current_device();
     {
         std::lock_guard<std::mutex> lk(cache().mu);
@@ -86,6 +93,7 @@ void scratch_cache_give_device(DevBuf &&b) {
 }
 
 void *scratch_cache_take_pinned(size_t min_bytes, size_t want_bytes, size_t &got) {
+    count_alloc();
     {
         std::lock_guard<std::mutex> lk(cache().mu);
         auto &v = cache().pin;
@@ -130,6 +138,7 @@ Work::~Work() {
 }
 
 int Work::dalloc_bytes(size_t bytes, void **out) {
+    count_alloc();
     bytes = (bytes + 255) & ~(size_t)255;
     while (ci < chunks.size() && cur + bytes > chunks[ci].bytes) {
         ++ci;
@@ -188,6 +197,8 @@ void Work::reset() {
 extern "C" {
 
 const char *hss_last_error(void) { return hssnd::g_last_error.c_str(); }
+
+long hss_alloc_count(void) { return hssnd::g_alloc_requests.load(std::memory_order_relaxed); }
 
 void hss_nd_opts_default(hss_nd_opts *o) {
     if (!o) return;

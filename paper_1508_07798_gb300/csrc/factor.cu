@@ -24,6 +24,17 @@ namespace hssnd {
 
 namespace {
 
+// flag = 1 when some stored value of A is NaN or infinite (the block count
+// comes from row_ptr[nb] on the device, so the host needs no read-back)
+__global__ void k_check_finite(const int *__restrict__ row_ptr, int nb, int bs2, const double *__restrict__ val,
+                               int *__restrict__ flag) {
+    const long tot = (long)row_ptr[nb] * bs2;
+    bool bad = false;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += (long)gridDim.x * blockDim.x)
+        bad |= !isfinite(val[g]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
 template <class T> struct StageCtx {
     std::vector<FrontDev> fronts;       // stage-local fronts
     std::vector<int> boxes;             // box of each front (-1: top)
@@ -748,11 +759,18 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     T *keep = F->keep.as<T>();
     // zero-pivot flags of every front of every stage and of the top blocks,
     // read once at the end of the call
+    // (one more flag after them: a NaN or infinite value in A)
     size_t nstat = (size_t)ninst;
     for (const auto &st : t->stages) nstat += st.size();
     ScratchPtr d_status_all;
-    if ((rc = WL.dalloc_bytes(sizeof(int) * std::max(nstat, (size_t)1), &d_status_all.p))) return rc;
-    HSS_CUDA(cudaMemsetAsync(d_status_all.p, 0, sizeof(int) * std::max(nstat, (size_t)1), s));
+    if ((rc = WL.dalloc_bytes(sizeof(int) * (nstat + 1), &d_status_all.p))) return rc;
+    HSS_CUDA(cudaMemsetAsync(d_status_all.p, 0, sizeof(int) * (nstat + 1), s));
+    {
+        HSS_PROF("check_finite", s);
+        k_check_finite<<<2 * 152, 256, 0, s>>>(A->row_ptr, A->nb, A->bs * A->bs, A->val,
+                                                d_status_all.as<int>() + nstat);
+        HSS_CHECK_LAUNCH("k_check_finite");
+    }
     std::vector<int> status_box;   // box id per flag (-1 - i: top block of instance i)
     Work W(s);
     HSS_CUDA(cudaMemsetAsync(d_tcerr.p, 0, sizeof(int), s));
@@ -878,10 +896,14 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
                                      F->d_topset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, eng, W, s)))
             return rc;
-        std::vector<int> hst(status_box.size());
+        std::vector<int> hst(nstat + 1);
         HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status_all.p, sizeof(int) * hst.size(), cudaMemcpyDeviceToHost, s));
         HSS_CUDA(cudaStreamSynchronize(s));
-        for (size_t q = 0; q < hst.size(); ++q)
+        if (hst[nstat]) {
+            set_error("hss_factor: the matrix A holds a NaN or infinite value");
+            return HSS_EINVAL;
+        }
+        for (size_t q = 0; q < status_box.size(); ++q)
             if (hst[q]) {
                 const int b = status_box[q];
                 if (b >= 0)

@@ -125,6 +125,36 @@ void gemm_tiles_for(const GemmDesc<T> &d, int desc_index, std::vector<GemmTile> 
     }
 }
 
+// C = alpha * 0 + beta * C for a product with k = 0 (no descriptor, no
+// allocation; the same arithmetic as k_gemm with an empty K loop).
+__global__ void k_gemm_k0(float *__restrict__ C, int ldc, int m, int n, float alpha, float beta) {
+    const long tot = (long)m * n;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(g % m), j = (int)(g / m);
+        float *c = C + i + (long)j * ldc;
+        float v = alpha * 0.f;
+        if (beta != 0.f) v = fmaf(beta, *c, v);
+        *c = v;
+    }
+}
+
+int gemm_f32_k0(float *C, int ldc, int m, int n, float alpha, float beta, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return HSS_OK;
+    HSS_PROF("gemm_f32", s, 0.0);
+    k_gemm_k0<<<(int)std::min<long>(cdiv((long)m * n, 256), 2 * 152 * 8), 256, 0, s>>>(C, ldc, m, n, alpha, beta);
+    HSS_CHECK_LAUNCH("k_gemm_k0");
+    return HSS_OK;
+}
+
+// Loads the FP32 GEMM kernels' module (with lazy loading a kernel's module is
+// loaded at its first launch or attribute query).
+int gemm_f32_prepare() {
+    cudaFuncAttributes fa;
+    HSS_CUDA(cudaFuncGetAttributes(&fa, k_gemm<float>));
+    HSS_CUDA(cudaFuncGetAttributes(&fa, k_gemm_k0));
+    return HSS_OK;
+}
+
 template int gemm_batched<double>(const GemmDesc<double> *, const GemmTile *, int, cudaStream_t, double);
 template int gemm_batched<float>(const GemmDesc<float> *, const GemmTile *, int, cudaStream_t, double);
 template void gemm_tiles_for<double>(const GemmDesc<double> &, int, std::vector<GemmTile> &);

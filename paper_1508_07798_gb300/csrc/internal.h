@@ -191,6 +191,13 @@ int gemm_batched(const GemmDesc<T> *d_desc, const GemmTile *d_tiles, int ntiles,
 int gemm_tc(const GemmDesc<float> *d_desc, const GemmTile *d_tiles, int ntiles, int split, int *err, cudaStream_t s,
             double flops);
 void gemm_tc_tiles_for(const GemmDesc<float> &d, int desc_index, std::vector<GemmTile> &tiles);
+// Sets the tensor-core kernel's shared-memory attribute on the current device
+// (once per device, thread-safe) and so loads its module.
+int gemm_tc_prepare();
+// C = alpha * 0 + beta * C (the product with k = 0) without descriptors.
+int gemm_f32_k0(float *C, int ldc, int m, int n, float alpha, float beta, cudaStream_t s);
+// Loads the module of the FP32 SIMT GEMM kernels.
+int gemm_f32_prepare();
 
 // 2 m n k of the written part of a problem
 template <class T> double gemm_flops(const GemmDesc<T> &d) {

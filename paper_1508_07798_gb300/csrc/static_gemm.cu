@@ -34,13 +34,18 @@ static_assert(alignof(GemmTile) <= 16 && alignof(GemmDesc<float>) <= 256, "scrat
 
 static __device__ __align__(256) unsigned char g_gemm_static_scratch[STATIC_SCRATCH_BYTES];
 
+__global__ void k_gemm_static_setup(GemmDesc<float> d, int tm, int ntiles, GemmDesc<float> *dd, int *err,
+                                    GemmTile *tiles);
+
 constexpr int MAX_DEVICES = 64;
 static std::mutex g_static_mu;
 static unsigned char *g_static_addr[MAX_DEVICES];
 
 // Device address of the scratch on the current device, looked up once per
-// device (the lookup may load the module, so the first call on a device does
-// it before any later call could be captured).
+// device.  The same first call also loads every kernel this entry point can
+// launch (the SIMT and tensor-core GEMMs, the k = 0 kernel, the setup kernel)
+// and sets the tensor-core kernel's shared-memory attribute, so after one
+// call of any engine on a device no later call does module work.
 static int static_scratch(unsigned char **out) {
     int dev = 0;
     HSS_CUDA(cudaGetDevice(&dev));
@@ -54,6 +59,11 @@ static int static_scratch(unsigned char **out) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_gemm_static_scratch);
         if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
                                                      "cudaGetSymbolAddress(gemm static scratch)");
+        int rc = gemm_f32_prepare();
+        if (!rc) rc = gemm_tc_prepare();
+        if (rc) return rc;
+        cudaFuncAttributes fa;
+        HSS_CUDA(cudaFuncGetAttributes(&fa, k_gemm_static_setup));
         g_static_addr[dev] = static_cast<unsigned char *>(p);
     }
     *out = g_static_addr[dev];
@@ -86,7 +96,7 @@ extern "C" int hss_gemm_f32_static(int m, int n, int k, const float *A, int lda,
     if (m == 0 || n == 0) return HSS_OK;
     const int tile_m = engine == 0 ? GEMM_TM : GEMM_TC_TM, tile_n = engine == 0 ? GEMM_TN : GEMM_TC_TN;
     const long tm = cdiv(m, tile_m), tn = cdiv(n, tile_n);
-    if (tm * tn > HSS_GEMM_STATIC_MAX_TILES) {
+    if (k > 0 && tm * tn > HSS_GEMM_STATIC_MAX_TILES) {   // (k = 0 needs no tile records)
         set_error("hss_gemm_f32_static: " + std::to_string(m) + " x " + std::to_string(n) + " needs " +
                   std::to_string(tm * tn) + " tiles of " + std::to_string(tile_m) + " x " + std::to_string(tile_n) +
                   ", more than the " + std::to_string(HSS_GEMM_STATIC_MAX_TILES) + " the fixed scratch holds");
@@ -96,6 +106,11 @@ extern "C" int hss_gemm_f32_static(int m, int n, int k, const float *A, int lda,
     int rc = static_scratch(&base);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    if (k == 0) {   // C = beta C: no product for any engine, no records needed
+        if ((rc = gemm_f32_k0(C, ldc, m, n, alpha, beta, s))) return rc;
+        HSS_CUDA(cudaStreamSynchronize(s));
+        return HSS_OK;
+    }
     GemmDesc<float> d{};
     d.A = A;
     d.B = B;

@@ -12,6 +12,7 @@
 // masks as the SIMT kernel (gemm.cu).  Same descriptor list and semantics as
 // k_gemm<float>, including the +-1 test-matrix operand generated on the fly.
 #include <cstdint>
+#include <mutex>
 
 #include "internal.h"
 #include "prof.h"
@@ -104,9 +105,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 }  // namespace
 
 // One 128 x 128 tile of one problem per CTA.  Tiles are in units of 128.
+// spin_limit bounds every mbarrier wait; issue = 0 stages the operands but
+// issues no MMA and no commit, so the first wait runs out (the self-test of
+// the timeout path: nothing is left in flight when the kernel returns).
 __global__ void __launch_bounds__(TC_NT) k_gemm_tc(const GemmDesc<float> *__restrict__ descs,
                                                    const GemmTile *__restrict__ tiles, int split,
-                                                   int *__restrict__ err) {
+                                                   int *__restrict__ err, long spin_limit, int issue) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(TC_NT) k_gemm_tc(const GemmDesc<float> *__rest
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && issue) {
             tc_fence_after();
             const uint32_t aH = smem_u32(sAh), bH = smem_u32(sBh), aL = smem_u32(sAl), bL = smem_u32(sBl);
 #pragma unroll
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(TC_NT) k_gemm_tc(const GemmDesc<float> *__rest
         long spins = 0;
         bool mine = false;
         while (!mbar_try_wait(&bar, phase)) {
-            if (++spins > TC_SPIN_LIMIT) {
+            if (++spins > spin_limit) {
                 mine = true;
                 break;
             }
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(TC_NT) k_gemm_tc(const GemmDesc<float> *__rest
         if (tid == 0) atomicExch(err, 1);
         // let the MMAs in flight finish (bounded) before the accumulator is freed
         long spins = 0;
-        while (!mbar_try_wait(&bar, phase ^ 1u) && ++spins < TC_SPIN_LIMIT) {
+        while (issue && !mbar_try_wait(&bar, phase ^ 1u) && ++spins < spin_limit) {
         }
     } else {
         // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows), 16 columns at a time
@@ -217,7 +221,12 @@ __global__ void __launch_bounds__(TC_NT) k_gemm_tc(const GemmDesc<float> *__rest
         const float beta_row = (gi >= d.zr_lo && gi < d.zr_hi) ? 0.f : d.beta;
         for (int c0 = 0; c0 < TC_N; c0 += 16) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (nk > 0) {
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            } else {   // k = 0: no MMA wrote the accumulator, A B is zero
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = 0.f;
+            }
             if (!rowok) continue;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -240,18 +249,41 @@ __global__ void __launch_bounds__(TC_NT) k_gemm_tc(const GemmDesc<float> *__rest
 
 constexpr size_t TC_SMEM = 4 * TC_TILE_BYTES + 1024;
 
-int gemm_tc(const GemmDesc<float> *d_desc, const GemmTile *d_tiles, int ntiles, int split, int *err, cudaStream_t s,
-            double flops) {
-    if (ntiles <= 0) return HSS_OK;
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-        configured = true;
+// The dynamic shared-memory attribute of k_gemm_tc, set once per device
+// (thread-safe; the attribute is per device context).  Setting it also loads
+// the kernel's module, so a call made early takes that work out of later ones.
+int gemm_tc_prepare() {
+    constexpr int MAXDEV = 64;
+    static std::mutex mu;
+    static bool done[MAXDEV] = {};
+    int dev = 0;
+    HSS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAXDEV) {
+        set_error("tensor-core GEMM: device ordinal beyond the supported 64");
+        return HSS_EINVAL;
     }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        HSS_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+        done[dev] = true;
+    }
+    return HSS_OK;
+}
+
+static int launch_tc(const GemmDesc<float> *d_desc, const GemmTile *d_tiles, int ntiles, int split, int *err,
+                     cudaStream_t s, double flops, long spin_limit, int issue) {
+    if (ntiles <= 0) return HSS_OK;
+    int rc = gemm_tc_prepare();
+    if (rc) return rc;
     HSS_PROF("gemm_tc", s, flops);
-    k_gemm_tc<<<ntiles, TC_NT, TC_SMEM, s>>>(d_desc, d_tiles, split, err);
+    k_gemm_tc<<<ntiles, TC_NT, TC_SMEM, s>>>(d_desc, d_tiles, split, err, spin_limit, issue);
     HSS_CHECK_LAUNCH("k_gemm_tc");
     return HSS_OK;
+}
+
+int gemm_tc(const GemmDesc<float> *d_desc, const GemmTile *d_tiles, int ntiles, int split, int *err, cudaStream_t s,
+            double flops) {
+    return launch_tc(d_desc, d_tiles, ntiles, split, err, s, flops, TC_SPIN_LIMIT, 1);
 }
 
 void gemm_tc_tiles_for(const GemmDesc<float> &d, int desc_index, std::vector<GemmTile> &tiles) {
@@ -276,6 +308,12 @@ extern "C" int hss_gemm_f32(int m, int n, int k, const float *A, int lda, const 
     }
     if (m == 0 || n == 0) return HSS_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (k == 0) {   // C = beta C: no product for any engine to run
+        int rc0 = gemm_f32_k0(C, ldc, m, n, alpha, beta, s);
+        if (rc0) return rc0;
+        HSS_CUDA(cudaStreamSynchronize(s));
+        return HSS_OK;
+    }
     GemmDesc<float> d{};
     d.A = A;
     d.B = B;
@@ -311,6 +349,48 @@ extern "C" int hss_gemm_f32(int m, int n, int k, const float *A, int lda, const 
     HSS_CUDA(cudaStreamSynchronize(s));
     if (herr) {
         set_error("hss_gemm_f32: tensor-core wait timed out");
+        return HSS_ETIMEOUT;
+    }
+    return HSS_OK;
+}
+
+// Test hook of the bounded tensor-core wait: one CTA of k_gemm_tc on a
+// 128 x 128 x 32 problem that issues no MMA, so its mbarrier never completes
+// and the wait gives up after spin_limit polls.
+extern "C" int hss_tc_timeout_selftest(long spin_limit, void *stream) {
+    if (spin_limit < 1 || spin_limit > TC_SPIN_LIMIT) {
+        set_error("hss_tc_timeout_selftest: spin_limit out of range");
+        return HSS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Work W(s);
+    float *buf;
+    GemmDesc<float> *dd;
+    GemmTile *dt;
+    int *err;
+    int rc;
+    if ((rc = W.dalloc((size_t)3 * TC_M * TC_N, &buf)) || (rc = W.dalloc(1, &err))) return rc;
+    HSS_CUDA(cudaMemsetAsync(buf, 0, sizeof(float) * 3 * TC_M * TC_N, s));
+    HSS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    GemmDesc<float> d{};
+    d.A = buf;
+    d.B = buf + TC_M * TC_N;
+    d.C = buf + 2 * TC_M * TC_N;
+    d.lda = d.ldc = TC_M;
+    d.ldb = TC_K;
+    d.m = TC_M;
+    d.n = TC_N;
+    d.k = TC_K;
+    d.alpha = 1.f;
+    std::vector<GemmDesc<float>> dv{d};
+    std::vector<GemmTile> tv{{0, 0, 0}};
+    if ((rc = W.up(dv, &dd)) || (rc = W.up(tv, &dt))) return rc;
+    if ((rc = launch_tc(dd, dt, 1, 0, err, s, 0.0, spin_limit, 0))) return rc;
+    int herr = 0;
+    HSS_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSS_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        set_error("hss_tc_timeout_selftest: the bounded tensor-core wait expired");
         return HSS_ETIMEOUT;
     }
     return HSS_OK;

@@ -32,7 +32,7 @@ EXPORTED = [
     "hss_rank_features", "hss_rank_model_create", "hss_rank_model_destroy", "hss_rank_model_get",
     "hss_rank_model_set", "hss_rank_model_fit_norm", "hss_rank_model_loss_grad", "hss_rank_model_train",
     "hss_rank_model_predict", "hss_factor_export_log", "ilu0_factor", "ilu0_apply", "fgmres_solve_ilu0",
-    "ilu0_destroy", "hss_factor_apply_plan",
+    "ilu0_destroy", "hss_factor_apply_plan", "hss_alloc_count", "hss_tc_timeout_selftest",
 ]
 
 
@@ -107,6 +107,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hss_factor_opts_default": (None, [C.POINTER(hss_factor_opts)]),
         "fgmres_opts_default": (None, [C.POINTER(fgmres_opts)]),
         "hss_launch_count": (C.c_long, []),
+        "hss_alloc_count": (C.c_long, []),
+        "hss_tc_timeout_selftest": (C.c_int, [C.c_long, P]),
         "hss_gemm_f32": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.c_int, P, C.c_int, C.c_float,
                                    C.c_float, C.c_int, P]),
         "hss_gemm_f32_static": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.c_int, P, C.c_int,
@@ -514,6 +516,17 @@ def launch_count() -> int:
     return int(_lib.hss_launch_count())
 
 
+def alloc_count() -> int:
+    """Memory requests the library has served so far (hss_alloc_count)."""
+    return int(_lib.hss_alloc_count())
+
+
+def tc_timeout_selftest(spin_limit: int = 1 << 12, stream=None) -> int:
+    """Runs the tensor-core kernel with its MMAs left out so that its bounded
+    wait expires; returns the library's code (HSS_ETIMEOUT expected)."""
+    return int(_lib.hss_tc_timeout_selftest(spin_limit, _stream(stream)))
+
+
 def profile_enable(on: bool = True):
     _check(_lib.hss_profile_enable(1 if on else 0))
 
@@ -546,7 +559,8 @@ def gemm_f32(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, al
     At, Bt, Ct = A.contiguous(), B.contiguous(), C
     assert Ct.is_contiguous()
     # row-major (m x n) C is column-major (n x m) C^t = B^t A^t
-    _check(_lib.hss_gemm_f32(n, m, k, _ptr(Bt), n, _ptr(At), k, _ptr(Ct), n, alpha, beta, engine, _stream(stream)))
+    _check(_lib.hss_gemm_f32(n, m, k, _ptr(Bt), n, _ptr(At), max(k, 1), _ptr(Ct), n, alpha, beta, engine,
+                             _stream(stream)))
     return Ct
 
 
@@ -562,6 +576,6 @@ def gemm_f32_static(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, alpha=1.0
     k2, n = B.shape
     assert k == k2 and C.shape == (m, n)
     assert A.is_contiguous() and B.is_contiguous() and C.is_contiguous()
-    _check(_lib.hss_gemm_f32_static(n, m, k, _ptr(B), n, _ptr(A), k, _ptr(C), n, alpha, beta, engine,
+    _check(_lib.hss_gemm_f32_static(n, m, k, _ptr(B), n, _ptr(A), max(k, 1), _ptr(C), n, alpha, beta, engine,
                                     _stream(stream)))
     return C

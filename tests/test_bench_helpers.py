@@ -21,7 +21,7 @@ def bench():
 
 
 def test_roofline_arithmetic(bench):
-    pk = dict(hbm=6000.0, src="measured")
+    pk = bench.with_simt_peak(dict(hbm=6000.0, sm_mhz=2070.0, src="measured"), 152)
     # 10 launches, 2 ms in all, 1e9 bytes of algorithmic traffic per launch: 5e12 B/s
     r = bench.roofline_of("apply", 2.0, 10, 1e10, 8.0, pk)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
@@ -31,6 +31,11 @@ def test_roofline_arithmetic(bench):
     g = bench.roofline_of("gj_panel_f32", 1.0, 4, 8e9, 4.0, pk)
     assert g["bound"] == "alu" and g["achieved"] == pytest.approx(8.0)
     assert g["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12) and g["traffic"] is None
+    assert "152 SMs" in g["peak_source"]
+    # the SM count and clock come from the device and the peaks file, not a constant
+    pk2 = bench.with_simt_peak(dict(hbm=6000.0, sm_mhz=1500.0, src="measured"), 100)
+    assert bench.roofline_of("gj_panel_f32", 1.0, 4, 8e9, 4.0, pk2)["peak"] == pytest.approx(
+        100 * 128 * 2 * 1.5e9 / 1e12)
     d = bench.roofline_of("gemm_f64", 1.0, 1, 1e9, 1.0, pk)
     assert d["peak"] == 1.25 and d["achieved"] == pytest.approx(1.0)
 
@@ -41,7 +46,11 @@ def test_peaks_file_and_fallback(bench, tmp_path, monkeypatch):
         assert pk["src"] == "measured" and pk["hbm"] > 1000
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     fb = bench.peaks()
-    assert fb["src"] == "fallback" and fb["hbm"] == 6800.0 and fb["bf16"] == 1900.0
+    assert fb["src"] == "fallback" and fb["hbm"] == 6800.0 and fb["bf16"] == 1900.0 and fb["sm_mhz"] == 2070.0
+
+
+def test_cpu_cores_is_the_process_affinity(bench):
+    assert bench.cpu_cores() == len(os.sched_getaffinity(0))
 
 
 def test_profiled_traffic_only_for_the_profiled_source(bench, tmp_path, monkeypatch):

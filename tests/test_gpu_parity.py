@@ -259,6 +259,35 @@ def test_errors_are_reported():
     b = torch.as_tensor(dg.random_rhs(A.n, 1, 0)[:, 0], device="cuda")
     x, st = hs.fgmres_solve(dA, None, b, rtol=1e-14, maxit=2)
     assert not st.converged and st.iters == 2
+    # a NaN or an infinite value anywhere in A is rejected (one stored value
+    # in an off-diagonal block, then in the last block)
+    for pos, bad in ((A.row_ptr[3] * A.bs * A.bs + 2, float("nan")), (A.val.size - 1, float("inf"))):
+        A3 = dg.assemble_sipg(mesh)
+        A3.val.reshape(-1)[pos] = bad
+        dA3 = hs.DeviceBSR.from_host(A3)
+        with pytest.raises(hs.HssError) as e:
+            hs.hss_factor(dA3, tree)
+        assert e.value.code == hs.HSS_EINVAL and "NaN or infinite" in str(e.value)
+    # the same matrix without the bad value factors (the context is still usable)
+    hs.hss_factor(dA, tree)
+
+
+def test_tensor_core_wait_timeout_is_reported():
+    """The tcgen05 kernel's bounded mbarrier wait: with its MMAs left out the
+    barrier never completes, the wait gives up after the given number of polls
+    and the call returns HSS_ETIMEOUT; the GPU stays usable (a tensor-core
+    GEMM right after it is correct)."""
+    import torch
+    hs = _hss()
+    assert hs.tc_timeout_selftest(1 << 10) == hs.HSS_ETIMEOUT
+    assert "expired" in hs._lib.hss_last_error().decode()
+    assert hs.tc_timeout_selftest(1 << 14) == hs.HSS_ETIMEOUT
+    g = torch.Generator(device="cpu").manual_seed(3)
+    A = torch.randn(256, 128, generator=g).cuda()
+    B = torch.randn(128, 192, generator=g).cuda()
+    C = hs.gemm_f32(A, B, engine=1)
+    ref = A.double() @ B.double()
+    assert (C.double() - ref).abs().max().item() <= 2e-6 * (A.double().abs() @ B.double().abs()).max().item()
 
 
 @pytest.mark.parametrize("m,n,k", [(300, 200, 70), (128, 128, 32), (513, 77, 257), (64, 300, 5), (1, 1, 1)])

@@ -4,13 +4,13 @@
 * cap policy "accept" (a front whose ranks outgrow the sample cap keeps the
   approximant from the samples it has): approximants and apply within 1e-10
   of the oracle in FP64, same capped fronts;
-* the anisotropic reaction-diffusion problem, eq. (60), a0 = 1e-3, fixed
-  width l = 16: GPU iteration counts within +-10% (at least +-1) of the
-  oracle's, same convergence outcome, for horizontal and vertical slabs in
-  the diffusion- and reaction-dominated regimes;
-* at 64 x 64 the GPU alone shows the paper's qualitative findings: vertical
-  slabs fail where diffusion dominates and horizontal slabs do not; with
-  reaction dominating, every scheme converges.
+* the anisotropic reaction-diffusion problem, eq. (60), with the anisotropy
+  a0 = 1e-6 and the reaction coefficients c0 = 1e-4, 1, 1e2, 1e3 printed with
+  Fig. 10, fixed width l = 16: GPU iteration counts within +-10% (at least
+  +-1) of the oracle's, same convergence outcome, for the three schemes;
+* the h-refinement study of Fig. 10 (16^2, 32^2, 64^2 elements, p = 1) on the
+  GPU: vertical slabs fail and horizontal slabs converge at every printed c0
+  and every h; the box scheme converges everywhere.
 """
 import numpy as np
 import pytest
@@ -67,13 +67,17 @@ def _solve(hs, mesh, A, scheme, l, b, maxit, precision="fp64"):
     return st
 
 
+RD_A0 = 1e-6                       # Fig. 10 caption
+RD_C0 = (1e-4, 1.0, 1e2, 1e3)      # Fig. 10 sub-figures
+
+
 def test_scheme_iterations_match_oracle():
     hs = _hss()
-    for c0 in (1e-3, 1e6):
-        mesh, A = dg.reaction_diffusion_2d(32, 1, a0=1e-3, c0=c0)
+    for c0 in (1e-4, 1e3):
+        mesh, A = dg.reaction_diffusion_2d(32, 1, a0=RD_A0, c0=c0)
         Acsr = dg.bsr_to_csr(A)
         b = dg.random_rhs(A.n, 1, 0)[:, 0]
-        for sc in ("hslab", "vslab"):
+        for sc in ("box", "hslab", "vslab"):
             st = _solve(hs, mesh, A, sc, 16, b, 120)
             nd = oracle.nd_order(2, mesh.n, 1, A.row_ptr, A.col_idx, scheme=sc)
             fac = oracle.factor(Acsr, nd, tol=1e-12, seed=0, r0=16, rmax=16, cap="accept")
@@ -85,21 +89,25 @@ def test_scheme_iterations_match_oracle():
                                                                                             info["iters"])
 
 
-def test_scheme_findings_at_64():
+def test_scheme_study_under_h_refinement():
+    """Fig. 10: a0 = 1e-6, the four printed c0, h-refinement 16^2 -> 64^2."""
     hs = _hss()
     table = {}
-    for c0 in (1e-3, 1.0, 1e6):
-        mesh, A = dg.reaction_diffusion_2d(64, 1, a0=1e-3, c0=c0)
-        b = dg.random_rhs(A.n, 1, 0)[:, 0]
-        for sc in ("box", "hslab", "vslab"):
-            st = _solve(hs, mesh, A, sc, 16, b, 300)
-            table[c0, sc] = st.iters if st.converged else None
-    print("\nreaction-diffusion a0=1e-3, l=16, 64x64 p=1 (iterations; None = not converged in 300):")
-    for c0 in (1e-3, 1.0, 1e6):
-        print(f"  c0={c0:g}: " + ", ".join(f"{sc} {table[c0, sc]}" for sc in ("box", "hslab", "vslab")))
-    for c0 in (1e-3, 1.0):
-        assert table[c0, "vslab"] is None and table[c0, "hslab"] is not None, table
-    assert all(table[1e6, sc] is not None for sc in ("box", "hslab", "vslab")), table
+    for n in (16, 32, 64):
+        for c0 in RD_C0:
+            mesh, A = dg.reaction_diffusion_2d(n, 1, a0=RD_A0, c0=c0)
+            b = dg.random_rhs(A.n, 1, 0)[:, 0]
+            for sc in ("box", "hslab", "vslab"):
+                st = _solve(hs, mesh, A, sc, 16, b, 300)
+                table[n, c0, sc] = st.iters if st.converged else None
+    print("\nreaction-diffusion a0=1e-6, l=16, p=1 (iterations; None = not converged in 300):")
+    for n in (16, 32, 64):
+        for c0 in RD_C0:
+            print(f"  {n}x{n} c0={c0:g}: " + ", ".join(f"{sc} {table[n, c0, sc]}" for sc in ("box", "hslab", "vslab")))
+    for n in (16, 32, 64):
+        for c0 in RD_C0:
+            assert table[n, c0, "vslab"] is None and table[n, c0, "hslab"] is not None, table
+            assert table[n, c0, "box"] is not None, table
 
 
 def test_density_helmholtz_schemes_at_64():

@@ -185,13 +185,16 @@ def test_accepted_approximant_is_hss_with_ranks_at_most_r():
 
 
 def test_partition_scheme_matters_for_anisotropic_diffusion():
-    """Sec. 5, eq. (60) with a0 = 1e-3 and a fixed sample width l = 16: when
-    diffusion dominates, vertical slabs (cuts across the strong x coupling)
-    fail while horizontal slabs converge; in the reaction-dominated regime the
-    scheme matters much less and both converge."""
+    """Sec. 5, eq. (60) with the printed anisotropy a0 = 1e-6 (Fig. 10) and a
+    fixed sample width l = 16, at the printed c0 = 1e-4, 1, 1e2, 1e3: vertical
+    slabs (cuts across the strong x coupling; the coupling between a slab's
+    left and right boundaries is one full-rank x chain per row) fail while
+    horizontal slabs converge.  The scheme stops mattering once reaction
+    dominates at the element scale (c0 h^2 >> 1; c0 = 1e6 at h = 1/16, beyond
+    the printed values)."""
     its = {}
-    for c0 in (1e-3, 1e6):
-        mesh, A = dg.reaction_diffusion_2d(32, 1, a0=1e-3, c0=c0)
+    for c0 in (1e-4, 1.0, 1e2, 1e3, 1e6):
+        mesh, A = dg.reaction_diffusion_2d(16, 1, a0=1e-6, c0=c0)
         Acsr = dg.bsr_to_csr(A)
         b = dg.random_rhs(A.n, 1, 0)[:, 0]
         for sc in ("hslab", "vslab"):
@@ -200,9 +203,9 @@ def test_partition_scheme_matters_for_anisotropic_diffusion():
             _, info = oracle.fgmres(lambda v: Acsr @ v, lambda v: oracle.apply(fac, v), b, rtol=1e-8,
                                     restart=30, maxit=120)
             its[c0, sc] = info["iters"] if info["converged"] else None
-    assert its[1e-3, "hslab"] is not None and its[1e-3, "vslab"] is None, its
-    assert its[1e6, "hslab"] is not None and its[1e6, "vslab"] is not None, its
-    assert its[1e6, "vslab"] <= 30 and its[1e6, "hslab"] <= its[1e-3, "hslab"], its
+    for c0 in (1e-4, 1.0, 1e2, 1e3):
+        assert its[c0, "hslab"] is not None and its[c0, "hslab"] <= 5 and its[c0, "vslab"] is None, its
+    assert its[1e6, "vslab"] is not None and its[1e6, "vslab"] <= 30, its
 
 
 # --- residual probe of accepted approximants (fallback check of the learned widths)

@@ -58,6 +58,59 @@ def test_static_gemm_matches_allocating_gemm_two_calls_in_a_row(engine, tol):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("engine", [0, 1, 2])
+def test_static_gemm_allocates_nothing(engine):
+    """The property the entry point exists for: after one warm-up call (which
+    does the per-device setup) a call makes no memory request of any kind --
+    the library's request counter and the device's free memory are the same
+    before and after it -- while hss_gemm_f32 on the same operands does make
+    requests (its workspace), so the counter does see them."""
+    import torch
+    hs = _hss()
+    g = torch.Generator(device="cpu").manual_seed(11 + engine)
+    m, n, k = 300, 260, 140
+    A = torch.randn(m, k, generator=g).cuda()
+    B = torch.randn(k, n, generator=g).cuda()
+    C = torch.zeros(m, n, device="cuda")
+    Ca = torch.zeros(m, n, device="cuda")
+    hs.gemm_f32_static(A, B, C, engine=engine)          # warm-up: per-device setup
+    torch.cuda.synchronize()
+    a0 = hs.alloc_count()
+    free0 = torch.cuda.mem_get_info()[0]
+    hs.gemm_f32_static(A, B, C, alpha=0.5, beta=0.5, engine=engine)
+    torch.cuda.synchronize()
+    assert hs.alloc_count() == a0
+    assert torch.cuda.mem_get_info()[0] == free0
+    hs.gemm_f32(A, B, Ca, engine=engine)
+    assert hs.alloc_count() > a0
+    ref = (A.double() @ B.double()) * 0.5 + 0.5 * (A.double() @ B.double())
+    scale = (A.double().abs() @ B.double().abs()).max().item()
+    assert (C.double() - ref).abs().max().item() / scale <= (2e-3 if engine == 2 else 2e-6)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("engine", [0, 1, 2])
+def test_k_zero_gives_beta_c(engine):
+    """k = 0: C = beta C for every engine in both entry points (no product;
+    the tensor-core engines must not read an accumulator nothing wrote)."""
+    import torch
+    hs = _hss()
+    lib = hs._lib
+    g = torch.Generator(device="cpu").manual_seed(5)
+    m, n = 200, 150
+    dummy = torch.zeros(4, device="cuda")   # A and B are never read when k = 0
+    for fn in (lib.hss_gemm_f32, lib.hss_gemm_f32_static):
+        for beta in (0.0, -1.5):
+            C0 = torch.randn(n, m, generator=g).cuda()   # column-major m x n
+            C = C0.clone()
+            rc = fn(m, n, 0, ctypes.c_void_p(dummy.data_ptr()), m, ctypes.c_void_p(dummy.data_ptr()), 1,
+                    ctypes.c_void_p(C.data_ptr()), m, 2.0, beta, engine, None)
+            torch.cuda.synchronize()
+            assert rc == hs.HSS_OK, lib.hss_last_error()
+            assert torch.equal(C, C0 * beta) if beta != 0.0 else torch.count_nonzero(C).item() == 0
+
+
+@pytest.mark.gpu
 def test_static_gemm_at_the_tile_limit():
     """m = n = 8192 with the SIMT engine fills all 16384 tile slots."""
     import torch
