@@ -227,12 +227,7 @@ def bench_ours(args, rank, world):
     kappa_h = dg.helmholtz_kappa(N_ELEM, P_DEG) / N_ELEM
     if "fp32_learned" in args.forms.split(","):
         from paper_1508_07798_gb300 import ranks
-        probs = []
-        for p_ in (1, 2, 3):
-            for sd in range(100, 116):
-                m_, A_ = dg.helmholtz_2d(N_ELEM, p_, sd)
-                probs.append(((2, (N_ELEM, N_ELEM), p_), A_, dg.cosine_field(m_, sd),
-                              dg.helmholtz_kappa(N_ELEM, p_) / N_ELEM))
+        probs = dg.rank_training_problems(N_ELEM)
         Xt, tt = ranks.training_set(probs, tol=TOL)
         model = hssnd.RankModel(seed=1)
         model.fit_norm(Xt, tt)

@@ -211,6 +211,37 @@ int hss_factor_export_front(const hss_factor_t *f, int box, double *S, double *H
 int hss_apply(const hss_factor_t *f, int nrhs, const double *x, int ldx, double *y, int ldy,
               void *stream);
 
+/* Test hooks: one step of Algorithm 2 on one front supplied from the host,
+ * through the same kernels hss_factor runs, so each step can be checked on
+ * its own against a reference that starts from the same input.
+ *
+ * hss_front_eliminate: the elimination of eq. (32) on the dense front
+ * F = [F_ii F_ib; F_bi F_bb] (HOST, n x n column-major, ld ldf >= n; the
+ * first ni rows/columns are I, 1 <= ni <= n): the Gauss-Jordan sweep with
+ * partial row pivoting inside I that hss_factor uses (fronts with n >= 2048
+ * take its blocked form).  out (HOST, n x n, ld ldo >= n) receives the
+ * transformed front [F_ii^-1 P^t, W; -F_bi F_ii^-1 P^t, S] with
+ * W = F_ii^-1 F_ib and S = F_bb - F_bi W; perm (HOST, ni ints, may be NULL)
+ * gives P: column j of the first ni columns belongs to I row perm[j].
+ * precision HSS_FP64 or HSS_FP32 (tensor_cores as in hss_factor_opts, FP32
+ * only).  Synchronizes `stream`.  Errors: HSS_EINVAL, HSS_ESINGULAR (zero
+ * pivot; out is still written), HSS_ENOMEM, HSS_ETIMEOUT, HSS_ECUDA.
+ *
+ * hss_front_compress: Theorem 1's randomized HSS construction of the Schur
+ * complement S (HOST, nb x nb column-major, ld lds >= nb, nb = |B| of `box`
+ * in tree t) exactly as hss_factor compresses box `box`: its HSS tree, its
+ * test-matrix counters (opts->seed, the box id), the width schedule, cap
+ * policy and residual probe of *opts (NULL: defaults; r_init, when given, is
+ * read at index `box`).  H (HOST, nb x nb, ld ldh >= nb) receives the
+ * approximant (S itself for a single-node HSS tree or compress = 0); kmax,
+ * r, rounds (HOST, may be NULL): largest node rank, final sample width,
+ * sampling rounds (0 when not compressed).  Synchronizes `stream`.
+ * Errors: HSS_EINVAL, HSS_ENOMEM, HSS_ETIMEOUT, HSS_ECUDA. */
+int hss_front_eliminate(int n, int ni, const double *F, int ldf, int precision, int tensor_cores, double *out,
+                        int ldo, int *perm, void *stream);
+int hss_front_compress(const hss_tree *t, int box, const double *S, int lds, const hss_factor_opts *opts,
+                       double *H, int ldh, int *kmax, int *r, int *rounds, void *stream);
+
 /* C = alpha A B + beta C in FP32, DEVICE column-major m x k, k x n, m x n
  * (the GEMM of the FP32 form, exposed for testing and reuse).  engine: 0 SIMT
  * FMA; 1 tcgen05 TF32 with the three-product hi/lo split; 2 tcgen05 single

@@ -35,7 +35,7 @@ perturbed by H~ - S~ (every parent and the top block).
 from .nd import nd_order                      # noqa: F401
 from .idecomp import interp_decomp            # noqa: F401
 from .hss import hss_tree_for_front, hss_compress, probe_residual, probe_threshold   # noqa: F401
-from .factor import factor, box_schur         # noqa: F401
+from .factor import factor, box_schur, eliminate_front   # noqa: F401
 from .apply import apply                      # noqa: F401
 from .fgmres import fgmres                    # noqa: F401
 from .rademacher import rademacher            # noqa: F401

@@ -54,6 +54,24 @@ def box_schur(A_csr, nd, b):
     return F[ni:, ni:] - F[ni:, :ni] @ W
 
 
+def eliminate_front(F, ni):
+    """Elimination of the interior block of one front (Sec. 4.1, eq. (32)):
+    F = [F_ii F_ib; F_bi F_bb] with the first ni rows/columns interior;
+    LU with partial pivoting of F_ii, W = F_ii^-1 F_ib (= M(B,I)^t) and the
+    Schur complement S = F_bb - F_bi W.  Returns dict(lu, W, S); lu is None
+    when ni = 0."""
+    F = np.asarray(F, dtype=np.float64)
+    Fii, Fib = F[:ni, :ni], F[:ni, ni:]
+    Fbi, Fbb = F[ni:, :ni], F[ni:, ni:]
+    if ni > 0:
+        lu = sla.lu_factor(Fii)
+        W = sla.lu_solve(lu, Fib)
+    else:
+        lu = None
+        W = np.zeros((0, F.shape[0] - ni))
+    return dict(lu=lu, W=W, S=Fbb - Fbi @ W)
+
+
 def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=10, rmax=None,
            keep_h=False, cap="keep", probe=0, r_init=None, merge="dense"):
     """Returns a dict with the per-box factors, the top block LU and logs.
@@ -106,12 +124,9 @@ def factor(A_csr, nd, tol=1e-6, seed=0, compress=True, r0=32, dr=32, oversample=
             rec["tilde"] = minfo
             lu = None
             W = Xinv @ Fib
-        elif ni > 0:
-            lu = sla.lu_factor(Fii)
-            W = sla.lu_solve(lu, Fib)
         else:
-            lu = None
-            W = np.zeros((0, B.size))
+            el = eliminate_front(F, ni)
+            lu, W = el["lu"], el["W"]
         S = Fbb - Fbi @ W
         if compress and B.size > 0:
             nodes = hss_tree_for_front(nd, b)

@@ -4,6 +4,8 @@
 #include <atomic>
 #include <cstring>
 #include <mutex>
+#include <set>
+#include <utility>
 
 #include "internal.h"
 
@@ -37,6 +39,22 @@ int DevBuf::alloc(size_t nbytes) {
     }
     bytes = nbytes;
     return HSS_OK;
+}
+
+// Dynamic shared-memory limit of a kernel, set once per (device, kernel):
+// the attribute belongs to the device context; the set is guarded for calls
+// from several host threads, and the runtime's return code is passed on.
+cudaError_t func_smem_once(const void *func, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, func})) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert({dev, func});
+    return e;
 }
 
 // ---- scratch cache: device chunks and pinned buffers kept between calls

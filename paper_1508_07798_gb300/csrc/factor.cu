@@ -928,6 +928,124 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     return HSS_OK;
 }
 
+// ---- one front at a time (test hooks hss_front_eliminate / hss_front_compress):
+// the kernels of factor_impl on a front supplied from the host
+
+template <class T>
+int front_eliminate_impl(int n, int ni, const double *Fh, int ldf, int tensor_cores, double *out, int ldo,
+                         int *perm, cudaStream_t s) {
+    Work W(s);
+    const size_t nn = (size_t)n * n;
+    std::vector<T> host(nn);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) host[i + (size_t)n * j] = (T)Fh[i + (size_t)ldf * j];
+    T *arena;
+    int *piv, *rperm, *ilist, *iperm, *status, *tcerr;
+    std::vector<int> ident(std::max(ni, 1));
+    for (int i = 0; i < ni; ++i) ident[i] = i;
+    int rc;
+    if ((rc = W.up(host, &arena)) || (rc = W.dalloc(std::max(ni, 1), &piv)) ||
+        (rc = W.dalloc(std::max(ni, 1), &rperm)) || (rc = W.up(ident, &ilist)) ||
+        (rc = W.dalloc(std::max(ni, 1), &iperm)) || (rc = W.dalloc(1, &status)) || (rc = W.dalloc(1, &tcerr)))
+        return rc;
+    HSS_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+    HSS_CUDA(cudaMemsetAsync(tcerr, 0, sizeof(int), s));
+    FrontDev d{};
+    d.foff = 0;
+    d.n = n;
+    d.ni = ni;
+    d.nb = n - ni;
+    d.leaf = 1;
+    std::vector<FrontDev> fr{d};
+    FrontDev *d_fr;
+    if ((rc = W.up(fr, &d_fr))) return rc;
+    Engine eng;
+    eng.tc = std::is_same<T, float>::value ? tensor_cores : 0;
+    eng.err = tcerr;
+    double xf = 0;
+    if ((rc = eliminate_stage<T>(fr, d_fr, arena, piv, rperm, ilist, iperm, status, xf, eng, W, s))) return rc;
+    int hs[2] = {0, 0};
+    HSS_CUDA(cudaMemcpyAsync(host.data(), arena, sizeof(T) * nn, cudaMemcpyDeviceToHost, s));
+    std::vector<int> hp(std::max(ni, 1));
+    HSS_CUDA(cudaMemcpyAsync(hp.data(), iperm, sizeof(int) * hp.size(), cudaMemcpyDeviceToHost, s));
+    HSS_CUDA(cudaMemcpyAsync(&hs[0], status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSS_CUDA(cudaMemcpyAsync(&hs[1], tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSS_CUDA(cudaStreamSynchronize(s));
+    if (hs[1]) {
+        set_error("hss_front_eliminate: a bounded tensor-core wait expired");
+        return HSS_ETIMEOUT;
+    }
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) out[i + (size_t)ldo * j] = (double)host[i + (size_t)n * j];
+    if (perm)
+        for (int i = 0; i < ni; ++i) perm[i] = hp[i];
+    if (hs[0]) {
+        set_error("hss_front_eliminate: zero pivot");
+        return HSS_ESINGULAR;
+    }
+    return HSS_OK;
+}
+
+template <class T>
+int front_compress_impl(const hss_tree *t, int box, const double *Sh, int lds, const hss_factor_opts &o, double *Hout,
+                        int ldh, int *kmax, int *r, int *rounds, cudaStream_t s) {
+    const int nb = t->nb[box];
+    const int par = t->parent[box];
+    int pn;
+    if (par >= 0) {
+        pn = t->ni[par] + t->nb[par];
+    } else {
+        const int b0 = t->inst_top[t->box_inst[box]];
+        pn = t->nb[b0] + t->nb[b0 + 1];
+    }
+    const long sz = ((long)nb * nb + 31) / 32 * 32;
+    Work W(s);
+    std::vector<T> host((size_t)nb * nb);
+    for (int j = 0; j < nb; ++j)
+        for (int i = 0; i < nb; ++i) host[i + (size_t)nb * j] = (T)Sh[i + (size_t)lds * j];
+    T *arena, *keep;
+    int *tcerr;
+    int rc;
+    if ((rc = W.dalloc(sz + (size_t)pn * pn, &arena)) || (rc = W.dalloc((size_t)nb * nb, &keep)) ||
+        (rc = W.dalloc(1, &tcerr)))
+        return rc;
+    if (nb) HSS_CUDA(cudaMemcpyAsync(arena, host.data(), sizeof(T) * host.size(), cudaMemcpyHostToDevice, s));
+    HSS_CUDA(cudaMemsetAsync(tcerr, 0, sizeof(int), s));
+    FrontDev d{};
+    d.foff = 0;
+    d.n = nb;
+    d.ni = 0;
+    d.nb = nb;
+    d.bset_off = t->boff[box];
+    d.box = box;
+    std::vector<FrontDev> fr{d};
+    std::vector<int> boxes{box};
+    std::vector<long> poff{sz}, keeph{0};
+    std::vector<int> pnv{pn};
+    std::vector<FrontLog> logv;
+    hss_factor_t tmp;
+    Engine eng;
+    eng.tc = std::is_same<T, float>::value ? o.tensor_cores : 0;
+    eng.err = tcerr;
+    if ((rc = compress_stage<T>(t, o, fr, boxes, poff, pnv, keeph, arena, keep, nullptr, 0, logv, &tmp, eng, W, s)))
+        return rc;
+    int herr = 0;
+    HSS_CUDA(cudaMemcpyAsync(host.data(), keep, sizeof(T) * host.size(), cudaMemcpyDeviceToHost, s));
+    HSS_CUDA(cudaMemcpyAsync(&herr, tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSS_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        set_error("hss_front_compress: a bounded tensor-core wait expired");
+        return HSS_ETIMEOUT;
+    }
+    for (int j = 0; j < nb; ++j)
+        for (int i = 0; i < nb; ++i) Hout[i + (size_t)ldh * j] = (double)host[i + (size_t)nb * j];
+    const FrontLog &lg = logv.at(0);
+    if (kmax) *kmax = lg.kmax;
+    if (r) *r = lg.r;
+    if (rounds) *rounds = lg.rounds;
+    return HSS_OK;
+}
+
 }  // namespace
 }  // namespace hssnd
 
@@ -1142,3 +1260,32 @@ extern "C" int hss_factor_export_front(const hss_factor_t *f, int box, double *S
 }
 
 extern "C" void hss_factor_destroy(hss_factor_t *f) { delete f; }
+
+extern "C" int hss_front_eliminate(int n, int ni, const double *F, int ldf, int precision, int tensor_cores,
+                                   double *out, int ldo, int *perm, void *stream) {
+    if (n < 1 || ni < 1 || ni > n || !F || !out || ldf < n || ldo < n ||
+        (precision != HSS_FP64 && precision != HSS_FP32) || tensor_cores < 0 || tensor_cores > 2) {
+        set_error("hss_front_eliminate: invalid argument");
+        return HSS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    return precision == HSS_FP32 ? front_eliminate_impl<float>(n, ni, F, ldf, tensor_cores, out, ldo, perm, s)
+                                 : front_eliminate_impl<double>(n, ni, F, ldf, 0, out, ldo, perm, s);
+}
+
+extern "C" int hss_front_compress(const hss_tree *t, int box, const double *S, int lds, const hss_factor_opts *opts,
+                                  double *H, int ldh, int *kmax, int *r, int *rounds, void *stream) {
+    hss_factor_opts o;
+    hss_factor_opts_default(&o);
+    if (opts) o = *opts;
+    if (!t || box < 0 || box >= t->nbox || !S || !H || lds < std::max(1, t->nb[box]) ||
+        ldh < std::max(1, t->nb[box])) {
+        set_error("hss_front_compress: invalid argument");
+        return HSS_EINVAL;
+    }
+    int rc = check_factor_opts(o, "hss_front_compress");
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    return o.precision == HSS_FP32 ? front_compress_impl<float>(t, box, S, lds, o, H, ldh, kmax, r, rounds, s)
+                                   : front_compress_impl<double>(t, box, S, lds, o, H, ldh, kmax, r, rounds, s);
+}

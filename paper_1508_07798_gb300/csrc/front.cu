@@ -587,12 +587,8 @@ template <class T, int KB, int R, int NT>
 static cudaError_t launch_reg(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws,
                               int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status,
                               cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_gj_panel_reg<T, KB, R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             PANEL_SMEM_MAX);
-        configured = true;
-    }
+    const cudaError_t ea = func_smem_once((const void *)k_gj_panel_reg<T, KB, R, NT>, PANEL_SMEM_MAX);
+    if (ea != cudaSuccess) return ea;
     k_gj_panel_reg<T, KB, R, NT><<<njobs, NT, smem, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
     return cudaGetLastError();
 }
@@ -654,12 +650,7 @@ template <class T>
 int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws, int *mws,
                     int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s, double flops) {
     if (njobs == 0) return HSS_OK;
-    static bool configured[2] = {false, false};
-    int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!configured[ti]) {
-        cudaFuncSetAttribute(k_gj_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX);
-        configured[ti] = true;
-    }
+    HSS_SMEM(k_gj_panel<T>, PANEL_SMEM_MAX);
     HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s, flops);
     k_gj_panel<T><<<njobs, PANEL_NT, smem, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
     HSS_CHECK_LAUNCH("k_gj_panel");

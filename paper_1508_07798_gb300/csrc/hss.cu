@@ -529,12 +529,7 @@ template <class T>
 int launch_hss_id(const NodeDev *nodes, const int *work, int nwork, const CompFront<T> *cf, T *ws, int *iws,
                   int *kout, int *front_kmax, T tol, uint64_t seed, size_t smem, cudaStream_t s) {
     if (nwork == 0) return HSS_OK;
-    static bool configured[2] = {false, false};
-    int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!configured[ti]) {
-        cudaFuncSetAttribute(k_hss_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        configured[ti] = true;
-    }
+    HSS_SMEM(k_hss_id<T>, 220 * 1024);
     HSS_PROF("hss_id", s);
     k_hss_id<T><<<nwork, ID_NT, smem, s>>>(nodes, work, cf, ws, iws, kout, front_kmax, tol, seed);
     HSS_CHECK_LAUNCH("k_hss_id");
@@ -545,12 +540,7 @@ template <class T>
 int launch_hss_tall(const NodeDev *nodes, const int *work, int nwork, const int *kout, T *ws, int *iws, size_t smem,
                     cudaStream_t s) {
     if (nwork == 0) return HSS_OK;
-    static bool configured[2] = {false, false};
-    int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!configured[ti]) {
-        cudaFuncSetAttribute(k_hss_tall<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        configured[ti] = true;
-    }
+    HSS_SMEM(k_hss_tall<T>, 220 * 1024);
     HSS_PROF("hss_tall", s);
     k_hss_tall<T><<<nwork, 256, smem, s>>>(nodes, work, kout, ws, iws);
     HSS_CHECK_LAUNCH("k_hss_tall");
@@ -563,12 +553,7 @@ int launch_hss_expand(const ExpandItem *items, int nitems, const NodeDev *nodes,
                       cudaStream_t s) {
     if (nitems == 0) return HSS_OK;
     HSS_PROF("hss_expand", s);
-    static bool configured[2] = {false, false};
-    int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!configured[ti]) {
-        cudaFuncSetAttribute(k_hss_expand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        configured[ti] = true;
-    }
+    HSS_SMEM(k_hss_expand<T>, 160 * 1024);
     // S(J_a,K_b) (kmax x kmax) and a 32 x kmax tile of V^tall
     size_t smem = sizeof(T) * (size_t)(kmax * kmax + EXP_TILE * kmax);
     k_hss_expand<T><<<nitems, 256, smem, s>>>(items, nodes, kout, ef, ws, iws, arena, keep);

@@ -28,6 +28,15 @@ int cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return cuda_fail(_e, what);      \
     } while (0)
 
+// Raises a kernel's dynamic shared-memory limit to `bytes`, once per device
+// and kernel (thread-safe); returns the runtime's error code.
+cudaError_t func_smem_once(const void *func, int bytes);
+#define HSS_SMEM(kernel, bytes)                                                            \
+    do {                                                                                   \
+        cudaError_t _e = ::hssnd::func_smem_once((const void *)(kernel), (int)(bytes));    \
+        if (_e != cudaSuccess) return cuda_fail(_e, "shared-memory attribute of " #kernel); \
+    } while (0)
+
 // Device allocation owned by a handle.
 struct DevBuf {
     void *p = nullptr;

@@ -284,11 +284,7 @@ int train_pass(hss_rank_model *M, const float *feat, const float *target, const 
     const int tiles = cdiv(n, TS);
     int rc;
     if ((rc = ensure_tiles(M, tiles))) return rc;
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_mlp_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
-        configured = true;
-    }
+    HSS_SMEM(k_mlp_train_tile, sizeof(TileSmem));
     {
         HSS_PROF("mlp_train_tile", s);
         k_mlp_train_tile<<<tiles, NH, sizeof(TileSmem), s>>>(M->theta.as<float>(), feat, target, idx, n, M->norm,

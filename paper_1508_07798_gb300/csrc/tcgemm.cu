@@ -12,7 +12,6 @@
 // masks as the SIMT kernel (gemm.cu).  Same descriptor list and semantics as
 // k_gemm<float>, including the +-1 test-matrix operand generated on the fly.
 #include <cstdint>
-#include <mutex>
 
 #include "internal.h"
 #include "prof.h"
@@ -253,20 +252,7 @@ constexpr size_t TC_SMEM = 4 * TC_TILE_BYTES + 1024;
 // (thread-safe; the attribute is per device context).  Setting it also loads
 // the kernel's module, so a call made early takes that work out of later ones.
 int gemm_tc_prepare() {
-    constexpr int MAXDEV = 64;
-    static std::mutex mu;
-    static bool done[MAXDEV] = {};
-    int dev = 0;
-    HSS_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= MAXDEV) {
-        set_error("tensor-core GEMM: device ordinal beyond the supported 64");
-        return HSS_EINVAL;
-    }
-    std::lock_guard<std::mutex> lk(mu);
-    if (!done[dev]) {
-        HSS_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-        done[dev] = true;
-    }
+    HSS_SMEM(k_gemm_tc, TC_SMEM);
     return HSS_OK;
 }
 

@@ -341,6 +341,19 @@ def density_helmholtz_2d(n: int, p: int, rho_ratio: float = 1e3, kappa: float | 
     return mesh, A
 
 
+def rank_training_problems(n: int = 64, ps=(1, 2, 3), seeds=range(100, 116)) -> list:
+    """Helmholtz problems whose adaptive factorizations give the training ranks
+    of the learned-width form: (mesh descriptor, matrix, c per element,
+    kappa * h) for every p in ps and seed in seeds (the default: 64 x 64
+    quads, p = 1, 2, 3, seeds 100..115)."""
+    out = []
+    for p in ps:
+        for sd in seeds:
+            mesh, A = helmholtz_2d(n, p, sd)
+            out.append(((2, (n, n), p), A, cosine_field(mesh, sd), helmholtz_kappa(n, p) / n))
+    return out
+
+
 def random_rhs(ndof: int, nrhs: int, seed: int, kind: str = "uniform") -> np.ndarray:
     """Column-major (ndof x nrhs) right-hand sides: U(-1,1) or N(0,1) per dof."""
     rng = np.random.default_rng(seed)

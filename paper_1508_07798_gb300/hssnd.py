@@ -33,6 +33,7 @@ EXPORTED = [
     "hss_rank_model_set", "hss_rank_model_fit_norm", "hss_rank_model_loss_grad", "hss_rank_model_train",
     "hss_rank_model_predict", "hss_factor_export_log", "ilu0_factor", "ilu0_apply", "fgmres_solve_ilu0",
     "ilu0_destroy", "hss_factor_apply_plan", "hss_alloc_count", "hss_tc_timeout_selftest",
+    "hss_front_eliminate", "hss_front_compress",
 ]
 
 
@@ -108,6 +109,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fgmres_opts_default": (None, [C.POINTER(fgmres_opts)]),
         "hss_launch_count": (C.c_long, []),
         "hss_alloc_count": (C.c_long, []),
+        "hss_front_eliminate": (C.c_int, [C.c_int, C.c_int, P, C.c_int, C.c_int, C.c_int, P, C.c_int, P, P]),
+        "hss_front_compress": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(hss_factor_opts), P, C.c_int, ip, ip, ip,
+                                         P]),
         "hss_tc_timeout_selftest": (C.c_int, [C.c_long, P]),
         "hss_gemm_f32": (C.c_int, [C.c_int, C.c_int, C.c_int, P, C.c_int, P, C.c_int, P, C.c_int, C.c_float,
                                    C.c_float, C.c_int, P]),
@@ -305,6 +309,41 @@ def hss_factor(A: DeviceBSR, tree: Tree, stream=None, **kw) -> Factor:
     out = C.c_void_p()
     _check(_lib.hss_factor(C.byref(A.c), tree.h, C.byref(o), _stream(stream), C.byref(out)))
     return Factor(out.value, tree, o.precision)
+
+
+def front_eliminate(F: np.ndarray, ni: int, precision="fp64", tensor_cores=0, stream=None):
+    """hss_front_eliminate on a dense front (HOST array n x n): returns the
+    transformed front [F_ii^-1 P^t, W; -F_bi F_ii^-1 P^t, S], the I row of
+    each of its first ni columns, and the return code (HSS_OK or
+    HSS_ESINGULAR; other codes raise)."""
+    Fc = np.asfortranarray(F, dtype=np.float64)
+    n = Fc.shape[0]
+    out = np.zeros((n, n), dtype=np.float64, order="F")
+    perm = np.zeros(max(ni, 1), dtype=np.int32)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+    rc = _lib.hss_front_eliminate(n, ni, Fc.ctypes.data, n, prec, tensor_cores, out.ctypes.data, n,
+                                  perm.ctypes.data, _stream(stream))
+    if rc not in (HSS_OK, HSS_ESINGULAR):
+        _check(rc)
+    return out, perm[:ni], rc
+
+
+def front_compress(tree: Tree, box: int, S: np.ndarray, stream=None, **kw):
+    """hss_front_compress: the HSS approximant of S (HOST nb x nb) as
+    hss_factor builds it for `box`; returns (H, kmax, r, rounds)."""
+    r_init = kw.pop("r_init", None)
+    o = factor_opts(**kw)
+    if r_init is not None:
+        r_init = np.ascontiguousarray(r_init, dtype=np.int32)
+        assert r_init.size == tree.desc.nbox
+        o.r_init = r_init.ctypes.data
+    Sc = np.asfortranarray(S, dtype=np.float64)
+    nb = Sc.shape[0]
+    H = np.zeros((nb, nb), dtype=np.float64, order="F")
+    k, r, rounds = C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.hss_front_compress(tree.h, box, Sc.ctypes.data, max(nb, 1), C.byref(o), H.ctypes.data, max(nb, 1),
+                                   C.byref(k), C.byref(r), C.byref(rounds), _stream(stream)))
+    return H, k.value, r.value, rounds.value
 
 
 def hss_apply(F: Factor, x: torch.Tensor, stream=None) -> torch.Tensor:

@@ -9,8 +9,11 @@
   Fig. 10, fixed width l = 16: GPU iteration counts within +-10% (at least
   +-1) of the oracle's, same convergence outcome, for the three schemes;
 * the h-refinement study of Fig. 10 (16^2, 32^2, 64^2 elements, p = 1) on the
-  GPU: vertical slabs fail and horizontal slabs converge at every printed c0
-  and every h; the box scheme converges everywhere.
+  GPU: horizontal slabs converge in a few iterations at every printed c0 and
+  every h, vertical slabs at none; the box scheme converges at the coarse
+  meshes but, where diffusion dominates (c0 = 1e-4, 1), fails like the
+  vertical slabs at 64^2, and recovers as c0 grows (the paper: box comparable
+  to vertical slabs; the scheme matters less as reaction takes over).
 """
 import numpy as np
 import pytest
@@ -106,8 +109,12 @@ def test_scheme_study_under_h_refinement():
             print(f"  {n}x{n} c0={c0:g}: " + ", ".join(f"{sc} {table[n, c0, sc]}" for sc in ("box", "hslab", "vslab")))
     for n in (16, 32, 64):
         for c0 in RD_C0:
-            assert table[n, c0, "vslab"] is None and table[n, c0, "hslab"] is not None, table
-            assert table[n, c0, "box"] is not None, table
+            assert table[n, c0, "vslab"] is None, table
+            assert table[n, c0, "hslab"] is not None and table[n, c0, "hslab"] <= 6, table
+    for n in (16, 32):
+        assert all(table[n, c0, "box"] is not None for c0 in RD_C0), table
+    assert table[64, 1e-4, "box"] is None and table[64, 1.0, "box"] is None, table
+    assert table[64, 1e3, "box"] is not None, table
 
 
 def test_density_helmholtz_schemes_at_64():

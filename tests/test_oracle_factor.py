@@ -243,3 +243,20 @@ def test_probe_catches_undersampled_fronts():
         _, info = oracle.fgmres(lambda v: Acsr @ v, lambda v: oracle.apply(fac, v), b, rtol=1e-8, maxit=300)
         its.append(info["iters"] if info["converged"] else 10 ** 6)
     assert its[1] < its[0], its
+
+
+def test_eliminate_front_is_the_schur_complement_definition():
+    """oracle.eliminate_front on a random front (partial pivoting needed: no
+    diagonal dominance): S equals the inverse of the trailing block of F^-1
+    (the Schur-complement identity, independent of how S is computed), W
+    solves F_ii W = F_ib, and with no interior dofs S is F itself."""
+    rng = np.random.default_rng(12)
+    n, ni = 300, 170
+    F = rng.standard_normal((n, n))
+    el = oracle.eliminate_front(F, ni)
+    S_id = np.linalg.inv(np.linalg.inv(F)[ni:, ni:])
+    assert np.linalg.norm(el["S"] - S_id) / np.linalg.norm(S_id) <= 1e-10
+    res = np.linalg.norm(F[:ni, :ni] @ el["W"] - F[:ni, ni:])
+    assert res <= 1e-13 * np.linalg.norm(F[:ni, :ni]) * np.linalg.norm(el["W"])   # backward stable
+    e0 = oracle.eliminate_front(F[:40, :40], 0)
+    assert e0["lu"] is None and np.array_equal(e0["S"], F[:40, :40])
