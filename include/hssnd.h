@@ -89,8 +89,11 @@ typedef struct hss_factor_opts {
     uint64_t seed;          /* seed of the +-1 test matrices; default 0 */
     int keep_schur;         /* 1: keep a copy of every front's S and H for hss_factor_export_front */
     int tensor_cores;       /* FP32 form only: 0 (default) SIMT FMA; 1 tcgen05 TF32 with the three-product
-                               hi/lo split (FP32 accuracy) for products with K >= 128 (the sampling
-                               products); 2 the same with a single TF32 product */
+                               hi/lo split (FP32 accuracy) for products with M, K >= 128 and N >= 32 (the
+                               sampling products and the K = 128 updates of the blocked sweep), operands
+                               brought in by TMA where they are 16-byte aligned with leading dimensions
+                               that are multiples of 4 (front sizes divisible by 4), staged by the threads
+                               otherwise; 2 tcgen05 with a single TF32 product (threads staging) */
     const int *r_init;      /* HOST array of one initial sample width per box (NULL, the default: r0 for
                                every front), e.g. from hss_rank_model_predict; the adaptive growth by dr
                                still applies whenever a rank exceeds r - oversample */
@@ -244,15 +247,19 @@ int hss_front_compress(const hss_tree *t, int box, const double *S, int lds, con
 
 /* C = alpha A B + beta C in FP32, DEVICE column-major m x k, k x n, m x n
  * (the GEMM of the FP32 form, exposed for testing and reuse).  engine: 0 SIMT
- * FMA; 1 tcgen05 TF32 with the three-product hi/lo split; 2 tcgen05 single
- * TF32.  No counterpart in the paper (a building block of eq. (32)'s update).
+ * FMA; 1 tcgen05 TF32 with the three-product hi/lo split, operands staged by
+ * the threads; 2 tcgen05 single TF32; 3 tcgen05 TF32 with the hi/lo split,
+ * operands brought in by TMA (cp.async.bulk.tensor) through a 3-stage ring
+ * (needs A and B 16-byte aligned and lda, ldb multiples of 4; other operands
+ * run on engine 1).  No counterpart in the paper (a building block of eq. (32)'s update).
  * k = 0 gives C = beta C with every engine.  Synchronizes `stream`;
  * HSS_ETIMEOUT if a bounded tensor-core wait expired. */
 int hss_gemm_f32(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
                  float alpha, float beta, int engine, void *stream);
 
 /* hss_gemm_f32 without any memory allocation.  No counterpart in the paper.
- * Same arguments, layout, engines and result as hss_gemm_f32; the difference
+ * Same arguments, layout, engines 0-2 and result as hss_gemm_f32 (engine 3,
+ * whose tensor maps are built per call, is not offered here); the difference
  * is where the launch records live: hss_gemm_f32 puts its GEMM descriptor,
  * tile list and tensor-core timeout flag in workspace it allocates per call,
  * this variant keeps them in one fixed device array inside the library

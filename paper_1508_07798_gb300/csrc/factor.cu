@@ -94,6 +94,72 @@ int run_gemm(const Engine &e, bool tc, const GemmDesc<T> *dd, const GemmTile *dt
     return gemm_batched<T>(dd, dt, n, s, flops);
 }
 
+// Tensor-core tiles of consecutive launch groups (group g owns tiles
+// [off[g], off[g + 1])) split between the TMA-fed kernel, for problems whose
+// operands it can address (engine 1 only), and the thread-staging kernel.
+struct TcSplit {
+    std::vector<GemmTile> tma, stg;
+    std::vector<int> tma_off, stg_off;
+    std::vector<double> tma_fl, stg_fl;
+    std::vector<char> use;          // per problem: on the TMA kernel
+    TmaGemmDesc *d_tdescs = nullptr;
+    GemmTile *d_tma = nullptr, *d_stg = nullptr;
+};
+
+template <class T>
+int split_tc(const Engine &eng, const std::vector<GemmDesc<T>> &descs, const std::vector<GemmTile> &tiles,
+             const std::vector<int> &off, TcSplit &out, Work &W) {
+    const int ng = (int)off.size() - 1;
+    out.use.assign(descs.size(), 0);
+    std::vector<int> ntile(descs.size(), 0);
+    for (const GemmTile &t : tiles) ntile[t.desc]++;
+    if constexpr (std::is_same<T, float>::value) {
+        if (eng.tc == 1)
+            for (size_t i = 0; i < descs.size(); ++i) out.use[i] = ntile[i] > 0 && gemm_tma_eligible(descs[i]);
+    }
+    out.tma.clear();
+    out.stg.clear();
+    out.tma_off.assign(ng + 1, 0);
+    out.stg_off.assign(ng + 1, 0);
+    out.tma_fl.assign(ng, 0.0);
+    out.stg_fl.assign(ng, 0.0);
+    for (int g = 0; g < ng; ++g) {
+        out.tma_off[g] = (int)out.tma.size();
+        out.stg_off[g] = (int)out.stg.size();
+        for (int q = off[g]; q < off[g + 1]; ++q) {
+            const GemmTile &t = tiles[q];
+            const double fl = gemm_flops(descs[t.desc]) / ntile[t.desc];
+            if (out.use[t.desc]) {
+                out.tma.push_back(t);
+                out.tma_fl[g] += fl;
+            } else {
+                out.stg.push_back(t);
+                out.stg_fl[g] += fl;
+            }
+        }
+    }
+    out.tma_off[ng] = (int)out.tma.size();
+    out.stg_off[ng] = (int)out.stg.size();
+    int rc;
+    if ((rc = W.up(out.stg, &out.d_stg))) return rc;
+    if constexpr (std::is_same<T, float>::value) {
+        if (!out.tma.empty()) {
+            if ((rc = W.up(out.tma, &out.d_tma)) || (rc = gemm_tma_descs(descs, out.use, W, &out.d_tdescs))) return rc;
+        }
+    }
+    return HSS_OK;
+}
+
+// Launch group g of a split: its TMA tiles, then its staging tiles.
+template <class T>
+int run_tc_group(const Engine &eng, const TcSplit &sp, const GemmDesc<T> *d_descs, int g, cudaStream_t s) {
+    int rc;
+    const int nt = sp.tma_off[g + 1] - sp.tma_off[g], ns = sp.stg_off[g + 1] - sp.stg_off[g];
+    if (nt > 0 && (rc = gemm_tma(sp.d_tdescs, sp.d_tma + sp.tma_off[g], nt, eng.err, s, sp.tma_fl[g]))) return rc;
+    if (ns > 0 && (rc = run_gemm<T>(eng, true, d_descs, sp.d_stg + sp.stg_off[g], ns, s, sp.stg_fl[g]))) return rc;
+    return HSS_OK;
+}
+
 template <class T> int choose_kb(int ni) {
     for (int kb = PANEL_KB_MAX; kb >= 8; kb /= 2)
         if ((long)ni * kb * (long)sizeof(T) + (long)ni * 4 <= PANEL_SMEM_MAX) return kb;
@@ -312,10 +378,16 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         (rc = W.dalloc(xtotal, &d_x)) || (rc = W.dalloc(mtotal, &d_mv)))
         return rc;
     for (size_t i = 0; i < descs.size(); ++i) descs[i].B = (desc_blk[i] ? d_aoldB : d_aold) + desc_b[i];
+    TcSplit tsp, btsp;   // tensor-core tiles of the in-block and block-end updates
     if ((rc = W.up(jobs, &d_jobs)) || (rc = W.up(bjobs, &d_bjobs)) || (rc = W.up(descs, &d_descs)) ||
-        (rc = W.up(tiles, &d_tiles)) || (rc = W.up(ttiles, &d_ttiles)) || (rc = W.up(btiles, &d_btiles)) ||
-        (rc = W.up(bttiles, &d_bttiles)) || (rc = W.up(ptiles, &d_ptiles)) || (rc = W.up(bptiles, &d_bptiles)))
+        (rc = W.up(tiles, &d_tiles)) || (rc = W.up(btiles, &d_btiles)) || (rc = W.up(ptiles, &d_ptiles)) ||
+        (rc = W.up(bptiles, &d_bptiles)))
         return rc;
+    if (eng.tc && ((rc = split_tc<T>(eng, descs, ttiles, ttile_off, tsp, W)) ||
+                   (rc = split_tc<T>(eng, descs, bttiles, bttile_off, btsp, W))))
+        return rc;
+    (void)d_ttiles;
+    (void)d_bttiles;
     for (int st = 0; st < maxsteps; ++st) {
         for (const Group &g : groups[st]) {
             if (g.reg)
@@ -332,18 +404,14 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         if ((rc = gemm_batched<T>(d_descs, d_tiles + tile_off[st], tile_off[st + 1] - tile_off[st], s,
                                   step_flops[st])))
             return rc;
-        if ((rc = run_gemm<T>(eng, true, d_descs, d_ttiles + ttile_off[st], ttile_off[st + 1] - ttile_off[st], s,
-                              tstep_flops[st])))
-            return rc;
+        if (eng.tc && (rc = run_tc_group<T>(eng, tsp, d_descs, st, s))) return rc;
         if ((rc = launch_gj_block_post<T>(d_bptiles + bptile_off[st], bptile_off[st + 1] - bptile_off[st], d_bjobs,
                                           d_jobs, d_fr, arena, d_aoldB, d_mv, s)))
             return rc;
         if ((rc = gemm_batched<T>(d_descs, d_btiles + btile_off[st], btile_off[st + 1] - btile_off[st], s,
                                   bstep_flops[st])))
             return rc;
-        if ((rc = run_gemm<T>(eng, true, d_descs, d_bttiles + bttile_off[st], bttile_off[st + 1] - bttile_off[st], s,
-                              btstep_flops[st])))
-            return rc;
+        if (eng.tc && (rc = run_tc_group<T>(eng, btsp, d_descs, st, s))) return rc;
     }
     return HSS_OK;
 }
@@ -517,14 +585,19 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         {
             GemmDesc<T> *a, *c2;
             GemmTile *b, *bc, *d2;
-            if ((rc = W.up(g1, &a)) || (rc = W.up(t1, &b)) || (rc = W.up(t1c, &bc)) || (rc = W.up(g2, &c2)) ||
-                (rc = W.up(t2, &d2)))
-                return rc;
-            double f1 = 0, f1c = 0, f2 = 0;
-            for (auto &d : g1) (use_tc(eng, d) ? f1c : f1) += gemm_flops(d);
+            if ((rc = W.up(g1, &a)) || (rc = W.up(t1, &b)) || (rc = W.up(g2, &c2)) || (rc = W.up(t2, &d2))) return rc;
+            (void)bc;
+            double f1 = 0, f2 = 0;
+            for (auto &d : g1)
+                if (!use_tc(eng, d)) f1 += gemm_flops(d);
             for (auto &d : g2) f2 += gemm_flops(d);
             if ((rc = gemm_batched<T>(a, b, (int)t1.size(), s, f1))) return rc;
-            if ((rc = run_gemm<T>(eng, true, a, bc, (int)t1c.size(), s, f1c))) return rc;
+            if (!t1c.empty()) {
+                TcSplit sp;
+                if ((rc = split_tc<T>(eng, g1, t1c, std::vector<int>{0, (int)t1c.size()}, sp, W)) ||
+                    (rc = run_tc_group<T>(eng, sp, a, 0, s)))
+                    return rc;
+            }
             if ((rc = gemm_batched<T>(c2, d2, (int)t2.size(), s, f2))) return rc;
         }
         // ---- interpolative decompositions, deepest HSS level first

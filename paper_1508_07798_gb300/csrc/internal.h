@@ -203,6 +203,19 @@ void gemm_tc_tiles_for(const GemmDesc<float> &d, int desc_index, std::vector<Gem
 // Sets the tensor-core kernel's shared-memory attribute on the current device
 // (once per device, thread-safe) and so loads its module.
 int gemm_tc_prepare();
+// Tensor-core GEMM fed by TMA (tcgemm_tma.cu): the same problems and 128 x 128
+// tiles as gemm_tc with the hi/lo split; for problems whose A (and B, unless
+// generated) are 16-byte aligned with leading dimensions that are multiples of
+// 4 floats.  gemm_tma_descs builds the tensor maps of the problems flagged in
+// `use` (zero entries elsewhere) and uploads them through W.
+struct TmaGemmDesc;
+bool gemm_tma_eligible(const GemmDesc<float> &d);
+int gemm_tma_prepare();
+struct Work;
+int gemm_tma_descs(const std::vector<GemmDesc<float>> &descs, const std::vector<char> &use, Work &W,
+                   TmaGemmDesc **out);
+int gemm_tma(const TmaGemmDesc *d_descs, const GemmTile *d_tiles, int ntiles, int *err, cudaStream_t s,
+             double flops);
 // C = alpha * 0 + beta * C (the product with k = 0) without descriptors.
 int gemm_f32_k0(float *C, int ldc, int m, int n, float alpha, float beta, cudaStream_t s);
 // Loads the module of the FP32 SIMT GEMM kernels.

@@ -288,7 +288,7 @@ using namespace hssnd;
 extern "C" int hss_gemm_f32(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
                             float alpha, float beta, int engine, void *stream) {
     if (m < 0 || n < 0 || k < 0 || !A || !B || !C || lda < std::max(1, m) || ldb < std::max(1, k) ||
-        ldc < std::max(1, m) || engine < 0 || engine > 2) {
+        ldc < std::max(1, m) || engine < 0 || engine > 3) {
         set_error("hss_gemm_f32: invalid argument");
         return HSS_EINVAL;
     }
@@ -312,6 +312,7 @@ extern "C" int hss_gemm_f32(int m, int n, int k, const float *A, int lda, const 
     d.k = k;
     d.alpha = alpha;
     d.beta = beta;
+    if (engine == 3 && !gemm_tma_eligible(d)) engine = 1;   // operands TMA cannot address
     std::vector<GemmTile> tiles;
     if (engine == 0)
         gemm_tiles_for(d, 0, tiles);
@@ -325,10 +326,15 @@ extern "C" int hss_gemm_f32(int m, int n, int k, const float *A, int lda, const 
     int rc;
     if ((rc = W.up(dv, &dd)) || (rc = W.up(tiles, &dt)) || (rc = W.dalloc(1, &err))) return rc;
     HSS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    if (engine == 0)
+    if (engine == 0) {
         rc = gemm_batched<float>(dd, dt, (int)tiles.size(), s, 2.0 * m * n * k);
-    else
+    } else if (engine == 3) {
+        TmaGemmDesc *td;
+        if ((rc = gemm_tma_descs(dv, std::vector<char>{1}, W, &td))) return rc;
+        rc = gemm_tma(td, dt, (int)tiles.size(), err, s, 2.0 * m * n * k);
+    } else {
         rc = gemm_tc(dd, dt, (int)tiles.size(), engine == 1 ? 1 : 0, err, s, 2.0 * m * n * k);
+    }
     if (rc) return rc;
     int herr = 0;
     HSS_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -290,10 +290,17 @@ def test_tensor_core_wait_timeout_is_reported():
     assert (C.double() - ref).abs().max().item() <= 2e-6 * (A.double().abs() @ B.double().abs()).max().item()
 
 
-@pytest.mark.parametrize("m,n,k", [(300, 200, 70), (128, 128, 32), (513, 77, 257), (64, 300, 5), (1, 1, 1)])
+@pytest.mark.parametrize("m,n,k", [(300, 200, 70), (128, 128, 32), (513, 77, 257), (64, 300, 5), (1, 1, 1),
+                                   (300, 260, 132), (256, 512, 1024), (130, 132, 16), (129, 4, 20)])
 def test_gemm_f32_engines(m, n, k):
     """The FP32 GEMM engines against an FP64 product: SIMT FMA and tcgen05
-    TF32 with the hi/lo split at FP32 accuracy, single TF32 at TF32 accuracy."""
+    TF32 with the hi/lo split at FP32 accuracy (threads staging the operands,
+    engine 1, or TMA through the 3-stage ring, engine 3), single TF32 at TF32
+    accuracy.  Engine 3 runs where the operands suit TMA (n and k multiples of
+    4 here: the column-major operands of the row-major call have leading
+    dimensions n and k), with ragged tiles and K chunks (k = 20, 132), one
+    chunk (16) and a long ring (1024 = 64 chunks of 16); elsewhere it falls
+    back to engine 1."""
     import torch
     hs = _hss()
     g = torch.Generator(device="cpu").manual_seed(m * 7 + n)
@@ -302,24 +309,34 @@ def test_gemm_f32_engines(m, n, k):
     C0 = torch.randn(m, n, generator=g).cuda()
     ref = (A.double() @ B.double()) * 0.5 + C0.double() * 2.0
     scale = (A.double().abs() @ B.double().abs()).max().item() + 1.0
-    for engine, tol in ((0, 2e-6), (1, 2e-6), (2, 2e-3)):
+    for engine, tol in ((0, 2e-6), (1, 2e-6), (2, 2e-3), (3, 2e-6)):
         C = C0.clone()
+        hs.profile_reset()
+        hs.profile_enable(True)
         hs.gemm_f32(A, B, C, alpha=0.5, beta=2.0, engine=engine)
+        hs.profile_enable(False)
+        cls = hs.profile_read()
+        if engine == 3:
+            assert ("gemm_tma" in cls) == (n % 4 == 0 and k % 4 == 0), (cls.keys(), n, k)
         torch.cuda.synchronize()
         err = (C.double() - ref).abs().max().item() / scale
         assert err <= tol, (engine, err)
 
 
-def test_fp32_form_tensor_cores_match_simt():
+@pytest.mark.parametrize("p", [2, 1])
+def test_fp32_form_tensor_cores_match_simt(p):
     """The FP32 form with tcgen05 GEMMs (TF32 hi/lo split) against the same form
     with SIMT FMA GEMMs.  With compression off (pure arithmetic), both FP32
     Schur complements stay within the same order of the FP64 ones; with
-    compression on, both solves converge alike."""
+    compression on, both solves converge alike.  p = 2 (9 dofs per element:
+    odd front sizes) runs the thread-staging kernel; p = 1 (4 dofs per
+    element: 16-byte aligned fronts) runs the sampling products Y = S Omega
+    and Z = S^t Psi on the TMA kernel (the profile shows it)."""
     import torch
     hs = _hss()
-    mesh, A = _setup("helm", (32, 32), 2)
+    mesh, A = _setup("helm", (32, 32), p)
     dA = hs.DeviceBSR.from_host(A)
-    tree = hs.nd_order((2, (32, 32), 2), dA)
+    tree = hs.nd_order((2, (32, 32), p), dA)
     F64 = hs.hss_factor(dA, tree, compress=0, keep_schur=1)
     Ft = hs.hss_factor(dA, tree, compress=0, precision="fp32", tensor_cores=1, keep_schur=1)
     Fs = hs.hss_factor(dA, tree, compress=0, precision="fp32", tensor_cores=0, keep_schur=1)
@@ -334,8 +351,20 @@ def test_fp32_form_tensor_cores_match_simt():
         # the split drops the lo*lo product and the tensor core's internal sums are
         # not single-rounded FMAs: a few times the FMA-chain error, same order
         assert et <= 10.0 * es + 1e-6 and et <= 1e-2, (b, et, es)
-    Ftc = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=1)
-    Fsi = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=0)
+    hs.profile_reset()
+    hs.profile_enable(True)
+    Ftc = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=1, keep_schur=1)
+    hs.profile_enable(False)
+    cls = hs.profile_read()
+    assert ("gemm_tma" in cls) == (p == 1), cls.keys()
+    Fsi = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=0, keep_schur=1)
+    # same ranks and widths from the two engines' samples, approximants of the same quality
+    lt, ls = Ftc.export_log(), Fsi.export_log()
+    assert (np.abs(lt["kmax"] - ls["kmax"]) <= 1).all() and (lt["r"] == ls["r"]).mean() >= 0.99
+    for b in big:
+        St, Ht, _, _ = Ftc.export_front(b)
+        Ss, Hs_, _, _ = Fsi.export_front(b)
+        assert _rel(Ht, St) <= 10.0 * _rel(Hs_, Ss) + 1e-5, b
     bvec = torch.as_tensor(dg.point_source_rhs(mesh, 0)[:, 0], device="cuda")
     xt, st = hs.fgmres_solve(dA, Ftc, bvec, rtol=1e-8)
     xs, ss = hs.fgmres_solve(dA, Fsi, bvec, rtol=1e-8)

@@ -192,3 +192,19 @@ def test_blocked_sweep_exact_mode_3d_poisson():
     print(f"FP32 exact factor: apply against the oracle {e32:.2e}; FGMRES {st.iters} iterations to {res:.2e}")
     assert e32 <= 1e-3
     assert st.converged and res <= 1e-10 and st.iters <= 6
+    # the same with the tensor cores: the K = 128 block-end updates of the
+    # blocked sweep (16-byte aligned fronts) run on the TMA-fed tcgen05 kernel
+    hs.profile_reset()
+    hs.profile_enable(True)
+    Ftc = hs.hss_factor(dA, tree, compress=0, precision="fp32", tensor_cores=1)
+    hs.profile_enable(False)
+    cls = hs.profile_read()
+    Ytc = hs.hss_apply(Ftc, torch.as_tensor(X, device="cuda")).cpu().numpy()
+    etc = rel_fro(Ytc, Yo)
+    xt, stt = hs.fgmres_solve(dA, Ftc, b, rtol=1e-10, restart=30)
+    rt = np.linalg.norm(X[:, 0] - Acsr @ xt.cpu().numpy()) / np.linalg.norm(X[:, 0])
+    print(f"FP32 exact factor, tensor cores ({cls.get('gemm_tma', (0, 0))[1]} TMA launches, "
+          f"{cls.get('gemm_tma', (0.0,))[0]:.2f} ms): apply {etc:.2e}; FGMRES {stt.iters} iterations to {rt:.2e}")
+    assert "gemm_tma" in cls
+    assert etc <= 10 * e32 + 1e-6
+    assert stt.converged and rt <= 1e-10 and stt.iters <= st.iters + 1
