@@ -328,10 +328,11 @@ def test_fp32_form_tensor_cores_match_simt(p):
     """The FP32 form with tcgen05 GEMMs (TF32 hi/lo split) against the same form
     with SIMT FMA GEMMs.  With compression off (pure arithmetic), both FP32
     Schur complements stay within the same order of the FP64 ones; with
-    compression on, both solves converge alike.  p = 2 (9 dofs per element:
-    odd front sizes) runs the thread-staging kernel; p = 1 (4 dofs per
-    element: 16-byte aligned fronts) runs the sampling products Y = S Omega
-    and Z = S^t Psi on the TMA kernel (the profile shows it)."""
+    compression on, both solves converge alike.  p = 2 (9 dofs per element)
+    runs the fronts whose size is not a multiple of 4 on the thread-staging
+    kernel and the others on the TMA kernel; p = 1 (4 dofs per element: every
+    front 16-byte aligned) runs all sampling products Y = S Omega and
+    Z = S^t Psi on the TMA kernel (the profile shows which ran)."""
     import torch
     hs = _hss()
     mesh, A = _setup("helm", (32, 32), p)
@@ -356,7 +357,8 @@ def test_fp32_form_tensor_cores_match_simt(p):
     Ftc = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=1, keep_schur=1)
     hs.profile_enable(False)
     cls = hs.profile_read()
-    assert ("gemm_tma" in cls) == (p == 1), cls.keys()
+    if p == 1:   # every front size is a multiple of 4 (p = 2: only those of 36 k dofs)
+        assert "gemm_tma" in cls and "gemm_tc" not in cls, cls.keys()
     Fsi = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=0, keep_schur=1)
     # same ranks and widths from the two engines' samples, approximants of the same quality
     lt, ls = Ftc.export_log(), Fsi.export_log()
