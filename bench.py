@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--workload", default="helmholtz64", choices=["helmholtz64", "batched256"],
                     help="helmholtz64: the timed workload (default); batched256: 256 independent "
                          "instances x 32 right-hand sides through the batched form (its own JSON line)")
+    ap.add_argument("--tensor-cores", type=int, default=0, choices=[0, 1, 3],
+                    help="GEMM engine of the FP32 forms: 0 SIMT, 1 tcgen05 (fixed rule), 3 per shape class by timing")
     ap.add_argument("--probe", type=int, default=4,
                     help="residual probe vectors per accepted front in the learned-width form (0: off)")
     ap.add_argument("--quick", action="store_true",
@@ -241,9 +243,11 @@ def bench_ours(args, rank, world):
             marks[0].record(stream)
         if prec == "fp32_learned":
             r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h))[1]
-            F = hssnd.hss_factor(dA, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1, probe=args.probe)
+            F = hssnd.hss_factor(dA, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1, probe=args.probe,
+                                 tensor_cores=args.tensor_cores)
         else:
-            F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec, autotune=1)
+            F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec, autotune=1,
+                                 tensor_cores=args.tensor_cores if prec == "fp32" else 0)
         if marks is not None:
             marks[1].record(stream)
         x, st = hssnd.fgmres_solve(dA, F, b, rtol=RTOL, restart=RESTART)

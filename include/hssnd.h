@@ -93,7 +93,10 @@ typedef struct hss_factor_opts {
                                sampling products and the K = 128 updates of the blocked sweep), operands
                                brought in by TMA where they are 16-byte aligned with leading dimensions
                                that are multiples of 4 (front sizes divisible by 4), staged by the threads
-                               otherwise; 2 tcgen05 with a single TF32 product (threads staging) */
+                               otherwise; 2 tcgen05 with a single TF32 product (threads staging); 3 per
+                               shape class (operand forms, TMA eligibility, m, n, k rounded up to powers of
+                               two) the faster of SIMT and the tcgen05 split kernel, timed on a scratch C
+                               the first time the class appears and cached for the process */
     const int *r_init;      /* HOST array of one initial sample width per box (NULL, the default: r0 for
                                every front), e.g. from hss_rank_model_predict; the adaptive growth by dr
                                still applies whenever a rank exceeds r - oversample */
@@ -197,6 +200,10 @@ typedef struct hss_factor_info {
     int nfronts;
     int capped_fronts;
     int probe_regrown;      /* sampling rounds added because a residual probe failed */
+    long gemm_simt;         /* GEMM problems (one per front and update/sampling step) run on SIMT FMA */
+    long gemm_tma;          /* ... on tcgen05 with TMA-fed operands */
+    long gemm_staged;       /* ... on tcgen05 with thread-staged operands */
+    long gemm_timed;        /* problems the GEMM engine tuner timed (tensor_cores = 3) */
 } hss_factor_info;
 int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info);
 
@@ -226,8 +233,8 @@ int hss_apply(const hss_factor_t *f, int nrhs, const double *x, int ldx, double 
  * transformed front [F_ii^-1 P^t, W; -F_bi F_ii^-1 P^t, S] with
  * W = F_ii^-1 F_ib and S = F_bb - F_bi W; perm (HOST, ni ints, may be NULL)
  * gives P: column j of the first ni columns belongs to I row perm[j].
- * precision HSS_FP64 or HSS_FP32 (tensor_cores as in hss_factor_opts, FP32
- * only).  Synchronizes `stream`.  Errors: HSS_EINVAL, HSS_ESINGULAR (zero
+ * precision HSS_FP64 or HSS_FP32 (tensor_cores 0..3 as in hss_factor_opts,
+ * FP32 only).  Synchronizes `stream`.  Errors: HSS_EINVAL, HSS_ESINGULAR (zero
  * pivot; out is still written), HSS_ENOMEM, HSS_ETIMEOUT, HSS_ECUDA.
  *
  * hss_front_compress: Theorem 1's randomized HSS construction of the Schur
@@ -464,6 +471,14 @@ int fgmres_history(int rhs, double *hist, int cap);
  * with nothing left in flight and the context usable.  Test hook. */
 long hss_launch_count(void);
 long hss_alloc_count(void);
+/* The GEMM engine tuner's process-wide choices (tensor_cores = 3): with
+ * idx < 0 the number of shape classes timed so far; otherwise class idx (in
+ * the order they were timed): its key (bits 0-11 log2 k, 12-23 log2 n, 24-35
+ * log2 m, rounded up; bit 38 generated B, 39 transposed A; bits 40-47 the
+ * tensor-core kernel timed, 1 TMA-fed, 2 thread-staged; bits 48+ device),
+ * the engine kept (0 SIMT, else the tensor-core kernel) and both times (ms,
+ * one problem alone on a scratch C).  Returns HSS_OK or -HSS_EINVAL. */
+int hss_gemm_tuner_read(int idx, long long *key, int *engine, float *ms_simt, float *ms_tc);
 int hss_tc_timeout_selftest(long spin_limit, void *stream);
 int hss_profile_enable(int on);
 int hss_profile_reset(void);

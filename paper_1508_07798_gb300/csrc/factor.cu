@@ -11,8 +11,11 @@
 // reads back one small array per sampling round (node ranks and pivot
 // status) to decide sample growth and to size the expansion.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 #include <cstdint>
 #include <cstring>
 
@@ -61,102 +64,207 @@ int assemble_stage(const hss_bsr *A, const hss_tree *t, const std::vector<FrontD
 }
 
 // GEMM engine of a factorization: SIMT FMA, or (FP32 form) tcgen05 TF32
-// tensor cores for problems of at least one 128-row tile.
+// tensor cores.
 struct Engine {
-    int tc = 0;          // 0 SIMT; 1 TF32 with hi/lo split; 2 single TF32
+    int tc = 0;          // tensor_cores option: 0 SIMT; 1 TF32 hi/lo split; 2 single TF32; 3 chosen by timing
     int *err = nullptr;  // set by a tensor-core kernel whose bounded wait expired
+    mutable long problems[3] = {0, 0, 0};   // GEMM problems run on SIMT / TMA-fed / staged tensor cores
+    mutable long timed = 0;                 // problems the engine tuner timed
 };
 
-// Tensor cores pay off for long contractions only: the Gauss-Jordan trailing
-// updates (K = panel width <= 32) are memory bound per 128 x 128 tile and ran
-// 2.4x slower on tcgen05 than the 64 x 64 SIMT tiles (fewer, heavier CTAs), so
-// they stay on FMA; the sampling products (K = |B|) go to the tensor cores.
+// The fixed rule of tensor_cores = 1 / 2: long contractions only.  The
+// Gauss-Jordan in-block updates (K = panel width <= 32) are memory bound per
+// 128 x 128 tile and stay on FMA; the sampling products (K = |B|) and the
+// K = 128 block-end updates of large fronts go to the tensor cores.
 template <class T> bool use_tc(const Engine &e, const GemmDesc<T> &d) {
     return std::is_same<T, float>::value && e.tc != 0 && d.m >= 128 && d.n >= 32 && d.k >= 128;
 }
 
-template <class T> void tiles_for(const Engine &e, const GemmDesc<T> &d, int idx, std::vector<GemmTile> &t) {
-    if constexpr (std::is_same<T, float>::value) {
-        if (use_tc(e, d)) {
-            gemm_tc_tiles_for(d, idx, t);
-            return;
-        }
-    }
-    gemm_tiles_for(d, idx, t);
-}
+enum { ENG_SIMT = 0, ENG_TMA = 1, ENG_STG = 2, NENG = 3 };
 
-template <class T>
-int run_gemm(const Engine &e, bool tc, const GemmDesc<T> *dd, const GemmTile *dt, int n, cudaStream_t s,
-             double flops) {
-    if constexpr (std::is_same<T, float>::value) {
-        if (tc) return gemm_tc(dd, dt, n, e.tc == 1 ? 1 : 0, e.err, s, flops);
-    }
-    return gemm_batched<T>(dd, dt, n, s, flops);
-}
-
-// Tensor-core tiles of consecutive launch groups (group g owns tiles
-// [off[g], off[g + 1])) split between the TMA-fed kernel, for problems whose
-// operands it can address (engine 1 only), and the thread-staging kernel.
-struct TcSplit {
-    std::vector<GemmTile> tma, stg;
-    std::vector<int> tma_off, stg_off;
-    std::vector<double> tma_fl, stg_fl;
-    std::vector<char> use;          // per problem: on the TMA kernel
-    TmaGemmDesc *d_tdescs = nullptr;
-    GemmTile *d_tma = nullptr, *d_stg = nullptr;
+// ---- GEMM engine autotuner (tensor_cores = 3): per shape class (operand
+// forms, TMA eligibility, sizes rounded up to powers of two) the first
+// problem of the class is timed on the SIMT kernel and on the tensor-core
+// kernel that can take it (TMA-fed where the operands allow, thread-staged
+// otherwise), writing a scratch C, and the faster engine serves the class from
+// then on (process-wide cache).
+struct EngChoice {
+    int engine;
+    float ms_simt, ms_tc;
 };
+static std::mutex g_eng_mu;
+static std::unordered_map<uint64_t, EngChoice> g_eng_choice;
+static std::vector<uint64_t> g_eng_order;   // keys in the order they were timed
+static std::atomic<long> g_eng_timings{0};
 
-template <class T>
-int split_tc(const Engine &eng, const std::vector<GemmDesc<T>> &descs, const std::vector<GemmTile> &tiles,
-             const std::vector<int> &off, TcSplit &out, Work &W) {
-    const int ng = (int)off.size() - 1;
-    out.use.assign(descs.size(), 0);
-    std::vector<int> ntile(descs.size(), 0);
-    for (const GemmTile &t : tiles) ntile[t.desc]++;
-    if constexpr (std::is_same<T, float>::value) {
-        if (eng.tc == 1)
-            for (size_t i = 0; i < descs.size(); ++i) out.use[i] = ntile[i] > 0 && gemm_tma_eligible(descs[i]);
+static int ilog2c(long v) {
+    int l = 0;
+    while ((1L << l) < v) ++l;
+    return l;
+}
+
+static uint64_t shape_key(const GemmDesc<float> &d, int tc_kind) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return ((uint64_t)dev << 48) | ((uint64_t)tc_kind << 40) | ((uint64_t)(d.transA != 0) << 39) |
+           ((uint64_t)(d.B == nullptr) << 38) | ((uint64_t)ilog2c(d.m) << 24) | ((uint64_t)ilog2c(d.n) << 12) |
+           (uint64_t)ilog2c(d.k);
+}
+
+// average time (ms) of two runs of problem d alone on engine `eng` after one warm-up run
+static int time_engine(const Engine &E, const GemmDesc<float> &d, int eng, Work &W, cudaStream_t s, float *ms) {
+    std::vector<GemmDesc<float>> dv{d};
+    std::vector<GemmTile> tl;
+    if (eng == ENG_SIMT) gemm_tiles_for(d, 0, tl);
+    else gemm_tc_tiles_for(d, 0, tl);
+    GemmDesc<float> *dd;
+    GemmTile *dt;
+    TmaGemmDesc *td = nullptr;
+    int rc;
+    if ((rc = W.up(dv, &dd)) || (rc = W.up(tl, &dt))) return rc;
+    if (eng == ENG_TMA && (rc = gemm_tma_descs(dv, std::vector<char>{1}, W, &td))) return rc;
+    auto launch = [&]() -> int {
+        if (eng == ENG_SIMT) return gemm_batched<float>(dd, dt, (int)tl.size(), s, 0.0);
+        if (eng == ENG_TMA) return gemm_tma(td, dt, (int)tl.size(), E.err, s, 0.0);
+        return gemm_tc(dd, dt, (int)tl.size(), E.tc == 2 ? 0 : 1, E.err, s, 0.0);
+    };
+    cudaEvent_t e0, e1;
+    HSS_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "tuner events");
     }
-    out.tma.clear();
-    out.stg.clear();
-    out.tma_off.assign(ng + 1, 0);
-    out.stg_off.assign(ng + 1, 0);
-    out.tma_fl.assign(ng, 0.0);
-    out.stg_fl.assign(ng, 0.0);
-    for (int g = 0; g < ng; ++g) {
-        out.tma_off[g] = (int)out.tma.size();
-        out.stg_off[g] = (int)out.stg.size();
-        for (int q = off[g]; q < off[g + 1]; ++q) {
-            const GemmTile &t = tiles[q];
-            const double fl = gemm_flops(descs[t.desc]) / ntile[t.desc];
-            if (out.use[t.desc]) {
-                out.tma.push_back(t);
-                out.tma_fl[g] += fl;
-            } else {
-                out.stg.push_back(t);
-                out.stg_fl[g] += fl;
+    rc = launch();
+    if (!rc) rc = cudaEventRecord(e0, s) == cudaSuccess ? HSS_OK : HSS_ECUDA;
+    for (int r = 0; r < 2 && !rc; ++r) rc = launch();
+    if (!rc) rc = cudaEventRecord(e1, s) == cudaSuccess ? HSS_OK : HSS_ECUDA;
+    if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess ? HSS_OK : HSS_ECUDA;
+    float t = 0.f;
+    if (!rc) rc = cudaEventElapsedTime(&t, e0, e1) == cudaSuccess ? HSS_OK : HSS_ECUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == HSS_ECUDA) return cuda_fail(cudaGetLastError(), "GEMM engine tuner");
+    *ms = t / 2;
+    return rc;
+}
+
+template <class T> int choose_engine(const Engine &E, const GemmDesc<T> &d, Work &W, cudaStream_t s, int *out) {
+    *out = ENG_SIMT;
+    if constexpr (std::is_same<T, float>::value) {
+        if (E.tc == 0) return HSS_OK;
+        const bool tma = gemm_tma_eligible(d);
+        if (E.tc == 1 || E.tc == 2) {
+            if (use_tc(E, d)) *out = (E.tc == 1 && tma) ? ENG_TMA : ENG_STG;
+            return HSS_OK;
+        }
+        // tensor_cores = 3: chosen by timing
+        if (d.m < 128 || d.n < 16 || d.k < 16) return HSS_OK;
+        const int tc = tma ? ENG_TMA : ENG_STG;
+        const uint64_t key = shape_key(d, tc);
+        {
+            std::lock_guard<std::mutex> lk(g_eng_mu);
+            auto it = g_eng_choice.find(key);
+            if (it != g_eng_choice.end()) {
+                *out = it->second.engine;
+                return HSS_OK;
             }
         }
-    }
-    out.tma_off[ng] = (int)out.tma.size();
-    out.stg_off[ng] = (int)out.stg.size();
-    int rc;
-    if ((rc = W.up(out.stg, &out.d_stg))) return rc;
-    if constexpr (std::is_same<T, float>::value) {
-        if (!out.tma.empty()) {
-            if ((rc = W.up(out.tma, &out.d_tma)) || (rc = gemm_tma_descs(descs, out.use, W, &out.d_tdescs))) return rc;
-        }
+        GemmDesc<float> t = d;   // same operands, a scratch C
+        float *scratch;
+        int rc;
+        if ((rc = W.dalloc((size_t)d.m * d.n, &scratch))) return rc;
+        t.C = scratch;
+        t.ldc = d.m;
+        t.beta = 0.f;
+        t.zr_lo = t.zr_hi = 0;
+        t.skip_lo = t.skip_hi = 0;
+        float ms_simt = 0.f, ms_tc = 0.f;
+        if ((rc = time_engine(E, t, ENG_SIMT, W, s, &ms_simt)) || (rc = time_engine(E, t, tc, W, s, &ms_tc))) return rc;
+        g_eng_timings.fetch_add(1);
+        E.timed++;
+        *out = ms_tc < ms_simt ? tc : ENG_SIMT;
+        std::lock_guard<std::mutex> lk(g_eng_mu);
+        if (!g_eng_choice.count(key)) g_eng_order.push_back(key);
+        g_eng_choice[key] = EngChoice{*out, ms_simt, ms_tc};
+    } else {
+        (void)E;
+        (void)d;
+        (void)W;
+        (void)s;
     }
     return HSS_OK;
 }
 
-// Launch group g of a split: its TMA tiles, then its staging tiles.
+// The GEMM launches of a stage: per launch group (a point of the kernel
+// sequence), the tiles of its problems on each engine.
+template <class T> struct GemmPlan {
+    std::vector<GemmTile> tl[NENG];
+    std::vector<int> off[NENG];
+    std::vector<double> fl[NENG];
+    TmaGemmDesc *d_tdescs = nullptr;
+    GemmTile *d_tl[NENG] = {nullptr, nullptr, nullptr};
+};
+
+// Engine of every problem, tiles per (group, engine), uploaded through W.
+// Problems of a group keep their order.
 template <class T>
-int run_tc_group(const Engine &eng, const TcSplit &sp, const GemmDesc<T> *d_descs, int g, cudaStream_t s) {
+int plan_gemms(const Engine &E, const std::vector<GemmDesc<T>> &descs, const std::vector<int> &group, int ngroups,
+               GemmPlan<T> &P, Work &W, cudaStream_t s) {
+    const size_t nd = descs.size();
+    std::vector<int> which(nd, ENG_SIMT);
+    std::vector<char> use_tma(nd, 0);
     int rc;
-    const int nt = sp.tma_off[g + 1] - sp.tma_off[g], ns = sp.stg_off[g + 1] - sp.stg_off[g];
-    if (nt > 0 && (rc = gemm_tma(sp.d_tdescs, sp.d_tma + sp.tma_off[g], nt, eng.err, s, sp.tma_fl[g]))) return rc;
-    if (ns > 0 && (rc = run_gemm<T>(eng, true, d_descs, sp.d_stg + sp.stg_off[g], ns, s, sp.stg_fl[g]))) return rc;
+    for (size_t i = 0; i < nd; ++i) {
+        if ((rc = choose_engine<T>(E, descs[i], W, s, &which[i]))) return rc;
+        use_tma[i] = which[i] == ENG_TMA;
+        E.problems[which[i]]++;
+    }
+    std::vector<std::vector<int>> of(ngroups);
+    for (size_t i = 0; i < nd; ++i) of[group[i]].push_back((int)i);
+    for (int e = 0; e < NENG; ++e) {
+        P.tl[e].clear();
+        P.off[e].assign(ngroups + 1, 0);
+        P.fl[e].assign(ngroups, 0.0);
+    }
+    for (int g = 0; g < ngroups; ++g) {
+        for (int e = 0; e < NENG; ++e) P.off[e][g] = (int)P.tl[e].size();
+        for (int i : of[g]) {
+            const int e = which[i];
+            if (e == ENG_SIMT) gemm_tiles_for(descs[i], i, P.tl[e]);
+            else if constexpr (std::is_same<T, float>::value) gemm_tc_tiles_for(descs[i], i, P.tl[e]);
+            P.fl[e][g] += gemm_flops(descs[i]);
+        }
+    }
+    for (int e = 0; e < NENG; ++e) {
+        P.off[e][ngroups] = (int)P.tl[e].size();
+        if (!P.tl[e].empty() && (rc = W.up(P.tl[e], &P.d_tl[e]))) return rc;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (!P.tl[ENG_TMA].empty() && (rc = gemm_tma_descs(descs, use_tma, W, &P.d_tdescs))) return rc;
+    }
+    return HSS_OK;
+}
+
+// Launch group g of a plan: SIMT tiles, TMA tiles, staged tensor-core tiles
+// (tma_class: the profile class of the TMA launches).
+template <class T>
+int run_gemm_group(const Engine &E, const GemmPlan<T> &P, const GemmDesc<T> *d_descs, int g, cudaStream_t s,
+                   const char *tma_class = "gemm_tma") {
+    int rc;
+    for (int e = 0; e < NENG; ++e) {
+        const int n = P.off[e][g + 1] - P.off[e][g];
+        if (n <= 0) continue;
+        const GemmTile *t = P.d_tl[e] + P.off[e][g];
+        if (e == ENG_SIMT) {
+            rc = gemm_batched<T>(d_descs, t, n, s, P.fl[e][g]);
+        } else if constexpr (std::is_same<T, float>::value) {
+            rc = e == ENG_TMA ? gemm_tma(P.d_tdescs, t, n, E.err, s, P.fl[e][g], tma_class)
+                              : gemm_tc(d_descs, t, n, E.tc == 2 ? 0 : 1, E.err, s, P.fl[e][g]);
+        } else {
+            rc = HSS_OK;
+        }
+        if (rc) return rc;
+    }
     return HSS_OK;
 }
 
@@ -222,34 +330,20 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
     std::vector<GemmDesc<T>> descs;
     std::vector<long> desc_b;        // offset of each descriptor's B operand in Aold (block: in AoldB)
     std::vector<char> desc_blk;
-    std::vector<GemmTile> tiles, ttiles, btiles, bttiles;   // in-block / block-end, SIMT / tensor cores
+    std::vector<int> desc_group;     // launch group: 2 st (in-block update), 2 st + 1 (block end)
     std::vector<PanelTile> ptiles;
     std::vector<BlockTile> bptiles;
     std::vector<std::vector<Group>> groups(maxsteps);
-    std::vector<int> tile_off(maxsteps + 1), ttile_off(maxsteps + 1), ptile_off(maxsteps + 1);
-    std::vector<int> btile_off(maxsteps + 1), bttile_off(maxsteps + 1), bptile_off(maxsteps + 1);
+    std::vector<int> ptile_off(maxsteps + 1), bptile_off(maxsteps + 1);
     long xtotal = 0, mtotal = 0;
-    std::vector<double> step_flops(maxsteps, 0.0), tstep_flops(maxsteps, 0.0);
-    std::vector<double> bstep_flops(maxsteps, 0.0), btstep_flops(maxsteps, 0.0);
-    auto add_desc = [&](const GemmDesc<T> &d, long boff, bool blk, std::vector<GemmTile> &simt,
-                        std::vector<GemmTile> &tc, double &fl, double &tfl) {
+    auto add_desc = [&](const GemmDesc<T> &d, long boff, bool blk, int grp) {
         descs.push_back(d);
         desc_b.push_back(boff);
         desc_blk.push_back(blk);
-        if (use_tc(eng, d)) {
-            tiles_for(eng, descs.back(), (int)descs.size() - 1, tc);
-            tfl += gemm_flops(d);
-        } else {
-            gemm_tiles_for(descs.back(), (int)descs.size() - 1, simt);
-            fl += gemm_flops(d);
-        }
+        desc_group.push_back(grp);
     };
     for (int st = 0; st < maxsteps; ++st) {
-        tile_off[st] = (int)tiles.size();
-        ttile_off[st] = (int)ttiles.size();
         ptile_off[st] = (int)ptiles.size();
-        btile_off[st] = (int)btiles.size();
-        bttile_off[st] = (int)bttiles.size();
         bptile_off[st] = (int)bptiles.size();
         std::vector<int> act;
         for (int f = 0; f < nf; ++f)
@@ -322,7 +416,7 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             d.zr_hi = k0 + kbs;
             d.skip_lo = k0 - K0;
             d.skip_hi = k0 - K0 + kbs;
-            if (bw > kbs) add_desc(d, aoff[f] + (long)kbs * K0, false, tiles, ttiles, step_flops[st], tstep_flops[st]);
+            if (bw > kbs) add_desc(d, aoff[f] + (long)kbs * K0, false, 2 * st);
             // end of the block: the other columns
             const bool block_end = blocked && ((st % PANEL_BLOCK == PANEL_BLOCK - 1) || st == nsteps[f] - 1);
             if (block_end && n > bw) {
@@ -355,22 +449,17 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
                 e.zr_hi = K0 + bw;
                 e.skip_lo = K0;
                 e.skip_hi = K0 + bw;
-                add_desc(e, aoffB[f], true, btiles, bttiles, bstep_flops[st], btstep_flops[st]);
+                add_desc(e, aoffB[f], true, 2 * st + 1);
             }
         }
     }
-    tile_off[maxsteps] = (int)tiles.size();
-    ttile_off[maxsteps] = (int)ttiles.size();
     ptile_off[maxsteps] = (int)ptiles.size();
-    btile_off[maxsteps] = (int)btiles.size();
-    bttile_off[maxsteps] = (int)bttiles.size();
     bptile_off[maxsteps] = (int)bptiles.size();
     T *d_aold, *d_aoldB, *d_x;
     int *d_mv;
     PanelJob *d_jobs;
     BlockJob *d_bjobs;
     GemmDesc<T> *d_descs;
-    GemmTile *d_tiles, *d_ttiles, *d_btiles, *d_bttiles;
     PanelTile *d_ptiles;
     BlockTile *d_bptiles;
     int rc;
@@ -378,16 +467,11 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         (rc = W.dalloc(xtotal, &d_x)) || (rc = W.dalloc(mtotal, &d_mv)))
         return rc;
     for (size_t i = 0; i < descs.size(); ++i) descs[i].B = (desc_blk[i] ? d_aoldB : d_aold) + desc_b[i];
-    TcSplit tsp, btsp;   // tensor-core tiles of the in-block and block-end updates
+    GemmPlan<T> plan;
     if ((rc = W.up(jobs, &d_jobs)) || (rc = W.up(bjobs, &d_bjobs)) || (rc = W.up(descs, &d_descs)) ||
-        (rc = W.up(tiles, &d_tiles)) || (rc = W.up(btiles, &d_btiles)) || (rc = W.up(ptiles, &d_ptiles)) ||
-        (rc = W.up(bptiles, &d_bptiles)))
+        (rc = W.up(ptiles, &d_ptiles)) || (rc = W.up(bptiles, &d_bptiles)) ||
+        (rc = plan_gemms<T>(eng, descs, desc_group, 2 * maxsteps, plan, W, s)))
         return rc;
-    if (eng.tc && ((rc = split_tc<T>(eng, descs, ttiles, ttile_off, tsp, W)) ||
-                   (rc = split_tc<T>(eng, descs, bttiles, bttile_off, btsp, W))))
-        return rc;
-    (void)d_ttiles;
-    (void)d_bttiles;
     for (int st = 0; st < maxsteps; ++st) {
         for (const Group &g : groups[st]) {
             if (g.reg)
@@ -401,17 +485,11 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         if ((rc = launch_gj_post<T>(d_ptiles + ptile_off[st], ptile_off[st + 1] - ptile_off[st], d_jobs, d_fr, arena,
                                     d_aold, d_x, d_mv, s)))
             return rc;
-        if ((rc = gemm_batched<T>(d_descs, d_tiles + tile_off[st], tile_off[st + 1] - tile_off[st], s,
-                                  step_flops[st])))
-            return rc;
-        if (eng.tc && (rc = run_tc_group<T>(eng, tsp, d_descs, st, s))) return rc;
+        if ((rc = run_gemm_group<T>(eng, plan, d_descs, 2 * st, s, "gemm_tma_update"))) return rc;
         if ((rc = launch_gj_block_post<T>(d_bptiles + bptile_off[st], bptile_off[st + 1] - bptile_off[st], d_bjobs,
                                           d_jobs, d_fr, arena, d_aoldB, d_mv, s)))
             return rc;
-        if ((rc = gemm_batched<T>(d_descs, d_btiles + btile_off[st], btile_off[st + 1] - btile_off[st], s,
-                                  bstep_flops[st])))
-            return rc;
-        if (eng.tc && (rc = run_tc_group<T>(eng, btsp, d_descs, st, s))) return rc;
+        if ((rc = run_gemm_group<T>(eng, plan, d_descs, 2 * st + 1, s, "gemm_tma_block"))) return rc;
     }
     return HSS_OK;
 }
@@ -531,7 +609,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         HSS_CUDA(cudaMemsetAsync(d_fk, 0, sizeof(int) * nc, s));
         // ---- sampling Y = S Omega, Z = S^t Psi, then the leaf corrections
         std::vector<GemmDesc<T>> g1, g2;
-        std::vector<GemmTile> t1, t1c, t2;   // sampling (SIMT / tensor cores), leaf corrections
+        std::vector<GemmTile> t2;   // leaf corrections (SIMT)
         for (int c = 0; c < nc; ++c) {
             GemmDesc<T> d{};
             d.A = cfs[c].S;
@@ -552,14 +630,10 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             d.transA = 0;
             d.stream = 0;
             g1.push_back(d);
-            if (use_tc(eng, d)) tiles_for(eng, g1.back(), (int)g1.size() - 1, t1c);
-            else gemm_tiles_for(g1.back(), (int)g1.size() - 1, t1);
             d.C = ws + cfs[c].zoff;
             d.transA = 1;
             d.stream = 1;
             g1.push_back(d);
-            if (use_tc(eng, d)) tiles_for(eng, g1.back(), (int)g1.size() - 1, t1c);
-            else gemm_tiles_for(g1.back(), (int)g1.size() - 1, t1);
             for (int i = node_base[c]; i < node_base[c + 1]; ++i) {
                 if (nodes[i].a >= 0) continue;
                 int lo = nodes[i].lo, m = nodes[i].hi - nodes[i].lo;
@@ -584,20 +658,14 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         }
         {
             GemmDesc<T> *a, *c2;
-            GemmTile *b, *bc, *d2;
-            if ((rc = W.up(g1, &a)) || (rc = W.up(t1, &b)) || (rc = W.up(g2, &c2)) || (rc = W.up(t2, &d2))) return rc;
-            (void)bc;
-            double f1 = 0, f2 = 0;
-            for (auto &d : g1)
-                if (!use_tc(eng, d)) f1 += gemm_flops(d);
+            GemmTile *d2;
+            GemmPlan<T> plan;
+            if ((rc = W.up(g1, &a)) || (rc = W.up(g2, &c2)) || (rc = W.up(t2, &d2)) ||
+                (rc = plan_gemms<T>(eng, g1, std::vector<int>(g1.size(), 0), 1, plan, W, s)))
+                return rc;
+            double f2 = 0;
             for (auto &d : g2) f2 += gemm_flops(d);
-            if ((rc = gemm_batched<T>(a, b, (int)t1.size(), s, f1))) return rc;
-            if (!t1c.empty()) {
-                TcSplit sp;
-                if ((rc = split_tc<T>(eng, g1, t1c, std::vector<int>{0, (int)t1c.size()}, sp, W)) ||
-                    (rc = run_tc_group<T>(eng, sp, a, 0, s)))
-                    return rc;
-            }
+            if ((rc = run_gemm_group<T>(eng, plan, a, 0, s, "gemm_tma_sample"))) return rc;
             if ((rc = gemm_batched<T>(c2, d2, (int)t2.size(), s, f2))) return rc;
         }
         // ---- interpolative decompositions, deepest HSS level first
@@ -988,6 +1056,10 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
                 return HSS_ESINGULAR;
             }
         if (eng.tc && (rc = check_tc())) return rc;
+        F->gemm_simt = eng.problems[ENG_SIMT];
+        F->gemm_tma = eng.problems[ENG_TMA];
+        F->gemm_staged = eng.problems[ENG_STG];
+        F->gemm_timed = eng.timed;
         for (int i = 0; i < ninst; ++i) {
             F->front_flops += 2.0 / 3.0 * (double)ntop_i[i] * ntop_i[i] * ntop_i[i];
             F->factor_bytes += sizeof(T) * (double)ntop_i[i] * ntop_i[i];
@@ -1136,8 +1208,9 @@ static int check_factor_opts(const hss_factor_opts &o, const char *who) {
     if (!(o.tol >= 0) || o.r0 < 1 || o.dr < 1 || o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 ||
         (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
         (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1) ||
-        o.probe < 0 || o.probe > PROBE_MAX || (o.probe > 0 && !(o.tol > 0))) {
-        set_error(std::string(who) + ": options out of range (rmax <= 128)");
+        o.probe < 0 || o.probe > PROBE_MAX || (o.probe > 0 && !(o.tol > 0)) || o.tensor_cores < 0 ||
+        o.tensor_cores > 3) {
+        set_error(std::string(who) + ": options out of range (rmax <= 128, tensor_cores 0..3)");
         return HSS_EINVAL;
     }
     return HSS_OK;
@@ -1242,8 +1315,10 @@ extern "C" int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_fact
     if (A->nb != tree->nelem || A->bs != tree->bs || !A->val || !(o.tol >= 0) || o.r0 < 1 || o.dr < 1 ||
         o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 || (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
         (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1) ||
-        o.probe < 0 || o.probe > PROBE_MAX || (o.probe > 0 && !(o.tol > 0))) {
-        set_error("hss_factor: invalid argument (matrix/tree mismatch or options out of range; rmax <= 128)");
+        o.probe < 0 || o.probe > PROBE_MAX || (o.probe > 0 && !(o.tol > 0)) || o.tensor_cores < 0 ||
+        o.tensor_cores > 3) {
+        set_error("hss_factor: invalid argument (matrix/tree mismatch or options out of range; rmax <= 128, "
+                  "tensor_cores 0..3)");
         return HSS_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -1276,6 +1351,10 @@ extern "C" int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info)
     info->nfronts = (int)f->log.size();
     info->capped_fronts = f->capped_fronts;
     info->probe_regrown = f->probe_regrown;
+    info->gemm_simt = f->gemm_simt;
+    info->gemm_tma = f->gemm_tma;
+    info->gemm_staged = f->gemm_staged;
+    info->gemm_timed = f->gemm_timed;
     return HSS_OK;
 }
 
@@ -1337,7 +1416,7 @@ extern "C" void hss_factor_destroy(hss_factor_t *f) { delete f; }
 extern "C" int hss_front_eliminate(int n, int ni, const double *F, int ldf, int precision, int tensor_cores,
                                    double *out, int ldo, int *perm, void *stream) {
     if (n < 1 || ni < 1 || ni > n || !F || !out || ldf < n || ldo < n ||
-        (precision != HSS_FP64 && precision != HSS_FP32) || tensor_cores < 0 || tensor_cores > 2) {
+        (precision != HSS_FP64 && precision != HSS_FP32) || tensor_cores < 0 || tensor_cores > 3) {
         set_error("hss_front_eliminate: invalid argument");
         return HSS_EINVAL;
     }
@@ -1361,4 +1440,20 @@ extern "C" int hss_front_compress(const hss_tree *t, int box, const double *S, i
     cudaStream_t s = (cudaStream_t)stream;
     return o.precision == HSS_FP32 ? front_compress_impl<float>(t, box, S, lds, o, H, ldh, kmax, r, rounds, s)
                                    : front_compress_impl<double>(t, box, S, lds, o, H, ldh, kmax, r, rounds, s);
+}
+
+extern "C" int hss_gemm_tuner_read(int idx, long long *key, int *engine, float *ms_simt, float *ms_tc) {
+    std::lock_guard<std::mutex> lk(g_eng_mu);
+    if (idx < 0) return (int)g_eng_order.size();
+    if (idx >= (int)g_eng_order.size()) {
+        set_error("hss_gemm_tuner_read: index out of range");
+        return -HSS_EINVAL;
+    }
+    const uint64_t k = g_eng_order[idx];
+    const EngChoice &c = g_eng_choice[k];
+    if (key) *key = (long long)k;
+    if (engine) *engine = c.engine;
+    if (ms_simt) *ms_simt = c.ms_simt;
+    if (ms_tc) *ms_tc = c.ms_tc;
+    return HSS_OK;
 }

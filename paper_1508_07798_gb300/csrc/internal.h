@@ -215,7 +215,7 @@ struct Work;
 int gemm_tma_descs(const std::vector<GemmDesc<float>> &descs, const std::vector<char> &use, Work &W,
                    TmaGemmDesc **out);
 int gemm_tma(const TmaGemmDesc *d_descs, const GemmTile *d_tiles, int ntiles, int *err, cudaStream_t s,
-             double flops);
+             double flops, const char *prof_class = "gemm_tma");
 // C = alpha * 0 + beta * C (the product with k = 0) without descriptors.
 int gemm_f32_k0(float *C, int ldc, int m, int n, float alpha, float beta, cudaStream_t s);
 // Loads the module of the FP32 SIMT GEMM kernels.

@@ -243,6 +243,13 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restric
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         for (int q = 0; q < 2 && q < nk; ++q) issue_chunk(td, amode, bmode, row0, col0, q, rawb + q * RAW_BYTES, &full[q]);
     }
+    // the epilogue reads C: start bringing this tile's C into L2 now (thread t:
+    // column col0 + t, the rows of the tile that exist, in 128-byte lines)
+    if (d.beta != 0.f && col0 + tid < d.n && !(col0 + tid >= d.skip_lo && col0 + tid < d.skip_hi)) {
+        const float *cc = d.C + row0 + (long)(col0 + tid) * d.ldc;
+        const int rows = min(TM, d.m - row0);
+        for (int r = 0; r < rows; r += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(cc + r));
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -444,11 +451,11 @@ int gemm_tma_descs(const std::vector<GemmDesc<float>> &descs, const std::vector<
 }
 
 int gemm_tma(const TmaGemmDesc *d_descs, const GemmTile *d_tiles, int ntiles, int *err, cudaStream_t s,
-             double flops) {
+             double flops, const char *prof_class) {
     if (ntiles <= 0) return HSS_OK;
     int rc = gemm_tma_prepare();
     if (rc) return rc;
-    HSS_PROF("gemm_tma", s, flops);
+    HSS_PROF(prof_class, s, flops);
     k_gemm_tma<<<ntiles, NT, SMEM, s>>>(d_descs, d_tiles, err);
     HSS_CHECK_LAUNCH("k_gemm_tma");
     return HSS_OK;

@@ -33,7 +33,7 @@ EXPORTED = [
     "hss_rank_model_set", "hss_rank_model_fit_norm", "hss_rank_model_loss_grad", "hss_rank_model_train",
     "hss_rank_model_predict", "hss_factor_export_log", "ilu0_factor", "ilu0_apply", "fgmres_solve_ilu0",
     "ilu0_destroy", "hss_factor_apply_plan", "hss_alloc_count", "hss_tc_timeout_selftest",
-    "hss_front_eliminate", "hss_front_compress",
+    "hss_front_eliminate", "hss_front_compress", "hss_gemm_tuner_read",
 ]
 
 
@@ -79,7 +79,8 @@ class hss_tree_desc(C.Structure):
 class hss_factor_info(C.Structure):
     _fields_ = [("factor_bytes", C.c_double), ("front_flops", C.c_double), ("executed_flops", C.c_double),
                 ("max_rank", C.c_int), ("max_r", C.c_int), ("rounds", C.c_int), ("nfronts", C.c_int),
-                ("capped_fronts", C.c_int), ("probe_regrown", C.c_int)]
+                ("capped_fronts", C.c_int), ("probe_regrown", C.c_int), ("gemm_simt", C.c_long),
+                ("gemm_tma", C.c_long), ("gemm_staged", C.c_long), ("gemm_timed", C.c_long)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
@@ -109,6 +110,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fgmres_opts_default": (None, [C.POINTER(fgmres_opts)]),
         "hss_launch_count": (C.c_long, []),
         "hss_alloc_count": (C.c_long, []),
+        "hss_gemm_tuner_read": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), ip, C.POINTER(C.c_float),
+                                          C.POINTER(C.c_float)]),
         "hss_front_eliminate": (C.c_int, [C.c_int, C.c_int, P, C.c_int, C.c_int, C.c_int, P, C.c_int, P, P]),
         "hss_front_compress": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(hss_factor_opts), P, C.c_int, ip, ip, ip,
                                          P]),
@@ -553,6 +556,23 @@ def fgmres_history(rhs=0, cap=100000) -> np.ndarray:
 
 def launch_count() -> int:
     return int(_lib.hss_launch_count())
+
+
+def gemm_tuner_choices() -> list:
+    """The GEMM engine tuner's choices so far: dicts with the shape class
+    (log2 of m, n, k rounded up, transposed A, generated B, tensor-core kernel
+    timed), the engine kept and both times in ms."""
+    n = _lib.hss_gemm_tuner_read(-1, None, None, None, None)
+    out = []
+    for i in range(n):
+        key, eng, t0, t1 = C.c_longlong(), C.c_int(), C.c_float(), C.c_float()
+        _check(_lib.hss_gemm_tuner_read(i, C.byref(key), C.byref(eng), C.byref(t0), C.byref(t1)))
+        k = key.value
+        out.append(dict(log2_m=(k >> 24) & 0xFFF, log2_n=(k >> 12) & 0xFFF, log2_k=k & 0xFFF,
+                        trans_a=bool((k >> 39) & 1), gen_b=bool((k >> 38) & 1),
+                        tc_kernel={1: "tma", 2: "staged"}.get((k >> 40) & 0xFF, "?"),
+                        engine="simt" if eng.value == 0 else "tc", ms_simt=t0.value, ms_tc=t1.value))
+    return out
 
 
 def alloc_count() -> int:

@@ -373,6 +373,41 @@ def test_fp32_form_tensor_cores_match_simt(p):
     assert st.converged and ss.converged and abs(st.iters - ss.iters) <= 2
 
 
+def test_gemm_engine_tuner_times_once_and_matches_simt():
+    """tensor_cores = 3: the first factorization times each GEMM shape class
+    on SIMT and on the tcgen05 split kernel and keeps the faster; a second
+    factorization of the same structure reuses every choice (no timing, same
+    engine split).  The result has the accuracy of the SIMT form: same widths
+    (ranks within one), approximants of the same quality, FGMRES alike."""
+    import torch
+    hs = _hss()
+    mesh, A = _setup("helm", (48, 48), 1)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((2, (48, 48), 1), dA)
+    F1 = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=3, keep_schur=1)
+    F2 = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=3, keep_schur=1)
+    Fs = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=0, keep_schur=1)
+    i1, i2, i0 = F1.info(), F2.info(), Fs.info()
+    print(f"\nengine split (SIMT, TMA, staged): {i1['gemm_simt']}, {i1['gemm_tma']}, {i1['gemm_staged']}; "
+          f"timed {i1['gemm_timed']} then {i2['gemm_timed']}")
+    assert i2["gemm_timed"] == 0
+    assert (i1["gemm_simt"], i1["gemm_tma"], i1["gemm_staged"]) == (i2["gemm_simt"], i2["gemm_tma"],
+                                                                   i2["gemm_staged"])
+    assert i0["gemm_tma"] == 0 and i0["gemm_staged"] == 0
+    l1, l0 = F1.export_log(), Fs.export_log()
+    assert (np.abs(l1["kmax"] - l0["kmax"]) <= 1).all() and (l1["r"] == l0["r"]).mean() >= 0.99
+    ex = tree.export()
+    for b in range(len(ex["nb"])):
+        if ex["nb"][b] >= 128:
+            S1, H1, _, _ = F1.export_front(b)
+            S0, H0, _, _ = Fs.export_front(b)
+            assert _rel(H1, S1) <= 10.0 * _rel(H0, S0) + 1e-5, b
+    bvec = torch.as_tensor(dg.point_source_rhs(mesh, 0)[:, 0], device="cuda")
+    _, s1 = hs.fgmres_solve(dA, F1, bvec, rtol=1e-8)
+    _, s0 = hs.fgmres_solve(dA, Fs, bvec, rtol=1e-8)
+    assert s1.converged and s0.converged and abs(s1.iters - s0.iters) <= 2
+
+
 def test_autotuned_apply_matches_oracle_and_is_cached():
     """The tuned work split (columns per apply work item, per stage and
     direction) changes only the summation order: the apply still matches the
