@@ -29,6 +29,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -47,9 +49,15 @@ def parse():
     ap.add_argument("--forms", default="fp32_learned,fp32,fp64",
                     help="fp32_learned: FP32 factor with learned sample widths (headline); fp32: FP32 "
                          "factor, adaptive widths; fp64: plain FP64 factor")
-    ap.add_argument("--workload", default="helmholtz64", choices=["helmholtz64", "batched256"],
+    ap.add_argument("--workload", default="helmholtz64",
+                    choices=["helmholtz64", "batched256", "helmholtz256", "diffusion32"],
                     help="helmholtz64: the timed workload (default); batched256: 256 independent "
-                         "instances x 32 right-hand sides through the batched form (its own JSON line)")
+                         "instances x 32 right-hand sides through the batched form; helmholtz256: "
+                         "Helmholtz p=3 on 256x256 quads (1,048,576 dofs), learned widths; diffusion32: "
+                         "3D diffusion p=1 on 32^3 hexes (262,144 dofs), 20 right-hand sides, learned "
+                         "widths (each its own JSON line)")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="large workloads: skip the plain FP64 comparison form")
     ap.add_argument("--tensor-cores", type=int, default=0, choices=[0, 1, 3],
                     help="GEMM engine of the FP32 forms: 0 SIMT, 1 tcgen05 (fixed rule), 3 per shape class by timing")
     ap.add_argument("--probe", type=int, default=4,
@@ -433,6 +441,229 @@ def bench_ours(args, rank, world):
     return res
 
 
+# ---- the large configurations: Helmholtz p = 3 on 256 x 256 quads and 3D diffusion p = 1 on 32^3 hexes
+LARGE = {
+    "helmholtz256": dict(dim=2, n=256, p=3, tol=1e-6, nrhs=1, rmax=96,
+                         workload="helmholtz_sipg_p3_256x256", small=(64, 3)),
+    "diffusion32": dict(dim=3, n=32, p=1, tol=1e-5, nrhs=20, rmax=96,
+                        workload="diffusion3d_sipg_p1_32cubed_20rhs", small=(16, 1)),
+}
+
+
+def large_problem(spec, seed, n=None, p=None):
+    """(mesh, A, b (ndof x nrhs), mesh descriptor, c per element for the features, kappa h)."""
+    from paper_1508_07798_gb300 import dg_inputs as dg
+    n = spec["n"] if n is None else n
+    p = spec["p"] if p is None else p
+    if spec["dim"] == 2:
+        mesh, A = dg.helmholtz_2d(n, p, seed)
+        b = dg.point_source_rhs(mesh, seed)
+        return mesh, A, b, (2, (n, n), p), dg.cosine_field(mesh, seed), dg.helmholtz_kappa(n, p) / n
+    mesh, A = dg.diffusion_3d(n, p, seed)
+    b = dg.random_rhs(A.n, spec["nrhs"], seed, kind="normal")
+    return mesh, A, b, (3, (n, n, n), p), np.log(dg.gaussian_log_field(mesh, seed)), 0.0
+
+
+def bench_large(args, rank, world):
+    """One step = nd_order + hss_factor + fgmres_solve (all right-hand sides
+    in lock step) of a large configuration.  Forms: FP32 factor with learned
+    widths and the residual probe (headline), FP32 with adaptive widths, plain
+    FP64 (unless --no-fp64).  The width model is trained before timing on the
+    ranks of adaptive runs of the method on smaller problems of the same
+    family (64 x 64 Helmholtz p = 1, 2, 3 or 16^3 diffusion, seeds
+    100..115)."""
+    import torch
+    from paper_1508_07798_gb300 import hssnd
+    from paper_1508_07798_gb300 import dg_inputs as dg
+    from paper_1508_07798_gb300 import ranks
+    spec = LARGE[args.workload]
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    mesh, A, b_host, meshdesc, c_elem, kappa_h = large_problem(spec, rank)
+    dA = hssnd.DeviceBSR.from_host(A)
+    B = torch.as_tensor(np.asfortranarray(b_host), device=dev)
+    nrhs = b_host.shape[1]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    Acsr = dg.bsr_to_csr(A)
+    tol = spec["tol"]
+    probs = dg.rank_training_problems(64) if spec["dim"] == 2 else dg.diffusion_training_problems(16)
+    Xt, tt = ranks.training_set(probs, tol=tol, rmax=spec["rmax"])
+    model = hssnd.RankModel(seed=1)
+    model.fit_norm(Xt, tt)
+    train_loss = model.train(Xt, tt, epochs=60, batch=256, lr=2e-3, seed=3)
+    forms = ["fp32_learned", "fp32"] + ([] if args.no_fp64 else ["fp64"])
+
+    def step(form, marks=None):
+        tree = hssnd.nd_order(meshdesc, dA, leaf_max=64)
+        if marks is not None:
+            marks[0].record(stream)
+        if form == "fp32_learned":
+            r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h), rmax=spec["rmax"])[1]
+            F = hssnd.hss_factor(dA, tree, tol=tol, precision="fp32", r_init=r0, autotune=1, probe=args.probe,
+                                 rmax=spec["rmax"], tensor_cores=args.tensor_cores)
+        else:
+            F = hssnd.hss_factor(dA, tree, tol=tol, precision=form, autotune=1, rmax=spec["rmax"],
+                                 tensor_cores=args.tensor_cores if form == "fp32" else 0)
+        if marks is not None:
+            marks[1].record(stream)
+        x, st = hssnd.fgmres_solve(dA, F, B, rtol=RTOL, restart=RESTART)
+        return tree, F, x, st
+
+    out, prof_all = {}, {}
+    clk = Clocks(dev.index)
+    launches = 0
+    for form in forms:
+        steps = args.steps if form != "fp64" else 1
+        warm = args.warmup if form != "fp64" else 1
+        for _ in range(warm):
+            step(form)
+        torch.cuda.synchronize()
+        if form == forms[0]:
+            clk.start()
+        ts, ph = [], {"nd_order": [], "factor": [], "fgmres": []}
+        l0 = hssnd.launch_count()
+        last = None
+        for _ in range(steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            last = step(form, ev[1:3])
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            ts.append(ev[0].elapsed_time(ev[3]))
+            ph["nd_order"].append(ev[0].elapsed_time(ev[1]))
+            ph["factor"].append(ev[1].elapsed_time(ev[2]))
+            ph["fgmres"].append(ev[2].elapsed_time(ev[3]))
+        if form == forms[0]:
+            clocks = clk.stop()
+            launches = (hssnd.launch_count() - l0) // steps
+        hssnd.profile_reset()
+        hssnd.profile_enable(True)
+        step(form)
+        hssnd.profile_enable(False)
+        prof_all[form] = hssnd.profile_read()
+        tree, F, x, st = last
+        X = x.cpu().numpy().reshape(A.n, -1)
+        relres = float((np.linalg.norm(b_host - Acsr @ X, axis=0) / np.linalg.norm(b_host, axis=0)).max())
+        info = F.info()
+        out[form] = dict(ms=statistics.mean(ts), ms_min=min(ts), steps=steps, warmup=warm,
+                         phases_ms={k: statistics.mean(v) for k, v in ph.items()}, iters_max=st.max_iters,
+                         iters_total=st.iters, true_relres=relres,
+                         converged=bool(st.converged and relres <= RTOL * 1.0001),
+                         factor_bytes=info["factor_bytes"], front_flops=info["front_flops"],
+                         executed_flops=info["executed_flops"], max_rank=info["max_rank"],
+                         capped_fronts=info["capped_fronts"], probe_regrown=info["probe_regrown"],
+                         sampling_rounds=int(F.export_log()["rounds"].sum()),
+                         gemm_engines=dict(simt=info["gemm_simt"], tma=info["gemm_tma"],
+                                           staged=info["gemm_staged"]))
+        del F, last
+    head = forms[0]
+    prof = prof_all[head]
+    pk = with_simt_peak(peaks(), device_sms(dev))
+    tracked = {k: v for k, v in prof.items() if v[2] > 0}
+    dom = max(tracked, key=lambda k: tracked[k][0])
+    total_ms = sum(v[0] for v in prof.values())
+    roof = roofline_of(dom, *prof[dom], total_ms, pk)
+    roof["others"] = [roofline_of(k, *prof[k], total_ms, pk) for k in
+                      sorted(tracked, key=lambda k: -tracked[k][0]) if k != dom][:3]
+    # e2e through host buffers: A and b in, x out
+    rp = torch.as_tensor(A.row_ptr).pin_memory()
+    ci = torch.as_tensor(A.col_idx).pin_memory()
+    va = torch.as_tensor(A.val.reshape(-1)).pin_memory()
+    bh = torch.as_tensor(np.asfortranarray(b_host).T.copy()).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    d_rp, d_ci, d_va = (torch.empty_like(t, device=dev) for t in (rp, ci, va))
+    d_b = torch.empty_like(bh, device=dev)
+    ets = []
+    for it in range(1 + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for dst, src in ((d_rp, rp), (d_ci, ci), (d_va, va), (d_b, bh)):
+            dst.copy_(src, non_blocking=True)
+        dA2 = hssnd.DeviceBSR.__new__(hssnd.DeviceBSR)
+        dA2.nb, dA2.bs, dA2.row_ptr, dA2.col_idx, dA2.val = A.nb, A.bs, d_rp, d_ci, d_va
+        dA2.c = hssnd.hss_bsr(A.nb, A.bs, d_rp.data_ptr(), d_ci.data_ptr(), d_va.data_ptr())
+        tree = hssnd.nd_order(meshdesc, dA2, leaf_max=64)
+        r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h), rmax=spec["rmax"])[1]
+        F = hssnd.hss_factor(dA2, tree, tol=tol, precision="fp32", r_init=r0, autotune=1, probe=args.probe,
+                             rmax=spec["rmax"], tensor_cores=args.tensor_cores)
+        x, st = hssnd.fgmres_solve(dA2, F, d_b.t(), rtol=RTOL, restart=RESTART)
+        xh.copy_(x.t() if x.dim() == 2 else x.reshape(1, -1), non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 1:
+            ets.append(e0.elapsed_time(e1))
+        del F
+    h2d = rp.numel() * 4 + ci.numel() * 4 + va.numel() * 8 + bh.numel() * 8
+    value = out[head]["ms"]
+    e2e_v = statistics.mean(ets)
+    if world > 1:
+        value, e2e_v = max_over_ranks([value, e2e_v], dev)
+    kernels = {form: {k: dict(ms=round(v[0], 3), launches=v[1]) for k, v in
+                      sorted(pf.items(), key=lambda kv: -kv[1][0])[:12]} for form, pf in prof_all.items()}
+    return dict(metric=METRIC, value=value, unit="ms", n_gpus=world, steps=out[head]["steps"],
+                warmup=out[head]["warmup"], ms_per_step=value, higher_is_better=False, scaling="weak",
+                vs_baseline=None, dtype="f32 factor / f64 Krylov", data="synthetic",
+                config=dict(workload=spec["workload"], dofs=A.n, p=spec["p"], dim=spec["dim"], id_tol=tol,
+                            rtol=RTOL, restart=RESTART, rhs=nrhs, leaf_max=64, rmax=spec["rmax"],
+                            headline_form=head, tensor_cores=args.tensor_cores,
+                            learned_widths=dict(train_samples=int(len(tt)), train_loss=train_loss,
+                                                trained_on="adaptive runs, " + (
+                                                    "Helmholtz 64x64 p=1,2,3" if spec["dim"] == 2 else
+                                                    "3D diffusion 16^3 p=1") + ", seeds 100..115"),
+                            learned_probe_vectors=args.probe,
+                            l2="flushed by a 256 MB write before every timed step (the factor is GBs)",
+                            parallelism=f"replicas x{world} (independent instances)"),
+                forms=out, roofline=roof, clocks=clocks, gpu_launches=int(launches), kernels=kernels,
+                tuner=hssnd.gemm_tuner_choices() if args.tensor_cores == 3 else None,
+                e2e=dict(value=e2e_v, unit="ms", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(bh.numel() * 8)))
+
+
+def cpu_baseline_large(args, res):
+    """SURVEY's rule for the large configurations: the oracle as it stands on
+    the same family at the reduced size (64 x 64 p = 3 Helmholtz, 16^3 p = 1
+    diffusion with one right-hand side), timed, plus the GPU headline form on
+    that same problem against the oracle (apply and solution); the full-size
+    check is the true FP64 residual of every solution in the bench line."""
+    import oracle
+    import torch
+    from paper_1508_07798_gb300 import hssnd
+    from paper_1508_07798_gb300 import dg_inputs as dg
+    spec = dict(LARGE[args.workload])
+    n_s, p_s = spec["small"]
+    spec["nrhs"] = 1
+    mesh, A, b, meshdesc, c_elem, kappa_h = large_problem(spec, 0, n_s, p_s)
+    b = b[:, 0]
+    Acsr = dg.bsr_to_csr(A)
+    t0 = time.perf_counter()
+    nd = oracle.nd_order(spec["dim"], mesh.n, p_s, A.row_ptr, A.col_idx, leaf_max=64)
+    fac = oracle.factor(Acsr, nd, tol=spec["tol"], seed=0, rmax=spec["rmax"])
+    xo, info = oracle.fgmres(lambda v: Acsr @ v, lambda v: oracle.apply(fac, v), b, rtol=RTOL, restart=RESTART)
+    dt = time.perf_counter() - t0
+    # the GPU forms on the same small problem, against the oracle
+    dA = hssnd.DeviceBSR.from_host(A)
+    tree = hssnd.nd_order(meshdesc, dA)
+    X = dg.random_rhs(A.n, 2, 7)
+    errs = {}
+    for form in ("fp64", "fp32"):
+        F = hssnd.hss_factor(dA, tree, tol=spec["tol"], precision=form, rmax=spec["rmax"],
+                             tensor_cores=args.tensor_cores if form == "fp32" else 0)
+        Y = hssnd.hss_apply(F, torch.as_tensor(X, device="cuda")).cpu().numpy()
+        Yo = oracle.apply(fac, X)
+        x, st = hssnd.fgmres_solve(dA, F, torch.as_tensor(b, device="cuda"), rtol=RTOL, restart=RESTART)
+        errs[form] = dict(apply_rel_err=float(np.linalg.norm(Y - Yo) / np.linalg.norm(Yo)),
+                          solution_rel_diff=float(np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)),
+                          iters=st.iters, oracle_iters=info["iters"])
+    return dict(value=dt * 1e3, unit="ms", cores=cpu_cores(), blas_threads=blas_threads(), kind="oracle",
+                sample=f"one {A.n}-dof solve of the same family ({n_s}^{spec['dim']} elements, p={p_s}), "
+                       "the reduced size SURVEY prescribes for the large configurations",
+                iters=info["iters"], gpu_vs_oracle_at_sample=errs)
+
+
 BATCH_COUNT, BATCH_RHS, BATCH_TOL = 256, 32, 1e-6
 
 
@@ -645,6 +876,17 @@ def main():
         dist.init_process_group("nccl")
     import __graft_entry__
     __graft_entry__.build()
+    if args.workload in LARGE:
+        res = bench_large(args, rank, world)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline_large(args, res)
+        if rank == 0:
+            print(json.dumps(res))
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     if args.workload == "batched256":
         res = bench_batched(args, rank, world)
         if rank == 0:

@@ -169,15 +169,13 @@ template <class T> int choose_engine(const Engine &E, const GemmDesc<T> &d, Work
                 return HSS_OK;
             }
         }
-        GemmDesc<float> t = d;   // same operands, a scratch C
+        GemmDesc<float> t = d;   // same operands, masks and beta (the C traffic counts), a scratch C
         float *scratch;
         int rc;
         if ((rc = W.dalloc((size_t)d.m * d.n, &scratch))) return rc;
+        HSS_CUDA(cudaMemsetAsync(scratch, 0, sizeof(float) * (size_t)d.m * d.n, s));
         t.C = scratch;
         t.ldc = d.m;
-        t.beta = 0.f;
-        t.zr_lo = t.zr_hi = 0;
-        t.skip_lo = t.skip_hi = 0;
         float ms_simt = 0.f, ms_tc = 0.f;
         if ((rc = time_engine(E, t, ENG_SIMT, W, s, &ms_simt)) || (rc = time_engine(E, t, tc, W, s, &ms_tc))) return rc;
         g_eng_timings.fetch_add(1);
@@ -282,7 +280,7 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
                     const int *ilist, int *iperm, int *status, double &exec_flops, const Engine &eng, Work &W,
                     cudaStream_t s) {
     int nf = (int)fr.size();
-    std::vector<int> kb(nf), nsteps(nf), isreg(nf), Rf(nf);
+    std::vector<int> kb(nf), nsteps(nf), isreg(nf), Rf(nf), clpath(nf, 0);
     std::vector<long> aoff(nf);
     long aold_total = 0;
     int maxsteps = 0;
@@ -295,6 +293,12 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
                 isreg[f] = 1;
                 break;
             }
+        // tall fronts: 32-column panels spread over a cluster while their rows
+        // exceed one CTA's registers, then the register panel
+        if (fr[f].ni > PANEL_CL_MIN_NI && panel_cl_fits(PANEL_KB_MAX, fr[f].ni, (int)sizeof(T))) {
+            kb[f] = PANEL_KB_MAX;
+            clpath[f] = 1;
+        }
         Rf[f] = cdiv(std::max(fr[f].ni, 1), PANEL_NT);
         nsteps[f] = fr[f].ni > 0 ? cdiv(fr[f].ni, kb[f]) : 0;
         aoff[f] = aold_total;
@@ -304,7 +308,7 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
     }
     if (maxsteps == 0) return HSS_OK;
     struct Group {
-        int off, cnt, reg, kb, rows;
+        int off, cnt, reg, kb, rows;   // reg: 0 memory panel, 1 register panel, 2 cluster panel
         size_t smem;
         double flops;   // algorithmic work of the group's panels: 2 hT kb^2 each
     };
@@ -348,6 +352,13 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         std::vector<int> act;
         for (int f = 0; f < nf; ++f)
             if (st < nsteps[f]) act.push_back(f);
+        // panel kind of this step: register (isreg, or a cluster-path front whose
+        // rows now fit one CTA), cluster, memory
+        auto kind = [&](int f) {
+            if (isreg[f]) return 1;
+            if (!clpath[f]) return 0;
+            return panel_reg_fits(kb[f], fr[f].ni - st * kb[f], (int)sizeof(T)) ? 1 : 2;
+        };
         // register panels grouped by (kb, rows of this step's variant), then the
         // memory panels; the variant follows the rows left at this step
         auto step_rows = [&](int f) {
@@ -356,10 +367,16 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             if (hTs <= 2 * PANEL_SMALL_NT) return 2 * PANEL_SMALL_NT;
             return cdiv(hTs, PANEL_NT) * PANEL_NT;
         };
+        auto group_rows = [&](int f) {
+            const int k = kind(f);
+            if (k == 1) return step_rows(f);
+            if (k == 2) return panel_cl_capacity(fr[f].ni - st * kb[f], (int)sizeof(T));
+            return Rf[f] * PANEL_NT;
+        };
         std::stable_sort(act.begin(), act.end(), [&](int a, int b) {
-            if (isreg[a] != isreg[b]) return isreg[a] > isreg[b];
+            if (kind(a) != kind(b)) return kind(a) > kind(b);
             if (kb[a] != kb[b]) return kb[a] < kb[b];
-            return step_rows(a) < step_rows(b);
+            return group_rows(a) < group_rows(b);
         });
         for (int f : act) {
             const int n = fr[f].n;
@@ -373,7 +390,8 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             size_t hT = (size_t)(fr[f].ni - k0);
             int use_smem = 0;
             size_t need = 0;
-            if (isreg[f]) {
+            const int knd = kind(f);
+            if (knd != 0) {
                 use_smem = 2;
                 need = 3 * hT * sizeof(int);
             } else {
@@ -382,9 +400,9 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
                 if (!use_smem) need = hT * sizeof(int);
             }
             auto &gs = groups[st];
-            if (gs.empty() || gs.back().reg != isreg[f] ||
-                (isreg[f] && (gs.back().kb != kb[f] || gs.back().rows != step_rows(f))))
-                gs.push_back({(int)jobs.size(), 0, isreg[f], kb[f], isreg[f] ? step_rows(f) : Rf[f] * PANEL_NT, 0, 0.0});
+            if (gs.empty() || gs.back().reg != knd ||
+                (knd != 0 && (gs.back().kb != kb[f] || gs.back().rows != group_rows(f))))
+                gs.push_back({(int)jobs.size(), 0, knd, kb[f], group_rows(f), 0, 0.0});
             gs.back().cnt++;
             gs.back().flops += 2.0 * (double)hT * kbs * kbs;
             gs.back().smem = std::max(gs.back().smem, need);
@@ -474,9 +492,12 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         return rc;
     for (int st = 0; st < maxsteps; ++st) {
         for (const Group &g : groups[st]) {
-            if (g.reg)
+            if (g.reg == 1)
                 rc = launch_gj_panel_reg<T>(d_jobs + g.off, g.cnt, g.kb, g.rows, d_fr, arena, d_x, d_mv, piv, rperm,
                                             ilist, iperm, status, s, g.flops);
+            else if (g.reg == 2)
+                rc = launch_gj_panel_cl<T>(d_jobs + g.off, g.cnt, g.rows, g.smem, d_fr, arena, d_x, d_mv, piv, rperm,
+                                           ilist, iperm, status, s, g.flops);
             else
                 rc = launch_gj_panel<T>(d_jobs + g.off, g.cnt, g.smem, d_fr, arena, d_x, d_mv, piv, rperm, ilist,
                                         iperm, status, s, g.flops);

@@ -14,7 +14,10 @@
 // the Schur complement of eq. (32).  P is the pivot row permutation; the
 // apply undoes it by gathering x_I through a permuted index list.
 #include <cfloat>
+#include <mutex>
 #include <type_traits>
+
+#include <cooperative_groups.h>
 
 #include "internal.h"
 #include "front.h"
@@ -455,6 +458,192 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(const PanelJob *__restrict_
         }
 }
 
+// Cluster-resident panel for tall panels (more rows than one CTA's registers
+// hold): a cluster of CL CTAs shares one panel, CTA c thread t owning rows
+// q (CL NT) + c NT + t, q < R, in registers.  Per pivot: every CTA reduces its
+// rows' candidates, the CL candidates are exchanged through distributed
+// shared memory (largest magnitude, lowest position on ties: the pivot of the
+// single-CTA kernel), the owner publishes the pivot row and every CTA reads
+// it from the owner's shared memory; the Gauss-Jordan step then runs in
+// registers as in k_gj_panel_reg.  The row <-> position bookkeeping (pos,
+// posinv, rp) is replicated in every CTA (the same swaps, applied by each),
+// so CTA 0 alone writes the global bookkeeping (pivots, rperm, move list,
+// gather list) and every CTA writes its own rows to their final positions.
+namespace cg = cooperative_groups;
+
+template <class T, int KB, int R, int NT, int CL>
+__global__ void __launch_bounds__(NT) k_gj_panel_cl(const PanelJob *__restrict__ jobs,
+                                                       const FrontDev *__restrict__ fr, T *__restrict__ arena,
+                                                       T *__restrict__ xws, int *__restrict__ mws,
+                                                       int *__restrict__ piv, int *__restrict__ rperm,
+                                                       const int *__restrict__ ilist, int *__restrict__ iperm,
+                                                       int *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ ArgMax<T> red[NT / 32];
+    __shared__ ArgMax<T> cand;        // this CTA's best candidate of the current step
+    __shared__ ArgMax<T> gbest;       // the cluster's pivot of the current step
+    __shared__ T rowx[KB];            // the pivot row, when this CTA owns it
+    __shared__ T rowj[KB];            // the pivot row, local copy
+    __shared__ int nmv;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int crank = (int)cluster.block_rank();
+    const PanelJob J = jobs[blockIdx.x / CL];
+    const FrontDev F = fr[J.front];
+    T *M = arena + F.foff;
+    const long ld = F.n;
+    const int k0 = J.k0, kb = J.kb, ni = F.ni;
+    const int hT = ni - k0;
+    constexpr int STRIDE = CL * NT;
+    int *pos = reinterpret_cast<int *>(smraw);   // hT, replicated
+    int *posinv = pos + hT;                       // hT
+    int *rp = posinv + hT;                        // hT
+    int *rglob = rperm + F.ioff;
+    T reg[R][KB];
+    bool done[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int i = q * STRIDE + crank * NT + threadIdx.x;
+        done[q] = false;
+#pragma unroll
+        for (int c = 0; c < KB; ++c) reg[q][c] = (i < hT && c < kb) ? M[(k0 + i) + ld * (k0 + c)] : T(0);
+    }
+    for (int i = threadIdx.x; i < hT; i += NT) {
+        pos[i] = i;
+        posinv[i] = i;
+        rp[i] = k0 == 0 ? i : rglob[k0 + i];
+    }
+    if (threadIdx.x == 0) nmv = 0;
+    __syncthreads();
+    int *pv = piv + F.ioff;
+    ArgMax<T> loc{-1LL, 0x7fffffff};
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int i = q * STRIDE + crank * NT + threadIdx.x;
+        if (i < hT) {
+            const long long v = mag_key(reg[q][0]);
+            if (v > loc.v || (v == loc.v && i < loc.i)) {
+                loc.v = v;
+                loc.i = i;
+            }
+        }
+    }
+#pragma unroll 1
+    for (int j = 0; j < kb; ++j) {
+        // 1. this CTA's best, then the cluster's (warp 0 reads the CL candidates)
+        const ArgMax<T> mine = block_argmax(loc, red);
+        if (threadIdx.x == 0) cand = mine;
+        cluster.sync();
+        if (threadIdx.x < 32) {
+            ArgMax<T> c{-1LL, 0x7fffffff};
+            if ((int)threadIdx.x < CL) c = *cluster.map_shared_rank(&cand, (unsigned)threadIdx.x);
+            c = warp_argmax(c);
+            if (threadIdx.x == 0) gbest = c;
+        }
+        __syncthreads();
+        const ArgMax<T> best = gbest;
+        int p = best.i;
+        if (best.v <= 0) {
+            if (threadIdx.x == 0 && crank == 0) atomicExch(&status[J.front], 1);
+            p = j;
+        }
+        const int x = posinv[p];   // row of the pivot
+        const int y = posinv[j];   // row at position j: trades places with the pivot
+        const int owner = (x % STRIDE) / NT;
+        if (owner == crank) {
+#pragma unroll
+            for (int q = 0; q < R; ++q)
+                if (q * STRIDE + crank * NT + (int)threadIdx.x == x) {
+#pragma unroll
+                    for (int c = 0; c < KB; ++c) rowx[c] = reg[q][c];
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (q * STRIDE + crank * NT + (int)threadIdx.x == x) done[q] = true;
+        cluster.sync();   // rowx of the owner is complete; every CTA has read cand and posinv
+        if (threadIdx.x < KB) rowj[threadIdx.x] = cluster.map_shared_rank(rowx, (unsigned)owner)[threadIdx.x];
+        if (threadIdx.x == 0) {
+            posinv[j] = x;
+            posinv[p] = y;
+            pos[x] = j;
+            pos[y] = p;
+            const int t = rp[j];
+            rp[j] = rp[p];
+            rp[p] = t;
+            if (crank == 0) pv[k0 + j] = k0 + p;
+        }
+        __syncthreads();
+        // 2. Gauss-Jordan step in registers, then rotate; candidates of the next column
+        const T dinv = rowj[0] != T(0) ? T(1) / rowj[0] : T(0);
+        loc = ArgMax<T>{-1LL, 0x7fffffff};
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = q * STRIDE + crank * NT + threadIdx.x;
+            if (i >= hT) continue;
+            T head;
+            if (i == x) {
+#pragma unroll
+                for (int c = 1; c < KB; ++c) reg[q][c] = rowj[c] * dinv;
+                head = dinv;
+            } else {
+                const T ad = reg[q][0] * dinv;
+#pragma unroll
+                for (int c = 1; c < KB; ++c) reg[q][c] -= ad * rowj[c];
+                head = -ad;
+            }
+#pragma unroll
+            for (int c = 0; c + 1 < KB; ++c) reg[q][c] = reg[q][c + 1];
+            reg[q][KB - 1] = head;
+            if (!done[q]) {
+                const long long v = mag_key(reg[q][0]);
+                const int ps = (i == y) ? p : pos[i];
+                if (v > loc.v || (v == loc.v && ps < loc.i)) {
+                    loc.v = v;
+                    loc.i = ps;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // 3. every row to its final position; the pivot block also to X
+    T *Xg = xws + J.xoff;
+    int *mv = mws + J.moff;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int i = q * STRIDE + crank * NT + threadIdx.x;
+        if (i >= hT) continue;
+        const int r = pos[i];
+#pragma unroll
+        for (int c = 0; c < KB; ++c) {
+            const int col = (kb + c) % KB;
+            if (col < kb) {
+                M[(k0 + r) + ld * (k0 + col)] = reg[q][c];
+                if (r < kb) Xg[r + kb * col] = reg[q][c];
+            }
+        }
+    }
+    if (crank == 0) {
+        // the move list (rows whose position changed) and the bookkeeping, from the replica
+        for (int i = threadIdx.x; i < hT; i += NT) {
+            const int r = pos[i];
+            if (r != i) {
+                const int m = atomicAdd(&nmv, 1);
+                mv[1 + m] = r;
+                mv[1 + 2 * PANEL_KB_MAX + m] = i;
+            }
+            rglob[k0 + i] = rp[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) mv[0] = nmv;
+        if (k0 + kb == ni)
+            for (int jj = threadIdx.x; jj < ni; jj += NT) {
+                const int r = jj < k0 ? rglob[jj] : rp[jj - k0];
+                iperm[F.iperm_off + jj] = ilist[F.iset_off + r];
+            }
+    }
+    cluster.sync();   // no CTA leaves while a peer may still read its shared memory
+}
+
 // Work that follows a panel, spread over many CTAs:
 //   type 0 (32 columns outside the panel): apply the panel's row moves, then
 //          copy the (moved) pivot rows into Aold, the B operand of the update;
@@ -638,6 +827,122 @@ int launch_gj_panel_reg(const PanelJob *jobs, int njobs, int kb, int rows, const
     return HSS_OK;
 }
 
+// Cluster panel for kb <= KB, rows <= R * NT * CL (NT = PANEL_NT): one
+// cluster of CL CTAs per job.  Clusters of 16 are beyond the portable size and
+// need the non-portable attribute; a configuration the GPU cannot place
+// (cudaOccupancyMaxActiveClusters = 0) is reported as unusable.
+template <class T, int KB, int R, int CL>
+static cudaError_t launch_cl(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws,
+                             int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status,
+                             cudaStream_t s) {
+    auto kern = k_gj_panel_cl<T, KB, R, PANEL_NT, CL>;
+    cudaError_t e = func_smem_once((const void *)kern, PANEL_SMEM_MAX);
+    if (e != cudaSuccess) return e;
+    if (CL > 8 && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(njobs * CL));
+    cfg.blockDim = dim3(PANEL_NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (njobs == 0) {   // placement query only
+        int nc = 0;
+        cfg.gridDim = dim3(CL);
+        e = cudaOccupancyMaxActiveClusters(&nc, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        return nc > 0 ? cudaSuccess : cudaErrorInvalidClusterSize;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
+}
+
+// rows of a cluster panel step -> (R, CL): CL the smallest of 2, 4, 8, 16 with
+// rows <= R PANEL_NT CL for R = 2 (FP32: 64 registers of panel values per
+// thread; FP64: R = 1)
+static void cl_shape(int rows, int tsize, int &R, int &CL) {
+    R = tsize == 8 ? 1 : 2;
+    for (CL = 2; CL < 16 && rows > R * PANEL_NT * CL; CL *= 2) {
+    }
+}
+
+bool panel_cl_fits(int kb, int rows, int tsize) {
+    if (kb != PANEL_KB_MAX) return false;
+    int R, CL;
+    cl_shape(rows, tsize, R, CL);
+    if (rows > R * PANEL_NT * CL || 3L * rows * 4 > PANEL_SMEM_MAX) return false;
+    // can the GPU place one cluster of this shape? (checked once per shape and device)
+    static std::mutex mu;
+    static int ok[2][5][64] = {};   // [tsize 4/8][log2 CL][device]: 0 unknown, 1 yes, -1 no
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return false;
+    int lc = 0;
+    while ((1 << lc) < CL) ++lc;
+    std::lock_guard<std::mutex> lk(mu);
+    int &st = ok[tsize == 8][lc][dev];
+    if (st == 0) {
+        cudaError_t e = cudaErrorInvalidValue;
+        const size_t smem = 3 * (size_t)rows * 4;
+        if (tsize == 8) {
+            if (CL == 2) e = launch_cl<double, 32, 1, 2>(nullptr, 0, smem, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                          nullptr, nullptr, nullptr, nullptr, nullptr);
+            else if (CL == 4) e = launch_cl<double, 32, 1, 4>(nullptr, 0, smem, nullptr, nullptr, nullptr, nullptr,
+                                                              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+            else if (CL == 8) e = launch_cl<double, 32, 1, 8>(nullptr, 0, smem, nullptr, nullptr, nullptr, nullptr,
+                                                              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+            else e = launch_cl<double, 32, 1, 16>(nullptr, 0, smem, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                  nullptr, nullptr, nullptr, nullptr, nullptr);
+        } else {
+            if (CL == 2) e = launch_cl<float, 32, 2, 2>(nullptr, 0, smem, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                         nullptr, nullptr, nullptr, nullptr, nullptr);
+            else if (CL == 4) e = launch_cl<float, 32, 2, 4>(nullptr, 0, smem, nullptr, nullptr, nullptr, nullptr,
+                                                             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+            else if (CL == 8) e = launch_cl<float, 32, 2, 8>(nullptr, 0, smem, nullptr, nullptr, nullptr, nullptr,
+                                                             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+            else e = launch_cl<float, 32, 2, 16>(nullptr, 0, smem, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                 nullptr, nullptr, nullptr, nullptr, nullptr);
+        }
+        if (e != cudaSuccess) cudaGetLastError();
+        st = e == cudaSuccess ? 1 : -1;
+    }
+    return st > 0;
+}
+
+int panel_cl_capacity(int rows, int tsize) {
+    int R, CL;
+    cl_shape(rows, tsize, R, CL);
+    return R * PANEL_NT * CL;
+}
+
+template <class T>
+int launch_gj_panel_cl(const PanelJob *jobs, int njobs, int cap, size_t smem, const FrontDev *fr, T *arena, T *xws,
+                       int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s,
+                       double flops) {
+    if (njobs == 0) return HSS_OK;
+    int R, CL;
+    cl_shape(cap, (int)sizeof(T), R, CL);
+    HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s, flops);
+    cudaError_t e;
+    if constexpr (sizeof(T) == 8) {
+        if (CL == 2) e = launch_cl<T, 32, 1, 2>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm, status, s);
+        else if (CL == 4) e = launch_cl<T, 32, 1, 4>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm, status, s);
+        else if (CL == 8) e = launch_cl<T, 32, 1, 8>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm, status, s);
+        else e = launch_cl<T, 32, 1, 16>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm, status, s);
+    } else {
+        if (CL == 2) e = launch_cl<T, 32, 2, 2>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm, status, s);
+        else if (CL == 4) e = launch_cl<T, 32, 2, 4>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm, status, s);
+        else if (CL == 8) e = launch_cl<T, 32, 2, 8>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm, status, s);
+        else e = launch_cl<T, 32, 2, 16>(jobs, njobs, smem, fr, arena, xws, mws, piv, rperm, ilist, iperm, status, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "k_gj_panel_cl");
+    return HSS_OK;
+}
+
 bool panel_reg_fits(int kb, int rows, int tsize) {
     const int R = cdiv(rows, PANEL_NT);
     // register budget of the panel rows: R * kb values of tsize bytes <= 96 32-bit registers
@@ -665,6 +970,10 @@ template int launch_gj_panel<double>(const PanelJob *, int, size_t, const FrontD
                                      int *, int *, const int *, int *, int *, cudaStream_t, double);
 template int launch_gj_panel<float>(const PanelJob *, int, size_t, const FrontDev *, float *, float *, int *, int *,
                                     int *, const int *, int *, int *, cudaStream_t, double);
+template int launch_gj_panel_cl<double>(const PanelJob *, int, int, size_t, const FrontDev *, double *, double *,
+                                        int *, int *, int *, const int *, int *, int *, cudaStream_t, double);
+template int launch_gj_panel_cl<float>(const PanelJob *, int, int, size_t, const FrontDev *, float *, float *, int *,
+                                       int *, int *, const int *, int *, int *, cudaStream_t, double);
 template int launch_gj_panel_reg<double>(const PanelJob *, int, int, int, const FrontDev *, double *, double *,
                                          int *, int *, int *, const int *, int *, int *, cudaStream_t, double);
 template int launch_gj_panel_reg<float>(const PanelJob *, int, int, int, const FrontDev *, float *, float *, int *,

@@ -75,6 +75,17 @@ int launch_gj_panel_reg(const PanelJob *jobs, int njobs, int kb, int rows, const
                         int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s,
                         double flops = 0.0);
 bool panel_reg_fits(int kb, int rows, int tsize);
+// Cluster-resident panel (k_gj_panel_cl): rows spread over a cluster of 2..16
+// CTAs; for kb = PANEL_KB_MAX and panels too tall for one CTA's registers.
+bool panel_cl_fits(int kb, int rows, int tsize);
+// rows a cluster panel of `rows` rows is launched for (its shape's capacity);
+// jobs of one launch share it
+int panel_cl_capacity(int rows, int tsize);
+constexpr int PANEL_CL_MIN_NI = 6144;   // fronts with more interior dofs take the cluster panel
+template <class T>
+int launch_gj_panel_cl(const PanelJob *jobs, int njobs, int cap, size_t smem, const FrontDev *fr, T *arena, T *xws,
+                       int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status, cudaStream_t s,
+                       double flops = 0.0);
 template <class T>
 int launch_gj_block_post(const BlockTile *tiles, int ntiles, const BlockJob *bjobs, const PanelJob *jobs,
                          const FrontDev *fr, T *arena, T *aold, const int *mws, cudaStream_t s);

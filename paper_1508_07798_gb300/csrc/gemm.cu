@@ -88,6 +88,20 @@ __global__ void __launch_bounds__(GT) k_gemm(const GemmDesc<T> *__restrict__ des
         if (kc + 1 < nk) store_regs(buf ^ 1);
         __syncthreads();
     }
+    // the 16 C values this thread updates are loaded before any store (a store
+    // could alias a later load: interleaved, they would run one at a time)
+    T cv[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int gj = col0 + ty + 16 * b;
+        const bool colok = gj < d.n && !(gj >= d.skip_lo && gj < d.skip_hi);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int gi = row0 + tx + 16 * a;
+            const T beta = (gi >= d.zr_lo && gi < d.zr_hi) ? T(0) : d.beta;
+            cv[a][b] = (colok && gi < d.m && beta != T(0)) ? d.C[gi + (long)gj * d.ldc] : T(0);
+        }
+    }
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         int gj = col0 + ty + 16 * b;
@@ -96,11 +110,10 @@ __global__ void __launch_bounds__(GT) k_gemm(const GemmDesc<T> *__restrict__ des
         for (int a = 0; a < 4; ++a) {
             int gi = row0 + tx + 16 * a;
             if (gi >= d.m) continue;
-            T *c = d.C + gi + (long)gj * d.ldc;
             T beta = (gi >= d.zr_lo && gi < d.zr_hi) ? T(0) : d.beta;
             T v = d.alpha * acc[a][b];
-            if (beta != T(0)) v = fma(beta, *c, v);
-            *c = v;
+            if (beta != T(0)) v = fma(beta, cv[a][b], v);
+            d.C[gi + (long)gj * d.ldc] = v;
         }
     }
 }

@@ -331,27 +331,37 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restric
             }
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows), 16 columns at a time
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows), 64 columns at a
+        // time; the 64 C values of a row are loaded together before any store
+        // (a store could alias a later load, so loads interleaved with stores
+        // would run one round trip at a time)
         const int gi = row0 + warp * 32 + lane;
         const bool rowok = gi < d.m;
         const float beta_row = (gi >= d.zr_lo && gi < d.zr_hi) ? 0.f : d.beta;
-        for (int c0 = 0; c0 < TN; c0 += 16) {
-            float v[16];
+        constexpr int EC = 64;
+        for (int c0 = 0; c0 < TN; c0 += EC) {
+            float v[EC], cv[EC];
+#pragma unroll
+            for (int u = 0; u < EC; ++u) {
+                const int gj = col0 + c0 + u;
+                const bool ok = rowok && gj < d.n && !(gj >= d.skip_lo && gj < d.skip_hi) && beta_row != 0.f;
+                cv[u] = ok ? d.C[gi + (long)gj * d.ldc] : 0.f;
+            }
             if (nk > 0) {
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+                for (int q = 0; q < EC; q += 16) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + q), v + q);
             } else {
 #pragma unroll
-                for (int u = 0; u < 16; ++u) v[u] = 0.f;
+                for (int u = 0; u < EC; ++u) v[u] = 0.f;
             }
             if (!rowok) continue;
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
+            for (int u = 0; u < EC; ++u) {
                 const int gj = col0 + c0 + u;
                 if (gj >= d.n || (gj >= d.skip_lo && gj < d.skip_hi)) continue;
-                float *c = d.C + gi + (long)gj * d.ldc;
                 float val = d.alpha * v[u];
-                if (beta_row != 0.f) val = fmaf(beta_row, *c, val);
-                *c = val;
+                if (beta_row != 0.f) val = fmaf(beta_row, cv[u], val);
+                d.C[gi + (long)gj * d.ldc] = val;
             }
         }
     }

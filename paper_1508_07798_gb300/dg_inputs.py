@@ -354,6 +354,17 @@ def rank_training_problems(n: int = 64, ps=(1, 2, 3), seeds=range(100, 116)) -> 
     return out
 
 
+def diffusion_training_problems(n: int = 16, p: int = 1, seeds=range(100, 116)) -> list:
+    """3D diffusion problems (a = exp(g) per `diffusion_3d`) whose adaptive
+    factorizations give training ranks for the 3D learned-width form: (mesh
+    descriptor, matrix, log a per element, kappa * h = 0) per seed."""
+    out = []
+    for sd in seeds:
+        mesh, A = diffusion_3d(n, p, sd)
+        out.append(((3, (n, n, n), p), A, np.log(gaussian_log_field(mesh, sd)), 0.0))
+    return out
+
+
 def random_rhs(ndof: int, nrhs: int, seed: int, kind: str = "uniform") -> np.ndarray:
     """Column-major (ndof x nrhs) right-hand sides: U(-1,1) or N(0,1) per dof."""
     rng = np.random.default_rng(seed)

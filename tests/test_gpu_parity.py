@@ -358,7 +358,7 @@ def test_fp32_form_tensor_cores_match_simt(p):
     hs.profile_enable(False)
     cls = hs.profile_read()
     if p == 1:   # every front size is a multiple of 4 (p = 2: only those of 36 k dofs)
-        assert "gemm_tma" in cls and "gemm_tc" not in cls, cls.keys()
+        assert any(k.startswith("gemm_tma") for k in cls) and "gemm_tc" not in cls, cls.keys()
     Fsi = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", tensor_cores=0, keep_schur=1)
     # same ranks and widths from the two engines' samples, approximants of the same quality
     lt, ls = Ftc.export_log(), Fsi.export_log()
