@@ -81,6 +81,7 @@ def peaks():
 # FP32 FMA/clk/SM x 2 flop x the maximum SM clock (from the peaks file, else
 # GB300's 2,070 MHz).  FP64: the nominal 1.25 TFLOP/s of GB300.
 FP64_TFLOPS = 1.25
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 rates of GB300
 
 
 def with_simt_peak(pk, sms):
@@ -114,6 +115,26 @@ def roofline_of(kernel, ms, cnt, work, total_ms, pk):
     classes (apply, SpMV) against the measured HBM bandwidth.  pk: peaks() with
     the FP32 SIMT peak of the device (with_simt_peak)."""
     per_launch_s = ms / cnt * 1e-3
+    if kernel == "gemm_tma_block":
+        # the blocked sweep's K = 256 updates C += A B of whole fronts on the TMA-fed tensor-core
+        # kernel: at K = 256 their arithmetic intensity against the C stream (read + write, 8 B per
+        # output; A and B come from L2) is 2 * 256 / 8 = 64 flop/B, below the TF32 ridge, so HBM
+        # bounds them: algorithmic bytes = flops / 64 (ragged last blocks have K < 256: an
+        # underestimate of their bytes)
+        tflops = work / cnt / per_launch_s / 1e12
+        ach = work / 64.0 / cnt / per_launch_s / 1e9
+        return dict(kernel=kernel, bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
+                    traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
+                    peak_source=f"{pk['src']} (MEASURED_PEAKS.json hbm_gbs)" if pk["src"] == "measured"
+                    else pk["src"], tflops=tflops, tf32_peak_tflops=pk["bf16"] * TF32_PER_BF16,
+                    tensor_frac=tflops / (pk["bf16"] * TF32_PER_BF16),
+                    note="bytes = flops / 64: the C stream of K = 256 updates; A, B from L2")
+    if kernel.startswith("gemm_tma") or kernel.startswith("gemm_tc"):
+        peak = pk["bf16"] * TF32_PER_BF16
+        ach = work / cnt / per_launch_s / 1e12
+        return dict(kernel=kernel, bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
+                    peak_source=f"TF32 = measured BF16 x {TF32_PER_BF16:.3f} (nominal 1.1 / 2.25 PFLOP/s)")
     if kernel.startswith("gemm") or kernel.startswith("gj_panel"):
         f32 = kernel.endswith("f32")
         peak = pk["fp32"] if f32 else FP64_TFLOPS

@@ -90,7 +90,7 @@ typedef struct hss_factor_opts {
     int keep_schur;         /* 1: keep a copy of every front's S and H for hss_factor_export_front */
     int tensor_cores;       /* FP32 form only: 0 (default) SIMT FMA; 1 tcgen05 TF32 with the three-product
                                hi/lo split (FP32 accuracy) for products with M, K >= 128 and N >= 32 (the
-                               sampling products and the K = 128 updates of the blocked sweep), operands
+                               sampling products and the K = 256 updates of the blocked sweep), operands
                                brought in by TMA where they are 16-byte aligned with leading dimensions
                                that are multiples of 4 (front sizes divisible by 4), staged by the threads
                                otherwise; 2 tcgen05 with a single TF32 product (threads staging); 3 per

@@ -75,7 +75,7 @@ struct Engine {
 // The fixed rule of tensor_cores = 1 / 2: long contractions only.  The
 // Gauss-Jordan in-block updates (K = panel width <= 32) are memory bound per
 // 128 x 128 tile and stay on FMA; the sampling products (K = |B|) and the
-// K = 128 block-end updates of large fronts go to the tensor cores.
+// K = 256 block-end updates of large fronts go to the tensor cores.
 template <class T> bool use_tc(const Engine &e, const GemmDesc<T> &d) {
     return std::is_same<T, float>::value && e.tc != 0 && d.m >= 128 && d.n >= 32 && d.k >= 128;
 }
@@ -319,7 +319,7 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
     // C_out <- F(:, B) Aold(B, out) + C_out with the block's pivot rows
     // zeroed, the panel formula with B for the panel).  This reads the
     // trailing matrix once per block instead of once per panel, and the
-    // K = 128 product suits the tensor cores; the cost is the explicit
+    // K = 256 product suits the tensor cores; the cost is the explicit
     // inverse of the block's pivot rows in the update, whose rounding grows
     // with that block's condition, so smaller fronts keep per-panel updates.
     std::vector<long> aoffB(nf);

@@ -49,7 +49,7 @@ struct PanelTile {
 // The end of a block of up to PANEL_BLOCK panels of one front: the columns
 // outside the block receive the block's row moves and one update of width
 // `width` (see k_gj_block_post).
-constexpr int PANEL_BLOCK = 4;
+constexpr int PANEL_BLOCK = 8;
 constexpr int PANEL_BLOCK_MIN_N = 2048;   // fronts at least this large run in blocks
 struct BlockJob {
     int front;        // stage-local front index

@@ -38,6 +38,14 @@ def test_roofline_arithmetic(bench):
         100 * 128 * 2 * 1.5e9 / 1e12)
     d = bench.roofline_of("gemm_f64", 1.0, 1, 1e9, 1.0, pk)
     assert d["peak"] == 1.25 and d["achieved"] == pytest.approx(1.0)
+    # tensor-core classes: the K = 256 block updates are bounded by their C stream (flops / 64 bytes),
+    # the other TMA launches by the TF32 rate (measured BF16 x 1.1 / 2.25)
+    pk3 = dict(pk, bf16=2000.0)
+    t = bench.roofline_of("gemm_tma_block", 1.0, 1, 6.4e10, 1.0, pk3)
+    assert t["bound"] == "hbm" and t["achieved"] == pytest.approx(1000.0) and t["tflops"] == pytest.approx(64.0)
+    assert t["tf32_peak_tflops"] == pytest.approx(2000.0 * 1.1 / 2.25)
+    u = bench.roofline_of("gemm_tma_sample", 1.0, 1, 1e10, 1.0, pk3)
+    assert u["bound"] == "tensor" and u["achieved"] == pytest.approx(10.0) and u["peak"] == pytest.approx(977.78, rel=1e-4)
 
 
 def test_peaks_file_and_fallback(bench, tmp_path, monkeypatch):
