@@ -58,8 +58,12 @@ def parse():
                          "widths (each its own JSON line)")
     ap.add_argument("--no-fp64", action="store_true",
                     help="large workloads: skip the plain FP64 comparison form")
-    ap.add_argument("--tensor-cores", type=int, default=0, choices=[0, 1, 3],
-                    help="GEMM engine of the FP32 forms: 0 SIMT, 1 tcgen05 (fixed rule), 3 per shape class by timing")
+    ap.add_argument("--tensor-cores", type=int, default=3, choices=[0, 1, 3],
+                    help="GEMM engine of the FP32 forms: 0 SIMT, 1 tcgen05 (fixed rule), 3 (default) per shape "
+                         "class the faster of SIMT and tcgen05, timed once (in the warm-up steps)")
+    ap.add_argument("--sample-bf16", type=int, default=None, choices=[0, 1],
+                    help="FP32 forms: sampling products on tcgen05 kind::f16 with S in three BF16 terms "
+                         "(default: on for diffusion32, whose configuration asks for BF16 sampling; off elsewhere)")
     ap.add_argument("--probe", type=int, default=4,
                     help="residual probe vectors per accepted front in the learned-width form (0: off)")
     ap.add_argument("--quick", action="store_true",
@@ -273,10 +277,11 @@ def bench_ours(args, rank, world):
         if prec == "fp32_learned":
             r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h))[1]
             F = hssnd.hss_factor(dA, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1, probe=args.probe,
-                                 tensor_cores=args.tensor_cores)
+                                 tensor_cores=args.tensor_cores, sample_bf16=args.sample_bf16 or 0)
         else:
             F = hssnd.hss_factor(dA, tree, tol=TOL, precision=prec, autotune=1,
-                                 tensor_cores=args.tensor_cores if prec == "fp32" else 0)
+                                 tensor_cores=args.tensor_cores if prec == "fp32" else 0,
+                                 sample_bf16=(args.sample_bf16 or 0) if prec == "fp32" else 0)
         if marks is not None:
             marks[1].record(stream)
         x, st = hssnd.fgmres_solve(dA, F, b, rtol=RTOL, restart=RESTART)
@@ -464,9 +469,9 @@ def bench_ours(args, rank, world):
 
 # ---- the large configurations: Helmholtz p = 3 on 256 x 256 quads and 3D diffusion p = 1 on 32^3 hexes
 LARGE = {
-    "helmholtz256": dict(dim=2, n=256, p=3, tol=1e-6, nrhs=1, rmax=96,
+    "helmholtz256": dict(dim=2, n=256, p=3, tol=1e-6, nrhs=1, rmax=96, bf16=0,
                          workload="helmholtz_sipg_p3_256x256", small=(64, 3)),
-    "diffusion32": dict(dim=3, n=32, p=1, tol=1e-5, nrhs=20, rmax=96,
+    "diffusion32": dict(dim=3, n=32, p=1, tol=1e-5, nrhs=20, rmax=96, bf16=1,
                         workload="diffusion3d_sipg_p1_32cubed_20rhs", small=(16, 1)),
 }
 
@@ -498,6 +503,7 @@ def bench_large(args, rank, world):
     from paper_1508_07798_gb300 import dg_inputs as dg
     from paper_1508_07798_gb300 import ranks
     spec = LARGE[args.workload]
+    bf16 = spec["bf16"] if args.sample_bf16 is None else args.sample_bf16
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
@@ -522,10 +528,11 @@ def bench_large(args, rank, world):
         if form == "fp32_learned":
             r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h), rmax=spec["rmax"])[1]
             F = hssnd.hss_factor(dA, tree, tol=tol, precision="fp32", r_init=r0, autotune=1, probe=args.probe,
-                                 rmax=spec["rmax"], tensor_cores=args.tensor_cores)
+                                 rmax=spec["rmax"], tensor_cores=args.tensor_cores, sample_bf16=bf16)
         else:
             F = hssnd.hss_factor(dA, tree, tol=tol, precision=form, autotune=1, rmax=spec["rmax"],
-                                 tensor_cores=args.tensor_cores if form == "fp32" else 0)
+                                 tensor_cores=args.tensor_cores if form == "fp32" else 0,
+                                 sample_bf16=bf16 if form == "fp32" else 0)
         if marks is not None:
             marks[1].record(stream)
         x, st = hssnd.fgmres_solve(dA, F, B, rtol=RTOL, restart=RESTART)
@@ -578,7 +585,7 @@ def bench_large(args, rank, world):
                          capped_fronts=info["capped_fronts"], probe_regrown=info["probe_regrown"],
                          sampling_rounds=int(F.export_log()["rounds"].sum()),
                          gemm_engines=dict(simt=info["gemm_simt"], tma=info["gemm_tma"],
-                                           staged=info["gemm_staged"]))
+                                           staged=info["gemm_staged"], bf16_sampling=info["gemm_bf16"]))
         del F, last
     head = forms[0]
     prof = prof_all[head]
@@ -611,7 +618,7 @@ def bench_large(args, rank, world):
         tree = hssnd.nd_order(meshdesc, dA2, leaf_max=64)
         r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h), rmax=spec["rmax"])[1]
         F = hssnd.hss_factor(dA2, tree, tol=tol, precision="fp32", r_init=r0, autotune=1, probe=args.probe,
-                             rmax=spec["rmax"], tensor_cores=args.tensor_cores)
+                             rmax=spec["rmax"], tensor_cores=args.tensor_cores, sample_bf16=bf16)
         x, st = hssnd.fgmres_solve(dA2, F, d_b.t(), rtol=RTOL, restart=RESTART)
         xh.copy_(x.t() if x.dim() == 2 else x.reshape(1, -1), non_blocking=True)
         e1.record(stream)
@@ -631,7 +638,7 @@ def bench_large(args, rank, world):
                 vs_baseline=None, dtype="f32 factor / f64 Krylov", data="synthetic",
                 config=dict(workload=spec["workload"], dofs=A.n, p=spec["p"], dim=spec["dim"], id_tol=tol,
                             rtol=RTOL, restart=RESTART, rhs=nrhs, leaf_max=64, rmax=spec["rmax"],
-                            headline_form=head, tensor_cores=args.tensor_cores,
+                            headline_form=head, tensor_cores=args.tensor_cores, sample_bf16=bf16,
                             learned_widths=dict(train_samples=int(len(tt)), train_loss=train_loss,
                                                 trained_on="adaptive runs, " + (
                                                     "Helmholtz 64x64 p=1,2,3" if spec["dim"] == 2 else
@@ -672,7 +679,9 @@ def cpu_baseline_large(args, res):
     errs = {}
     for form in ("fp64", "fp32"):
         F = hssnd.hss_factor(dA, tree, tol=spec["tol"], precision=form, rmax=spec["rmax"],
-                             tensor_cores=args.tensor_cores if form == "fp32" else 0)
+                             tensor_cores=args.tensor_cores if form == "fp32" else 0,
+                             sample_bf16=(spec["bf16"] if args.sample_bf16 is None else args.sample_bf16)
+                             if form == "fp32" else 0)
         Y = hssnd.hss_apply(F, torch.as_tensor(X, device="cuda")).cpu().numpy()
         Yo = oracle.apply(fac, X)
         x, st = hssnd.fgmres_solve(dA, F, torch.as_tensor(b, device="cuda"), rtol=RTOL, restart=RESTART)

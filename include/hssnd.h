@@ -115,6 +115,12 @@ typedef struct hss_factor_opts {
                                most 8) from stream 2 of the counter generator, a front with
                                ||(S - H) W||_F > 10 tol depth ||S W||_F (depth = depth of its HSS tree, at
                                least 1) samples again with r + dr while r + dr <= rmax.  Needs tol > 0. */
+    int sample_bf16;        /* FP32 form: 1 runs the sampling products Y = S Omega, Z = S^t Psi of every front
+                               whose S the TMA can address (front sizes divisible by 4, |B| >= 128) on
+                               tcgen05 kind::f16 with FP32 accumulation: S is split into three BF16 terms
+                               (x ~ t0 + t1 + t2, each the BF16 rounding of what the previous left, about
+                               FP32 accuracy) and the +-1 test matrix is exact in BF16.  0 (default): the
+                               sampling follows tensor_cores. */
 } hss_factor_opts;
 
 enum { HSS_CAP_KEEP = 0, HSS_CAP_ACCEPT = 1 };
@@ -204,6 +210,7 @@ typedef struct hss_factor_info {
     long gemm_tma;          /* ... on tcgen05 with TMA-fed operands */
     long gemm_staged;       /* ... on tcgen05 with thread-staged operands */
     long gemm_timed;        /* problems the GEMM engine tuner timed (tensor_cores = 3) */
+    long gemm_bf16;         /* sampling products run on the BF16 tensor-core kernel (sample_bf16) */
 } hss_factor_info;
 int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info);
 

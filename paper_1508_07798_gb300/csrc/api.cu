@@ -240,6 +240,7 @@ void hss_factor_opts_default(hss_factor_opts *o) {
     o->cap_policy = HSS_CAP_KEEP;
     o->autotune = 0;
     o->probe = 0;
+    o->sample_bf16 = 0;
 }
 
 void fgmres_opts_default(fgmres_opts *o) {

@@ -67,9 +67,10 @@ int assemble_stage(const hss_bsr *A, const hss_tree *t, const std::vector<FrontD
 // tensor cores.
 struct Engine {
     int tc = 0;          // tensor_cores option: 0 SIMT; 1 TF32 hi/lo split; 2 single TF32; 3 chosen by timing
+    int bf16 = 0;        // sample_bf16 option: sampling products on tcgen05 kind::f16, A in three BF16 terms
     int *err = nullptr;  // set by a tensor-core kernel whose bounded wait expired
-    mutable long problems[3] = {0, 0, 0};   // GEMM problems run on SIMT / TMA-fed / staged tensor cores
-    mutable long timed = 0;                 // problems the engine tuner timed
+    mutable long problems[4] = {0, 0, 0, 0};   // GEMM problems per engine (SIMT, TMA, staged, BF16 sampling)
+    mutable long timed = 0;                    // problems the engine tuner timed
 };
 
 // The fixed rule of tensor_cores = 1 / 2: long contractions only.  The
@@ -80,7 +81,7 @@ template <class T> bool use_tc(const Engine &e, const GemmDesc<T> &d) {
     return std::is_same<T, float>::value && e.tc != 0 && d.m >= 128 && d.n >= 32 && d.k >= 128;
 }
 
-enum { ENG_SIMT = 0, ENG_TMA = 1, ENG_STG = 2, NENG = 3 };
+enum { ENG_SIMT = 0, ENG_TMA = 1, ENG_STG = 2, ENG_BF16 = 3, NENG = 4 };
 
 // ---- GEMM engine autotuner (tensor_cores = 3): per shape class (operand
 // forms, TMA eligibility, sizes rounded up to powers of two) the first
@@ -151,6 +152,12 @@ static int time_engine(const Engine &E, const GemmDesc<float> &d, int eng, Work 
 template <class T> int choose_engine(const Engine &E, const GemmDesc<T> &d, Work &W, cudaStream_t s, int *out) {
     *out = ENG_SIMT;
     if constexpr (std::is_same<T, float>::value) {
+        // BF16 sampling: a precision choice of the FP32 form, for every sampling
+        // product of at least one 128-row tile whose S the TMA can address
+        if (E.bf16 && d.B == nullptr && d.m >= 128 && gemm_tma_eligible(d)) {
+            *out = ENG_BF16;
+            return HSS_OK;
+        }
         if (E.tc == 0) return HSS_OK;
         const bool tma = gemm_tma_eligible(d);
         if (E.tc == 1 || E.tc == 2) {
@@ -200,7 +207,7 @@ template <class T> struct GemmPlan {
     std::vector<int> off[NENG];
     std::vector<double> fl[NENG];
     TmaGemmDesc *d_tdescs = nullptr;
-    GemmTile *d_tl[NENG] = {nullptr, nullptr, nullptr};
+    GemmTile *d_tl[NENG] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // Engine of every problem, tiles per (group, engine), uploaded through W.
@@ -214,7 +221,7 @@ int plan_gemms(const Engine &E, const std::vector<GemmDesc<T>> &descs, const std
     int rc;
     for (size_t i = 0; i < nd; ++i) {
         if ((rc = choose_engine<T>(E, descs[i], W, s, &which[i]))) return rc;
-        use_tma[i] = which[i] == ENG_TMA;
+        use_tma[i] = which[i] == ENG_TMA || which[i] == ENG_BF16;
         E.problems[which[i]]++;
     }
     std::vector<std::vector<int>> of(ngroups);
@@ -238,7 +245,10 @@ int plan_gemms(const Engine &E, const std::vector<GemmDesc<T>> &descs, const std
         if (!P.tl[e].empty() && (rc = W.up(P.tl[e], &P.d_tl[e]))) return rc;
     }
     if constexpr (std::is_same<T, float>::value) {
-        if (!P.tl[ENG_TMA].empty() && (rc = gemm_tma_descs(descs, use_tma, W, &P.d_tdescs))) return rc;
+        // the tensor maps serve both TMA-fed kernels (TF32 split and BF16 sampling)
+        if ((!P.tl[ENG_TMA].empty() || !P.tl[ENG_BF16].empty()) &&
+            (rc = gemm_tma_descs(descs, use_tma, W, &P.d_tdescs)))
+            return rc;
     }
     return HSS_OK;
 }
@@ -256,8 +266,13 @@ int run_gemm_group(const Engine &E, const GemmPlan<T> &P, const GemmDesc<T> *d_d
         if (e == ENG_SIMT) {
             rc = gemm_batched<T>(d_descs, t, n, s, P.fl[e][g]);
         } else if constexpr (std::is_same<T, float>::value) {
-            rc = e == ENG_TMA ? gemm_tma(P.d_tdescs, t, n, E.err, s, P.fl[e][g], tma_class)
-                              : gemm_tc(d_descs, t, n, E.tc == 2 ? 0 : 1, E.err, s, P.fl[e][g]);
+            if ((e == ENG_TMA || e == ENG_BF16) && !P.d_tdescs) {
+                set_error("GEMM plan: tensor-core tiles without tensor maps");
+                return HSS_ECUDA;
+            }
+            if (e == ENG_TMA) rc = gemm_tma(P.d_tdescs, t, n, E.err, s, P.fl[e][g], tma_class);
+            else if (e == ENG_BF16) rc = gemm_tma(P.d_tdescs, t, n, E.err, s, P.fl[e][g], "gemm_bf16_sample", true);
+            else rc = gemm_tc(d_descs, t, n, E.tc == 2 ? 0 : 1, E.err, s, P.fl[e][g]);
         } else {
             rc = HSS_OK;
         }
@@ -938,6 +953,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     HSS_CUDA(cudaMemsetAsync(d_tcerr.p, 0, sizeof(int), s));
     Engine eng;
     eng.tc = std::is_same<T, float>::value ? o.tensor_cores : 0;
+    eng.bf16 = std::is_same<T, float>::value ? o.sample_bf16 : 0;
     eng.err = d_tcerr.as<int>();
     auto check_tc = [&]() -> int {
         int h = 0;
@@ -1081,6 +1097,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         F->gemm_tma = eng.problems[ENG_TMA];
         F->gemm_staged = eng.problems[ENG_STG];
         F->gemm_timed = eng.timed;
+        F->gemm_bf16 = eng.problems[ENG_BF16];
         for (int i = 0; i < ninst; ++i) {
             F->front_flops += 2.0 / 3.0 * (double)ntop_i[i] * ntop_i[i] * ntop_i[i];
             F->factor_bytes += sizeof(T) * (double)ntop_i[i] * ntop_i[i];
@@ -1192,6 +1209,7 @@ int front_compress_impl(const hss_tree *t, int box, const double *Sh, int lds, c
     hss_factor_t tmp;
     Engine eng;
     eng.tc = std::is_same<T, float>::value ? o.tensor_cores : 0;
+    eng.bf16 = std::is_same<T, float>::value ? o.sample_bf16 : 0;
     eng.err = tcerr;
     if ((rc = compress_stage<T>(t, o, fr, boxes, poff, pnv, keeph, arena, keep, nullptr, 0, logv, &tmp, eng, W, s)))
         return rc;
@@ -1230,8 +1248,8 @@ static int check_factor_opts(const hss_factor_opts &o, const char *who) {
         (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
         (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1) ||
         o.probe < 0 || o.probe > PROBE_MAX || (o.probe > 0 && !(o.tol > 0)) || o.tensor_cores < 0 ||
-        o.tensor_cores > 3) {
-        set_error(std::string(who) + ": options out of range (rmax <= 128, tensor_cores 0..3)");
+        o.tensor_cores > 3 || (o.sample_bf16 != 0 && o.sample_bf16 != 1)) {
+        set_error(std::string(who) + ": options out of range (rmax <= 128, tensor_cores 0..3, sample_bf16 0/1)");
         return HSS_EINVAL;
     }
     return HSS_OK;
@@ -1337,9 +1355,9 @@ extern "C" int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_fact
         o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 || (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
         (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1) ||
         o.probe < 0 || o.probe > PROBE_MAX || (o.probe > 0 && !(o.tol > 0)) || o.tensor_cores < 0 ||
-        o.tensor_cores > 3) {
+        o.tensor_cores > 3 || (o.sample_bf16 != 0 && o.sample_bf16 != 1)) {
         set_error("hss_factor: invalid argument (matrix/tree mismatch or options out of range; rmax <= 128, "
-                  "tensor_cores 0..3)");
+                  "tensor_cores 0..3, sample_bf16 0/1)");
         return HSS_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -1376,6 +1394,7 @@ extern "C" int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info)
     info->gemm_tma = f->gemm_tma;
     info->gemm_staged = f->gemm_staged;
     info->gemm_timed = f->gemm_timed;
+    info->gemm_bf16 = f->gemm_bf16;
     return HSS_OK;
 }
 

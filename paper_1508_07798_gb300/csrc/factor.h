@@ -102,6 +102,7 @@ struct hss_factor_t {
     int capped_fronts = 0;   // fronts that kept S because the sample width reached rmax
     int probe_regrown = 0;   // sampling rounds added by failed residual probes
     long gemm_simt = 0, gemm_tma = 0, gemm_staged = 0, gemm_timed = 0;   // GEMM problems per engine, tuner timings
+    long gemm_bf16 = 0;      // sampling products on the BF16 tensor-core kernel
     // captured apply sweeps (slot 0: one right-hand side, slot 1: blocks of APPLY_RB)
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_kernels[2] = {0, 0};

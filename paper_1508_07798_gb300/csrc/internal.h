@@ -214,8 +214,10 @@ int gemm_tma_prepare();
 struct Work;
 int gemm_tma_descs(const std::vector<GemmDesc<float>> &descs, const std::vector<char> &use, Work &W,
                    TmaGemmDesc **out);
+// bf16: the sampling variant (generated +-1 B only): A as three BF16 terms,
+// tcgen05 kind::f16 with FP32 accumulation
 int gemm_tma(const TmaGemmDesc *d_descs, const GemmTile *d_tiles, int ntiles, int *err, cudaStream_t s,
-             double flops, const char *prof_class = "gemm_tma");
+             double flops, const char *prof_class = "gemm_tma", bool bf16 = false);
 // C = alpha * 0 + beta * C (the product with k = 0) without descriptors.
 int gemm_f32_k0(float *C, int ldc, int m, int n, float alpha, float beta, cudaStream_t s);
 // Loads the module of the FP32 SIMT GEMM kernels.

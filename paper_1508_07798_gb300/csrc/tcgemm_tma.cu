@@ -154,6 +154,41 @@ __device__ __forceinline__ uint32_t idesc_tf32() {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
+// ---- BF16 sampling (kind::f16): A as three BF16 terms, the exact +-1 B in BF16.
+// Canonical K-major layout of a 16-K BF16 tile: core matrices of 8 rows x 16
+// bytes (8 values along K), 128 B apart along K, 8-row groups 256 B apart.
+constexpr uint32_t LBO16 = 128, SBO16 = 256;
+constexpr int OPB16 = TM * TK * 2;   // bytes of one BF16 tile of a chunk (4 KB)
+
+__device__ __forceinline__ uint32_t koff16(int row, int k) {
+    return (uint32_t)((row >> 3) * SBO16 + (k >> 3) * LBO16 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t kdesc16(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((LBO16 >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((SBO16 >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: D f32, A/B bf16, both K-major, M x N
+__device__ __forceinline__ uint32_t idesc_bf16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// round to nearest BF16 (bit pattern), and back
+__device__ __forceinline__ unsigned short to_bf16(float x) {
+    unsigned short r;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float from_bf16(unsigned short b) { return __uint_as_float((uint32_t)b << 16); }
+
 }  // namespace
 
 // One problem of the TMA engine: the tensor maps of its operands and its
@@ -207,8 +242,32 @@ __device__ __forceinline__ void convert_tile(const unsigned char *raw, int mode,
     }
 }
 
+// raw FP32 tile (layout `mode`) -> three BF16 terms x ~ t0 + t1 + t2 (each
+// the BF16 rounding of what the previous terms left), canonical K-major BF16
+// layout; each thread handles 8 consecutive K of one row
+__device__ __forceinline__ void convert_tile_bf16(const unsigned char *raw, int mode, unsigned char *t0,
+                                                  unsigned char *t1, unsigned char *t2) {
+    for (int q = threadIdx.x; q < TM * TK / 8; q += NT) {
+        const int row = q & (TM - 1), k8 = (q >> 7) * 8;
+        unsigned short h[8], m[8], l[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float x = *reinterpret_cast<const float *>(raw + raw_off(mode, row, k8 + u));
+            h[u] = to_bf16(x);
+            const float r1 = x - from_bf16(h[u]);
+            m[u] = to_bf16(r1);
+            l[u] = to_bf16(r1 - from_bf16(m[u]));
+        }
+        const uint32_t o = koff16(row, k8);
+        *reinterpret_cast<uint4 *>(t0 + o) = *reinterpret_cast<const uint4 *>(h);
+        *reinterpret_cast<uint4 *>(t1 + o) = *reinterpret_cast<const uint4 *>(m);
+        *reinterpret_cast<uint4 *>(t2 + o) = *reinterpret_cast<const uint4 *>(l);
+    }
+}
+
 }  // namespace
 
+template <bool BF16>
 __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restrict__ descs,
                                                   const GemmTile *__restrict__ tiles, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smraw[];
@@ -254,7 +313,7 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restric
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = idesc_tf32();
+    const uint32_t idesc = BF16 ? idesc_bf16() : idesc_tf32();
 
     bool failed = false;
     int issued = nk < 2 ? nk : 2;   // chunks whose copies were issued (thread 0's view)
@@ -273,6 +332,20 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restric
             kc_stop = kc;
             break;
         }
+        if constexpr (BF16) {   // A in three BF16 terms, the +-1 B in BF16 (the host routes only generated B here)
+            convert_tile_bf16(raw, amode, cb, cb + OPB16, cb + 2 * OPB16);
+            unsigned char *bt = cb + 3 * OPB16;
+            const int k0 = kc * TK;
+            for (int idx = tid; idx < TN * TK; idx += NT) {
+                const int kk = idx & (TK - 1), j = idx >> 4;
+                const int gj = col0 + j, gk = k0 + kk;
+                unsigned short v = 0;
+                if (gj < d.n && gk < d.k)
+                    v = rademacher(d.seed, d.stream, d.front, d.brow0 + gk, gj) > 0 ? (unsigned short)0x3F80
+                                                                                   : (unsigned short)0xBF80;
+                *reinterpret_cast<unsigned short *>(bt + koff16(j, kk)) = v;
+            }
+        } else {
         convert_tile(raw, amode, cb, cb + OPB);
         if (bmode == OP_GEN) {
             unsigned char *bt = cb + 2 * OPB;
@@ -287,6 +360,7 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restric
         } else {
             convert_tile(raw + OPB, bmode, cb + 2 * OPB, cb + 3 * OPB);
         }
+        }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();   // every thread is done with the raw slot and the buffer is written
@@ -296,6 +370,13 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restric
                 issue_chunk(td, amode, bmode, row0, col0, issued, raw, &full[q]);
                 ++issued;
             }
+            if constexpr (BF16) {   // one K = 16 MMA per term
+                const uint32_t a0 = smem_u32(cb), b0 = a0 + 3 * OPB16;
+                const uint64_t bd = kdesc16(b0);
+                mma_bf16(tmem, kdesc16(a0), bd, idesc, kc > 0 ? 1 : 0);
+                mma_bf16(tmem, kdesc16(a0 + OPB16), bd, idesc, 1);
+                mma_bf16(tmem, kdesc16(a0 + 2 * OPB16), bd, idesc, 1);
+            } else {
             const uint32_t aH = smem_u32(cb), aL = aH + OPB, bH = aH + 2 * OPB, bL = aH + 3 * OPB;
 #pragma unroll
             for (int ks = 0; ks < TK / 8; ++ks) {
@@ -303,6 +384,7 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restric
                 mma_tf32(tmem, kdesc(aH, ks), kdesc(bH, ks), idesc, acc0);
                 if (bmode != OP_GEN) mma_tf32(tmem, kdesc(aH, ks), kdesc(bL, ks), idesc, 1);
                 mma_tf32(tmem, kdesc(aL, ks), kdesc(bH, ks), idesc, 1);
+            }
             }
             mma_commit(&mdone[q]);
             ++committed;
@@ -419,7 +501,8 @@ bool gemm_tma_eligible(const GemmDesc<float> &d) {
 }
 
 int gemm_tma_prepare() {
-    HSS_SMEM(k_gemm_tma, SMEM);
+    HSS_SMEM(k_gemm_tma<false>, SMEM);
+    HSS_SMEM(k_gemm_tma<true>, SMEM);
     return HSS_OK;
 }
 
@@ -461,12 +544,15 @@ int gemm_tma_descs(const std::vector<GemmDesc<float>> &descs, const std::vector<
 }
 
 int gemm_tma(const TmaGemmDesc *d_descs, const GemmTile *d_tiles, int ntiles, int *err, cudaStream_t s,
-             double flops, const char *prof_class) {
+             double flops, const char *prof_class, bool bf16) {
     if (ntiles <= 0) return HSS_OK;
     int rc = gemm_tma_prepare();
     if (rc) return rc;
     HSS_PROF(prof_class, s, flops);
-    k_gemm_tma<<<ntiles, NT, SMEM, s>>>(d_descs, d_tiles, err);
+    if (bf16)
+        k_gemm_tma<true><<<ntiles, NT, SMEM, s>>>(d_descs, d_tiles, err);
+    else
+        k_gemm_tma<false><<<ntiles, NT, SMEM, s>>>(d_descs, d_tiles, err);
     HSS_CHECK_LAUNCH("k_gemm_tma");
     return HSS_OK;
 }

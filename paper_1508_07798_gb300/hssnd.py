@@ -60,7 +60,7 @@ class hss_factor_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("compress", C.c_int), ("r0", C.c_int), ("dr", C.c_int),
                 ("rmax", C.c_int), ("oversample", C.c_int), ("precision", C.c_int),
                 ("seed", C.c_uint64), ("keep_schur", C.c_int), ("tensor_cores", C.c_int), ("r_init", C.c_void_p),
-                ("cap_policy", C.c_int), ("autotune", C.c_int), ("probe", C.c_int)]
+                ("cap_policy", C.c_int), ("autotune", C.c_int), ("probe", C.c_int), ("sample_bf16", C.c_int)]
 
 
 class fgmres_opts(C.Structure):
@@ -80,7 +80,8 @@ class hss_factor_info(C.Structure):
     _fields_ = [("factor_bytes", C.c_double), ("front_flops", C.c_double), ("executed_flops", C.c_double),
                 ("max_rank", C.c_int), ("max_r", C.c_int), ("rounds", C.c_int), ("nfronts", C.c_int),
                 ("capped_fronts", C.c_int), ("probe_regrown", C.c_int), ("gemm_simt", C.c_long),
-                ("gemm_tma", C.c_long), ("gemm_staged", C.c_long), ("gemm_timed", C.c_long)]
+                ("gemm_tma", C.c_long), ("gemm_staged", C.c_long), ("gemm_timed", C.c_long),
+                ("gemm_bf16", C.c_long)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:

@@ -408,6 +408,43 @@ def test_gemm_engine_tuner_times_once_and_matches_simt():
     assert s1.converged and s0.converged and abs(s1.iters - s0.iters) <= 2
 
 
+def test_bf16_sampling_matches_fp32_sampling():
+    """sample_bf16 = 1: the sampling products of the 16-byte aligned fronts
+    (|B| >= 128) run on tcgen05 kind::f16 with S in three BF16 terms (about
+    FP32 accuracy; the +-1 matrix is exact in BF16).  Against the same FP32
+    form with SIMT sampling: the same widths, largest ranks within one,
+    approximants of the same quality against the oracle's (the compression of
+    the oracle's own S through hss_front_compress), and FGMRES alike."""
+    import torch
+    hs = _hss()
+    mesh, A = _setup("helm", (32, 32), 1)
+    dA = hs.DeviceBSR.from_host(A)
+    tree = hs.nd_order((2, (32, 32), 1), dA)
+    Fb = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", sample_bf16=1, keep_schur=1)
+    Fs = hs.hss_factor(dA, tree, tol=1e-4, precision="fp32", keep_schur=1)
+    ib = Fb.info()
+    assert ib["gemm_bf16"] > 0 and Fs.info()["gemm_bf16"] == 0
+    lb, ls = Fb.export_log(), Fs.export_log()
+    assert (np.abs(lb["kmax"] - ls["kmax"]) <= 1).all() and (lb["r"] == ls["r"]).mean() >= 0.99
+    nd = oracle.nd_order(2, mesh.n, 1, A.row_ptr, A.col_idx)
+    fac = oracle.factor(dg.bsr_to_csr(A), nd, tol=1e-4, seed=0, rmax=96, keep_h=True)
+    checked = 0
+    for b in range(int(nd["nbox"])):
+        if nd["nb"][b] < 128:
+            continue
+        S = fac["boxes"][b]["S"]
+        Hb = hs.front_compress(tree, b, S, tol=1e-4, seed=0, rmax=96, precision="fp32", sample_bf16=1)[0]
+        Hs_ = hs.front_compress(tree, b, S, tol=1e-4, seed=0, rmax=96, precision="fp32")[0]
+        eb, es = _rel(Hb, fac["boxes"][b]["H"]), _rel(Hs_, fac["boxes"][b]["H"])
+        assert eb <= 10.0 * es + 1e-5, (b, eb, es)
+        checked += 1
+    assert checked > 0
+    bvec = torch.as_tensor(dg.point_source_rhs(mesh, 0)[:, 0], device="cuda")
+    _, sb = hs.fgmres_solve(dA, Fb, bvec, rtol=1e-8)
+    _, ss = hs.fgmres_solve(dA, Fs, bvec, rtol=1e-8)
+    assert sb.converged and ss.converged and abs(sb.iters - ss.iters) <= 2
+
+
 def test_autotuned_apply_matches_oracle_and_is_cached():
     """The tuned work split (columns per apply work item, per stage and
     direction) changes only the summation order: the apply still matches the
