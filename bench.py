@@ -50,12 +50,13 @@ def parse():
                     help="fp32_learned: FP32 factor with learned sample widths (headline); fp32: FP32 "
                          "factor, adaptive widths; fp64: plain FP64 factor")
     ap.add_argument("--workload", default="helmholtz64",
-                    choices=["helmholtz64", "batched256", "helmholtz256", "diffusion32"],
+                    choices=["helmholtz64", "batched256", "helmholtz256", "diffusion32", "gemm_update"],
                     help="helmholtz64: the timed workload (default); batched256: 256 independent "
                          "instances x 32 right-hand sides through the batched form; helmholtz256: "
                          "Helmholtz p=3 on 256x256 quads (1,048,576 dofs), learned widths; diffusion32: "
                          "3D diffusion p=1 on 32^3 hexes (262,144 dofs), 20 right-hand sides, learned "
-                         "widths (each its own JSON line)")
+                         "widths; gemm_update: the blocked sweep's update C += A B alone, m = n = 8192, "
+                         "K = 256, FP32 (each its own JSON line)")
     ap.add_argument("--no-fp64", action="store_true",
                     help="large workloads: skip the plain FP64 comparison form")
     ap.add_argument("--tensor-cores", type=int, default=3, choices=[0, 1, 3],
@@ -423,9 +424,12 @@ def bench_ours(args, rank, world):
         tree = hssnd.nd_order(meshdesc, dA2, leaf_max=64)
         if head == "fp32_learned":
             r0 = model.predict(hssnd.rank_features(tree, c_elem, kappa_h))[1]
-            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1, probe=args.probe)
+            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision="fp32", r_init=r0, autotune=1, probe=args.probe,
+                                 tensor_cores=args.tensor_cores, sample_bf16=args.sample_bf16 or 0)
         else:
-            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision=head, autotune=1)
+            F = hssnd.hss_factor(dA2, tree, tol=TOL, precision=head, autotune=1,
+                                 tensor_cores=args.tensor_cores if head == "fp32" else 0,
+                                 sample_bf16=(args.sample_bf16 or 0) if head == "fp32" else 0)
         x, st = hssnd.fgmres_solve(dA2, F, d_b, rtol=RTOL, restart=RESTART)
         xh.copy_(x, non_blocking=True)
         e1.record(stream)
@@ -456,7 +460,8 @@ def bench_ours(args, rank, world):
                config=dict(workload=WORKLOAD, dofs=A.n, p=P_DEG, mesh=f"{N_ELEM}x{N_ELEM}", id_tol=TOL,
                            rtol=RTOL, restart=RESTART, leaf_max=64, headline_form=head,
                            learned_widths=learned_info if model is not None else None,
-                           learned_probe_vectors=args.probe,
+                           learned_probe_vectors=args.probe, tensor_cores=args.tensor_cores,
+                           sample_bf16=args.sample_bf16 or 0,
                            l2="flushed by a 256 MB write before every timed step",
                            apply_autotune="per-level work split timed on the first factorization of the "
                                           "structure (a warm-up step), cached for the process",
@@ -649,6 +654,51 @@ def bench_large(args, rank, world):
                 forms=out, roofline=roof, clocks=clocks, gpu_launches=int(launches), kernels=kernels,
                 tuner=hssnd.gemm_tuner_choices() if args.tensor_cores == 3 else None,
                 e2e=dict(value=e2e_v, unit="ms", h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(bh.numel() * 8)))
+
+
+def bench_gemm_update(args, rank, world):
+    """The GEMM of the blocked Gauss-Jordan sweep's block updates, alone:
+    C += A B in FP32 with m = n = 8192 (C is 256 MB, beyond L2), K = 256
+    (eight 32-column panels), through hss_gemm_f32 on the SIMT engine and on
+    the TMA-fed tcgen05 engine (TF32 hi/lo split).  Per engine: kernel time by
+    CUDA events (library instrumentation), TFLOP/s and the C stream's GB/s
+    (read + write, 8 bytes per output: the HBM bound of this shape)."""
+    import torch
+    from paper_1508_07798_gb300 import hssnd
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    m = n = 8192
+    k = 256
+    g = torch.Generator(device="cpu").manual_seed(rank)
+    A = torch.randn(n, k, generator=g).to(dev)   # row-major n x k: the column-major k x n operand B^t
+    B = torch.randn(k, m, generator=g).to(dev)
+    C = torch.randn(n, m, generator=g).to(dev)
+    pk = with_simt_peak(peaks(), device_sms(dev))
+    out = {}
+    for name, eng in (("simt", 0), ("tma_tf32_split", 3)):
+        for _ in range(args.warmup):
+            hssnd.gemm_f32(A, B, C, alpha=1.0, beta=1.0, engine=eng)
+        hssnd.profile_reset()
+        hssnd.profile_enable(True)
+        for _ in range(args.steps):
+            hssnd.gemm_f32(A, B, C, alpha=1.0, beta=1.0, engine=eng)
+        hssnd.profile_enable(False)
+        pr = hssnd.profile_read()
+        ms = sum(v[0] for kk, v in pr.items() if kk.startswith("gemm")) / args.steps
+        fl = 2.0 * m * n * k
+        gbs = 8.0 * m * n / (ms * 1e-3) / 1e9
+        out[name] = dict(ms=ms, tflops=fl / (ms * 1e-3) / 1e12, c_stream_gbs=gbs, hbm_frac=gbs / pk["hbm"])
+    head = out["tma_tf32_split"]
+    roof = dict(kernel="gemm_tma", bound="hbm", achieved=head["c_stream_gbs"], peak=pk["hbm"], unit="GB/s",
+                frac=head["hbm_frac"], traffic=None, tflops=head["tflops"],
+                tf32_peak_tflops=pk["bf16"] * TF32_PER_BF16,
+                note="C += A B with K = 256: 64 flop per byte of the C stream, below the TF32 ridge: HBM bounds it")
+    return dict(metric="GEMM of the block update, TFLOP/s (FP32 via TF32 split)", value=head["tflops"],
+                unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=head["ms"],
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32 (tf32 hi/lo split)",
+                data="synthetic", config=dict(workload="gemm_update_8192x8192_k256", m=m, n=n, k=k, beta=1.0,
+                                              l2="C (256 MB) exceeds L2"),
+                engines=out, roofline=roof, gpu_launches=1)
 
 
 def cpu_baseline_large(args, res):
@@ -906,6 +956,10 @@ def main():
         dist.init_process_group("nccl")
     import __graft_entry__
     __graft_entry__.build()
+    if args.workload == "gemm_update":
+        if rank == 0:
+            print(json.dumps(bench_gemm_update(args, rank, world)))
+        return
     if args.workload in LARGE:
         res = bench_large(args, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
