@@ -159,7 +159,9 @@ def profiled_traffic(kernel):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
     when there is none or the kernel's source changed since the capture."""
     import hashlib
-    files = {"gemm_f32": ("profiles/k_gemm_f32_dram_helmholtz64_p2.md", "paper_1508_07798_gb300/csrc/gemm.cu")}
+    files = {"gemm_f32": ("profiles/k_gemm_f32_dram_helmholtz64_p2.md", "paper_1508_07798_gb300/csrc/gemm.cu"),
+             "gemm_tma": ("profiles/k_gemm_tma_gemm_update_8192x8192_k256.md",
+                          "paper_1508_07798_gb300/csrc/tcgemm_tma.cu")}
     if kernel not in files:
         return None
     summary, src = (os.path.join(ROOT, f) for f in files[kernel])
@@ -690,7 +692,7 @@ def bench_gemm_update(args, rank, world):
         out[name] = dict(ms=ms, tflops=fl / (ms * 1e-3) / 1e12, c_stream_gbs=gbs, hbm_frac=gbs / pk["hbm"])
     head = out["tma_tf32_split"]
     roof = dict(kernel="gemm_tma", bound="hbm", achieved=head["c_stream_gbs"], peak=pk["hbm"], unit="GB/s",
-                frac=head["hbm_frac"], traffic=None, tflops=head["tflops"],
+                frac=head["hbm_frac"], traffic=profiled_traffic("gemm_tma"), tflops=head["tflops"],
                 tf32_peak_tflops=pk["bf16"] * TF32_PER_BF16,
                 note="C += A B with K = 256: 64 flop per byte of the C stream, below the TF32 ridge: HBM bounds it")
     return dict(metric="GEMM of the block update, TFLOP/s (FP32 via TF32 split)", value=head["tflops"],

@@ -94,9 +94,10 @@ typedef struct hss_factor_opts {
                                brought in by TMA where they are 16-byte aligned with leading dimensions
                                that are multiples of 4 (front sizes divisible by 4), staged by the threads
                                otherwise; 2 tcgen05 with a single TF32 product (threads staging); 3 per
-                               shape class (operand forms, TMA eligibility, m, n, k rounded up to powers of
-                               two) the faster of SIMT and the tcgen05 split kernel, timed on a scratch C
-                               the first time the class appears and cached for the process */
+                               shape class (operand forms, m, n, k rounded up to powers of two) of the
+                               problems the TMA-fed kernel can take: SIMT or that kernel, timed on a scratch
+                               C the first time the class appears (the tensor cores need a 15% lead) and
+                               cached for the process; other problems on SIMT */
     const int *r_init;      /* HOST array of one initial sample width per box (NULL, the default: r0 for
                                every front), e.g. from hss_rank_model_predict; the adaptive growth by dr
                                still applies whenever a rank exceeds r - oversample */
@@ -482,7 +483,7 @@ long hss_alloc_count(void);
  * idx < 0 the number of shape classes timed so far; otherwise class idx (in
  * the order they were timed): its key (bits 0-11 log2 k, 12-23 log2 n, 24-35
  * log2 m, rounded up; bit 38 generated B, 39 transposed A; bits 40-47 the
- * tensor-core kernel timed, 1 TMA-fed, 2 thread-staged; bits 48+ device),
+ * tensor-core kernel timed, 1 = TMA-fed; bits 48+ device),
  * the engine kept (0 SIMT, else the tensor-core kernel) and both times (ms,
  * one problem alone on a scratch C).  Returns HSS_OK or -HSS_EINVAL. */
 int hss_gemm_tuner_read(int idx, long long *key, int *engine, float *ms_simt, float *ms_tc);

@@ -38,7 +38,7 @@ namespace hssnd {
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = 16;   // output tile, K per chunk
-constexpr int NT = 128;
+constexpr int NT = 256;                      // 8 warps: two per TMEM lane quarter
 constexpr int OPB = TM * TK * 4;             // bytes of one operand tile of a chunk (8 KB)
 constexpr int RAW_BYTES = 2 * OPB;           // raw A, raw B of one ring slot
 constexpr int CONV_BYTES = 4 * OPB;          // A hi, A lo, B hi, B lo of one buffer
@@ -304,10 +304,14 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restric
     }
     // the epilogue reads C: start bringing this tile's C into L2 now (thread t:
     // column col0 + t, the rows of the tile that exist, in 128-byte lines)
-    if (d.beta != 0.f && col0 + tid < d.n && !(col0 + tid >= d.skip_lo && col0 + tid < d.skip_hi)) {
-        const float *cc = d.C + row0 + (long)(col0 + tid) * d.ldc;
-        const int rows = min(TM, d.m - row0);
-        for (int r = 0; r < rows; r += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(cc + r));
+    {
+        const int pc = col0 + (tid & (TN - 1)), half = tid >> 7;   // column, half of the tile's rows
+        if (d.beta != 0.f && pc < d.n && !(pc >= d.skip_lo && pc < d.skip_hi)) {
+            const float *cc = d.C + row0 + (long)pc * d.ldc;
+            const int rows = min(TM, d.m - row0);
+            for (int r = half * (TM / 2); r < min(rows, (half + 1) * (TM / 2)); r += 32)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(cc + r));
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -413,15 +417,17 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restric
             }
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows), 64 columns at a
-        // time; the 64 C values of a row are loaded together before any store
-        // (a store could alias a later load, so loads interleaved with stores
-        // would run one round trip at a time)
-        const int gi = row0 + warp * 32 + lane;
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its lane quarter:
+        // rows) and the columns of half w / 4, 32 at a time; the 32 C values of
+        // a row are loaded together before any store (a store could alias a
+        // later load, so loads interleaved with stores would run one round trip
+        // at a time)
+        const int quarter = warp & 3, chalf = warp >> 2;
+        const int gi = row0 + quarter * 32 + lane;
         const bool rowok = gi < d.m;
         const float beta_row = (gi >= d.zr_lo && gi < d.zr_hi) ? 0.f : d.beta;
-        constexpr int EC = 64;
-        for (int c0 = 0; c0 < TN; c0 += EC) {
+        constexpr int EC = 16;
+        for (int c0 = chalf * (TN / 2); c0 < (chalf + 1) * (TN / 2); c0 += EC) {
             float v[EC], cv[EC];
 #pragma unroll
             for (int u = 0; u < EC; ++u) {
@@ -431,7 +437,8 @@ __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restric
             }
             if (nk > 0) {
 #pragma unroll
-                for (int q = 0; q < EC; q += 16) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + q), v + q);
+                for (int q = 0; q < EC; q += 16)
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c0 + q), v + q);
             } else {
 #pragma unroll
                 for (int u = 0; u < EC; ++u) v[u] = 0.f;
