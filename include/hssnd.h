@@ -122,6 +122,16 @@ typedef struct hss_factor_opts {
                                (x ~ t0 + t1 + t2, each the BF16 rounding of what the previous left, about
                                FP32 accuracy) and the +-1 test matrix is exact in BF16.  0 (default): the
                                sampling follows tensor_cores. */
+    int merge;              /* 0 (default): the interior block of every front factored densely (reading R1).
+                               1: the structured merge of Algorithm 1 (eq. (37)) and Algorithm 3: in a parent
+                               front the first child's interior pivots are eliminated first, the second
+                               Schur complement S~ = S2 - A21 S1^-1 A12 left in the trailing interior block
+                               is replaced by its HSS approximant (Theorem 1, tree: the second child's
+                               subtree restricted to those dofs, test-matrix key nbox + box; for the top
+                               block the second level-1 box's tree, key 2 nbox), then the rest; the front is
+                               thus factored with A_ii + blockdiag(0, H~ - S~) in place of A_ii, whose inverse
+                               is eq. (37)'s block solve.  Dense fronts throughout (the approximation of R2,
+                               not its complexity).  Needs probe = 0 and a single instance. */
 } hss_factor_opts;
 
 enum { HSS_CAP_KEEP = 0, HSS_CAP_ACCEPT = 1 };

@@ -241,6 +241,7 @@ void hss_factor_opts_default(hss_factor_opts *o) {
     o->autotune = 0;
     o->probe = 0;
     o->sample_bf16 = 0;
+    o->merge = 0;
 }
 
 void fgmres_opts_default(fgmres_opts *o) {

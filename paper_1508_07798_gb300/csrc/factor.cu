@@ -293,12 +293,17 @@ template <class T> int choose_kb(int ni) {
 // Blocked Gauss-Jordan sweep over the I pivots of every front of a stage.
 // Per panel step: the panel kernels (register-resident where the panel fits,
 // shared/global memory otherwise), the post-panel tiles, the trailing GEMM.
+// pbeg/pend (HOST, per front, may be null): eliminate only the I columns
+// [pbeg, pend), with pivots searched among the rows below pend -- one phase of
+// an elimination split into phases (the structured merge; a phased sweep
+// updates every column per panel, no blocking).
 template <class T>
 int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *arena, int *piv, int *rperm,
                     const int *ilist, int *iperm, int *status, double &exec_flops, const Engine &eng, Work &W,
-                    cudaStream_t s) {
+                    cudaStream_t s, const int *pbeg = nullptr, const int *pend = nullptr) {
     int nf = (int)fr.size();
-    std::vector<int> kb(nf), nsteps(nf), isreg(nf), Rf(nf), clpath(nf, 0);
+    const bool phased = pbeg != nullptr;
+    std::vector<int> kb(nf), nsteps(nf), isreg(nf), Rf(nf), clpath(nf, 0), beg(nf), end(nf);
     std::vector<long> aoff(nf);
     long aold_total = 0;
     int maxsteps = 0;
@@ -318,11 +323,13 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             clpath[f] = 1;
         }
         Rf[f] = cdiv(std::max(fr[f].ni, 1), PANEL_NT);
-        nsteps[f] = fr[f].ni > 0 ? cdiv(fr[f].ni, kb[f]) : 0;
+        beg[f] = phased ? pbeg[f] : 0;
+        end[f] = phased ? pend[f] : fr[f].ni;
+        nsteps[f] = end[f] > beg[f] ? cdiv(end[f] - beg[f], kb[f]) : 0;
         aoff[f] = aold_total;
         aold_total += (long)kb[f] * fr[f].n;
         maxsteps = std::max(maxsteps, nsteps[f]);
-        exec_flops += 2.0 * fr[f].n * (double)fr[f].n * fr[f].ni;
+        exec_flops += 2.0 * fr[f].n * (double)fr[f].n * std::max(0, end[f] - beg[f]);
     }
     if (maxsteps == 0) return HSS_OK;
     struct Group {
@@ -372,15 +379,16 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             if (st < nsteps[f]) act.push_back(f);
         // panel kind of this step: register (isreg, or a cluster-path front whose
         // rows now fit one CTA), cluster, memory
+        auto hT_at = [&](int f) { return fr[f].ni - (beg[f] + st * kb[f]); };
         auto kind = [&](int f) {
             if (isreg[f]) return 1;
             if (!clpath[f]) return 0;
-            return panel_reg_fits(kb[f], fr[f].ni - st * kb[f], (int)sizeof(T)) ? 1 : 2;
+            return panel_reg_fits(kb[f], hT_at(f), (int)sizeof(T)) ? 1 : 2;
         };
         // register panels grouped by (kb, rows of this step's variant), then the
         // memory panels; the variant follows the rows left at this step
         auto step_rows = [&](int f) {
-            const int hTs = fr[f].ni - st * kb[f];
+            const int hTs = hT_at(f);
             if (hTs <= PANEL_SMALL_NT) return PANEL_SMALL_NT;
             if (hTs <= 2 * PANEL_SMALL_NT) return 2 * PANEL_SMALL_NT;
             return cdiv(hTs, PANEL_NT) * PANEL_NT;
@@ -388,7 +396,7 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         auto group_rows = [&](int f) {
             const int k = kind(f);
             if (k == 1) return step_rows(f);
-            if (k == 2) return panel_cl_capacity(fr[f].ni - st * kb[f], (int)sizeof(T));
+            if (k == 2) return panel_cl_capacity(hT_at(f), (int)sizeof(T));
             return Rf[f] * PANEL_NT;
         };
         std::stable_sort(act.begin(), act.end(), [&](int a, int b) {
@@ -398,11 +406,11 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         });
         for (int f : act) {
             const int n = fr[f].n;
-            int k0 = st * kb[f];
-            int kbs = std::min(kb[f], fr[f].ni - k0);
-            // fronts below PANEL_BLOCK_MIN_N: one block spanning every column
-            // (the plain per-panel update)
-            const bool blocked = n >= PANEL_BLOCK_MIN_N;
+            int k0 = beg[f] + st * kb[f];
+            int kbs = std::min(kb[f], end[f] - k0);
+            // fronts below PANEL_BLOCK_MIN_N (and phased sweeps): one block
+            // spanning every column (the plain per-panel update)
+            const bool blocked = n >= PANEL_BLOCK_MIN_N && !phased;
             const int K0 = blocked ? (st / PANEL_BLOCK) * PANEL_BLOCK * kb[f] : 0;
             const int bw = blocked ? std::min(PANEL_BLOCK * kb[f], fr[f].ni - K0) : n;
             size_t hT = (size_t)(fr[f].ni - k0);
@@ -425,7 +433,7 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
             gs.back().flops += 2.0 * (double)hT * kbs * kbs;
             gs.back().smem = std::max(gs.back().smem, need);
             int jid = (int)jobs.size();
-            jobs.push_back({f, k0, kbs, use_smem, aoff[f], xtotal, mtotal});
+            jobs.push_back({f, k0, kbs, end[f], use_smem, aoff[f], xtotal, mtotal});
             jobs_of[f].push_back(jid);
             xtotal += (long)kbs * kbs;
             mtotal += 1 + 4 * PANEL_KB_MAX;
@@ -538,23 +546,37 @@ struct RoundFront {     // a front of the current sampling round
     int r;
 };
 
+// Blocks compressed that are not a box's Schur complement (the structured
+// merge's second Schur complement S~ of a parent's interior block, Algorithm 1
+// step 2.2): per front its HSS nodes, its test-matrix counter key and the map
+// of its rows to positions in the target front (DEVICE); these take r0 as
+// their first width and no residual probe, and leave no log record.
+struct CompressOverride {
+    std::vector<const std::vector<HssNode> *> nodes;
+    std::vector<int> key;
+    std::vector<const int *> fmap;
+};
+
 // Randomized HSS compression of the stage's Schur complements, written into
 // the parent fronts.  Fronts whose HSS tree is a single node (or with
-// compression off) copy S unchanged.
+// compression off) copy S unchanged.  With `ov`, the blocks of `ov` instead.
 template <class T>
 int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vector<FrontDev> &fr,
                    const std::vector<int> &boxes, const std::vector<long> &poff, const std::vector<int> &pn,
                    const std::vector<long> &keep_h, T *arena, T *keep, int *status_dev, int nstatus,
-                   std::vector<FrontLog> &logv, hss_factor_t *F, const Engine &eng, Work &W, cudaStream_t s) {
+                   std::vector<FrontLog> &logv, hss_factor_t *F, const Engine &eng, Work &W, cudaStream_t s,
+                   const CompressOverride *ov = nullptr) {
     int nf = (int)fr.size();
     int rc;
+    auto nodes_of = [&](int f) -> const std::vector<HssNode> & { return ov ? *ov->nodes[f] : t->hss[boxes[f]]; };
+    auto key_of = [&](int f) { return ov ? ov->key[f] : t->box_local[boxes[f]]; };
     std::vector<ExpandFront> ef(nf);
     for (int f = 0; f < nf; ++f) {
         const FrontDev &d = fr[f];
         ef[f].S = arena + d.foff + d.ni + (long)d.n * d.ni;
         ef[f].lds = d.n;
         ef[f].nb = d.nb;
-        ef[f].fmap = t->d_fmap.as<int>() + t->boff[boxes[f]];
+        ef[f].fmap = ov ? ov->fmap[f] : t->d_fmap.as<int>() + t->boff[boxes[f]];
         ef[f].poff = poff[f];
         ef[f].pn = pn[f];
         ef[f].keep_h = keep_h[f];
@@ -569,9 +591,9 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
     for (int f = 0; f < nf; ++f) {
         int b = boxes[f];
         if (fr[f].nb == 0) continue;
-        bool comp = o.compress && t->hss[b].size() > 1;
+        bool comp = o.compress && nodes_of(f).size() > 1;
         if (comp) {
-            const int r_first = o.r_init ? std::max(1, std::min(o.r_init[b], o.rmax)) : std::min(o.r0, o.rmax);
+            const int r_first = (o.r_init && !ov) ? std::max(1, std::min(o.r_init[b], o.rmax)) : std::min(o.r0, o.rmax);
             active.push_back({f, r_first});
         } else {
             for (int r0 = 0; r0 < fr[f].nb; r0 += EXP_TILE)
@@ -601,12 +623,12 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             cfs[c].lds = d.n;
             cfs[c].nb = d.nb;
             cfs[c].r = r;
-            cfs[c].box = t->box_local[boxes[active[c].f]];
+            cfs[c].box = key_of(active[c].f);
             cfs[c].yoff = wsz;
             wsz += (long)d.nb * r;
             cfs[c].zoff = wsz;
             wsz += (long)d.nb * r;
-            const auto &hn = t->hss[boxes[active[c].f]];
+            const auto &hn = nodes_of(active[c].f);
             node_base[c] = (int)nodes.size();
             int root = (int)hn.size() - 1;
             for (int i = 0; i < (int)hn.size(); ++i) {
@@ -711,7 +733,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         int maxd = 0;
         std::vector<int> ndepth(nn, 0);
         for (int c = 0; c < nc; ++c) {
-            const auto &hn = t->hss[boxes[active[c].f]];
+            const auto &hn = nodes_of(active[c].f);
             for (int i = 0; i < (int)hn.size(); ++i) {
                 ndepth[node_base[c] + i] = hn[i].depth;
                 maxd = std::max(maxd, hn[i].depth);
@@ -812,7 +834,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         }
         // ---- residual probe of the approximants accepted in this sampling round: a front
         // with ||(S - H) W|| > 10 tol depth ||S W|| samples again with r + dr
-        if (o.probe > 0) {
+        if (o.probe > 0 && !ov) {
             std::vector<ProbeItem> pit;
             std::vector<ProbeFront> pfr;
             std::vector<int> pc;   // round-front index of each probed front
@@ -856,6 +878,11 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
         active.swap(next);
     }
     for (int f = 0; f < nf; ++f) {
+        if (ov) {   // blocks of the structured merge: no log record, the widths and ranks still counted
+            F->max_rank = std::max(F->max_rank, kmax[f]);
+            F->max_r = std::max(F->max_r, rfin[f]);
+            continue;
+        }
         int b = boxes[f];
         FrontLog lg{b, t->level[b], fr[f].ni, fr[f].nb, rfin[f], rounds[f], kmax[f], (int)t->hss[b].size()};
         logv.push_back(lg);
@@ -883,6 +910,77 @@ static void build_apply_stage(ApplyStage &as, const std::vector<FrontDev> &fr, b
         as.fwd_vec += fr[f].ni + fr[f].ni + 2.0 * fr[f].nb;      // x_I read, t written, x_B read+written
         as.bwd_vec += fr[f].nb + fr[f].ni + fr[f].ni;           // x_B read, t read, x_I written
     }
+}
+
+// The structured merge (reading R2: eq. (37), Algorithm 1 step 2, Algorithm 3)
+// on dense fronts.  The interior of a parent front is [B^mu n I ; B^nu n I]
+// (n1 rows from the first child).  Phase 1 eliminates the first n1 pivots with
+// pivots searched among those rows only, which leaves the second Schur
+// complement S~ = S2 - A21 S1^-1 A12 in the trailing interior block; S~ is
+// replaced there by its HSS approximant H~ (Theorem 1, its own tree and test
+// matrices); phase 2 eliminates the remaining pivots.  The result is the
+// Gauss-Jordan factorization of the front with A_ii + blockdiag(0, H~ - S~) in
+// place of A_ii, whose inverse is eq. (37)'s block solve, so W, S and the
+// stored blocks the apply uses are those of R2.
+template <class T>
+int eliminate_structured(const hss_tree *t, const hss_factor_opts &o, const std::vector<FrontDev> &fr,
+                         const FrontDev *d_fr, const std::vector<int> &n1, const std::vector<std::vector<int>> &dofs2,
+                         const std::vector<int> &tree_box, const std::vector<int> &key,
+                         const std::vector<int> &hss_of_box, T *arena, int *piv, int *rperm, const int *ilist,
+                         int *iperm, int *status, double &exec_flops, hss_factor_t *F, const Engine &eng, Work &W,
+                         cudaStream_t s) {
+    const int nf = (int)fr.size();
+    std::vector<int> zero(nf, 0), ni(nf);
+    for (int f = 0; f < nf; ++f) ni[f] = fr[f].ni;
+    int rc;
+    if ((rc = eliminate_stage<T>(fr, d_fr, arena, piv, rperm, ilist, iperm, status, exec_flops, eng, W, s, zero.data(),
+                                 n1.data())))
+        return rc;
+    // S~ blocks: one pseudo-front per front with a trailing interior block
+    std::vector<FrontDev> sv;
+    std::vector<int> svbox;
+    std::vector<long> poff, keeph;
+    std::vector<int> pn;
+    CompressOverride ov;
+    std::vector<std::vector<HssNode>> nodes_store(nf);
+    std::vector<int> fmap_all;
+    std::vector<long> fmap_off;
+    const std::vector<int> elem_pos = elem_positions(t);
+    for (int f = 0; f < nf; ++f) {
+        const int m2 = fr[f].ni - n1[f];
+        if (m2 <= 0) continue;
+        FrontDev d{};
+        d.foff = fr[f].foff + n1[f] + (long)fr[f].n * n1[f];
+        d.n = fr[f].n;   // leading dimension
+        d.ni = 0;
+        d.nb = m2;
+        d.box = fr[f].box;
+        sv.push_back(d);
+        svbox.push_back(fr[f].box >= 0 ? fr[f].box : 0);
+        poff.push_back(fr[f].foff);
+        pn.push_back(fr[f].n);
+        keeph.push_back(-1);
+        if (hss_of_box[f] >= 0) {
+            ov.nodes.push_back(&t->hss[hss_of_box[f]]);
+        } else {
+            hss_nodes_over(t, elem_pos, tree_box[f], dofs2[f], nodes_store[f]);
+            ov.nodes.push_back(&nodes_store[f]);
+        }
+        ov.key.push_back(key[f]);
+        fmap_off.push_back((long)fmap_all.size());
+        for (int i = 0; i < m2; ++i) fmap_all.push_back(n1[f] + i);   // in place: H~ over S~
+    }
+    if (!sv.empty()) {
+        int *d_fmap;
+        if ((rc = W.up(fmap_all, &d_fmap))) return rc;
+        for (long off : fmap_off) ov.fmap.push_back(d_fmap + off);
+        std::vector<FrontLog> nolog;
+        if ((rc = compress_stage<T>(t, o, sv, svbox, poff, pn, keeph, arena, (T *)nullptr, nullptr, 0, nolog, F, eng,
+                                    W, s, &ov)))
+            return rc;
+    }
+    return eliminate_stage<T>(fr, d_fr, arena, piv, rperm, ilist, iperm, status, exec_flops, eng, W, s, n1.data(),
+                              ni.data());
 }
 
 template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hss_factor_opts &o, cudaStream_t s,
@@ -915,6 +1013,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     HSS_CUDA(cudaMemsetAsync(F->arena.p, 0, sizeof(T) * total, s));
     T *arena = F->arena_ptr<T>();
     const int ilen = t->ioff[nbox];
+    const bool structured = o.merge == 1 && o.compress;
     Work WL(s);   // scratch for the whole call (never reset)
     ScratchPtr d_piv, d_scratch, d_slot, d_tcerr;
     if ((rc = upload(F->d_topset, topset, s)) || (rc = F->d_iperm.alloc(sizeof(int) * (ilen + ntop + 1))) ||
@@ -1027,9 +1126,36 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         d_fr.p = d_frp;
         if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
             return rc;
-        if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
-                                     t->d_iset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, eng, W, s)))
+        const bool leaves = std::all_of(boxes.begin(), boxes.end(), [&](int b) { return t->child0[b] < 0; });
+        if (structured && !leaves) {
+            // Algorithm 1 on every parent front of the stage; a leaf in the same
+            // stage eliminates all its pivots in the first phase (n1 = ni)
+            std::vector<int> n1(fr.size()), tb(fr.size()), key(fr.size()), nohss(fr.size(), -1);
+            std::vector<std::vector<int>> d2(fr.size());
+            for (size_t f = 0; f < fr.size(); ++f) {
+                const int b = boxes[f], mu = t->child0[b], nu = t->child1[b];
+                tb[f] = b;
+                key[f] = t->nbox + b;
+                if (mu < 0) {
+                    n1[f] = t->ni[b];
+                    continue;
+                }
+                int cnt = 0;
+                for (int i = t->boff[mu]; i < t->boff[mu + 1]; ++i) cnt += t->fmap[i] < t->ni[b];
+                n1[f] = cnt;
+                tb[f] = nu;
+                key[f] = t->nbox + b;
+                d2[f].assign(t->iset.begin() + t->ioff[b] + cnt, t->iset.begin() + t->ioff[b + 1]);
+            }
+            if ((rc = eliminate_structured<T>(t, o, fr, d_fr.as<FrontDev>(), n1, d2, tb, key, nohss, arena,
+                                              d_piv.as<int>(), d_scratch.as<int>(), t->d_iset.as<int>(),
+                                              F->d_iperm.as<int>(), d_status, F->exec_flops, F, eng, W, s)))
+                return rc;
+        } else if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
+                                            t->d_iset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, eng,
+                                            W, s))) {
             return rc;
+        }
         if (o.keep_schur)
             for (size_t f = 0; f < fr.size(); ++f) {
                 const FrontDev &d = fr[f];
@@ -1074,9 +1200,26 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         d_fr.p = d_frp;
         if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
             return rc;
-        if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
-                                     F->d_topset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops, eng, W, s)))
+        if (structured) {
+            // Algorithm 3: S^1 = H^1 eliminated first, S~2 = H^2 - A21 (H^1)^-1 A12
+            // compressed over the tree of the second level-1 box
+            std::vector<int> n1(ninst), tb(ninst), key(ninst), hb(ninst);
+            std::vector<std::vector<int>> d2(ninst);
+            for (int i = 0; i < ninst; ++i) {
+                n1[i] = t->nb[t->inst_top[i]];
+                tb[i] = t->inst_top[i] + 1;
+                hb[i] = t->inst_top[i] + 1;
+                key[i] = 2 * t->nbox;
+            }
+            if ((rc = eliminate_structured<T>(t, o, fr, d_fr.as<FrontDev>(), n1, d2, tb, key, hb, arena,
+                                              d_piv.as<int>(), d_scratch.as<int>(), F->d_topset.as<int>(),
+                                              F->d_iperm.as<int>(), d_status, F->exec_flops, F, eng, W, s)))
+                return rc;
+        } else if ((rc = eliminate_stage<T>(fr, d_fr.as<FrontDev>(), arena, d_piv.as<int>(), d_scratch.as<int>(),
+                                            F->d_topset.as<int>(), F->d_iperm.as<int>(), d_status, F->exec_flops,
+                                            eng, W, s))) {
             return rc;
+        }
         std::vector<int> hst(nstat + 1);
         HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status_all.p, sizeof(int) * hst.size(), cudaMemcpyDeviceToHost, s));
         HSS_CUDA(cudaStreamSynchronize(s));
@@ -1251,8 +1394,10 @@ static int check_factor_opts(const hss_factor_opts &o, const char *who) {
         (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
         (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1) ||
         o.probe < 0 || o.probe > PROBE_MAX || (o.probe > 0 && !(o.tol > 0)) || o.tensor_cores < 0 ||
-        o.tensor_cores > 3 || (o.sample_bf16 != 0 && o.sample_bf16 != 1)) {
-        set_error(std::string(who) + ": options out of range (rmax <= 128, tensor_cores 0..3, sample_bf16 0/1)");
+        o.tensor_cores > 3 || (o.sample_bf16 != 0 && o.sample_bf16 != 1) || (o.merge != 0 && o.merge != 1) ||
+        (o.merge == 1 && o.probe > 0)) {
+        set_error(std::string(who) + ": options out of range (rmax <= 128, tensor_cores 0..3, sample_bf16 0/1, "
+                                     "merge 0/1 and no probe with merge = 1)");
         return HSS_EINVAL;
     }
     return HSS_OK;
@@ -1270,6 +1415,10 @@ extern "C" int hss_factor_batched(int ninst, const hss_bsr *As, const hss_tree *
     if (opts) o = *opts;
     int rc;
     if ((rc = check_factor_opts(o, "hss_factor_batched"))) return rc;
+    if (o.merge != 0) {
+        set_error("hss_factor_batched: the structured merge (merge = 1) is for single instances");
+        return HSS_EINVAL;
+    }
     if (forest->ninst != ninst) {
         set_error("hss_factor_batched: the tree is not a forest of ninst instances (use nd_order_batched)");
         return HSS_EINVAL;
@@ -1358,9 +1507,11 @@ extern "C" int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_fact
         o.rmax < o.r0 || o.rmax > 128 || o.oversample < 0 || (o.precision != HSS_FP64 && o.precision != HSS_FP32) ||
         (o.cap_policy != HSS_CAP_KEEP && o.cap_policy != HSS_CAP_ACCEPT) || (o.autotune != 0 && o.autotune != 1) ||
         o.probe < 0 || o.probe > PROBE_MAX || (o.probe > 0 && !(o.tol > 0)) || o.tensor_cores < 0 ||
-        o.tensor_cores > 3 || (o.sample_bf16 != 0 && o.sample_bf16 != 1)) {
+        o.tensor_cores > 3 || (o.sample_bf16 != 0 && o.sample_bf16 != 1) || (o.merge != 0 && o.merge != 1) ||
+        (o.merge == 1 && (o.probe > 0 || tree->ninst != 1))) {
         set_error("hss_factor: invalid argument (matrix/tree mismatch or options out of range; rmax <= 128, "
-                  "tensor_cores 0..3, sample_bf16 0/1)");
+                  "tensor_cores 0..3, sample_bf16 0/1, merge 0/1; merge = 1 needs probe = 0 and a single "
+                  "instance)");
         return HSS_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;

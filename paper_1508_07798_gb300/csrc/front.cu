@@ -162,9 +162,10 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
     for (int i = threadIdx.x; i < hT; i += PANEL_NT) rp[i] = k0 == 0 ? i : rglob[k0 + i];
     __syncthreads();
     int *pv = piv + F.ioff;
-    // candidates of the first pivot column
+    // candidates of the first pivot column (rows below the pivot limit)
+    const int hP = min(hT, J.rlim - k0);
     ArgMax<T> loc{-1LL, 0x7fffffff};
-    for (int i = threadIdx.x; i < hT; i += PANEL_NT) {
+    for (int i = threadIdx.x; i < hP; i += PANEL_NT) {
         long long a = mag_key(P[i]);
         if (a > loc.v) {
             loc.v = a;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
                 for (int c = 0; c < kb; ++c) P[i + ldp * c] -= ad * rowj[c];
                 P[i + ldp * j] = -ad;
             }
-            if (i > j && j + 1 < kb) {
+            if (i > j && j + 1 < kb && i < hP) {
                 long long v2 = mag_key(P[i + ldp * (j + 1)]);
                 if (v2 > loc.v) {
                     loc.v = v2;
@@ -347,12 +348,14 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(const PanelJob *__restrict_
     if (threadIdx.x == 0) nmv = 0;
     __syncthreads();
     int *pv = piv + F.ioff;
-    // candidates of the first column
+    // candidates of the first column (rows below the pivot limit; a row's
+    // position stays fixed while it is not a pivot candidate)
+    const int hP = min(hT, J.rlim - k0);
     ArgMax<T> loc{-1LL, 0x7fffffff};
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int i = threadIdx.x + NT * q;
-        if (i < hT) {
+        if (i < hP) {
             const long long v = mag_key(reg[q][0]);
             if (v > loc.v || (v == loc.v && i < loc.i)) {
                 loc.v = v;
@@ -417,7 +420,7 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(const PanelJob *__restrict_
             if (!done[q]) {
                 const long long v = mag_key(reg[q][0]);
                 const int ps = (i == y) ? p : pos[i];
-                if (v > loc.v || (v == loc.v && ps < loc.i)) {
+                if (ps < hP && (v > loc.v || (v == loc.v && ps < loc.i))) {
                     loc.v = v;
                     loc.i = ps;
                 }
@@ -515,11 +518,12 @@ __global__ void __launch_bounds__(NT) k_gj_panel_cl(const PanelJob *__restrict__
     if (threadIdx.x == 0) nmv = 0;
     __syncthreads();
     int *pv = piv + F.ioff;
+    const int hP = min(hT, J.rlim - k0);   // pivot candidates: positions below the limit
     ArgMax<T> loc{-1LL, 0x7fffffff};
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int i = q * STRIDE + crank * NT + threadIdx.x;
-        if (i < hT) {
+        if (i < hP) {
             const long long v = mag_key(reg[q][0]);
             if (v > loc.v || (v == loc.v && i < loc.i)) {
                 loc.v = v;
@@ -597,7 +601,7 @@ __global__ void __launch_bounds__(NT) k_gj_panel_cl(const PanelJob *__restrict__
             if (!done[q]) {
                 const long long v = mag_key(reg[q][0]);
                 const int ps = (i == y) ? p : pos[i];
-                if (v > loc.v || (v == loc.v && ps < loc.i)) {
+                if (ps < hP && (v > loc.v || (v == loc.v && ps < loc.i))) {
                     loc.v = v;
                     loc.i = ps;
                 }

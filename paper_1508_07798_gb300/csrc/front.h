@@ -32,6 +32,9 @@ struct StageElem {
 struct PanelJob {
     int front;        // stage-local front index
     int k0, kb;
+    int rlim;         // pivots are searched among the rows (positions) below rlim only: an
+                      // elimination split into phases (the structured merge) keeps each
+                      // phase's pivots inside its own block of rows; ni for a plain sweep
     int smem;         // 1: panel in shared memory
     long aoff;        // offset of this job's Aold (kb x n) in the workspace
     long xoff;        // offset of the pivot-block inverse X (kb x kb)

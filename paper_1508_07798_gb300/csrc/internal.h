@@ -140,6 +140,16 @@ struct HssNode {          // one node of the HSS tree of a front's S (host view)
 
 }  // namespace hssnd
 
+struct hss_tree;
+namespace hssnd {
+// HSS tree over `dofs` (ascending depth-first positions) from the
+// nested-dissection subtree of `box` (nd.cu); elem_positions: depth-first
+// position of every element.
+void hss_nodes_over(const hss_tree *t, const std::vector<int> &elem_pos, int box, const std::vector<int> &dofs,
+                    std::vector<HssNode> &nodes);
+std::vector<int> elem_positions(const hss_tree *t);
+}  // namespace hssnd
+
 struct hss_tree {
     int dim = 2, n[3] = {1, 1, 1}, p = 1, bs = 1, ndof = 0, nelem = 0, nbox = 0, maxlev = 0;
     hss_nd_opts opts{};

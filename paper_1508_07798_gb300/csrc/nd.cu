@@ -215,50 +215,60 @@ __global__ void k_nd_emit(const NdBoxDev *__restrict__ box, const int *__restric
 }
 
 // ---------------------------------------------------------------- host
-static void build_hss_trees(hss_tree *t) {
-    // depth-first dof position of a dof: position of its element * bs + local
-    std::vector<int> elem_pos(t->nelem);
-    for (int q = 0; q < t->nelem; ++q) elem_pos[t->dfs_elem[q]] = q;
-    t->hss.assign(t->nbox, {});
-    for (int b = 0; b < t->nbox; ++b) {
-        int nbb = t->nb[b];
-        if (nbb == 0) continue;
-        std::vector<long> pos(nbb);
-        for (int i = 0; i < nbb; ++i) {
-            int d = t->bset[t->boff[b] + i];
-            pos[i] = (long)elem_pos[d / t->bs] * t->bs + d % t->bs;
-        }
-        auto &nodes = t->hss[b];
-        // recursive build (post-order), collapsing empty and single-child boxes
-        struct Rec {
-            hss_tree *t;
-            std::vector<long> &pos;
-            std::vector<HssNode> &nodes;
-            int go(int bx) {
-                long p0 = t->pos0[bx], p1 = t->pos1[bx];
-                int lo = (int)(std::lower_bound(pos.begin(), pos.end(), p0) - pos.begin());
-                int hi = (int)(std::lower_bound(pos.begin(), pos.end(), p1) - pos.begin());
-                if (hi == lo) return -1;
-                if (t->child0[bx] < 0) {
-                    nodes.push_back({lo, hi, -1, -1, 0});
-                    return (int)nodes.size() - 1;
-                }
-                int c0 = go(t->child0[bx]);
-                int c1 = go(t->child1[bx]);
-                if (c0 < 0) return c1;
-                if (c1 < 0) return c0;
-                nodes.push_back({lo, hi, c0, c1, 0});
+// HSS tree over the dofs `dofs` (ascending depth-first positions, e.g. B^box
+// or a subset of it) from the nested-dissection subtree of `box`: a node per
+// box of the subtree that holds some of the dofs, empty boxes removed and
+// single-child chains collapsed; nodes in post-order, root last.
+void hss_nodes_over(const hss_tree *t, const std::vector<int> &elem_pos, int box, const std::vector<int> &dofs,
+                    std::vector<HssNode> &nodes) {
+    nodes.clear();
+    if (dofs.empty()) return;
+    std::vector<long> pos(dofs.size());
+    for (size_t i = 0; i < dofs.size(); ++i) pos[i] = (long)elem_pos[dofs[i] / t->bs] * t->bs + dofs[i] % t->bs;
+    struct Rec {
+        const hss_tree *t;
+        std::vector<long> &pos;
+        std::vector<HssNode> &nodes;
+        int go(int bx) {
+            long p0 = t->pos0[bx], p1 = t->pos1[bx];
+            int lo = (int)(std::lower_bound(pos.begin(), pos.end(), p0) - pos.begin());
+            int hi = (int)(std::lower_bound(pos.begin(), pos.end(), p1) - pos.begin());
+            if (hi == lo) return -1;
+            if (t->child0[bx] < 0) {
+                nodes.push_back({lo, hi, -1, -1, 0});
                 return (int)nodes.size() - 1;
             }
-        } rec{t, pos, nodes};
-        rec.go(b);
-        int root = (int)nodes.size() - 1;
-        nodes[root].depth = 0;
-        for (int i = root; i >= 0; --i)
-            if (nodes[i].a >= 0) {
-                nodes[nodes[i].a].depth = nodes[i].depth + 1;
-                nodes[nodes[i].b].depth = nodes[i].depth + 1;
-            }
+            int c0 = go(t->child0[bx]);
+            int c1 = go(t->child1[bx]);
+            if (c0 < 0) return c1;
+            if (c1 < 0) return c0;
+            nodes.push_back({lo, hi, c0, c1, 0});
+            return (int)nodes.size() - 1;
+        }
+    } rec{t, pos, nodes};
+    rec.go(box);
+    int root = (int)nodes.size() - 1;
+    nodes[root].depth = 0;
+    for (int i = root; i >= 0; --i)
+        if (nodes[i].a >= 0) {
+            nodes[nodes[i].a].depth = nodes[i].depth + 1;
+            nodes[nodes[i].b].depth = nodes[i].depth + 1;
+        }
+}
+
+std::vector<int> elem_positions(const hss_tree *t) {
+    std::vector<int> elem_pos(t->nelem);
+    for (int q = 0; q < t->nelem; ++q) elem_pos[t->dfs_elem[q]] = q;
+    return elem_pos;
+}
+
+static void build_hss_trees(hss_tree *t) {
+    const std::vector<int> elem_pos = elem_positions(t);
+    t->hss.assign(t->nbox, {});
+    for (int b = 0; b < t->nbox; ++b) {
+        if (t->nb[b] == 0) continue;
+        std::vector<int> dofs(t->bset.begin() + t->boff[b], t->bset.begin() + t->boff[b + 1]);
+        hss_nodes_over(t, elem_pos, b, dofs, t->hss[b]);
     }
 }
 

@@ -60,7 +60,8 @@ class hss_factor_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("compress", C.c_int), ("r0", C.c_int), ("dr", C.c_int),
                 ("rmax", C.c_int), ("oversample", C.c_int), ("precision", C.c_int),
                 ("seed", C.c_uint64), ("keep_schur", C.c_int), ("tensor_cores", C.c_int), ("r_init", C.c_void_p),
-                ("cap_policy", C.c_int), ("autotune", C.c_int), ("probe", C.c_int), ("sample_bf16", C.c_int)]
+                ("cap_policy", C.c_int), ("autotune", C.c_int), ("probe", C.c_int), ("sample_bf16", C.c_int),
+                ("merge", C.c_int)]
 
 
 class fgmres_opts(C.Structure):
