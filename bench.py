@@ -331,6 +331,10 @@ def bench_ours(args, rank, world):
         phases = {"nd_order": [], "factor": [], "fgmres": []}
         times, last = timed(args.steps, phases)
         launches_total += hssnd.launch_count() - l0
+        # the factorization's host side, from the last uninstrumented step
+        hinfo = last[1].info()
+        host = dict(syncs=hinfo["host_syncs"], sync_wait_ms=hinfo["host_sync_ms"], call_ms=hinfo["host_ms"],
+                    work_ms=hinfo["host_ms"] - hinfo["host_sync_ms"])
         # pass 2: the same steps with every kernel launch bracketed by CUDA events
         hssnd.profile_reset()
         hssnd.profile_enable(True)
@@ -349,7 +353,7 @@ def bench_ours(args, rank, world):
                            factor_bytes=info["factor_bytes"], front_flops=info["front_flops"],
                            executed_flops=info["executed_flops"], max_rank=info["max_rank"], max_r=info["max_r"],
                            sampling_rounds=int(F.export_log()["rounds"].sum()),
-                           probe_regrown=info["probe_regrown"],
+                           probe_regrown=info["probe_regrown"], factor_host=host,
                            kernel_ms_sum=sum(v[0] for v in prof.values()) / args.steps)
     clocks = clk.stop()
     barrier()

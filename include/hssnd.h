@@ -222,6 +222,11 @@ typedef struct hss_factor_info {
     long gemm_staged;       /* ... on tcgen05 with thread-staged operands */
     long gemm_timed;        /* problems the GEMM engine tuner timed (tensor_cores = 3) */
     long gemm_bf16;         /* sampling products run on the BF16 tensor-core kernel (sample_bf16) */
+    long host_syncs;        /* blocking device->host read-backs inside the call (ranks of each
+                               sampling round, probe norms, pivot flags, the end of the call) */
+    double host_sync_ms;    /* host time spent waiting in them */
+    double host_ms;         /* host time of the whole call; host_ms - host_sync_ms is the host's
+                               own work (planning, launches), during which the device may idle */
 } hss_factor_info;
 int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info);
 
@@ -470,7 +475,11 @@ int fgmres_history(int rhs, double *hist, int cap);
  * hss_launch_count: number of CUDA kernels the library has launched since it
  * was loaded (all threads).
  * hss_profile_enable(1) brackets every subsequent launch with two CUDA events
- * on its stream, grouped by kernel class; hss_profile_enable(0) stops.
+ * on its stream, grouped by kernel class; hss_profile_enable(0) stops.  Both
+ * modes 1 and 2 also time named sections of the library's host code (classes
+ * "host:<section>", host wall time in ms, entries in place of launches; nested
+ * sections each count their inclusive time); mode 2 records those only, with
+ * no events, so the host path runs as it does unprofiled.
  * hss_profile_read(-1, ...) returns the number of classes; for idx >= 0 it
  * fills the class name (HOST buffer of cap bytes), the summed event time in
  * ms, the launch count and the algorithmic work the library attributes to

@@ -12,6 +12,7 @@
 // status) to decide sample growth and to size the expansion.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <mutex>
 #include <type_traits>
@@ -24,6 +25,23 @@
 #include "prof.h"
 
 namespace hssnd {
+
+// A blocking read-back of the factorization (ranks of a sampling round, probe
+// norms, pivot flags): the copy and the stream synchronize, counted, with the
+// host time spent in them (a copy to pageable memory already waits for the
+// stream), so that the host's share of a factorization can be told from the
+// device's.
+static int factor_readback(void *dst, const void *src, size_t bytes, cudaStream_t s, hss_factor_t *F) {
+    HSS_HOST("readback");
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaError_t e = bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (F) {
+        F->host_syncs++;
+        F->host_sync_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return e == cudaSuccess ? HSS_OK : cuda_fail(e, "device read-back");
+}
 
 namespace {
 
@@ -301,6 +319,7 @@ template <class T>
 int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *arena, int *piv, int *rperm,
                     const int *ilist, int *iperm, int *status, double &exec_flops, const Engine &eng, Work &W,
                     cudaStream_t s, const int *pbeg = nullptr, const int *pend = nullptr) {
+    HSS_HOST("eliminate_stage");
     int nf = (int)fr.size();
     const bool phased = pbeg != nullptr;
     std::vector<int> kb(nf), nsteps(nf), isreg(nf), Rf(nf), clpath(nf, 0), beg(nf), end(nf);
@@ -512,10 +531,14 @@ int eliminate_stage(const std::vector<FrontDev> &fr, const FrontDev *d_fr, T *ar
         return rc;
     for (size_t i = 0; i < descs.size(); ++i) descs[i].B = (desc_blk[i] ? d_aoldB : d_aold) + desc_b[i];
     GemmPlan<T> plan;
-    if ((rc = W.up(jobs, &d_jobs)) || (rc = W.up(bjobs, &d_bjobs)) || (rc = W.up(descs, &d_descs)) ||
-        (rc = W.up(ptiles, &d_ptiles)) || (rc = W.up(bptiles, &d_bptiles)) ||
-        (rc = plan_gemms<T>(eng, descs, desc_group, 2 * maxsteps, plan, W, s)))
-        return rc;
+    {
+        HSS_HOST("eliminate_upload_plan");
+        if ((rc = W.up(jobs, &d_jobs)) || (rc = W.up(bjobs, &d_bjobs)) || (rc = W.up(descs, &d_descs)) ||
+            (rc = W.up(ptiles, &d_ptiles)) || (rc = W.up(bptiles, &d_bptiles)) ||
+            (rc = plan_gemms<T>(eng, descs, desc_group, 2 * maxsteps, plan, W, s)))
+            return rc;
+    }
+    HSS_HOST("eliminate_launch");
     for (int st = 0; st < maxsteps; ++st) {
         for (const Group &g : groups[st]) {
             if (g.reg == 1)
@@ -566,6 +589,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
                    const std::vector<long> &keep_h, T *arena, T *keep, int *status_dev, int nstatus,
                    std::vector<FrontLog> &logv, hss_factor_t *F, const Engine &eng, Work &W, cudaStream_t s,
                    const CompressOverride *ov = nullptr) {
+    HSS_HOST("compress_stage");
     int nf = (int)fr.size();
     int rc;
     auto nodes_of = [&](int f) -> const std::vector<HssNode> & { return ov ? *ov->nodes[f] : t->hss[boxes[f]]; };
@@ -611,6 +635,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
 
     while (!active.empty()) {
         int nc = (int)active.size();
+        HSS_HOST("compress_round");
         // ---- node table, workspace layout
         std::vector<CompFront<T>> cfs(nc);
         std::vector<NodeDev> nodes;
@@ -718,6 +743,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             }
         }
         {
+            HSS_HOST("compress_sample");
             GemmDesc<T> *a, *c2;
             GemmTile *d2;
             GemmPlan<T> plan;
@@ -730,6 +756,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             if ((rc = gemm_batched<T>(c2, d2, (int)t2.size(), s, f2))) return rc;
         }
         // ---- interpolative decompositions, deepest HSS level first
+        HSS_HOST("compress_id_decide_expand");
         int maxd = 0;
         std::vector<int> ndepth(nn, 0);
         for (int c = 0; c < nc; ++c) {
@@ -748,7 +775,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
             int mcap = nodes[i].s[0].mcap, kcap = nodes[i].s[0].kcap;
             work[dpt].push_back(2 * i);
             work[dpt].push_back(2 * i + 1);
-            idsmem[dpt] = std::max(idsmem[dpt], sizeof(T) * ((size_t)(r + 1) * mcap + r + mcap) + sizeof(int) * mcap + 16);
+            idsmem[dpt] = std::max(idsmem[dpt], id_smem_bytes(r, mcap, (int)sizeof(T)));
             tallsmem[dpt] = std::max(tallsmem[dpt], sizeof(int) * (mcap + 2) + sizeof(T) * (size_t)mcap * kcap + 16);
         }
         for (int dpt = maxd; dpt >= 1; --dpt) {
@@ -760,8 +787,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
                 return rc;
         }
         std::vector<int> hfk(nc);
-        HSS_CUDA(cudaMemcpyAsync(hfk.data(), d_fk, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
-        HSS_CUDA(cudaStreamSynchronize(s));
+        if ((rc = factor_readback(hfk.data(), d_fk, sizeof(int) * nc, s, F))) return rc;
         // ---- decide: fronts whose rank reached r - oversample sample again, wider
         // A front whose rank still needs more samples when the cap rmax stops
         // the growth has no oversampling margin left: Theorem 1's error bound
@@ -861,8 +887,7 @@ int compress_stage(const hss_tree *t, const hss_factor_opts &o, const std::vecto
                                               o.probe, d_rowacc, d_acc, s)))
                     return rc;
                 std::vector<double> acc(2 * pc.size());
-                HSS_CUDA(cudaMemcpyAsync(acc.data(), d_acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, s));
-                HSS_CUDA(cudaStreamSynchronize(s));
+                if ((rc = factor_readback(acc.data(), d_acc, sizeof(double) * acc.size(), s, F))) return rc;
                 for (size_t k = 0; k < pc.size(); ++k) {
                     const int f = active[pc[k]].f, r = active[pc[k]].r;
                     int depth = 1;
@@ -1100,22 +1125,26 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     };
 
     for (size_t si = 0; si < t->stages.size(); ++si) {
+        HSS_HOST("stage");
         const auto &boxes = t->stages[si];
         std::vector<FrontDev> fr;
         std::vector<std::vector<int>> dofs(boxes.size()), sides(boxes.size());
         std::vector<long> poff(boxes.size()), keeph(boxes.size());
         std::vector<int> pn(boxes.size());
-        for (size_t f = 0; f < boxes.size(); ++f) {
-            int b = boxes[f];
-            fr.push_back(front_of(b));
-            front_dofs(b, dofs[f], sides[f]);
-            int par = t->parent[b];
-            poff[f] = par >= 0 ? foff[par] : foff_top[t->box_inst[b]];
-            pn[f] = par >= 0 ? t->ni[par] + t->nb[par] : ntop_i[t->box_inst[b]];
-            keeph[f] = F->keep_h[b];
-            const double ni = fr.back().ni, nb = fr.back().nb;
-            F->front_flops += 2.0 / 3.0 * ni * ni * ni + 2.0 * ni * ni * nb + 2.0 * nb * nb * ni;
-            F->factor_bytes += sizeof(T) * (ni * (ni + nb) + ni * nb);
+        {
+            HSS_HOST("stage_fronts");
+            for (size_t f = 0; f < boxes.size(); ++f) {
+                int b = boxes[f];
+                fr.push_back(front_of(b));
+                front_dofs(b, dofs[f], sides[f]);
+                int par = t->parent[b];
+                poff[f] = par >= 0 ? foff[par] : foff_top[t->box_inst[b]];
+                pn[f] = par >= 0 ? t->ni[par] + t->nb[par] : ntop_i[t->box_inst[b]];
+                keeph[f] = F->keep_h[b];
+                const double ni = fr.back().ni, nb = fr.back().nb;
+                F->front_flops += 2.0 / 3.0 * ni * ni * ni + 2.0 * ni * ni * nb + 2.0 * nb * nb * ni;
+                F->factor_bytes += sizeof(T) * (ni * (ni + nb) + ni * nb);
+            }
         }
         W.reset_device();
         ScratchPtr d_fr;
@@ -1124,8 +1153,11 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         FrontDev *d_frp;
         if ((rc = W.up(fr, &d_frp))) return rc;
         d_fr.p = d_frp;
-        if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
-            return rc;
+        {
+            HSS_HOST("assemble_stage");
+            if ((rc = assemble_stage<T>(A, t, fr, d_fr.as<FrontDev>(), dofs, sides, d_slot.as<int>(), arena, W, s)))
+                return rc;
+        }
         const bool leaves = std::all_of(boxes.begin(), boxes.end(), [&](int b) { return t->child0[b] < 0; });
         if (structured && !leaves) {
             // Algorithm 1 on every parent front of the stage; a leaf in the same
@@ -1172,6 +1204,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     }
     // ---- top blocks A^(0): cross couplings from A, then full Gauss-Jordan inversion
     {
+        HSS_HOST("top");
         std::vector<FrontDev> fr(ninst);
         std::vector<std::vector<int>> dofs(ninst), sides(ninst);
         for (int i = 0; i < ninst; ++i) {
@@ -1221,8 +1254,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
             return rc;
         }
         std::vector<int> hst(nstat + 1);
-        HSS_CUDA(cudaMemcpyAsync(hst.data(), d_status_all.p, sizeof(int) * hst.size(), cudaMemcpyDeviceToHost, s));
-        HSS_CUDA(cudaStreamSynchronize(s));
+        if ((rc = factor_readback(hst.data(), d_status_all.p, sizeof(int) * hst.size(), s, F))) return rc;
         if (hst[nstat]) {
             set_error("hss_factor: the matrix A holds a NaN or infinite value");
             return HSS_EINVAL;
@@ -1252,9 +1284,11 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
         build_apply_stage(F->apply.back(), fr, true);
     }
     // the apply's work items: tuned (packed by the tuner) or the default split
-    if ((rc = o.autotune ? tune_apply(F, s) : pack_apply(F, s))) return rc;
-    HSS_CUDA(cudaStreamSynchronize(s));
-    return HSS_OK;
+    {
+        HSS_HOST("apply_plan");
+        if ((rc = o.autotune ? tune_apply(F, s) : pack_apply(F, s))) return rc;
+    }
+    return factor_readback(nullptr, nullptr, 0, s, F);
 }
 
 // ---- one front at a time (test hooks hss_front_eliminate / hss_front_compress):
@@ -1520,7 +1554,9 @@ extern "C" int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_fact
     F->ndof = tree->ndof;
     F->precision = o.precision;
     F->opts = o;
+    const auto t0 = std::chrono::steady_clock::now();
     int rc = o.precision == HSS_FP32 ? factor_impl<float>(A, tree, o, s, F) : factor_impl<double>(A, tree, o, s, F);
+    F->host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc) {
         cudaStreamSynchronize(s);
         delete F;
@@ -1549,6 +1585,9 @@ extern "C" int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info)
     info->gemm_staged = f->gemm_staged;
     info->gemm_timed = f->gemm_timed;
     info->gemm_bf16 = f->gemm_bf16;
+    info->host_syncs = f->host_syncs;
+    info->host_sync_ms = f->host_sync_ms;
+    info->host_ms = f->host_ms;
     return HSS_OK;
 }
 

@@ -103,6 +103,9 @@ struct hss_factor_t {
     int probe_regrown = 0;   // sampling rounds added by failed residual probes
     long gemm_simt = 0, gemm_tma = 0, gemm_staged = 0, gemm_timed = 0;   // GEMM problems per engine, tuner timings
     long gemm_bf16 = 0;      // sampling products on the BF16 tensor-core kernel
+    long host_syncs = 0;       // blocking read-backs of the factorization
+    double host_sync_ms = 0;   // host time spent waiting in them
+    double host_ms = 0;        // host time of the whole call
     // captured apply sweeps (slot 0: one right-hand side, slot 1: blocks of APPLY_RB)
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_kernels[2] = {0, 0};

@@ -304,12 +304,50 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
     }
 }
 
+// One warp's pivot candidate at one step of the register panel: the largest
+// |value| of the active column among its rows (ties to the lowest position),
+// that row's position and panel row, and the row's KB register values.
+template <class T, int KB> struct __align__(16) PanelCand {
+    T v[KB];
+    long long key;   // -1: the warp has no candidate
+    int pos, row;
+};
+
+template <class T, int KB> __device__ __forceinline__ void put_row(T *dst, const T (&src)[KB]) {
+    if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+        for (int c = 0; c < KB; c += 4)
+            *reinterpret_cast<float4 *>(dst + c) = make_float4(src[c], src[c + 1], src[c + 2], src[c + 3]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < KB; c += 2) *reinterpret_cast<double2 *>(dst + c) = make_double2(src[c], src[c + 1]);
+    }
+}
+
+// 16 bytes of a shared-memory row, loaded where the code asks for them (the
+// pivot row is re-read per owned row instead of being held in registers).
+template <class T> __device__ __forceinline__ void get_vec(const T *src, T *dst) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(src);
+    if constexpr (std::is_same<T, float>::value)
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(dst[0]), "=f"(dst[1]), "=f"(dst[2]), "=f"(dst[3])
+                     : "r"(a));
+    else
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(dst[0]), "=d"(dst[1]) : "r"(a));
+}
+
 // Register-resident panel: thread t owns panel rows t, t + NT, ... (R rows of
-// KB values each) for the whole panel, so the 32 pivot steps touch no shared
-// memory besides the pivot row.  Rows are not moved while pivoting: pos[]
-// (row -> position) and posinv[] (position -> row) replay the interchanges of
-// partial pivoting exactly (the search runs over rows not yet pivoted, ties to
-// the lowest position), and every row is written once, to its final position.
+// KB values each) for the whole panel.  Rows are not moved while pivoting:
+// each thread keeps its rows' current positions in registers and replays the
+// interchanges of partial pivoting exactly (the search runs over rows not yet
+// pivoted and below the pivot limit, ties to the lowest position); every row
+// is written once, to its final position.
+// One barrier per pivot step: every warp publishes its best candidate row to
+// a double-buffered shared slot, and after the barrier every thread reduces
+// the NT/32 slots and reads the pivot row from the winning one.  The pivot
+// loop runs in unrolled groups of U steps, so the active column sits in a
+// register fixed at compile time; the registers rotate left by U once per
+// group (after G groups register c holds column (G U + c) mod KB).
 template <class T, int KB, int R, int NT>
 __global__ void __launch_bounds__(NT) k_gj_panel_reg(const PanelJob *__restrict__ jobs,
                                                         const FrontDev *__restrict__ fr, T *__restrict__ arena,
@@ -317,148 +355,206 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(const PanelJob *__restrict_
                                                         int *__restrict__ piv, int *__restrict__ rperm,
                                                         const int *__restrict__ ilist, int *__restrict__ iperm,
                                                         int *__restrict__ status) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ ArgMax<T> red[NT / 32];
-    __shared__ T rowj[KB];
-    __shared__ int nmv;
+    constexpr int NW = NT / 32;
+    // steps per rotation group: fewer where the rows fill more of the register budget
+    constexpr int DREGS = R * KB * (int)sizeof(T) / 4;
+    constexpr int U = DREGS <= 48 ? 4 : DREGS <= 64 ? 2 : 1;
+    constexpr int V = 16 / (int)sizeof(T);   // values per 16-byte shared load
+    // row positions in registers for up to two rows per thread, else in shared memory
+    constexpr bool POS_REG = R <= 2;
+    static_assert(KB % U == 0 && KB > U && U <= 4, "panel width");
+    __shared__ PanelCand<T, KB> cand[2][NW];
+    __shared__ int pos_s[POS_REG ? 1 : R * NT];
+    __shared__ int swp[KB];   // pivot position of each step
+    __shared__ int nmv, zero_piv;
     const PanelJob J = jobs[blockIdx.x];
     const FrontDev F = fr[J.front];
     T *M = arena + F.foff;
     const long ld = F.n;
     const int k0 = J.k0, kb = J.kb, ni = F.ni;
     const int hT = ni - k0;
-    int *pos = reinterpret_cast<int *>(smraw);   // hT
-    int *posinv = pos + hT;                       // hT
-    int *rp = posinv + hT;                        // hT: position -> original I row
+    const int hP = min(hT, J.rlim - k0);   // pivot candidates: positions below hP
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int *rglob = rperm + F.ioff;
+    // position of owned row q; a pivoted row keeps its position j as
+    // j - PIV_DONE (negative); rows past hT keep positions >= hP
+    constexpr int PIV_DONE = 1 << 30;
+    int pos_r[POS_REG ? R : 1];
+    auto getpos = [&](int q) -> int {
+        if constexpr (POS_REG)
+            return pos_r[q];
+        else
+            return pos_s[threadIdx.x + NT * q];
+    };
+    auto setpos = [&](int q, int v) {
+        if constexpr (POS_REG)
+            pos_r[q] = v;
+        else
+            pos_s[threadIdx.x + NT * q] = v;
+    };
     T reg[R][KB];
-    bool done[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int i = threadIdx.x + NT * q;
-        done[q] = false;
+        setpos(q, i);
 #pragma unroll
         for (int c = 0; c < KB; ++c) reg[q][c] = (i < hT && c < kb) ? M[(k0 + i) + ld * (k0 + c)] : T(0);
     }
-    for (int i = threadIdx.x; i < hT; i += NT) {
-        pos[i] = i;
-        posinv[i] = i;
-        rp[i] = k0 == 0 ? i : rglob[k0 + i];
+    if (threadIdx.x == 0) {
+        nmv = 0;
+        zero_piv = 0;
     }
-    if (threadIdx.x == 0) nmv = 0;
-    __syncthreads();
-    int *pv = piv + F.ioff;
-    // candidates of the first column (rows below the pivot limit; a row's
-    // position stays fixed while it is not a pivot candidate)
-    const int hP = min(hT, J.rlim - k0);
+    // candidates of the first column
     ArgMax<T> loc{-1LL, 0x7fffffff};
+    int lq = 0;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-        const int i = threadIdx.x + NT * q;
-        if (i < hP) {
+        const int ps = getpos(q);
+        if (ps >= 0 && ps < hP) {
             const long long v = mag_key(reg[q][0]);
-            if (v > loc.v || (v == loc.v && i < loc.i)) {
+            if (v > loc.v || (v == loc.v && ps < loc.i)) {
                 loc.v = v;
-                loc.i = i;
+                loc.i = ps;
+                lq = q;
             }
         }
     }
-    // Pivot loop, not unrolled (the unrolled body overflows the instruction
-    // cache): each row's registers rotate left by one per step, so the active
-    // column always sits in register 0; after kb steps register c holds
-    // column (kb + c) mod KB.
 #pragma unroll 1
-    for (int j = 0; j < kb; ++j) {
-        // 1. pivot among the rows not yet pivoted: largest |value|, lowest position on ties
-        const ArgMax<T> best = block_argmax(loc, red);
-        int p = best.i;
-        if (best.v <= 0) {
-            if (threadIdx.x == 0) atomicExch(&status[J.front], 1);
-            p = j;
-        }
-        const int x = posinv[p];   // row of the pivot
-        const int y = posinv[j];   // row at position j: trades places with the pivot
+    for (int g = 0; g < kb; g += U) {
 #pragma unroll
-        for (int q = 0; q < R; ++q)
-            if (threadIdx.x + NT * q == x) {
+        for (int u = 0; u < U; ++u) {
+            const int j = g + u;
+            if (j < kb) {   // uniform over the block
+                // 1. this warp's candidate to its slot
+                PanelCand<T, KB> *slot = cand[j & 1];
+                const ArgMax<T> wb = warp_argmax(loc);
+                const unsigned own = __ballot_sync(0xffffffffu, loc.v >= 0 && loc.v == wb.v && loc.i == wb.i);
+                if (own == 0u) {
+                    if (lane == 0) slot[w].key = -1LL;
+                } else if (lane == __ffs(own) - 1) {
+                    slot[w].key = wb.v;
+                    slot[w].pos = wb.i;
+                    slot[w].row = threadIdx.x + NT * lq;
 #pragma unroll
-                for (int c = 0; c < KB; ++c) rowj[c] = reg[q][c];
-                done[q] = true;
-            }
-        __syncthreads();   // every thread has read posinv; rowj is complete
-        if (threadIdx.x == 0) {
-            posinv[j] = x;
-            posinv[p] = y;
-            pos[x] = j;
-            pos[y] = p;
-            const int t = rp[j];
-            rp[j] = rp[p];
-            rp[p] = t;
-            pv[k0 + j] = k0 + p;
-        }
-        // 2. Gauss-Jordan step in registers, then rotate; candidates of the next column
-        const T dinv = rowj[0] != T(0) ? T(1) / rowj[0] : T(0);
-        loc = ArgMax<T>{-1LL, 0x7fffffff};
+                    for (int q = 0; q < R; ++q)
+                        if (q == lq) put_row<T, KB>(slot[w].v, reg[q]);
+                }
+                __syncthreads();
+                // 2. the pivot: best slot (largest key, lowest position)
+                ArgMax<T> y{-1LL, 0x7fffffff};
+                if (lane < NW) {
+                    const long long k = slot[lane].key;
+                    if (k >= 0) y = ArgMax<T>{k, slot[lane].pos};
+                }
+                const ArgMax<T> best = warp_argmax(y);
+                const unsigned wm = __ballot_sync(0xffffffffu, lane < NW && y.v >= 0 && y.v == best.v && y.i == best.i);
+                // (position j always holds a candidate, so wm != 0; an empty wm would
+                // leave every row in place and is reported as a zero pivot)
+                const int ws = wm ? __ffs(wm) - 1 : 0;
+                const T *prow = slot[ws].v;
+                const int p = wm ? best.i : j, x = wm ? slot[ws].row : -1;
+                if (threadIdx.x == 0) {
+                    swp[j] = p;
+                    if (best.v <= 0) zero_piv = 1;
+                }
+                // 3. Gauss-Jordan step, row by row (every row, then the pivot row overwritten)
+                const T pj = prow[u];
+                const T dinv = pj != T(0) ? T(1) / pj : T(0);
+                loc = ArgMax<T>{-1LL, 0x7fffffff};
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int i = threadIdx.x + NT * q;
-            if (i >= hT) continue;
-            T head;
-            if (i == x) {
+                for (int q = 0; q < R; ++q) {
+                    const bool isx = threadIdx.x + NT * q == x;
+                    const T ad = reg[q][u] * dinv;
 #pragma unroll
-                for (int c = 1; c < KB; ++c) reg[q][c] = rowj[c] * dinv;
-                head = dinv;
-            } else {
-                const T ad = reg[q][0] * dinv;
+                    for (int c0 = 0; c0 < KB; c0 += V) {
+                        T rv[V];
+                        get_vec<T>(prow + c0, rv);
 #pragma unroll
-                for (int c = 1; c < KB; ++c) reg[q][c] -= ad * rowj[c];
-                head = -ad;
-            }
+                        for (int e = 0; e < V; ++e)
+                            if (c0 + e != u) reg[q][c0 + e] -= ad * rv[e];
+                    }
+                    reg[q][u] = -ad;
+                    if (__builtin_expect(isx, 0)) {   // the pivot row: one thread of the block
 #pragma unroll
-            for (int c = 0; c + 1 < KB; ++c) reg[q][c] = reg[q][c + 1];
-            reg[q][KB - 1] = head;
-            if (!done[q]) {
-                const long long v = mag_key(reg[q][0]);
-                const int ps = (i == y) ? p : pos[i];
-                if (ps < hP && (v > loc.v || (v == loc.v && ps < loc.i))) {
-                    loc.v = v;
-                    loc.i = ps;
+                        for (int c0 = 0; c0 < KB; c0 += V) {
+                            T rv[V];
+                            get_vec<T>(prow + c0, rv);
+#pragma unroll
+                            for (int e = 0; e < V; ++e)
+                                if (c0 + e != u) reg[q][c0 + e] = rv[e] * dinv;
+                        }
+                        reg[q][u] = dinv;
+                    }
+                    int ps = getpos(q);
+                    if (isx)
+                        setpos(q, j - PIV_DONE);
+                    else if (ps == j)
+                        setpos(q, ps = p);   // the row at position j trades places with the pivot
+                    // 4. candidates of the next column (register u + 1 of this group)
+                    if (!isx && ps >= 0 && ps < hP) {
+                        const long long v = mag_key(reg[q][u + 1]);
+                        if (v > loc.v || (v == loc.v && ps < loc.i)) {
+                            loc.v = v;
+                            loc.i = ps;
+                            lq = q;
+                        }
+                    }
                 }
             }
         }
+        // rotate left by U
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            T t[U];
+#pragma unroll
+            for (int c = 0; c < U; ++c) t[c] = reg[q][c];
+#pragma unroll
+            for (int c = 0; c + U < KB; ++c) reg[q][c] = reg[q][c + U];
+#pragma unroll
+            for (int c = 0; c < U; ++c) reg[q][KB - U + c] = t[c];
+        }
+    }
+    // original I rows of the owned rows, read before any thread rewrites rperm
+    int orow[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int i = threadIdx.x + NT * q;
+        orow[q] = i < hT ? (k0 == 0 ? i : rglob[k0 + i]) : 0;
     }
     __syncthreads();
-    // 3. every row to its final position (register c holds column (kb + c) mod KB);
-    //    the pivot block also to X
+    // every row to its final position; the pivot block also to X
+    const int S = U * ((kb + U - 1) / U);
     T *Xg = xws + J.xoff;
     int *mv = mws + J.moff;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int i = threadIdx.x + NT * q;
         if (i >= hT) continue;
-        const int r = pos[i];
+        const int ps = getpos(q);
+        const int r = ps < 0 ? ps + PIV_DONE : ps;
 #pragma unroll
         for (int c = 0; c < KB; ++c) {
-            const int col = (kb + c) % KB;
+            const int col = (S + c) % KB;
             if (col < kb) {
                 M[(k0 + r) + ld * (k0 + col)] = reg[q][c];
                 if (r < kb) Xg[r + kb * col] = reg[q][c];
             }
         }
+        rglob[k0 + r] = orow[q];
         if (r != i) {   // the other columns move the same way (k_gj_post)
             int m = atomicAdd(&nmv, 1);
             mv[1 + m] = r;
             mv[1 + 2 * PANEL_KB_MAX + m] = i;
         }
     }
-    for (int i = threadIdx.x; i < hT; i += NT) rglob[k0 + i] = rp[i];
+    if (threadIdx.x < kb) piv[F.ioff + k0 + threadIdx.x] = k0 + swp[threadIdx.x];
     __syncthreads();
-    if (threadIdx.x == 0) mv[0] = nmv;
+    if (threadIdx.x == 0) {
+        mv[0] = nmv;
+        if (zero_piv) atomicExch(&status[J.front], 1);
+    }
     if (k0 + kb == ni)
-        for (int j = threadIdx.x; j < ni; j += NT) {
-            int r = j < k0 ? rglob[j] : rp[j - k0];
-            iperm[F.iperm_off + j] = ilist[F.iset_off + r];
-        }
+        for (int j = threadIdx.x; j < ni; j += NT) iperm[F.iperm_off + j] = ilist[F.iset_off + rglob[j]];
 }
 
 // Cluster-resident panel for tall panels (more rows than one CTA's registers
@@ -780,9 +876,7 @@ template <class T, int KB, int R, int NT>
 static cudaError_t launch_reg(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws,
                               int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status,
                               cudaStream_t s) {
-    const cudaError_t ea = func_smem_once((const void *)k_gj_panel_reg<T, KB, R, NT>, PANEL_SMEM_MAX);
-    if (ea != cudaSuccess) return ea;
-    k_gj_panel_reg<T, KB, R, NT><<<njobs, NT, smem, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
+    k_gj_panel_reg<T, KB, R, NT><<<njobs, NT, 0, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
     return cudaGetLastError();
 }
 
@@ -795,7 +889,7 @@ int launch_gj_panel_reg(const PanelJob *jobs, int njobs, int kb, int rows, const
                         double flops) {
     if (njobs == 0) return HSS_OK;
     HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s, flops);
-    const size_t smem = sizeof(int) * 3 * (size_t)rows;
+    const size_t smem = 0;   // the bookkeeping lives in registers
     cudaError_t e = cudaErrorInvalidValue;
     if (rows <= 2 * PANEL_SMALL_NT) {   // one row per thread on 128 or 256 threads
 #define ONE(NT_)                                                                                                   \

@@ -77,6 +77,27 @@ template <class T> __device__ AM<T> blk_argmax(AM<T> x, AM<T> *sh) {
     return reduce_candidates(sh);
 }
 
+// 16 bytes of a shared-memory column (4 floats or 2 doubles), 16-byte aligned.
+template <class T> __device__ __forceinline__ void ld16(const T *p, T *a) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        a[0] = v.x;
+        a[1] = v.y;
+        a[2] = v.z;
+        a[3] = v.w;
+    } else {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        a[0] = v.x;
+        a[1] = v.y;
+    }
+}
+template <class T> __device__ __forceinline__ void st16(T *p, const T *a) {
+    if constexpr (std::is_same<T, float>::value)
+        *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
+    else
+        *reinterpret_cast<double2 *>(p) = make_double2(a[0], a[1]);
+}
+
 template <class T> __device__ T blk_sum(T x, T *sh) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -138,7 +159,7 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
         ka = kout[2 * N.a + side];
         m = ka + kout[2 * N.b + side];
     }
-    const int lda = r + 1;                                 // odd: column-wise access is conflict free
+    const int lda = id_lda(r, (int)sizeof(T));           // 16-byte column starts (hss.h)
     T *A = reinterpret_cast<T *>(smraw);                 // r x m, ld lda
     T *v = A + (long)lda * mcap;                          // r
     T *nrm2 = v + r;                                      // mcap
@@ -199,133 +220,146 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
     for (int c = threadIdx.x; c < m; c += ID_NT) order[c] = c;
     __syncthreads();
 
-    // ---- column-pivoted QR of A = L^t with the relative rank cut; trailing
-    // column norms are recomputed (not downdated) by the warp that updates
-    // the column
-    // The pivot search is fused into the column updates: each warp keeps the
-    // largest key (ties: lowest column) among the columns it just updated, and
-    // the next step reduces the warps' candidates after one barrier.
+    // ---- column-pivoted QR of A = L^t with the relative rank cut.  One thread
+    // per column (c = threadIdx.x + ID_NT q): it applies the step's reflector
+    // to its columns in 16-byte pieces, reading the pivot column by broadcast,
+    // recomputes their trailing squared norms and offers the largest (ties:
+    // lowest column) as its pivot candidate.  Per step, one barrier publishes
+    // the candidates and one the interchanged pivot column.  The reflector is
+    // v = A(j:r, j) with v_j = x0 - alpha; R(j, j) = alpha is kept in v[j] and
+    // placed after the loop (the pivot column is read unchanged during its step).
+    constexpr int VW = 16 / (int)sizeof(T);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __shared__ AM<T> cand[ID_NT / 32];
-    {
-        AM<T> wbest{-1LL, INT_MAX};
-        for (int c = w; c < m; c += ID_NT / 32) {
-            T sq = 0;
-            for (int i = lane; i < r; i += 32) sq += A[i + (long)lda * c] * A[i + (long)lda * c];
-            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if (lane == 0) {
-                nrm2[c] = sq;
-                const long long kc = nn_key(sq);
-                if (kc > wbest.v || (kc == wbest.v && c < wbest.i)) wbest = AM<T>{kc, c};
+    auto offer = [&](AM<T> mine) {
+        if constexpr (std::is_same<T, float>::value) {
+            mine = warp_am_redux(mine);
+        } else {
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long v2 = __shfl_xor_sync(0xffffffffu, mine.v, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, mine.i, o);
+                if (v2 > mine.v || (v2 == mine.v && i2 < mine.i)) {
+                    mine.v = v2;
+                    mine.i = i2;
+                }
             }
         }
-        if (lane == 0) cand[w] = wbest;
+        if (lane == 0) cand[w] = mine;
+    };
+    {
+        AM<T> mine{-1LL, INT_MAX};
+        for (int c = threadIdx.x; c < m; c += ID_NT) {
+            const T *Ac = A + (long)lda * c;
+            T sp[VW] = {};
+            for (int q0 = 0; q0 < r; q0 += VW) {
+                T a[VW];
+                ld16(Ac + q0, a);
+#pragma unroll
+                for (int e = 0; e < VW; ++e)
+                    if (q0 + e < r) sp[e] += a[e] * a[e];
+            }
+            T sq = 0;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) sq += sp[e];
+            const long long kc = nn_key(sq);
+            if (kc > mine.v || (kc == mine.v && c < mine.i)) mine = AM<T>{kc, c};
+        }
+        offer(mine);
     }
     int k = 0;
     T first = 0;
     const int kmx = min(r, m);
     for (int j = 0; j < kmx; ++j) {
-        __syncthreads();   // candidates, nrm2, order and the updated columns are visible
+        __syncthreads();   // candidates and the updated columns are visible
         const AM<T> best = reduce_candidates(cand);
         const T nn2 = key_val(best.v, T(0));
         const T nrm = sqrt(nn2);
         if (j == 0) first = nrm;
         if (best.v < 0 || first == T(0) || nrm <= tol * first) break;
         const int p = best.i;
-        if (threadIdx.x == 0 && p != j) {
-            int t = order[j];
-            order[j] = order[p];
-            order[p] = t;
-            nrm2[p] = nrm2[j];
-        }
-        if (p != j)
+        if (p != j) {
+            if (threadIdx.x == 0) {
+                const int t = order[j];
+                order[j] = order[p];
+                order[p] = t;
+            }
             for (int i = threadIdx.x; i < r; i += ID_NT) {
-                T t = A[i + (long)lda * j];
+                const T t = A[i + (long)lda * j];
                 A[i + (long)lda * j] = A[i + (long)lda * p];
                 A[i + (long)lda * p] = t;
             }
+        }
         __syncthreads();   // every thread has read cand; column j holds the pivot column
-        const T x0 = A[j + (long)lda * j];
+        const T *vj = A + (long)lda * j;
+        const T x0 = vj[j];
         const T alpha = (x0 != T(0)) ? -copysign(nrm, x0) : -nrm;
-        const T vn = (x0 - alpha) * (x0 - alpha) + (nn2 - x0 * x0);
-        for (int i = j + threadIdx.x; i < r; i += ID_NT) v[i] = (i == j) ? x0 - alpha : A[i + (long)lda * j];
-        __syncthreads();
-        // FP32: two columns per warp iteration (c and c + ID_NT / 32): their
-        // reductions are independent, so their shuffle chains overlap (FP64
-        // keeps one column per iteration: the pair spills registers)
-        AM<T> wbest{-1LL, INT_MAX};
-        constexpr int NW = ID_NT / 32;
-        auto track = [&](int c, T sq) {
-            nrm2[c] = sq;
-            const long long kc = nn_key(sq);
-            if (kc > wbest.v || (kc == wbest.v && c < wbest.i)) wbest = AM<T>{kc, c};
-        };
-        if constexpr (sizeof(T) == 4) {
-            for (int c = j + 1 + w; c < m; c += 2 * NW) {
-                const int c2 = c + NW;
-                const bool two = c2 < m;
-                T *A1 = A + (long)lda * c;
-                T *A2 = A + (long)lda * (two ? c2 : c);
-                T d1 = 0, d2 = 0;
-                for (int i = j + lane; i < r; i += 32) {
-                    d1 += v[i] * A1[i];
-                    d2 += v[i] * A2[i];
+        const T vhead = x0 - alpha;
+        const T vn = vhead * vhead + (nn2 - x0 * x0);
+        const int q0 = j - j % VW;   // first 16-byte piece holding row j
+        AM<T> mine{-1LL, INT_MAX};
+        for (int c = j + 1 + threadIdx.x; c < m; c += ID_NT) {
+            T *Ac = A + (long)lda * c;
+            T dp[VW] = {};
+            for (int q = q0; q < r; q += VW) {
+                T a[VW], vv[VW];
+                ld16(Ac + q, a);
+                ld16(vj + q, vv);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const int i = q + e;
+                    if (i >= j && i < r) dp[e] += (i == j ? vhead : vv[e]) * a[e];
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-                    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-                }
-                const T coef1 = vn > T(0) ? T(2) * d1 / vn : T(0);
-                const T coef2 = vn > T(0) ? T(2) * d2 / vn : T(0);
-                T sq1 = 0, sq2 = 0;
-                for (int i = j + lane; i < r; i += 32) {
-                    const T a1 = A1[i] - coef1 * v[i];
-                    A1[i] = a1;
-                    if (i > j) sq1 += a1 * a1;
-                    if (two) {
-                        const T a2 = A2[i] - coef2 * v[i];
-                        A2[i] = a2;
-                        if (i > j) sq2 += a2 * a2;
+            }
+            T d = 0;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) d += dp[e];
+            const T coef = vn > T(0) ? T(2) * d / vn : T(0);
+            T sp[VW] = {};
+            for (int q = q0; q < r; q += VW) {
+                T a[VW], vv[VW];
+                ld16(Ac + q, a);
+                ld16(vj + q, vv);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const int i = q + e;
+                    if (i >= j && i < r) {
+                        a[e] -= coef * (i == j ? vhead : vv[e]);
+                        if (i > j) sp[e] += a[e] * a[e];
                     }
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    sq1 += __shfl_xor_sync(0xffffffffu, sq1, o);
-                    sq2 += __shfl_xor_sync(0xffffffffu, sq2, o);
-                }
-                if (lane == 0) {
-                    track(c, sq1);
-                    if (two) track(c2, sq2);
-                }
+                st16(Ac + q, a);
             }
-        } else {
-            for (int c = j + 1 + w; c < m; c += NW) {
-                T d = 0;
-                for (int i = j + lane; i < r; i += 32) d += v[i] * A[i + (long)lda * c];
-                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                const T coef = vn > T(0) ? T(2) * d / vn : T(0);
-                T sq = 0;
-                for (int i = j + lane; i < r; i += 32) {
-                    T a = A[i + (long)lda * c] - coef * v[i];
-                    A[i + (long)lda * c] = a;
-                    if (i > j) sq += a * a;
-                }
-                for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-                if (lane == 0) track(c, sq);
-            }
+            T sq = 0;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) sq += sp[e];
+            const long long kc = nn_key(sq);
+            if (kc > mine.v || (kc == mine.v && c < mine.i)) mine = AM<T>{kc, c};
         }
-        if (lane == 0) cand[w] = wbest;
-        for (int i = j + threadIdx.x; i < r; i += ID_NT) A[i + (long)lda * j] = (i == j) ? alpha : T(0);
+        offer(mine);
+        if (threadIdx.x == 0) v[j] = alpha;
         k = j + 1;
     }
     __syncthreads();
-    // T = R11^-1 R12 in place (one thread per column of R12)
+    for (int jj = threadIdx.x; jj < k; jj += ID_NT) A[jj + (long)lda * jj] = v[jj];   // R(j, j)
+    __syncthreads();
+    // T = R11^-1 R12 in place, one thread per column of R12, by columns of R11:
+    // t_i = x_i / R_ii, then x_(0..i) -= t_i R(0..i, i)
     auto solve_T_inplace = [&]() {
         for (int c = k + threadIdx.x; c < m; c += ID_NT) {
             T *col = A + (long)lda * c;
             for (int i = k - 1; i >= 0; --i) {
-                T t = col[i];
-                for (int l = i + 1; l < k; ++l) t -= A[i + (long)lda * l] * col[l];
-                col[i] = t / A[i + (long)lda * i];
+                const T ti = col[i] / A[i + (long)lda * i];
+                col[i] = ti;
+                const T *Ri = A + (long)lda * i;
+                for (int q = 0; q < i; q += VW) {
+                    T a[VW], rr[VW];
+                    ld16(col + q, a);
+                    ld16(Ri + q, rr);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e)
+                        if (q + e < i) a[e] -= ti * rr[e];
+                    st16(col + q, a);
+                }
             }
         }
         __syncthreads();

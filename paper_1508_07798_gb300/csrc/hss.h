@@ -8,6 +8,21 @@ constexpr int ID_NT = 256;
 constexpr int ID_MAX_SWAPS = 64;
 constexpr int EXP_TILE = 32;
 
+// Leading dimension of the ID's r x m sample block in shared memory: columns
+// start on 16-byte boundaries and lda * esize / 16 is odd, so the 16-byte
+// accesses of eight threads to eight columns fall in distinct banks.
+__host__ __device__ inline int id_lda(int r, int esize) {
+    const int q = 16 / esize;                      // values per 16 bytes
+    int l = (r + q - 1) / q;                       // 16-byte units per column
+    if ((l & 1) == 0) ++l;
+    return l * q;
+}
+// Shared memory of one ID CTA: the sample block (lda x mcap), v (r), the
+// squared norms (mcap) and the column order (mcap ints).
+inline size_t id_smem_bytes(int r, int mcap, int esize) {
+    return (size_t)esize * ((size_t)id_lda(r, esize) * mcap + r + mcap) + sizeof(int) * (size_t)mcap + 16;
+}
+
 // A front being compressed in the current sampling round.
 template <class T> struct CompFront {
     const T *S;       // Schur complement inside the front (column-major)

@@ -24,6 +24,7 @@ struct ClassStat {
 std::mutex g_mu;
 std::atomic<long> g_launches{0};
 bool g_on = false;
+bool g_host_only = false;   // mode 2: host sections only, no events
 std::vector<ClassStat> g_cls;
 std::vector<Rec> g_pending;
 std::vector<cudaEvent_t> g_pool;
@@ -67,7 +68,7 @@ void prof_add_launches(long n) { g_launches.fetch_add(n, std::memory_order_relax
 ProfScope::ProfScope(const char *name, cudaStream_t stream, double work) : cls(-1), s(stream), slot(-1) {
     if (g_capturing) return;
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (!g_on) return;
+    if (!g_on || g_host_only) return;
     std::lock_guard<std::mutex> lk(g_mu);
     cls = class_of(name);
     g_cls[cls].launches++;
@@ -92,6 +93,21 @@ ProfScope::~ProfScope() {
     if (slot < (int)g_pending.size()) cudaEventRecord(g_pending[slot].b, s);
 }
 
+HostScope::HostScope(const char *name) : cls(-1) {
+    if (!g_on || g_capturing) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cls = class_of((std::string("host:") + name).c_str());
+    t0 = std::chrono::steady_clock::now();
+}
+
+HostScope::~HostScope() {
+    if (cls < 0) return;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cls[cls].total_ms += ms;
+    g_cls[cls].launches++;
+}
+
 }  // namespace hssnd
 
 using namespace hssnd;
@@ -102,6 +118,7 @@ extern "C" int hss_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!on) drain_locked();
     g_on = on != 0;
+    g_host_only = on == 2;
     return HSS_OK;
 }
 

@@ -1,5 +1,6 @@
 // Launch accounting and optional per-kernel-class CUDA-event timing.
 #pragma once
+#include <chrono>
 #include <cuda_runtime.h>
 
 namespace hssnd {
@@ -16,6 +17,16 @@ struct ProfScope {
     ~ProfScope();
 };
 
+// Host wall time of a named section of library host code (planning, uploads,
+// launches), recorded as class "host:<name>" while profiling is enabled.
+// Sections nest; each records its inclusive time.
+struct HostScope {
+    int cls;
+    std::chrono::steady_clock::time_point t0;
+    explicit HostScope(const char *name);
+    ~HostScope();
+};
+
 bool prof_enabled();
 void prof_set_capture(bool on);     // while a graph is being captured, scopes record nothing
 void prof_add_launches(long n);     // kernels executed by a graph launch
@@ -23,3 +34,6 @@ void prof_add_launches(long n);     // kernels executed by a graph launch
 }  // namespace hssnd
 
 #define HSS_PROF(name, stream, ...) ::hssnd::ProfScope _prof_scope_(name, stream, ##__VA_ARGS__)
+#define HSS_HOST_CAT2(a, b) a##b
+#define HSS_HOST_CAT(a, b) HSS_HOST_CAT2(a, b)
+#define HSS_HOST(name) ::hssnd::HostScope HSS_HOST_CAT(_host_scope_, __LINE__)(name)

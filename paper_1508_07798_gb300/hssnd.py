@@ -82,7 +82,8 @@ class hss_factor_info(C.Structure):
                 ("max_rank", C.c_int), ("max_r", C.c_int), ("rounds", C.c_int), ("nfronts", C.c_int),
                 ("capped_fronts", C.c_int), ("probe_regrown", C.c_int), ("gemm_simt", C.c_long),
                 ("gemm_tma", C.c_long), ("gemm_staged", C.c_long), ("gemm_timed", C.c_long),
-                ("gemm_bf16", C.c_long)]
+                ("gemm_bf16", C.c_long), ("host_syncs", C.c_long), ("host_sync_ms", C.c_double),
+                ("host_ms", C.c_double)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
@@ -588,16 +589,17 @@ def tc_timeout_selftest(spin_limit: int = 1 << 12, stream=None) -> int:
     return int(_lib.hss_tc_timeout_selftest(spin_limit, _stream(stream)))
 
 
-def profile_enable(on: bool = True):
-    _check(_lib.hss_profile_enable(1 if on else 0))
+def profile_enable(on: bool = True, host_only: bool = False):
+    """Per-kernel-class event timing plus host-section timing; host_only
+    records the host sections alone (no events)."""
+    _check(_lib.hss_profile_enable((2 if host_only else 1) if on else 0))
 
 
 def profile_reset():
     _check(_lib.hss_profile_reset())
 
 
-def profile_read() -> dict:
-    """{kernel class: (total_ms, launches, work)} of the events recorded so far."""
+def _profile_classes() -> dict:
     n = _lib.hss_profile_read(-1, None, 0, None, None, None)
     out = {}
     for i in range(n):
@@ -606,6 +608,16 @@ def profile_read() -> dict:
         _check(_lib.hss_profile_read(i, name, 64, C.byref(ms), C.byref(cnt), C.byref(work)))
         out[name.value.decode()] = (ms.value, cnt.value, work.value)
     return out
+
+
+def profile_read() -> dict:
+    """{kernel class: (total_ms, launches, work)} of the events recorded so far."""
+    return {k: v for k, v in _profile_classes().items() if not k.startswith("host:")}
+
+
+def profile_read_host() -> dict:
+    """{host section: (total host ms, entries)} recorded so far."""
+    return {k[5:]: (v[0], v[1]) for k, v in _profile_classes().items() if k.startswith("host:")}
 
 
 def gemm_f32(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, alpha=1.0, beta=0.0, engine=1,
