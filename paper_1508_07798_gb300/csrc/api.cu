@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -44,6 +45,20 @@ int DevBuf::alloc(size_t nbytes) {
 // Dynamic shared-memory limit of a kernel, set once per (device, kernel):
 // the attribute belongs to the device context; the set is guarded for calls
 // from several host threads, and the runtime's return code is passed on.
+int device_sms() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cache[dev] = n;
+    return n;
+}
+
 cudaError_t func_smem_once(const void *func, int bytes) {
     static std::mutex mu;
     static std::set<std::pair<int, const void *>> done;

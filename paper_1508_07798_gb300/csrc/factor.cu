@@ -1071,7 +1071,7 @@ template <class T> int factor_impl(const hss_bsr *A, const hss_tree *t, const hs
     HSS_CUDA(cudaMemsetAsync(d_status_all.p, 0, sizeof(int) * (nstat + 1), s));
     {
         HSS_PROF("check_finite", s);
-        k_check_finite<<<2 * 152, 256, 0, s>>>(A->row_ptr, A->nb, A->bs * A->bs, A->val,
+        k_check_finite<<<2 * device_sms(), 256, 0, s>>>(A->row_ptr, A->nb, A->bs * A->bs, A->val,
                                                 d_status_all.as<int>() + nstat);
         HSS_CHECK_LAUNCH("k_check_finite");
     }

@@ -31,6 +31,7 @@ int cuda_fail(cudaError_t e, const char *what);
 // Raises a kernel's dynamic shared-memory limit to `bytes`, once per device
 // and kernel (thread-safe); returns the runtime's error code.
 cudaError_t func_smem_once(const void *func, int bytes);
+int device_sms();   // multiprocessors of the current device (cached per device)
 #define HSS_SMEM(kernel, bytes)                                                            \
     do {                                                                                   \
         cudaError_t _e = ::hssnd::func_smem_once((const void *)(kernel), (int)(bytes));    \
