@@ -24,6 +24,84 @@ namespace hssnd {
 constexpr int AP_NT = 256;
 constexpr int AP_WPB = AP_NT / 32;   // warps (work items) per CTA
 
+// Programmatic dependent launch: the sweep's kernels are launched while the
+// previous one still runs; each lets the next one launch once its own CTAs
+// are all running, reads what the previous kernel does not write (work
+// items, fronts, gather indices, the factor), then waits for the previous
+// kernel to complete before it reads or writes the vectors.  Without the
+// launch attribute both instructions return at once.
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// One warp per work item = (front, 32-row tile, column chunk of at most
+// APPLY_CHUNK columns).  Lane l owns row row0 + l; x is gathered one value per
+// lane and broadcast by shuffles; 32 matrix loads per lane are in flight per
+// group of 32 columns.  A tile split over several chunks writes partial sums;
+// the last warp to finish (atomic ticket) adds them in chunk order and writes
+// the result, so the sum order is fixed.  No barrier, no waiting.
+//   FWD: y = [F_ii^-1 P^t ; -F_bi F_ii^-1 P^t] x(Iperm)  ->  t = y[0,ni), x_B += y[ni,n)
+//   BWD: x_I = t - W x_B
+// The products of one work item: lane l's sums for row row0 + l.
+template <class T, int RB, bool FWD>
+__device__ __forceinline__ void apply_item_sums(const ApplyItem &it, const FrontDev &F, const T *__restrict__ arena,
+                                                const int *__restrict__ iperm, const int *__restrict__ blist,
+                                                const double *__restrict__ w, long ldw, int nrhs, T (&acc)[RB]) {
+    const int lane = threadIdx.x & 31;
+    const T *M = arena + F.foff;
+    const int colbase = FWD ? 0 : F.ni, nrows = FWD ? F.n : F.ni;
+    const int i = it.row0 + lane;
+    const bool rowok = i < nrows;
+    // arithmetic in the factor's precision (FP32 factors: FP32 products and sums;
+    // GB300's FP64 pipe is a small fraction of its FP32 rate)
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = T(0);
+    bool waited = false;
+    for (int cg = it.c0; cg < it.c1; cg += 32) {
+        const int c = cg + lane;
+        T m[32];
+        const T *col = M + i + (long)F.n * (colbase + cg);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) m[q] = (rowok && cg + q < it.c1) ? col[(long)F.n * q] : T(0);
+        const int dof = c < it.c1 ? (FWD ? iperm[F.iperm_off + c] : blist[F.bset_off + c]) : -1;
+        if (!waited) {   // the vectors are the previous kernel's output
+            pdl_wait_prev();
+            waited = true;
+        }
+        T z[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) z[r] = (dof >= 0 && r < nrhs) ? (T)w[dof + ldw * r] : T(0);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r) acc[r] = fma(m[q], __shfl_sync(0xffffffffu, z[r], q), acc[r]);
+        }
+    }
+}
+
+// The results of one work item (row row0 + lane):
+//   FWD: rows [0, ni) to t, rows [ni, n) added into x_B;  BWD: x_I = t - sums
+template <class T, int RB, bool FWD>
+__device__ __forceinline__ void apply_item_store(const ApplyItem &it, const FrontDev &F, const int *__restrict__ ilist,
+                                                 const int *__restrict__ blist, double *__restrict__ w, long ldw,
+                                                 double *__restrict__ tv, long ldt, int nrhs, const T (&acc)[RB]) {
+    const int i = it.row0 + (threadIdx.x & 31);
+    if (i >= (FWD ? F.n : F.ni)) return;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        if (r >= nrhs) break;
+        const double y = (double)acc[r];
+        if (FWD) {
+            if (i < F.ni)
+                tv[ilist[F.iset_off + i] + ldt * r] = y;
+            else
+                w[blist[F.bset_off + i - F.ni] + ldw * r] += y;
+        } else {
+            const int dof = ilist[F.iset_off + i];
+            w[dof + ldw * r] = tv[dof + ldt * r] - y;
+        }
+    }
+}
+
 // One warp per work item = (front, 32-row tile, column chunk of at most
 // APPLY_CHUNK columns).  Lane l owns row row0 + l; x is gathered one value per
 // lane and broadcast by shuffles; 32 matrix loads per lane are in flight per
@@ -38,46 +116,15 @@ __global__ void __launch_bounds__(AP_NT) k_apply(const ApplyItem *__restrict__ i
                                                const int *__restrict__ iperm, const int *__restrict__ ilist,
                                                const int *__restrict__ blist, const ApplyParams *__restrict__ prm,
                                                double *__restrict__ part, int *__restrict__ tickets) {
+    pdl_launch_next();
     const int lane = threadIdx.x & 31;
     const int item = blockIdx.x * AP_WPB + (threadIdx.x >> 5);
     if (item >= nitems) return;   // whole warps leave together
-    double *__restrict__ w = prm->w;
-    const long ldw = prm->ldw;
-    double *__restrict__ tv = prm->tv;
-    const long ldt = prm->ldt;
-    const int nrhs = prm->nrhs;   // <= RB
     const ApplyItem it = items[item];
     const FrontDev F = fr[it.front];
-    const T *M = arena + F.foff;
-    const int colbase = FWD ? 0 : F.ni, nrows = FWD ? F.n : F.ni;
-    const int i = it.row0 + lane;
-    const bool rowok = i < nrows;
-    // arithmetic in the factor's precision (FP32 factors: FP32 products and sums;
-    // GB300's FP64 pipe is a small fraction of its FP32 rate)
     T acc[RB];
-#pragma unroll
-    for (int r = 0; r < RB; ++r) acc[r] = T(0);
-    for (int cg = it.c0; cg < it.c1; cg += 32) {
-        const int c = cg + lane;
-        T z[RB];
-        if (c < it.c1) {
-            const int dof = FWD ? iperm[F.iperm_off + c] : blist[F.bset_off + c];
-#pragma unroll
-            for (int r = 0; r < RB; ++r) z[r] = r < nrhs ? (T)w[dof + ldw * r] : T(0);
-        } else {
-#pragma unroll
-            for (int r = 0; r < RB; ++r) z[r] = T(0);
-        }
-        T m[32];
-        const T *col = M + i + (long)F.n * (colbase + cg);
-#pragma unroll
-        for (int q = 0; q < 32; ++q) m[q] = (rowok && cg + q < it.c1) ? col[(long)F.n * q] : T(0);
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-#pragma unroll
-            for (int r = 0; r < RB; ++r) acc[r] = fma(m[q], __shfl_sync(0xffffffffu, z[r], q), acc[r]);
-        }
-    }
+    apply_item_sums<T, RB, FWD>(it, F, arena, iperm, blist, prm->w, prm->ldw, prm->nrhs, acc);
+    pdl_wait_prev();   // (an item without columns has not waited yet)
     if (it.nchunk > 1) {
         T *mine = reinterpret_cast<T *>(part) + (long)item * 32 * RB;
 #pragma unroll
@@ -97,20 +144,39 @@ __global__ void __launch_bounds__(AP_NT) k_apply(const ApplyItem *__restrict__ i
         }
         if (lane == 0) tickets[it.tile] = 0;   // ready for the next apply
     }
-    if (!rowok) return;
-#pragma unroll
-    for (int r = 0; r < RB; ++r) {
-        if (r >= nrhs) break;
-        const double y = (double)acc[r];
-        if (FWD) {
-            if (i < F.ni)
-                tv[ilist[F.iset_off + i] + ldt * r] = y;
-            else
-                w[blist[F.bset_off + i - F.ni] + ldw * r] += y;
-        } else {
-            const int dof = ilist[F.iset_off + i];
-            w[dof + ldw * r] = tv[dof + ldt * r] - y;
+    apply_item_store<T, RB, FWD>(it, F, ilist, blist, prm->w, prm->ldw, prm->tv, prm->ldt, prm->nrhs, acc);
+}
+
+// The deepest levels as one launch: CTA s walks the stages of subtree s (the
+// fronts below its root in stage nst - 1), deepest stage first forward and
+// root first backward, its eight warps taking the stage's items (one 32-row
+// tile, every column) and a block barrier between stages.  Subtrees hold
+// disjoint dofs (DG dofs belong to elements), so the CTAs never meet; inside
+// one, the barrier orders a stage's writes of x before the next stage's reads.
+template <class T, int RB, bool FWD>
+__global__ void __launch_bounds__(AP_NT) k_apply_sub(const ApplyItem *__restrict__ items, const int *__restrict__ off,
+                                                   int nst, const FrontDev *__restrict__ fr, const T *__restrict__ arena,
+                                                   const int *__restrict__ iperm, const int *__restrict__ ilist,
+                                                   const int *__restrict__ blist, const ApplyParams *__restrict__ prm) {
+    pdl_launch_next();
+    const int sub = blockIdx.x, warp = threadIdx.x >> 5;
+    double *w = prm->w;
+    double *tv = prm->tv;
+    const long ldw = prm->ldw, ldt = prm->ldt;
+    const int nrhs = prm->nrhs;
+    for (int l = 0; l < nst; ++l) {
+        const int q = FWD ? l : nst - 1 - l;
+        const int b = off[sub * (nst + 1) + q], e = off[sub * (nst + 1) + q + 1];
+        for (int k = b + warp; k < e; k += AP_WPB) {
+            const ApplyItem it = items[k];
+            const FrontDev F = fr[it.front];
+            T acc[RB];
+            apply_item_sums<T, RB, FWD>(it, F, arena, iperm, blist, w, ldw, nrhs, acc);
+            pdl_wait_prev();
+            apply_item_store<T, RB, FWD>(it, F, ilist, blist, w, ldw, tv, ldt, nrhs, acc);
         }
+        pdl_wait_prev();   // warps without items
+        __syncthreads();
     }
 }
 
@@ -120,6 +186,7 @@ __global__ void k_apply_set(ApplyParams *d, ApplyParams v) {
 
 // w = x (every right-hand side), skipped when they alias
 __global__ void k_apply_copyin(const ApplyParams *__restrict__ prm, long N) {
+    pdl_launch_next();
     const double *x = prm->x;
     double *w = prm->w;
     if (x == w) return;
@@ -130,35 +197,73 @@ __global__ void k_apply_copyin(const ApplyParams *__restrict__ prm, long N) {
     }
 }
 
+// A launch that may begin while the previous kernel on the stream runs (the
+// kernel waits for it with griddepcontrol.wait before touching its output).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(AP_NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // The whole sweep (copy-in, forward levels, top block, backward levels) as
-// one kernel sequence on stream s; parameters come from f->d_aparams.
+// one kernel sequence on stream s, each launch overlapping the previous one's
+// tail (launch_pdl); parameters come from f->d_aparams.
 template <class T, int RB> static int record_sweep(const hss_factor_t *f, cudaStream_t s, int &nk) {
     const T *arena = f->arena_ptr<T>();
     const ApplyParams *prm = f->d_aparams.as<ApplyParams>();
     nk = 0;
-    k_apply_copyin<<<2 * 152, 256, 0, s>>>(prm, f->ndof);
+    k_apply_copyin<<<2 * device_sms(), 256, 0, s>>>(prm, f->ndof);
     ++nk;
+    cudaError_t e = cudaSuccess;
+    auto sub = [&](bool fwd) {
+        if (f->sub_nst == 0 || e != cudaSuccess) return;
+        const int *il = f->tree->d_iset.as<int>(), *bl = f->tree->d_bset.as<int>();
+        if (fwd)
+            e = launch_pdl(k_apply_sub<T, RB, true>, f->sub_n, s, (const ApplyItem *)f->d_sub_fwd,
+                           (const int *)f->d_sub_off_fwd, f->sub_nst, (const FrontDev *)f->d_sub_fronts, arena,
+                           (const int *)f->d_iperm.as<int>(), il, bl, prm);
+        else
+            e = launch_pdl(k_apply_sub<T, RB, false>, f->sub_n, s, (const ApplyItem *)f->d_sub_bwd,
+                           (const int *)f->d_sub_off_bwd, f->sub_nst, (const FrontDev *)f->d_sub_fronts, arena,
+                           (const int *)f->d_iperm.as<int>(), il, bl, prm);
+        ++nk;
+    };
     for (int pass = 0; pass < 2; ++pass) {
         const bool fwd = pass == 0;
-        for (size_t q = 0; q < f->apply.size(); ++q) {
-            const ApplyStage &st = fwd ? f->apply[q] : f->apply[f->apply.size() - 1 - q];
+        if (fwd) sub(true);
+        for (size_t k = 0; k < f->apply.size(); ++k) {
+            const size_t q = fwd ? k : f->apply.size() - 1 - k;
+            if ((int)q < f->sub_nst) continue;   // in the subtree launch
+            const ApplyStage &st = f->apply[q];
             const int *ilist = st.top ? f->d_topset.as<int>() : f->tree->d_iset.as<int>();
             const int nt = fwd ? st.nfwd : st.nbwd;
             if (nt == 0) continue;
             const ApplyItem *itm = fwd ? st.d_fwd : st.d_bwd;
             double *part = f->d_apart.as<double>() + (fwd ? st.part_fwd : st.part_bwd) * 32 * APPLY_RB;
             int *tk = f->d_tickets.as<int>() + (fwd ? st.tk_fwd : st.tk_bwd);
+            if (e != cudaSuccess) break;
             if (fwd)
-                k_apply<T, RB, true><<<cdiv(nt, AP_WPB), AP_NT, 0, s>>>(itm, nt, st.d_fronts, arena,
-                                                                        f->d_iperm.as<int>(), ilist,
-                                                                        f->tree->d_bset.as<int>(), prm, part, tk);
+                e = launch_pdl(k_apply<T, RB, true>, cdiv(nt, AP_WPB), s, itm, nt, (const FrontDev *)st.d_fronts,
+                               arena, (const int *)f->d_iperm.as<int>(), ilist, (const int *)f->tree->d_bset.as<int>(),
+                               prm, part, tk);
             else
-                k_apply<T, RB, false><<<cdiv(nt, AP_WPB), AP_NT, 0, s>>>(itm, nt, st.d_fronts, arena,
-                                                                         f->d_iperm.as<int>(), ilist,
-                                                                         f->tree->d_bset.as<int>(), prm, part, tk);
+                e = launch_pdl(k_apply<T, RB, false>, cdiv(nt, AP_WPB), s, itm, nt, (const FrontDev *)st.d_fronts,
+                               arena, (const int *)f->d_iperm.as<int>(), ilist, (const int *)f->tree->d_bset.as<int>(),
+                               prm, part, tk);
             ++nk;
         }
+        if (!fwd) sub(false);
     }
+    if (e != cudaSuccess) return cuda_fail(e, "apply sweep launch");
     HSS_CHECK_LAUNCH("apply sweep");
     return HSS_OK;
 }
@@ -213,6 +318,65 @@ int pack_apply(hss_factor_t *F, cudaStream_t s) {
         bytes += al(sizeof(FrontDev) * st.h_fronts.size()) + al(sizeof(ApplyItem) * st.nfwd) +
                  al(sizeof(ApplyItem) * st.nbwd);
     }
+    // subtree part: root stage = the shallowest stage (below the top block)
+    // with at least APPLY_SUB_MIN fronts; every front of the stages up to it
+    // belongs to the subtree of its ancestor in the root stage
+    int qr = -1;
+    for (size_t q = 0; q < nst; ++q) {
+        if (F->apply[q].top) break;
+        if (F->apply[q].nfronts >= APPLY_SUB_MIN) qr = (int)q;
+    }
+    std::vector<FrontDev> sfr;
+    std::vector<ApplyItem> sit[2];
+    std::vector<int> soff[2];
+    F->sub_nst = 0;
+    F->sub_n = 0;
+    if (qr >= 1) {
+        const hss_tree *t = F->tree;
+        const int nsub = (int)F->apply[qr].h_fronts.size();
+        const int root_level = t->level[F->apply[qr].h_fronts[0].box];
+        std::unordered_map<int, int> sub_of_root;
+        for (int f = 0; f < nsub; ++f) sub_of_root[F->apply[qr].h_fronts[f].box] = f;
+        // per subtree and stage, its fronts
+        std::vector<std::vector<int>> lists((size_t)nsub * (qr + 1));
+        for (int q = 0; q <= qr; ++q) {
+            const ApplyStage &st = F->apply[q];
+            for (int f = 0; f < (int)st.h_fronts.size(); ++f) {
+                int b = st.h_fronts[f].box;
+                while (b >= 0 && t->level[b] > root_level) b = t->parent[b];
+                const auto it = sub_of_root.find(b);
+                if (it == sub_of_root.end()) {   // not below a root (cannot happen in a box tree)
+                    qr = -1;
+                    break;
+                }
+                lists[(size_t)it->second * (qr + 1) + q].push_back((int)sfr.size());
+                sfr.push_back(st.h_fronts[f]);
+            }
+            if (qr < 0) break;
+        }
+        if (qr >= 1) {
+            for (int pass = 0; pass < 2; ++pass) {
+                soff[pass].assign((size_t)nsub * (qr + 2), 0);
+                for (int sb = 0; sb < nsub; ++sb)
+                    for (int q = 0; q <= qr; ++q) {
+                        soff[pass][(size_t)sb * (qr + 2) + q] = (int)sit[pass].size();
+                        for (int fi : lists[(size_t)sb * (qr + 1) + q]) {
+                            const FrontDev &d = sfr[fi];
+                            if (d.ni == 0) continue;
+                            const int nrows = pass == 0 ? d.n : d.ni, ncols = pass == 0 ? d.ni : d.nb;
+                            for (int r0 = 0; r0 < nrows; r0 += 32)
+                                sit[pass].push_back({fi, r0, 0, ncols, -1, (int)sit[pass].size(), 1});
+                        }
+                        soff[pass][(size_t)sb * (qr + 2) + q + 1] = (int)sit[pass].size();
+                    }
+            }
+            F->sub_nst = qr + 1;
+            F->sub_n = nsub;
+            bytes += al(sizeof(FrontDev) * sfr.size()) + al(sizeof(ApplyItem) * sit[0].size()) +
+                     al(sizeof(ApplyItem) * sit[1].size()) + al(sizeof(int) * soff[0].size()) +
+                     al(sizeof(int) * soff[1].size());
+        }
+    }
     // every stage's fronts and work items in one device allocation
     std::vector<char> pack(std::max(bytes, (size_t)1));
     int rc;
@@ -231,6 +395,13 @@ int pack_apply(hss_factor_t *F, cudaStream_t s) {
         st.d_fwd = reinterpret_cast<ApplyItem *>(put(items[2 * q].data(), sizeof(ApplyItem) * st.nfwd));
         st.d_bwd = reinterpret_cast<ApplyItem *>(put(items[2 * q + 1].data(), sizeof(ApplyItem) * st.nbwd));
     }
+    if (F->sub_nst > 0) {
+        F->d_sub_fronts = reinterpret_cast<FrontDev *>(put(sfr.data(), sizeof(FrontDev) * sfr.size()));
+        F->d_sub_fwd = reinterpret_cast<ApplyItem *>(put(sit[0].data(), sizeof(ApplyItem) * sit[0].size()));
+        F->d_sub_bwd = reinterpret_cast<ApplyItem *>(put(sit[1].data(), sizeof(ApplyItem) * sit[1].size()));
+        F->d_sub_off_fwd = reinterpret_cast<int *>(put(soff[0].data(), sizeof(int) * soff[0].size()));
+        F->d_sub_off_bwd = reinterpret_cast<int *>(put(soff[1].data(), sizeof(int) * soff[1].size()));
+    }
     HSS_CUDA(cudaMemcpyAsync(base, pack.data(), pack.size(), cudaMemcpyHostToDevice, s));
     if ((rc = F->d_apart.alloc(sizeof(double) * 32 * APPLY_RB * std::max(part_total, 1L))) ||
         (rc = F->d_tickets.alloc(sizeof(int) * std::max(tk_total, 1))))
@@ -247,7 +418,7 @@ template <class T> static int timed_sweep(const hss_factor_t *f, cudaStream_t s,
     const T *arena = f->arena_ptr<T>();
     const ApplyParams *prm = f->d_aparams.as<ApplyParams>();
     const size_t nst = f->apply.size();
-    k_apply_copyin<<<2 * 152, 256, 0, s>>>(prm, f->ndof);
+    k_apply_copyin<<<2 * device_sms(), 256, 0, s>>>(prm, f->ndof);
     for (int pass = 0; pass < 2; ++pass) {
         const bool fwd = pass == 0;
         for (size_t k = 0; k < nst; ++k) {

@@ -10,6 +10,7 @@ namespace hssnd {
 constexpr int APPLY_ROWS = 32;
 
 constexpr int APPLY_CHUNK = 64;   // columns per warp work item of the apply
+constexpr int APPLY_SUB_MIN = 256;   // fronts of the level that roots the apply's subtrees (one CTA each)
 
 struct ApplyItem {
     int front;        // stage-local front index
@@ -113,6 +114,13 @@ struct hss_factor_t {
     hssnd::DevBuf d_apart;       // partial sums of split apply tiles (items x 32 x 4)
     hssnd::DevBuf d_tickets;     // one ticket counter per split tile
     hssnd::DevBuf apply_buf;     // fronts and work items of every apply stage, one allocation
+    // subtree part of the apply: stages [0, sub_nst) (the deepest levels) run
+    // as one launch per direction, one CTA per subtree rooted in stage
+    // sub_nst - 1; items and per-(subtree, stage) offsets live in apply_buf
+    int sub_nst = 0, sub_n = 0;
+    hssnd::FrontDev *d_sub_fronts = nullptr;
+    hssnd::ApplyItem *d_sub_fwd = nullptr, *d_sub_bwd = nullptr;
+    int *d_sub_off_fwd = nullptr, *d_sub_off_bwd = nullptr;
     // batched factor (hss_factor_batched): device copy of the block-diagonal
     // union of the instances' matrices, used by the batched solver
     int batched = 0;
