@@ -24,14 +24,6 @@ namespace hssnd {
 constexpr int AP_NT = 256;
 constexpr int AP_WPB = AP_NT / 32;   // warps (work items) per CTA
 
-// Programmatic dependent launch: the sweep's kernels are launched while the
-// previous one still runs; each lets the next one launch once its own CTAs
-// are all running, reads what the previous kernel does not write (work
-// items, fronts, gather indices, the factor), then waits for the previous
-// kernel to complete before it reads or writes the vectors.  Without the
-// launch attribute both instructions return at once.
-__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // One warp per work item = (front, 32-row tile, column chunk of at most
 // APPLY_CHUNK columns).  Lane l owns row row0 + l; x is gathered one value per
@@ -197,23 +189,6 @@ __global__ void k_apply_copyin(const ApplyParams *__restrict__ prm, long N) {
     }
 }
 
-// A launch that may begin while the previous kernel on the stream runs (the
-// kernel waits for it with griddepcontrol.wait before touching its output).
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, cudaStream_t s, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(AP_NT);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
 // The whole sweep (copy-in, forward levels, top block, backward levels) as
 // one kernel sequence on stream s, each launch overlapping the previous one's
 // tail (launch_pdl); parameters come from f->d_aparams.
@@ -228,11 +203,11 @@ template <class T, int RB> static int record_sweep(const hss_factor_t *f, cudaSt
         if (f->sub_nst == 0 || e != cudaSuccess) return;
         const int *il = f->tree->d_iset.as<int>(), *bl = f->tree->d_bset.as<int>();
         if (fwd)
-            e = launch_pdl(k_apply_sub<T, RB, true>, f->sub_n, s, (const ApplyItem *)f->d_sub_fwd,
+            e = launch_pdl(k_apply_sub<T, RB, true>, dim3(f->sub_n), dim3(AP_NT), s, (const ApplyItem *)f->d_sub_fwd,
                            (const int *)f->d_sub_off_fwd, f->sub_nst, (const FrontDev *)f->d_sub_fronts, arena,
                            (const int *)f->d_iperm.as<int>(), il, bl, prm);
         else
-            e = launch_pdl(k_apply_sub<T, RB, false>, f->sub_n, s, (const ApplyItem *)f->d_sub_bwd,
+            e = launch_pdl(k_apply_sub<T, RB, false>, dim3(f->sub_n), dim3(AP_NT), s, (const ApplyItem *)f->d_sub_bwd,
                            (const int *)f->d_sub_off_bwd, f->sub_nst, (const FrontDev *)f->d_sub_fronts, arena,
                            (const int *)f->d_iperm.as<int>(), il, bl, prm);
         ++nk;
@@ -252,11 +227,11 @@ template <class T, int RB> static int record_sweep(const hss_factor_t *f, cudaSt
             int *tk = f->d_tickets.as<int>() + (fwd ? st.tk_fwd : st.tk_bwd);
             if (e != cudaSuccess) break;
             if (fwd)
-                e = launch_pdl(k_apply<T, RB, true>, cdiv(nt, AP_WPB), s, itm, nt, (const FrontDev *)st.d_fronts,
+                e = launch_pdl(k_apply<T, RB, true>, dim3(cdiv(nt, AP_WPB)), dim3(AP_NT), s, itm, nt, (const FrontDev *)st.d_fronts,
                                arena, (const int *)f->d_iperm.as<int>(), ilist, (const int *)f->tree->d_bset.as<int>(),
                                prm, part, tk);
             else
-                e = launch_pdl(k_apply<T, RB, false>, cdiv(nt, AP_WPB), s, itm, nt, (const FrontDev *)st.d_fronts,
+                e = launch_pdl(k_apply<T, RB, false>, dim3(cdiv(nt, AP_WPB)), dim3(AP_NT), s, itm, nt, (const FrontDev *)st.d_fronts,
                                arena, (const int *)f->d_iperm.as<int>(), ilist, (const int *)f->tree->d_bset.as<int>(),
                                prm, part, tk);
             ++nk;

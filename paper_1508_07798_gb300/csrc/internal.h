@@ -32,6 +32,30 @@ int cuda_fail(cudaError_t e, const char *what);
 // and kernel (thread-safe); returns the runtime's error code.
 cudaError_t func_smem_once(const void *func, int bytes);
 int device_sms();   // multiprocessors of the current device (cached per device)
+
+// Programmatic dependent launch.  A kernel launched by launch_pdl may begin
+// while the previous kernel on its stream still runs: it calls
+// pdl_launch_next() to let the kernel after it launch early, reads only what
+// the previous kernel does not write, and calls pdl_wait_prev() (which returns
+// once the previous kernel has completed and its writes are visible) before
+// it reads or writes that kernel's output.  Launched without the attribute,
+// both calls return at once.
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 #define HSS_SMEM(kernel, bytes)                                                            \
     do {                                                                                   \
         cudaError_t _e = ::hssnd::func_smem_once((const void *)(kernel), (int)(bytes));    \

@@ -20,6 +20,8 @@ constexpr int DOT_BLOCKS = 304;   // 2 x 152 SMs
 __global__ void k_spmv(int nb, int bs, const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                        const double *__restrict__ val, const double *__restrict__ x, long ldx,
                        double *__restrict__ y, long ldy, int nrhs) {
+    pdl_launch_next();
+    pdl_wait_prev();
     long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long N = (long)nb * bs;
     if (g >= N * nrhs) return;
@@ -43,6 +45,8 @@ constexpr int SPMV_RB = 8;
 __global__ void k_spmv_multi(int nb, int bs, const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                              const double *__restrict__ val, const double *__restrict__ x, long ldx,
                              double *__restrict__ y, long ldy, int nrhs) {
+    pdl_launch_next();
+    pdl_wait_prev();
     long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long N = (long)nb * bs;
     if (row >= N) return;
@@ -71,6 +75,8 @@ __global__ void k_spmv_multi(int nb, int bs, const int *__restrict__ row_ptr, co
 // partial[b * KRY_MAXM + q] = sum over this CTA's rows of V(:,q) . w, q < nq
 __global__ void k_dots(const double *__restrict__ V, long ldv, int nq, const double *__restrict__ w, long N,
                        double *__restrict__ partial) {
+    pdl_launch_next();
+    pdl_wait_prev();
     __shared__ double sh[KRY_NT / 32][KRY_MAXM + 1];
     double acc[KRY_MAXM];
 #pragma unroll
@@ -100,6 +106,8 @@ __global__ void k_dots(const double *__restrict__ V, long ldv, int nq, const dou
 // out[q] (= or +=) sum of the partials, q < nq, one warp per q, fixed order.
 __global__ void k_dots_final(const double *__restrict__ partial, int nblk, int nq, double *__restrict__ out,
                              int accumulate) {
+    pdl_launch_next();
+    pdl_wait_prev();
     int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (q >= nq) return;
     double s = 0.0;
@@ -111,6 +119,8 @@ __global__ void k_dots_final(const double *__restrict__ partial, int nblk, int n
 // w -= V(:, 0:nq) h
 __global__ void k_sub_Vh(const double *__restrict__ V, long ldv, int nq, const double *__restrict__ h,
                          double *__restrict__ w, long N) {
+    pdl_launch_next();
+    pdl_wait_prev();
     __shared__ double hs[KRY_MAXM];
     if (threadIdx.x < nq) hs[threadIdx.x] = h[threadIdx.x];
     __syncthreads();
@@ -124,17 +134,23 @@ __global__ void k_sub_Vh(const double *__restrict__ V, long ldv, int nq, const d
 // y = alpha * x / s[0] (s on the device; s[0] == 0 leaves y = 0)
 __global__ void k_scale_by(const double *__restrict__ x, const double *__restrict__ s, double *__restrict__ y,
                            long N) {
+    pdl_launch_next();
+    pdl_wait_prev();
     double d = s[0];
     double inv = d != 0.0 ? 1.0 / d : 0.0;
     for (long i = (long)blockIdx.x * KRY_NT + threadIdx.x; i < N; i += (long)gridDim.x * KRY_NT) y[i] = x[i] * inv;
 }
 
 __global__ void k_sqrt_into(const double *__restrict__ s2, double *__restrict__ out) {
+    pdl_launch_next();
+    pdl_wait_prev();
     if (threadIdx.x == 0) out[0] = sqrt(s2[0]);
 }
 
 // r = b - r (r holds A x)
 __global__ void k_resid(const double *__restrict__ b, double *__restrict__ r, long N) {
+    pdl_launch_next();
+    pdl_wait_prev();
     for (long i = (long)blockIdx.x * KRY_NT + threadIdx.x; i < N; i += (long)gridDim.x * KRY_NT) r[i] = b[i] - r[i];
 }
 
@@ -142,6 +158,8 @@ __global__ void k_resid(const double *__restrict__ b, double *__restrict__ r, lo
 // State layout: H (m+1) x m column-major, cs[m], sn[m], g[m+1]; est = |g[j+1]|.
 __global__ void k_givens(double *__restrict__ H, int m, int j, double *__restrict__ cs, double *__restrict__ sn,
                          double *__restrict__ g, double *__restrict__ est) {
+    pdl_launch_next();
+    pdl_wait_prev();
     if (threadIdx.x != 0) return;
     double *h = H + (long)(m + 1) * j;
     for (int i = 0; i < j; ++i) {
@@ -164,6 +182,8 @@ __global__ void k_givens(double *__restrict__ H, int m, int j, double *__restric
 // y = R^-1 g for the leading jend x jend triangle of H
 __global__ void k_backsolve(const double *__restrict__ H, int m, int jend, const double *__restrict__ g,
                             double *__restrict__ y) {
+    pdl_launch_next();
+    pdl_wait_prev();
     if (threadIdx.x != 0) return;
     for (int i = jend - 1; i >= 0; --i) {
         double s = g[i];
@@ -175,6 +195,8 @@ __global__ void k_backsolve(const double *__restrict__ H, int m, int jend, const
 // x += Z(:, 0:jend) y
 __global__ void k_update_x(const double *__restrict__ Z, long ldz, int jend, const double *__restrict__ y,
                            double *__restrict__ x, long N) {
+    pdl_launch_next();
+    pdl_wait_prev();
     __shared__ double ys[KRY_MAXM];
     if (threadIdx.x < jend) ys[threadIdx.x] = y[threadIdx.x];
     __syncthreads();
@@ -186,6 +208,8 @@ __global__ void k_update_x(const double *__restrict__ Z, long ldz, int jend, con
 }
 
 __global__ void k_init_g(double *__restrict__ g, int m, const double *__restrict__ beta) {
+    pdl_launch_next();
+    pdl_wait_prev();
     for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = i == 0 ? beta[0] : 0.0;
 }
 
@@ -210,11 +234,11 @@ int spmv(const hss_bsr *A, int nrhs, const double *x, long ldx, double *y, long 
     if (tot == 0) return HSS_OK;
     if (nrhs == 1) {
         HSS_PROF("spmv", s, spmv_bytes(A, nrhs));
-        k_spmv<<<cdiv(tot, KRY_NT), KRY_NT, 0, s>>>(A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy, nrhs);
+        HSS_CUDA(launch_pdl(k_spmv, dim3(cdiv(tot, KRY_NT)), dim3(KRY_NT), s, A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy, nrhs));
     } else {
         HSS_PROF("spmv", s, spmv_bytes(A, nrhs));
-        k_spmv_multi<<<cdiv(N, KRY_NT), KRY_NT, 0, s>>>(A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy,
-                                                       nrhs);
+        HSS_CUDA(launch_pdl(k_spmv_multi, dim3(cdiv(N, KRY_NT)), dim3(KRY_NT), s, A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy,
+                                                       nrhs));
     }
     HSS_CHECK_LAUNCH("k_spmv");
     return HSS_OK;
@@ -246,8 +270,8 @@ static thread_local std::vector<std::vector<double>> g_hist;
 
 // sum_i v_i w_i into out[0] (deterministic two-pass)
 static int dot1(const double *v, const double *w, long N, double *part, double *out, int acc, cudaStream_t s) {
-    { HSS_PROF("dots", s); k_dots<<<DOT_BLOCKS, KRY_NT, 0, s>>>(v, N, 1, w, N, part); }
-    { HSS_PROF("dots_final", s); k_dots_final<<<1, 32, 0, s>>>(part, DOT_BLOCKS, 1, out, acc); }
+    { HSS_PROF("dots", s); HSS_CUDA(launch_pdl(k_dots, dim3(DOT_BLOCKS), dim3(KRY_NT), s, v, N, 1, w, N, part)); }
+    { HSS_PROF("dots_final", s); HSS_CUDA(launch_pdl(k_dots_final, dim3(1), dim3(32), s, part, DOT_BLOCKS, 1, out, acc)); }
     HSS_CHECK_LAUNCH("dot");
     return HSS_OK;
 }
@@ -263,7 +287,7 @@ static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, doub
     double host[2];
     // ||b||
     if ((rc = dot1(b, b, N, part, sc + 0, 0, s))) return rc;
-    { HSS_PROF("sqrt_into", s); k_sqrt_into<<<1, 32, 0, s>>>(sc + 0, sc + 1); }
+    { HSS_PROF("sqrt_into", s); HSS_CUDA(launch_pdl(k_sqrt_into, dim3(1), dim3(32), s, sc + 0, sc + 1)); }
     HSS_CUDA(cudaMemcpyAsync(host, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     HSS_CUDA(cudaStreamSynchronize(s));
     const double bnorm = host[0];
@@ -278,9 +302,9 @@ static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, doub
     while (true) {
         // r = b - A x, beta = ||r||
         if ((rc = spmv(A, 1, x, N, r, N, s))) return rc;
-        { HSS_PROF("resid", s); k_resid<<<gb, KRY_NT, 0, s>>>(b, r, N); }
+        { HSS_PROF("resid", s); HSS_CUDA(launch_pdl(k_resid, dim3(gb), dim3(KRY_NT), s, b, r, N)); }
         if ((rc = dot1(r, r, N, part, sc + 2, 0, s))) return rc;
-        { HSS_PROF("sqrt_into", s); k_sqrt_into<<<1, 32, 0, s>>>(sc + 2, sc + 3); }
+        { HSS_PROF("sqrt_into", s); HSS_CUDA(launch_pdl(k_sqrt_into, dim3(1), dim3(32), s, sc + 2, sc + 3)); }
         HSS_CUDA(cudaMemcpyAsync(host, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
         HSS_CUDA(cudaStreamSynchronize(s));
         double beta = host[0];
@@ -290,8 +314,8 @@ static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, doub
             return HSS_OK;
         }
         if (iters >= o.maxit) return HSS_OK;
-        { HSS_PROF("scale_by", s); k_scale_by<<<gb, KRY_NT, 0, s>>>(r, sc + 3, V, N); }
-        { HSS_PROF("init_g", s); k_init_g<<<1, 64, 0, s>>>(K.g.as<double>(), m, sc + 3); }
+        { HSS_PROF("scale_by", s); HSS_CUDA(launch_pdl(k_scale_by, dim3(gb), dim3(KRY_NT), s, r, sc + 3, V, N)); }
+        { HSS_PROF("init_g", s); HSS_CUDA(launch_pdl(k_init_g, dim3(1), dim3(64), s, K.g.as<double>(), m, sc + 3)); }
         HSS_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (m + 1) * m, s));
         int jend = 0;
         for (int j = 0; j < m; ++j) {
@@ -305,16 +329,16 @@ static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, doub
             double *hcol = H + (long)(m + 1) * j;
             // classical Gram-Schmidt, twice
             for (int pass = 0; pass < 2; ++pass) {
-                { HSS_PROF("dots", s); k_dots<<<gb, KRY_NT, 0, s>>>(V, N, j + 1, w, N, part); }
-                { HSS_PROF("dots_final", s); k_dots_final<<<1, 32 * (j + 1), 0, s>>>(part, gb, j + 1, pass ? K.y.as<double>() : hcol, 0); }
-                { HSS_PROF("sub_Vh", s); k_sub_Vh<<<gb, KRY_NT, 0, s>>>(V, N, j + 1, pass ? K.y.as<double>() : hcol, w, N); }
+                { HSS_PROF("dots", s); HSS_CUDA(launch_pdl(k_dots, dim3(gb), dim3(KRY_NT), s, V, N, j + 1, w, N, part)); }
+                { HSS_PROF("dots_final", s); HSS_CUDA(launch_pdl(k_dots_final, dim3(1), dim3(32 * (j + 1)), s, part, gb, j + 1, pass ? K.y.as<double>() : hcol, 0)); }
+                { HSS_PROF("sub_Vh", s); HSS_CUDA(launch_pdl(k_sub_Vh, dim3(gb), dim3(KRY_NT), s, V, N, j + 1, pass ? K.y.as<double>() : hcol, w, N)); }
             }
             // h += h2 (the second-pass coefficients, read as a one-block partial sum)
-            { HSS_PROF("dots_final", s); k_dots_final<<<1, 32 * (j + 1), 0, s>>>(K.y.as<double>(), 1, j + 1, hcol, 1); }
+            { HSS_PROF("dots_final", s); HSS_CUDA(launch_pdl(k_dots_final, dim3(1), dim3(32 * (j + 1)), s, K.y.as<double>(), 1, j + 1, hcol, 1)); }
             if ((rc = dot1(w, w, N, part, sc + 4, 0, s))) return rc;
-            { HSS_PROF("sqrt_into", s); k_sqrt_into<<<1, 32, 0, s>>>(sc + 4, hcol + j + 1); }
-            { HSS_PROF("scale_by", s); k_scale_by<<<gb, KRY_NT, 0, s>>>(w, hcol + j + 1, V + N * (j + 1), N); }
-            { HSS_PROF("givens", s); k_givens<<<1, 32, 0, s>>>(H, m, j, K.cs.as<double>(), K.sn.as<double>(), K.g.as<double>(), sc + 5); }
+            { HSS_PROF("sqrt_into", s); HSS_CUDA(launch_pdl(k_sqrt_into, dim3(1), dim3(32), s, sc + 4, hcol + j + 1)); }
+            { HSS_PROF("scale_by", s); HSS_CUDA(launch_pdl(k_scale_by, dim3(gb), dim3(KRY_NT), s, w, hcol + j + 1, V + N * (j + 1), N)); }
+            { HSS_PROF("givens", s); HSS_CUDA(launch_pdl(k_givens, dim3(1), dim3(32), s, H, m, j, K.cs.as<double>(), K.sn.as<double>(), K.g.as<double>(), sc + 5)); }
             HSS_CHECK_LAUNCH("arnoldi step");
             HSS_CUDA(cudaMemcpyAsync(host, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
             HSS_CUDA(cudaStreamSynchronize(s));
@@ -324,8 +348,8 @@ static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, doub
             hist.push_back(est);
             if (est <= o.rtol || iters >= o.maxit || !(est == est)) break;
         }
-        { HSS_PROF("backsolve", s); k_backsolve<<<1, 32, 0, s>>>(H, m, jend, K.g.as<double>(), K.y.as<double>()); }
-        { HSS_PROF("update_x", s); k_update_x<<<gb, KRY_NT, 0, s>>>(Z, N, jend, K.y.as<double>(), x, N); }
+        { HSS_PROF("backsolve", s); HSS_CUDA(launch_pdl(k_backsolve, dim3(1), dim3(32), s, H, m, jend, K.g.as<double>(), K.y.as<double>())); }
+        { HSS_PROF("update_x", s); HSS_CUDA(launch_pdl(k_update_x, dim3(gb), dim3(KRY_NT), s, Z, N, jend, K.y.as<double>(), x, N)); }
         HSS_CHECK_LAUNCH("fgmres update");
     }
 }
