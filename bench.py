@@ -334,7 +334,7 @@ def bench_ours(args, rank, world):
         # the factorization's host side, from the last uninstrumented step
         hinfo = last[1].info()
         host = dict(syncs=hinfo["host_syncs"], sync_wait_ms=hinfo["host_sync_ms"], call_ms=hinfo["host_ms"],
-                    work_ms=hinfo["host_ms"] - hinfo["host_sync_ms"])
+                    work_ms=hinfo["host_ms"] - hinfo["host_sync_ms"], idle_after_readback_ms=hinfo["host_gap_ms"])
         # pass 2: the same steps with every kernel launch bracketed by CUDA events
         hssnd.profile_reset()
         hssnd.profile_enable(True)

@@ -227,6 +227,9 @@ typedef struct hss_factor_info {
     double host_sync_ms;    /* host time spent waiting in them */
     double host_ms;         /* host time of the whole call; host_ms - host_sync_ms is the host's
                                own work (planning, launches), during which the device may idle */
+    double host_gap_ms;     /* host time from each read-back to the next kernel launch: the
+                               device has no work queued meanwhile (the last read-back of the
+                               call, with nothing after it, counts toward the next call) */
 } hss_factor_info;
 int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info);
 

@@ -203,11 +203,11 @@ template <class T, int RB> static int record_sweep(const hss_factor_t *f, cudaSt
         if (f->sub_nst == 0 || e != cudaSuccess) return;
         const int *il = f->tree->d_iset.as<int>(), *bl = f->tree->d_bset.as<int>();
         if (fwd)
-            e = launch_pdl(k_apply_sub<T, RB, true>, dim3(f->sub_n), dim3(AP_NT), s, (const ApplyItem *)f->d_sub_fwd,
+            e = launch_pdl(k_apply_sub<T, RB, true>, dim3(f->sub_n), dim3(AP_NT), 0, s, (const ApplyItem *)f->d_sub_fwd,
                            (const int *)f->d_sub_off_fwd, f->sub_nst, (const FrontDev *)f->d_sub_fronts, arena,
                            (const int *)f->d_iperm.as<int>(), il, bl, prm);
         else
-            e = launch_pdl(k_apply_sub<T, RB, false>, dim3(f->sub_n), dim3(AP_NT), s, (const ApplyItem *)f->d_sub_bwd,
+            e = launch_pdl(k_apply_sub<T, RB, false>, dim3(f->sub_n), dim3(AP_NT), 0, s, (const ApplyItem *)f->d_sub_bwd,
                            (const int *)f->d_sub_off_bwd, f->sub_nst, (const FrontDev *)f->d_sub_fronts, arena,
                            (const int *)f->d_iperm.as<int>(), il, bl, prm);
         ++nk;
@@ -227,11 +227,11 @@ template <class T, int RB> static int record_sweep(const hss_factor_t *f, cudaSt
             int *tk = f->d_tickets.as<int>() + (fwd ? st.tk_fwd : st.tk_bwd);
             if (e != cudaSuccess) break;
             if (fwd)
-                e = launch_pdl(k_apply<T, RB, true>, dim3(cdiv(nt, AP_WPB)), dim3(AP_NT), s, itm, nt, (const FrontDev *)st.d_fronts,
+                e = launch_pdl(k_apply<T, RB, true>, dim3(cdiv(nt, AP_WPB)), dim3(AP_NT), 0, s, itm, nt, (const FrontDev *)st.d_fronts,
                                arena, (const int *)f->d_iperm.as<int>(), ilist, (const int *)f->tree->d_bset.as<int>(),
                                prm, part, tk);
             else
-                e = launch_pdl(k_apply<T, RB, false>, dim3(cdiv(nt, AP_WPB)), dim3(AP_NT), s, itm, nt, (const FrontDev *)st.d_fronts,
+                e = launch_pdl(k_apply<T, RB, false>, dim3(cdiv(nt, AP_WPB)), dim3(AP_NT), 0, s, itm, nt, (const FrontDev *)st.d_fronts,
                                arena, (const int *)f->d_iperm.as<int>(), ilist, (const int *)f->tree->d_bset.as<int>(),
                                prm, part, tk);
             ++nk;

@@ -40,6 +40,7 @@ static int factor_readback(void *dst, const void *src, size_t bytes, cudaStream_
         F->host_syncs++;
         F->host_sync_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
+    prof_mark_readback();
     return e == cudaSuccess ? HSS_OK : cuda_fail(e, "device read-back");
 }
 
@@ -49,6 +50,8 @@ namespace {
 // comes from row_ptr[nb] on the device, so the host needs no read-back)
 __global__ void k_check_finite(const int *__restrict__ row_ptr, int nb, int bs2, const double *__restrict__ val,
                                int *__restrict__ flag) {
+    pdl_launch_next();
+    pdl_wait_prev();
     const long tot = (long)row_ptr[nb] * bs2;
     bool bad = false;
     for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += (long)gridDim.x * blockDim.x)
@@ -1555,7 +1558,9 @@ extern "C" int hss_factor(const hss_bsr *A, const hss_tree *tree, const hss_fact
     F->precision = o.precision;
     F->opts = o;
     const auto t0 = std::chrono::steady_clock::now();
+    const double gap0 = prof_readback_gap_ms();
     int rc = o.precision == HSS_FP32 ? factor_impl<float>(A, tree, o, s, F) : factor_impl<double>(A, tree, o, s, F);
+    F->host_gap_ms = prof_readback_gap_ms() - gap0;
     F->host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc) {
         cudaStreamSynchronize(s);
@@ -1588,6 +1593,7 @@ extern "C" int hss_factor_get_info(const hss_factor_t *f, hss_factor_info *info)
     info->host_syncs = f->host_syncs;
     info->host_sync_ms = f->host_sync_ms;
     info->host_ms = f->host_ms;
+    info->host_gap_ms = f->host_gap_ms;
     return HSS_OK;
 }
 

@@ -107,6 +107,7 @@ struct hss_factor_t {
     long host_syncs = 0;       // blocking read-backs of the factorization
     double host_sync_ms = 0;   // host time spent waiting in them
     double host_ms = 0;        // host time of the whole call
+    double host_gap_ms = 0;    // host time from each read-back to the next kernel launch (device idle)
     // captured apply sweeps (slot 0: one right-hand side, slot 1: blocks of APPLY_RB)
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_kernels[2] = {0, 0};

@@ -32,6 +32,8 @@ template <class T>
 __global__ void k_scatter_A(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                             const double *__restrict__ val, int bs, const StageElem *__restrict__ se, int nse,
                             const int *__restrict__ elem_slot, const FrontDev *__restrict__ fr, T *__restrict__ arena) {
+    pdl_launch_next();
+    pdl_wait_prev();
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (w >= nse) return;
@@ -55,6 +57,8 @@ __global__ void k_scatter_A(const int *__restrict__ row_ptr, const int *__restri
 }
 
 __global__ void k_set_slots(const StageElem *__restrict__ se, int nse, int *__restrict__ elem_slot, int value_is_index) {
+    pdl_launch_next();
+    pdl_wait_prev();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nse) elem_slot[se[i].elem] = value_is_index ? i : -1;
 }
@@ -122,6 +126,8 @@ __global__ void __launch_bounds__(PANEL_NT) k_gj_panel(const PanelJob *__restric
                                                     int *__restrict__ mws, int *__restrict__ piv,
                                                     int *__restrict__ rperm, const int *__restrict__ ilist,
                                                     int *__restrict__ iperm, int *__restrict__ status) {
+    pdl_launch_next();
+    pdl_wait_prev();
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ ArgMax<T> red[PANEL_NT / 32];
     __shared__ T rowj[PANEL_KB_MAX];
@@ -355,6 +361,8 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(const PanelJob *__restrict_
                                                         int *__restrict__ piv, int *__restrict__ rperm,
                                                         const int *__restrict__ ilist, int *__restrict__ iperm,
                                                         int *__restrict__ status) {
+    pdl_launch_next();
+    pdl_wait_prev();
     constexpr int NW = NT / 32;
     // steps per rotation group: fewer where the rows fill more of the register budget
     constexpr int DREGS = R * KB * (int)sizeof(T) / 4;
@@ -577,6 +585,8 @@ __global__ void __launch_bounds__(NT) k_gj_panel_cl(const PanelJob *__restrict__
                                                        int *__restrict__ piv, int *__restrict__ rperm,
                                                        const int *__restrict__ ilist, int *__restrict__ iperm,
                                                        int *__restrict__ status) {
+    pdl_launch_next();
+    pdl_wait_prev();
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ ArgMax<T> red[NT / 32];
     __shared__ ArgMax<T> cand;        // this CTA's best candidate of the current step
@@ -753,6 +763,8 @@ __global__ void __launch_bounds__(256) k_gj_post(const PanelTile *__restrict__ t
                                              const FrontDev *__restrict__ fr, T *__restrict__ arena,
                                              T *__restrict__ aold_ws, const T *__restrict__ xws,
                                              const int *__restrict__ mws) {
+    pdl_launch_next();
+    pdl_wait_prev();
     __shared__ T Xs[PANEL_KB_MAX * PANEL_KB_MAX];
     __shared__ T old[64][PANEL_KB_MAX + 1];
     const PanelTile tl = tiles[blockIdx.x];
@@ -809,6 +821,8 @@ __global__ void __launch_bounds__(256) k_gj_block_post(const BlockTile *__restri
                                                    const PanelJob *__restrict__ jobs,
                                                    const FrontDev *__restrict__ fr, T *__restrict__ arena,
                                                    T *__restrict__ aold_ws, const int *__restrict__ mws) {
+    pdl_launch_next();
+    pdl_wait_prev();
     const BlockTile tl = tiles[blockIdx.x];
     const BlockJob B = bjobs[tl.bjob];
     const FrontDev F = fr[B.front];
@@ -843,11 +857,11 @@ template <class T>
 int launch_scatter_A(const hss_bsr *A, const StageElem *se, int nse, int *elem_slot, const FrontDev *fr, T *arena,
                      cudaStream_t s) {
     if (nse == 0) return HSS_OK;
-    { HSS_PROF("set_slots", s); k_set_slots<<<cdiv(nse, 256), 256, 0, s>>>(se, nse, elem_slot, 1); }
+    { HSS_PROF("set_slots", s); HSS_CUDA(launch_pdl(k_set_slots, dim3(cdiv(nse, 256)), dim3(256), 0, s, se, nse, elem_slot, 1)); }
     { HSS_PROF("scatter_A", s);
-    k_scatter_A<T><<<cdiv((long)nse * 32, 256), 256, 0, s>>>(A->row_ptr, A->col_idx, A->val, A->bs, se, nse,
-                                                             elem_slot, fr, arena); }
-    { HSS_PROF("set_slots", s); k_set_slots<<<cdiv(nse, 256), 256, 0, s>>>(se, nse, elem_slot, 0); }
+    HSS_CUDA(launch_pdl(k_scatter_A<T>, dim3(cdiv((long)nse * 32, 256)), dim3(256), 0, s, A->row_ptr, A->col_idx, A->val, A->bs, se, nse,
+                                                             elem_slot, fr, arena)); }
+    { HSS_PROF("set_slots", s); HSS_CUDA(launch_pdl(k_set_slots, dim3(cdiv(nse, 256)), dim3(256), 0, s, se, nse, elem_slot, 0)); }
     HSS_CHECK_LAUNCH("k_scatter_A");
     return HSS_OK;
 }
@@ -857,7 +871,7 @@ int launch_gj_block_post(const BlockTile *tiles, int ntiles, const BlockJob *bjo
                          const FrontDev *fr, T *arena, T *aold, const int *mws, cudaStream_t s) {
     if (ntiles == 0) return HSS_OK;
     HSS_PROF(sizeof(T) == 8 ? "gj_post_f64" : "gj_post_f32", s);
-    k_gj_block_post<T><<<ntiles, 256, 0, s>>>(tiles, bjobs, jobs, fr, arena, aold, mws);
+    HSS_CUDA(launch_pdl(k_gj_block_post<T>, dim3(ntiles), dim3(256), 0, s, tiles, bjobs, jobs, fr, arena, aold, mws));
     HSS_CHECK_LAUNCH("k_gj_block_post");
     return HSS_OK;
 }
@@ -867,7 +881,7 @@ int launch_gj_post(const PanelTile *tiles, int ntiles, const PanelJob *jobs, con
                    const T *xws, const int *mws, cudaStream_t s) {
     if (ntiles == 0) return HSS_OK;
     HSS_PROF(sizeof(T) == 8 ? "gj_post_f64" : "gj_post_f32", s);
-    k_gj_post<T><<<ntiles, 256, 0, s>>>(tiles, jobs, fr, arena, aold, xws, mws);
+    HSS_CUDA(launch_pdl(k_gj_post<T>, dim3(ntiles), dim3(256), 0, s, tiles, jobs, fr, arena, aold, xws, mws));
     HSS_CHECK_LAUNCH("k_gj_post");
     return HSS_OK;
 }
@@ -876,8 +890,8 @@ template <class T, int KB, int R, int NT>
 static cudaError_t launch_reg(const PanelJob *jobs, int njobs, size_t smem, const FrontDev *fr, T *arena, T *xws,
                               int *mws, int *piv, int *rperm, const int *ilist, int *iperm, int *status,
                               cudaStream_t s) {
-    k_gj_panel_reg<T, KB, R, NT><<<njobs, NT, 0, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
-    return cudaGetLastError();
+    return launch_pdl(k_gj_panel_reg<T, KB, R, NT>, dim3(njobs), dim3(NT), 0, s, jobs, fr, arena, xws, mws, piv, rperm, ilist,
+                      iperm, status);
 }
 
 // Register panel for kb <= KB and rows <= R * NT: panels of at most 128 or 256
@@ -939,7 +953,7 @@ static cudaError_t launch_cl(const PanelJob *jobs, int njobs, size_t smem, const
     if (CL > 8 && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
         return e;
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CL;
     attr[0].val.clusterDim.y = 1;
@@ -957,6 +971,9 @@ static cudaError_t launch_cl(const PanelJob *jobs, int njobs, size_t smem, const
         if (e != cudaSuccess) return e;
         return nc > 0 ? cudaSuccess : cudaErrorInvalidClusterSize;
     }
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see launch_pdl
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kern, jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
 }
 
@@ -1055,7 +1072,8 @@ int launch_gj_panel(const PanelJob *jobs, int njobs, size_t smem, const FrontDev
     if (njobs == 0) return HSS_OK;
     HSS_SMEM(k_gj_panel<T>, PANEL_SMEM_MAX);
     HSS_PROF(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s, flops);
-    k_gj_panel<T><<<njobs, PANEL_NT, smem, s>>>(jobs, fr, arena, xws, mws, piv, rperm, ilist, iperm, status);
+    HSS_CUDA(launch_pdl(k_gj_panel<T>, dim3(njobs), dim3(PANEL_NT), smem, s, jobs, fr, arena, xws, mws, piv, rperm, ilist,
+                        iperm, status));
     HSS_CHECK_LAUNCH("k_gj_panel");
     return HSS_OK;
 }

@@ -14,6 +14,8 @@ constexpr int GT = 256;     // threads per CTA (16 x 16, 4 x 4 outputs each)
 
 template <class T>
 __global__ void __launch_bounds__(GT) k_gemm(const GemmDesc<T> *__restrict__ descs, const GemmTile *__restrict__ tiles) {
+    pdl_launch_next();
+    pdl_wait_prev();
     __shared__ T As[2][GK][GEMM_TM + 1];
     __shared__ T Bs[2][GK][GEMM_TN + 1];
     const GemmTile tl = tiles[blockIdx.x];
@@ -122,7 +124,7 @@ template <class T>
 int gemm_batched(const GemmDesc<T> *d_desc, const GemmTile *d_tiles, int ntiles, cudaStream_t s, double flops) {
     if (ntiles <= 0) return HSS_OK;
     HSS_PROF(sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", s, flops);
-    k_gemm<T><<<ntiles, GT, 0, s>>>(d_desc, d_tiles);
+    HSS_CUDA(launch_pdl(k_gemm<T>, dim3(ntiles), dim3(GT), 0, s, d_desc, d_tiles));
     HSS_CHECK_LAUNCH("k_gemm");
     return HSS_OK;
 }
@@ -141,6 +143,8 @@ void gemm_tiles_for(const GemmDesc<T> &d, int desc_index, std::vector<GemmTile> 
 // C = alpha * 0 + beta * C for a product with k = 0 (no descriptor, no
 // allocation; the same arithmetic as k_gemm with an empty K loop).
 __global__ void k_gemm_k0(float *__restrict__ C, int ldc, int m, int n, float alpha, float beta) {
+    pdl_launch_next();
+    pdl_wait_prev();
     const long tot = (long)m * n;
     for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += (long)gridDim.x * blockDim.x) {
         const int i = (int)(g % m), j = (int)(g / m);
@@ -154,7 +158,7 @@ __global__ void k_gemm_k0(float *__restrict__ C, int ldc, int m, int n, float al
 int gemm_f32_k0(float *C, int ldc, int m, int n, float alpha, float beta, cudaStream_t s) {
     if (m <= 0 || n <= 0) return HSS_OK;
     HSS_PROF("gemm_f32", s, 0.0);
-    k_gemm_k0<<<(int)std::min<long>(cdiv((long)m * n, 256), 2 * 152 * 8), 256, 0, s>>>(C, ldc, m, n, alpha, beta);
+    HSS_CUDA(launch_pdl(k_gemm_k0, dim3((int)std::min<long>(cdiv((long)m * n, 256), 2 * 152 * 8)), dim3(256), 0, s, C, ldc, m, n, alpha, beta));
     HSS_CHECK_LAUNCH("k_gemm_k0");
     return HSS_OK;
 }

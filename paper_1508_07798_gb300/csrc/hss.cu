@@ -143,6 +143,8 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
                                                 const CompFront<T> *__restrict__ cfs, T *__restrict__ ws,
                                                 int *__restrict__ iws, int *__restrict__ kout,
                                                 int *__restrict__ front_kmax, T tol, uint64_t seed) {
+    pdl_launch_next();
+    pdl_wait_prev();
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ AM<T> sham[ID_NT / 32];
     __shared__ T shs[ID_NT / 32];
@@ -454,6 +456,8 @@ __global__ void __launch_bounds__(ID_NT) k_hss_id(const NodeDev *__restrict__ no
 template <class T>
 __global__ void k_hss_tall(const NodeDev *__restrict__ nodes, const int *__restrict__ work,
                            const int *__restrict__ kout, T *__restrict__ ws, const int *__restrict__ iws) {
+    pdl_launch_next();
+    pdl_wait_prev();
     extern __shared__ __align__(16) unsigned char smraw[];
     const int node = work[blockIdx.x] >> 1, side = work[blockIdx.x] & 1;
     const NodeDev N = nodes[node];
@@ -506,6 +510,8 @@ __global__ void k_hss_expand(const ExpandItem *__restrict__ items, const NodeDev
                              const int *__restrict__ kout, const ExpandFront *__restrict__ efs,
                              const T *__restrict__ ws, const int *__restrict__ iws, T *__restrict__ arena,
                              T *__restrict__ keep) {
+    pdl_launch_next();
+    pdl_wait_prev();
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ T Pm[128 * EXP_TILE];
     const ExpandItem it = items[blockIdx.x];
@@ -565,7 +571,7 @@ int launch_hss_id(const NodeDev *nodes, const int *work, int nwork, const CompFr
     if (nwork == 0) return HSS_OK;
     HSS_SMEM(k_hss_id<T>, 220 * 1024);
     HSS_PROF("hss_id", s);
-    k_hss_id<T><<<nwork, ID_NT, smem, s>>>(nodes, work, cf, ws, iws, kout, front_kmax, tol, seed);
+    HSS_CUDA(launch_pdl(k_hss_id<T>, dim3(nwork), dim3(ID_NT), smem, s, nodes, work, cf, ws, iws, kout, front_kmax, tol, seed));
     HSS_CHECK_LAUNCH("k_hss_id");
     return HSS_OK;
 }
@@ -576,7 +582,7 @@ int launch_hss_tall(const NodeDev *nodes, const int *work, int nwork, const int 
     if (nwork == 0) return HSS_OK;
     HSS_SMEM(k_hss_tall<T>, 220 * 1024);
     HSS_PROF("hss_tall", s);
-    k_hss_tall<T><<<nwork, 256, smem, s>>>(nodes, work, kout, ws, iws);
+    HSS_CUDA(launch_pdl(k_hss_tall<T>, dim3(nwork), dim3(256), smem, s, nodes, work, kout, ws, (const int *)iws));
     HSS_CHECK_LAUNCH("k_hss_tall");
     return HSS_OK;
 }
@@ -590,7 +596,7 @@ int launch_hss_expand(const ExpandItem *items, int nitems, const NodeDev *nodes,
     HSS_SMEM(k_hss_expand<T>, 160 * 1024);
     // S(J_a,K_b) (kmax x kmax) and a 32 x kmax tile of V^tall
     size_t smem = sizeof(T) * (size_t)(kmax * kmax + EXP_TILE * kmax);
-    k_hss_expand<T><<<nitems, 256, smem, s>>>(items, nodes, kout, ef, ws, iws, arena, keep);
+    HSS_CUDA(launch_pdl(k_hss_expand<T>, dim3(nitems), dim3(256), smem, s, items, nodes, kout, ef, ws, iws, arena, keep));
     HSS_CHECK_LAUNCH("k_hss_expand");
     return HSS_OK;
 }
@@ -607,6 +613,8 @@ __global__ void __launch_bounds__(PROBE_NT) k_hss_probe(const ProbeItem *__restr
                                                         const ExpandFront *__restrict__ ef,
                                                         const T *__restrict__ arena, uint64_t seed, int nprobe,
                                                         double *__restrict__ rowacc) {
+    pdl_launch_next();
+    pdl_wait_prev();
     __shared__ T w[PROBE_NT * PROBE_MAX];
     __shared__ long hcol[PROBE_NT];
     const ProbeItem it = items[blockIdx.x];
@@ -653,6 +661,8 @@ __global__ void __launch_bounds__(PROBE_NT) k_hss_probe_norms(const ProbeFront *
                                                               const ExpandFront *__restrict__ ef, int nprobe,
                                                               const double *__restrict__ rowacc,
                                                               double *__restrict__ acc) {
+    pdl_launch_next();
+    pdl_wait_prev();
     __shared__ double red[2][PROBE_NT / 32];
     const ProbeFront P = pf[blockIdx.x];
     const int nb = ef[P.f].nb, ntc = (nb + PROBE_NT - 1) / PROBE_NT;
@@ -695,11 +705,11 @@ int launch_hss_probe(const ProbeItem *items, int nitems, const ProbeFront *pf, i
     if (nitems == 0) return HSS_OK;
     {
         HSS_PROF("hss_probe", s);
-        k_hss_probe<T><<<nitems, PROBE_NT, 0, s>>>(items, ef, arena, seed, nprobe, rowacc);
+        HSS_CUDA(launch_pdl(k_hss_probe<T>, dim3(nitems), dim3(PROBE_NT), 0, s, items, ef, arena, seed, nprobe, rowacc));
     }
     {
         HSS_PROF("hss_probe", s);
-        k_hss_probe_norms<<<nfronts, PROBE_NT, 0, s>>>(pf, ef, nprobe, rowacc, acc);
+        HSS_CUDA(launch_pdl(k_hss_probe_norms, dim3(nfronts), dim3(PROBE_NT), 0, s, pf, ef, nprobe, rowacc, acc));
     }
     HSS_CHECK_LAUNCH("k_hss_probe");
     return HSS_OK;

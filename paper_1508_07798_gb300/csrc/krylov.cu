@@ -234,10 +234,10 @@ int spmv(const hss_bsr *A, int nrhs, const double *x, long ldx, double *y, long 
     if (tot == 0) return HSS_OK;
     if (nrhs == 1) {
         HSS_PROF("spmv", s, spmv_bytes(A, nrhs));
-        HSS_CUDA(launch_pdl(k_spmv, dim3(cdiv(tot, KRY_NT)), dim3(KRY_NT), s, A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy, nrhs));
+        HSS_CUDA(launch_pdl(k_spmv, dim3(cdiv(tot, KRY_NT)), dim3(KRY_NT), 0, s, A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy, nrhs));
     } else {
         HSS_PROF("spmv", s, spmv_bytes(A, nrhs));
-        HSS_CUDA(launch_pdl(k_spmv_multi, dim3(cdiv(N, KRY_NT)), dim3(KRY_NT), s, A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy,
+        HSS_CUDA(launch_pdl(k_spmv_multi, dim3(cdiv(N, KRY_NT)), dim3(KRY_NT), 0, s, A->nb, A->bs, A->row_ptr, A->col_idx, A->val, x, ldx, y, ldy,
                                                        nrhs));
     }
     HSS_CHECK_LAUNCH("k_spmv");
@@ -270,8 +270,8 @@ static thread_local std::vector<std::vector<double>> g_hist;
 
 // sum_i v_i w_i into out[0] (deterministic two-pass)
 static int dot1(const double *v, const double *w, long N, double *part, double *out, int acc, cudaStream_t s) {
-    { HSS_PROF("dots", s); HSS_CUDA(launch_pdl(k_dots, dim3(DOT_BLOCKS), dim3(KRY_NT), s, v, N, 1, w, N, part)); }
-    { HSS_PROF("dots_final", s); HSS_CUDA(launch_pdl(k_dots_final, dim3(1), dim3(32), s, part, DOT_BLOCKS, 1, out, acc)); }
+    { HSS_PROF("dots", s); HSS_CUDA(launch_pdl(k_dots, dim3(DOT_BLOCKS), dim3(KRY_NT), 0, s, v, N, 1, w, N, part)); }
+    { HSS_PROF("dots_final", s); HSS_CUDA(launch_pdl(k_dots_final, dim3(1), dim3(32), 0, s, part, DOT_BLOCKS, 1, out, acc)); }
     HSS_CHECK_LAUNCH("dot");
     return HSS_OK;
 }
@@ -287,7 +287,7 @@ static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, doub
     double host[2];
     // ||b||
     if ((rc = dot1(b, b, N, part, sc + 0, 0, s))) return rc;
-    { HSS_PROF("sqrt_into", s); HSS_CUDA(launch_pdl(k_sqrt_into, dim3(1), dim3(32), s, sc + 0, sc + 1)); }
+    { HSS_PROF("sqrt_into", s); HSS_CUDA(launch_pdl(k_sqrt_into, dim3(1), dim3(32), 0, s, sc + 0, sc + 1)); }
     HSS_CUDA(cudaMemcpyAsync(host, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     HSS_CUDA(cudaStreamSynchronize(s));
     const double bnorm = host[0];
@@ -302,9 +302,9 @@ static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, doub
     while (true) {
         // r = b - A x, beta = ||r||
         if ((rc = spmv(A, 1, x, N, r, N, s))) return rc;
-        { HSS_PROF("resid", s); HSS_CUDA(launch_pdl(k_resid, dim3(gb), dim3(KRY_NT), s, b, r, N)); }
+        { HSS_PROF("resid", s); HSS_CUDA(launch_pdl(k_resid, dim3(gb), dim3(KRY_NT), 0, s, b, r, N)); }
         if ((rc = dot1(r, r, N, part, sc + 2, 0, s))) return rc;
-        { HSS_PROF("sqrt_into", s); HSS_CUDA(launch_pdl(k_sqrt_into, dim3(1), dim3(32), s, sc + 2, sc + 3)); }
+        { HSS_PROF("sqrt_into", s); HSS_CUDA(launch_pdl(k_sqrt_into, dim3(1), dim3(32), 0, s, sc + 2, sc + 3)); }
         HSS_CUDA(cudaMemcpyAsync(host, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
         HSS_CUDA(cudaStreamSynchronize(s));
         double beta = host[0];
@@ -314,8 +314,8 @@ static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, doub
             return HSS_OK;
         }
         if (iters >= o.maxit) return HSS_OK;
-        { HSS_PROF("scale_by", s); HSS_CUDA(launch_pdl(k_scale_by, dim3(gb), dim3(KRY_NT), s, r, sc + 3, V, N)); }
-        { HSS_PROF("init_g", s); HSS_CUDA(launch_pdl(k_init_g, dim3(1), dim3(64), s, K.g.as<double>(), m, sc + 3)); }
+        { HSS_PROF("scale_by", s); HSS_CUDA(launch_pdl(k_scale_by, dim3(gb), dim3(KRY_NT), 0, s, r, sc + 3, V, N)); }
+        { HSS_PROF("init_g", s); HSS_CUDA(launch_pdl(k_init_g, dim3(1), dim3(64), 0, s, K.g.as<double>(), m, sc + 3)); }
         HSS_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (m + 1) * m, s));
         int jend = 0;
         for (int j = 0; j < m; ++j) {
@@ -329,16 +329,16 @@ static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, doub
             double *hcol = H + (long)(m + 1) * j;
             // classical Gram-Schmidt, twice
             for (int pass = 0; pass < 2; ++pass) {
-                { HSS_PROF("dots", s); HSS_CUDA(launch_pdl(k_dots, dim3(gb), dim3(KRY_NT), s, V, N, j + 1, w, N, part)); }
-                { HSS_PROF("dots_final", s); HSS_CUDA(launch_pdl(k_dots_final, dim3(1), dim3(32 * (j + 1)), s, part, gb, j + 1, pass ? K.y.as<double>() : hcol, 0)); }
-                { HSS_PROF("sub_Vh", s); HSS_CUDA(launch_pdl(k_sub_Vh, dim3(gb), dim3(KRY_NT), s, V, N, j + 1, pass ? K.y.as<double>() : hcol, w, N)); }
+                { HSS_PROF("dots", s); HSS_CUDA(launch_pdl(k_dots, dim3(gb), dim3(KRY_NT), 0, s, V, N, j + 1, w, N, part)); }
+                { HSS_PROF("dots_final", s); HSS_CUDA(launch_pdl(k_dots_final, dim3(1), dim3(32 * (j + 1)), 0, s, part, gb, j + 1, pass ? K.y.as<double>() : hcol, 0)); }
+                { HSS_PROF("sub_Vh", s); HSS_CUDA(launch_pdl(k_sub_Vh, dim3(gb), dim3(KRY_NT), 0, s, V, N, j + 1, pass ? K.y.as<double>() : hcol, w, N)); }
             }
             // h += h2 (the second-pass coefficients, read as a one-block partial sum)
-            { HSS_PROF("dots_final", s); HSS_CUDA(launch_pdl(k_dots_final, dim3(1), dim3(32 * (j + 1)), s, K.y.as<double>(), 1, j + 1, hcol, 1)); }
+            { HSS_PROF("dots_final", s); HSS_CUDA(launch_pdl(k_dots_final, dim3(1), dim3(32 * (j + 1)), 0, s, K.y.as<double>(), 1, j + 1, hcol, 1)); }
             if ((rc = dot1(w, w, N, part, sc + 4, 0, s))) return rc;
-            { HSS_PROF("sqrt_into", s); HSS_CUDA(launch_pdl(k_sqrt_into, dim3(1), dim3(32), s, sc + 4, hcol + j + 1)); }
-            { HSS_PROF("scale_by", s); HSS_CUDA(launch_pdl(k_scale_by, dim3(gb), dim3(KRY_NT), s, w, hcol + j + 1, V + N * (j + 1), N)); }
-            { HSS_PROF("givens", s); HSS_CUDA(launch_pdl(k_givens, dim3(1), dim3(32), s, H, m, j, K.cs.as<double>(), K.sn.as<double>(), K.g.as<double>(), sc + 5)); }
+            { HSS_PROF("sqrt_into", s); HSS_CUDA(launch_pdl(k_sqrt_into, dim3(1), dim3(32), 0, s, sc + 4, hcol + j + 1)); }
+            { HSS_PROF("scale_by", s); HSS_CUDA(launch_pdl(k_scale_by, dim3(gb), dim3(KRY_NT), 0, s, w, hcol + j + 1, V + N * (j + 1), N)); }
+            { HSS_PROF("givens", s); HSS_CUDA(launch_pdl(k_givens, dim3(1), dim3(32), 0, s, H, m, j, K.cs.as<double>(), K.sn.as<double>(), K.g.as<double>(), sc + 5)); }
             HSS_CHECK_LAUNCH("arnoldi step");
             HSS_CUDA(cudaMemcpyAsync(host, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
             HSS_CUDA(cudaStreamSynchronize(s));
@@ -348,8 +348,8 @@ static int fgmres_one(const hss_bsr *A, const Precond &pc, const double *b, doub
             hist.push_back(est);
             if (est <= o.rtol || iters >= o.maxit || !(est == est)) break;
         }
-        { HSS_PROF("backsolve", s); HSS_CUDA(launch_pdl(k_backsolve, dim3(1), dim3(32), s, H, m, jend, K.g.as<double>(), K.y.as<double>())); }
-        { HSS_PROF("update_x", s); HSS_CUDA(launch_pdl(k_update_x, dim3(gb), dim3(KRY_NT), s, Z, N, jend, K.y.as<double>(), x, N)); }
+        { HSS_PROF("backsolve", s); HSS_CUDA(launch_pdl(k_backsolve, dim3(1), dim3(32), 0, s, H, m, jend, K.g.as<double>(), K.y.as<double>())); }
+        { HSS_PROF("update_x", s); HSS_CUDA(launch_pdl(k_update_x, dim3(gb), dim3(KRY_NT), 0, s, Z, N, jend, K.y.as<double>(), x, N)); }
         HSS_CHECK_LAUNCH("fgmres update");
     }
 }

@@ -60,6 +60,15 @@ void drain_locked() {
 }  // namespace
 
 thread_local bool g_capturing = false;
+thread_local bool g_rb_pending = false;
+thread_local std::chrono::steady_clock::time_point g_rb_t;
+thread_local double g_rb_gap_ms = 0.0;
+
+void prof_mark_readback() {
+    g_rb_pending = true;
+    g_rb_t = std::chrono::steady_clock::now();
+}
+double prof_readback_gap_ms() { return g_rb_gap_ms; }
 
 bool prof_enabled() { return g_on; }
 void prof_set_capture(bool on) { g_capturing = on; }
@@ -67,6 +76,10 @@ void prof_add_launches(long n) { g_launches.fetch_add(n, std::memory_order_relax
 
 ProfScope::ProfScope(const char *name, cudaStream_t stream, double work) : cls(-1), s(stream), slot(-1) {
     if (g_capturing) return;
+    if (g_rb_pending) {
+        g_rb_pending = false;
+        g_rb_gap_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g_rb_t).count();
+    }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_on || g_host_only) return;
     std::lock_guard<std::mutex> lk(g_mu);

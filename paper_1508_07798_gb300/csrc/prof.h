@@ -27,6 +27,12 @@ struct HostScope {
     ~HostScope();
 };
 
+// Host reaction time after a blocking read-back: mark_readback() notes the
+// moment a read-back returns, the next kernel launch adds the time since then
+// to a running total (the device has nothing queued meanwhile).
+void prof_mark_readback();
+double prof_readback_gap_ms();   // running total (ms)
+
 bool prof_enabled();
 void prof_set_capture(bool on);     // while a graph is being captured, scopes record nothing
 void prof_add_launches(long n);     // kernels executed by a graph launch

@@ -110,6 +110,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 __global__ void __launch_bounds__(TC_NT) k_gemm_tc(const GemmDesc<float> *__restrict__ descs,
                                                    const GemmTile *__restrict__ tiles, int split,
                                                    int *__restrict__ err, long spin_limit, int issue) {
+    pdl_launch_next();
+    pdl_wait_prev();
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
@@ -262,7 +264,7 @@ static int launch_tc(const GemmDesc<float> *d_desc, const GemmTile *d_tiles, int
     int rc = gemm_tc_prepare();
     if (rc) return rc;
     HSS_PROF("gemm_tc", s, flops);
-    k_gemm_tc<<<ntiles, TC_NT, TC_SMEM, s>>>(d_desc, d_tiles, split, err, spin_limit, issue);
+    HSS_CUDA(launch_pdl(k_gemm_tc, dim3(ntiles), dim3(TC_NT), TC_SMEM, s, d_desc, d_tiles, split, err, spin_limit, issue));
     HSS_CHECK_LAUNCH("k_gemm_tc");
     return HSS_OK;
 }

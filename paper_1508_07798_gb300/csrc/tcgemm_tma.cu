@@ -270,6 +270,8 @@ __device__ __forceinline__ void convert_tile_bf16(const unsigned char *raw, int 
 template <bool BF16>
 __global__ void __launch_bounds__(NT, 2) k_gemm_tma(const TmaGemmDesc *__restrict__ descs,
                                                   const GemmTile *__restrict__ tiles, int *__restrict__ err) {
+    pdl_launch_next();
+    pdl_wait_prev();
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t full[2];     // raw slot landed (TMA transaction count)
     __shared__ __align__(8) uint64_t mdone[2];    // MMAs reading converted buffer b finished
@@ -557,9 +559,9 @@ int gemm_tma(const TmaGemmDesc *d_descs, const GemmTile *d_tiles, int ntiles, in
     if (rc) return rc;
     HSS_PROF(prof_class, s, flops);
     if (bf16)
-        k_gemm_tma<true><<<ntiles, NT, SMEM, s>>>(d_descs, d_tiles, err);
+        HSS_CUDA(launch_pdl(k_gemm_tma<true>, dim3(ntiles), dim3(NT), SMEM, s, d_descs, d_tiles, err));
     else
-        k_gemm_tma<false><<<ntiles, NT, SMEM, s>>>(d_descs, d_tiles, err);
+        HSS_CUDA(launch_pdl(k_gemm_tma<false>, dim3(ntiles), dim3(NT), SMEM, s, d_descs, d_tiles, err));
     HSS_CHECK_LAUNCH("k_gemm_tma");
     return HSS_OK;
 }

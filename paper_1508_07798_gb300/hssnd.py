@@ -83,7 +83,7 @@ class hss_factor_info(C.Structure):
                 ("capped_fronts", C.c_int), ("probe_regrown", C.c_int), ("gemm_simt", C.c_long),
                 ("gemm_tma", C.c_long), ("gemm_staged", C.c_long), ("gemm_timed", C.c_long),
                 ("gemm_bf16", C.c_long), ("host_syncs", C.c_long), ("host_sync_ms", C.c_double),
-                ("host_ms", C.c_double)]
+                ("host_ms", C.c_double), ("host_gap_ms", C.c_double)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
