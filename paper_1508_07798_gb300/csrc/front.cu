@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(NT) k_gj_panel_reg(const PanelJob *__restrict_
     constexpr int NW = NT / 32;
     // steps per rotation group: fewer where the rows fill more of the register budget
     constexpr int DREGS = R * KB * (int)sizeof(T) / 4;
-    constexpr int U = DREGS <= 48 ? 4 : DREGS <= 64 ? 2 : 1;
+    constexpr int U = (NT > 256 || DREGS > 64) ? 1 : DREGS <= 48 ? 4 : 2;
     constexpr int V = 16 / (int)sizeof(T);   // values per 16-byte shared load
     // row positions in registers for up to two rows per thread, else in shared memory
     constexpr bool POS_REG = R <= 2;
