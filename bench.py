@@ -114,7 +114,7 @@ def max_over_ranks(values, device):
     return [float(v) for v in t.cpu()]
 
 
-def roofline_of(kernel, ms, cnt, work, total_ms, pk):
+def roofline_of(kernel, ms, cnt, work, total_ms, pk, workload=None):
     """Roofline entry of one kernel class: FLOP-counted classes (GEMMs and the
     Gauss-Jordan panels) against the FP32/FP64 arithmetic peak, byte-counted
     classes (apply, SpMV) against the measured HBM bandwidth.  pk: peaks() with
@@ -150,21 +150,26 @@ def roofline_of(kernel, ms, cnt, work, total_ms, pk):
                     peak_source=pk["fp32_src"] if f32 else "nominal GB300 FP64 1.25 TFLOP/s")
     ach = work / cnt / per_launch_s / 1e9
     return dict(kernel=kernel, bound="hbm", achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
-                traffic=None, launches=cnt, avg_launch_us=ms / cnt * 1e3, share=ms / total_ms,
+                traffic=profiled_traffic(kernel, workload), launches=cnt, avg_launch_us=ms / cnt * 1e3,
+                share=ms / total_ms,
                 peak_source=f"{pk['src']} (MEASURED_PEAKS.json hbm_gbs)" if pk["src"] == "measured"
                 else pk["src"])
 
 
-def profiled_traffic(kernel):
+def profiled_traffic(kernel, workload=None):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
-    when there is none or the kernel's source changed since the capture."""
+    when there is none or the kernel's source changed since the capture.  The
+    apply class (one launch = one whole apply) is keyed by workload too."""
     import hashlib
     files = {"gemm_f32": ("profiles/k_gemm_f32_dram_helmholtz64_p2.md", "paper_1508_07798_gb300/csrc/gemm.cu"),
              "gemm_tma": ("profiles/k_gemm_tma_gemm_update_8192x8192_k256.md",
-                          "paper_1508_07798_gb300/csrc/tcgemm_tma.cu")}
-    if kernel not in files:
+                          "paper_1508_07798_gb300/csrc/tcgemm_tma.cu"),
+             ("apply", "helmholtz64"): ("profiles/k_apply_dram_helmholtz64_p2_fp32.md",
+                                        "paper_1508_07798_gb300/csrc/apply.cu")}
+    key = (kernel, workload) if (kernel, workload) in files else kernel
+    if key not in files:
         return None
-    summary, src = (os.path.join(ROOT, f) for f in files[kernel])
+    summary, src = (os.path.join(ROOT, f) for f in files[key])
     try:
         kv = {}
         for line in open(summary):
@@ -454,9 +459,9 @@ def bench_ours(args, rank, world):
     tracked = {k: v for k, v in prof.items() if v[2] > 0}
     dom = max(tracked, key=lambda k: tracked[k][0]) if tracked else max(prof, key=lambda k: prof[k][0])
     total_ms = sum(v[0] for v in prof.values())
-    roof = roofline_of(dom, *prof[dom], total_ms, pk)
+    roof = roofline_of(dom, *prof[dom], total_ms, pk, workload="helmholtz64")
     # the next tracked classes by time, for context
-    roof["others"] = [roofline_of(k, *prof[k], total_ms, pk) for k in
+    roof["others"] = [roofline_of(k, *prof[k], total_ms, pk, workload="helmholtz64") for k in
                       sorted(tracked, key=lambda k: -tracked[k][0]) if k != dom][:3]
     kernels = {form: {k: dict(ms=round(v[0] / args.steps, 4), launches=v[1] // args.steps) for k, v in
                       sorted(pf.items(), key=lambda kv: -kv[1][0])} for form, pf in prof_all.items()}

@@ -294,11 +294,15 @@ int pack_apply(hss_factor_t *F, cudaStream_t s) {
                  al(sizeof(ApplyItem) * st.nbwd);
     }
     // subtree part: root stage = the shallowest stage (below the top block)
-    // with at least APPLY_SUB_MIN fronts; every front of the stages up to it
+    // with at least APPLY_SUB_MIN fronts, none larger than APPLY_SUB_MAXN
+    // (this and every deeper stage); every front of the stages up to it
     // belongs to the subtree of its ancestor in the root stage
     int qr = -1;
     for (size_t q = 0; q < nst; ++q) {
         if (F->apply[q].top) break;
+        int nmax = 0;
+        for (const FrontDev &d : F->apply[q].h_fronts) nmax = std::max(nmax, d.n);
+        if (nmax > APPLY_SUB_MAXN) break;   // larger fronts need the level launch's parallelism
         if (F->apply[q].nfronts >= APPLY_SUB_MIN) qr = (int)q;
     }
     std::vector<FrontDev> sfr;

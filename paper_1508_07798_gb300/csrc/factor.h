@@ -11,6 +11,7 @@ constexpr int APPLY_ROWS = 32;
 
 constexpr int APPLY_CHUNK = 64;   // columns per warp work item of the apply
 constexpr int APPLY_SUB_MIN = 256;   // fronts of the level that roots the apply's subtrees (one CTA each)
+constexpr int APPLY_SUB_MAXN = 192;  // largest front (n) of the levels the subtree launch takes
 
 struct ApplyItem {
     int front;        // stage-local front index
