@@ -162,6 +162,8 @@ def profiled_traffic(kernel, workload=None):
     apply class (one launch = one whole apply) is keyed by workload too."""
     import hashlib
     files = {"gemm_f32": ("profiles/k_gemm_f32_dram_helmholtz64_p2.md", "paper_1508_07798_gb300/csrc/gemm.cu"),
+             "gj_panel_f32": ("profiles/k_gj_panel_reg_dram_helmholtz64_p2_fp32.md",
+                              "paper_1508_07798_gb300/csrc/front.cu"),
              "gemm_tma": ("profiles/k_gemm_tma_gemm_update_8192x8192_k256.md",
                           "paper_1508_07798_gb300/csrc/tcgemm_tma.cu"),
              ("apply", "helmholtz64"): ("profiles/k_apply_dram_helmholtz64_p2_fp32.md",

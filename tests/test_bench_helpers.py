@@ -30,7 +30,8 @@ def test_roofline_arithmetic(bench):
     # 4 launches, 1 ms in all, 2e9 flops per launch: 8e12 flop/s against the FP32 SIMT peak
     g = bench.roofline_of("gj_panel_f32", 1.0, 4, 8e9, 4.0, pk)
     assert g["bound"] == "alu" and g["achieved"] == pytest.approx(8.0)
-    assert g["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12) and g["traffic"] is None
+    assert g["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert g["traffic"] == bench.profiled_traffic("gj_panel_f32")   # the committed capture, if current
     assert "152 SMs" in g["peak_source"]
     # the SM count and clock come from the device and the peaks file, not a constant
     pk2 = bench.with_simt_peak(dict(hbm=6000.0, sm_mhz=1500.0, src="measured"), 100)
