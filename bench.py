@@ -715,8 +715,9 @@ def bench_gemm_update(args, rank, world):
 
 
 def cpu_baseline_large(args, res):
-    """SURVEY's rule for the large configurations: the oracle as it stands on
-    the same family at the reduced size (64 x 64 p = 3 Helmholtz, 16^3 p = 1
+    """CPU baseline of the large configurations, where one full-size oracle
+    solve would run far beyond the bench's few minutes: the oracle as it stands on the same family at a
+    reduced size (64 x 64 p = 3 Helmholtz, 16^3 p = 1
     diffusion with one right-hand side), timed, plus the GPU headline form on
     that same problem against the oracle (apply and solution); the full-size
     check is the true FP64 residual of every solution in the bench line."""
@@ -753,7 +754,7 @@ def cpu_baseline_large(args, res):
                           iters=st.iters, oracle_iters=info["iters"])
     return dict(value=dt * 1e3, unit="ms", cores=cpu_cores(), blas_threads=blas_threads(), kind="oracle",
                 sample=f"one {A.n}-dof solve of the same family ({n_s}^{spec['dim']} elements, p={p_s}), "
-                       "the reduced size SURVEY prescribes for the large configurations",
+                       "a reduced size of the same family (a full-size oracle solve would run far beyond the bench's minutes)",
                 iters=info["iters"], gpu_vs_oracle_at_sample=errs)
 
 
