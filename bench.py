@@ -470,15 +470,8 @@ def bench_ours(args, rank, world):
     res = dict(metric=METRIC, value=value, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup,
                ms_per_step=value, higher_is_better=False, scaling="weak", vs_baseline=None,
                dtype="f32 factor / f64 Krylov" if head.startswith("fp32") else "f64", data="synthetic",
-               config=dict(workload=WORKLOAD, dofs=A.n, p=P_DEG, mesh=f"{N_ELEM}x{N_ELEM}", id_tol=TOL,
-                           rtol=RTOL, restart=RESTART, leaf_max=64, headline_form=head,
-                           learned_widths=learned_info if model is not None else None,
-                           learned_probe_vectors=args.probe, tensor_cores=args.tensor_cores,
-                           sample_bf16=args.sample_bf16 or 0,
-                           l2="flushed by a 256 MB write before every timed step",
-                           apply_autotune="per-level work split timed on the first factorization of the "
-                                          "structure (a warm-up step), cached for the process",
-                           parallelism=f"replicas x{world} (independent instances)"),
+               config=headline_config(args, world),
+               learned_widths=learned_info if model is not None else None,
                forms={k: {kk: vv for kk, vv in v.items() if kk != "ms_all"} for k, v in forms.items()},
                apply=apply, roofline=roof, e2e=e2e, clocks=clocks, gpu_launches=int(launches_total // max(1, len(forms))),
                kernels_per_step=kernels)
@@ -905,6 +898,19 @@ def bench_batched(args, rank, world):
                 clocks=clocks, gpu_launches=int(launches), kernels_instrumented_step=kernels)
 
 
+def headline_config(args, world):
+    """Configuration of the default workload, the same dictionary in both arms
+    of the bench (the GPU line and the oracle's reference line)."""
+    return dict(workload=WORKLOAD, dofs=N_ELEM * N_ELEM * (P_DEG + 1) ** 2, p=P_DEG, mesh=f"{N_ELEM}x{N_ELEM}",
+                id_tol=TOL, rtol=RTOL, restart=RESTART, leaf_max=64, headline_form=args.forms.split(",")[0],
+                learned_probe_vectors=args.probe, tensor_cores=args.tensor_cores,
+                sample_bf16=args.sample_bf16 or 0,
+                l2="flushed by a 256 MB write before every timed step",
+                apply_autotune="per-level work split timed on the first factorization of the "
+                               "structure (a warm-up step), cached for the process",
+                parallelism=f"replicas x{world} (independent instances)")
+
+
 def cpu_baseline_run(seed=0):
     """The oracle, as it stands, on one full problem of the workload."""
     import numpy as np
@@ -955,7 +961,7 @@ def main():
         line = dict(metric=METRIC, value=v, unit="ms", n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=v, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
                     data="synthetic", impl="reference",
-                    config=dict(workload=WORKLOAD, dofs=N_ELEM * N_ELEM * (P_DEG + 1) ** 2, id_tol=TOL, rtol=RTOL),
+                    config=headline_config(args, world),
                     cpu_baseline=dict(kind="oracle", cores=cpu_cores(), blas_threads=blas_threads(), value=v,
                                       unit="ms",
                                       sample="one full 36,864-dof solve per step (nd + factor + FGMRES), "

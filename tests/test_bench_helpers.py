@@ -75,3 +75,22 @@ def test_profiled_traffic_only_for_the_profiled_source(bench, tmp_path, monkeypa
     assert bench.profiled_traffic("apply") is None
     src.write_text("// kernel source, changed\n")
     assert bench.profiled_traffic("gemm_f32") is None
+
+
+def test_reference_line_has_the_workload_config(bench, monkeypatch, capsys):
+    """The reference arm (the oracle) prints the same config dictionary as the
+    GPU arm builds (headline_config), with its own cpu_baseline and e2e; the
+    oracle solve itself is replaced by a stub here."""
+    import json
+    monkeypatch.setattr(bench, "cpu_baseline_run", lambda seed=0: (1234.0, {"iters": 19}))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"])
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    bench.main()
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    assert line["impl"] == "reference" and line["value"] == pytest.approx(1234.0)
+    assert line["config"] == bench.headline_config(bench.parse(), 1)
+    assert line["config"]["dofs"] == 36864 and line["config"]["workload"] == bench.WORKLOAD
+    assert line["e2e"] == dict(value=line["value"], unit="ms", h2d_bytes_per_step=0, d2h_bytes_per_step=0)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
